@@ -1,0 +1,144 @@
+"""Element matrices by plain quadrature and assembled CSR operators (oracle, FP64).
+
+Bilinear forms (Sec. 2, Eqs. a(u,v), b(v,q)):
+    a(u,v) = int mu grad u : grad v + gamma*rho u.v
+    b(v,q) = -int q div v
+The sign of b follows the reading that makes K x = b the discretisation of
+-mu Lap u + grad p = f (the paper prints both signs; the velocity is unaffected,
+only p flips).  The linear system is K = [A B^T; B -C] with C = 0 (Eq. Kx=f).
+
+Dirichlet treatment: a constrained velocity DoF keeps its slot in the vector;
+its row and column of K are replaced by the identity (y_i = x_i).
+
+Geometry: each cell is the image of (0,1)^d under the bi/trilinear map through
+its 2^d vertices; gradients transform with J^{-T} and integrals pick up det J.
+Quadrature: (k+1)-point Gauss-Legendre per direction for every term.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+from .fe import Element1D, tensor_tables
+
+
+class Tables:
+    """Reference-cell tables for Q_k / Q_{k-1} / Q_1 (geometry) at the (k+1)^d Gauss points."""
+
+    def __init__(self, dim, k, quad_points=None):
+        nq = k + 1 if quad_points is None else quad_points
+        self.dim, self.k = dim, k
+        self.vel = Element1D(k, nq)
+        self.pre = Element1D(k - 1, nq)
+        self.geo = Element1D(1, nq)
+        self.phi, self.dphi, self.w = tensor_tables(self.vel, dim)
+        self.psi, _, _ = tensor_tables(self.pre, dim)
+        self.gphi, self.gdphi, _ = tensor_tables(self.geo, dim)
+
+
+def geometry(tab, Xv):
+    """Jacobians at quadrature points for cells with vertex coordinates Xv (nc, 2^d, d).
+
+    Returns J (nc, nq, d, d) with J[.., a, b] = d x_a / d xi_b, det J (nc, nq), J^{-T} (nc, nq, d, d).
+    """
+    J = np.einsum("cva,vqb->cqab", Xv, tab.gdphi)
+    detJ = np.linalg.det(J)
+    JinvT = np.linalg.inv(J).swapaxes(-1, -2)
+    return J, detJ, JinvT
+
+
+def element_matrices(level, tab, mu, gamma_rho, mu_cell=None, cells=None):
+    """Element matrices of a block of cells.
+
+    Returns dict with
+      As  (nc, nphi, nphi)        scalar velocity block: mu_c grad.grad + gamma*rho mass
+      B   (nc, npsi, d, nphi)     B_tau[i, c, j] = -int psi_i d(phi_j)/dx_c
+      Mv  (nc, nphi, nphi)        scalar velocity mass
+      Mp  (nc, npsi, npsi)        pressure mass
+      K0  (nc, nphi, nphi)        scalar stiffness grad.grad (no mu)
+    """
+    Xv = level.cell_vertices()
+    if cells is not None:
+        Xv = Xv[cells]
+    _, detJ, JinvT = geometry(tab, Xv)
+    if np.any(detJ <= 0):
+        raise ValueError("inverted or degenerate cell")
+    wdet = detJ * tab.w[None, :]                                   # (nc, nq)
+    grad = np.einsum("cqab,iqb->ciqa", JinvT, tab.dphi)             # physical gradients (nc, nphi, nq, d)
+    K0 = np.einsum("cq,ciqa,cjqa->cij", wdet, grad, grad)
+    Mv = np.einsum("cq,iq,jq->cij", wdet, tab.phi, tab.phi)
+    Mp = np.einsum("cq,iq,jq->cij", wdet, tab.psi, tab.psi)
+    B = -np.einsum("cq,iq,cjqa->ciaj", wdet, tab.psi, grad)
+    if mu_cell is None:
+        muv = np.full(len(Xv), float(mu))
+    else:
+        muv = np.asarray(mu_cell, dtype=np.float64)
+        if cells is not None:
+            muv = muv[cells]
+    As = muv[:, None, None] * K0 + gamma_rho * Mv
+    return {"As": As, "B": B, "Mv": Mv, "Mp": Mp, "K0": K0}
+
+
+def _scatter(rows_loc, cols_loc, vals, shape):
+    nc, a, b = vals.shape
+    r = np.broadcast_to(rows_loc[:, :, None], (nc, a, b)).reshape(-1)
+    c = np.broadcast_to(cols_loc[:, None, :], (nc, a, b)).reshape(-1)
+    return sp.coo_matrix((vals.reshape(-1), (r, c)), shape=shape).tocsr()
+
+
+def assemble(level, mu=1.0, gamma_rho=0.0, mu_cell=None, chunk=4096):
+    """Assembled operators of one level.
+
+    Returns dict of CSR matrices (all FP64):
+      As_full  scalar velocity block without constraints (nv x nv)
+      Mv_full  scalar velocity mass without constraints
+      Mp       pressure mass
+      B_full   n_p x n_u divergence block without constraints
+      A        n_u x n_u velocity block, Dirichlet rows/columns -> identity
+      B        n_p x n_u with constrained columns zeroed
+      K        [A B^T; B 0]
+      free     boolean mask of unconstrained entries of the full vector
+    """
+    tab = Tables(level.dim, level.k)
+    vn = level.cell_velocity_nodes()
+    pn = level.cell_pressure_nodes()
+    nv, d = level.nv, level.dim
+    As = sp.csr_matrix((nv, nv))
+    Mv = sp.csr_matrix((nv, nv))
+    Mp = sp.csr_matrix((level.n_p, level.n_p))
+    Bf = sp.csr_matrix((level.n_p, level.n_u))
+    for s in range(0, level.n_cells, chunk):
+        cells = np.arange(s, min(s + chunk, level.n_cells))
+        E = element_matrices(level, tab, mu, gamma_rho, mu_cell, cells)
+        As = As + _scatter(vn[cells], vn[cells], E["As"], (nv, nv))
+        Mv = Mv + _scatter(vn[cells], vn[cells], E["Mv"], (nv, nv))
+        Mp = Mp + _scatter(pn[cells], pn[cells], E["Mp"], (level.n_p, level.n_p))
+        nc = len(cells)
+        cols = (vn[cells][:, None, :] + (np.arange(d) * nv)[None, :, None]).reshape(nc, -1)
+        Bf = Bf + _scatter(pn[cells], cols, E["B"].reshape(nc, pn.shape[1], -1), (level.n_p, level.n_u))
+    return finish(level, As, Mv, Mp, Bf)
+
+
+def finish(level, As, Mv, Mp, Bf):
+    d = level.dim
+    vmask = level.velocity_constrained()
+    umask = np.tile(vmask, d)
+    Zu = sp.diags((~umask).astype(np.float64))
+    A_full = sp.block_diag([As] * d, format="csr")
+    A = (Zu @ A_full @ Zu + sp.diags(umask.astype(np.float64))).tocsr()
+    B = (Bf @ Zu).tocsr()
+    K = sp.bmat([[A, B.T], [B, None]], format="csr")
+    free = ~level.constrained()
+    return {"As_full": As.tocsr(), "Mv_full": Mv.tocsr(), "Mp": Mp.tocsr(), "B_full": Bf.tocsr(),
+            "A": A, "B": B, "K": K, "free": free, "umask": umask}
+
+
+def load_vector_nodal(level, ops, f_nodal):
+    """Right-hand side b = [Z M_v f ; 0] for a velocity field given by its nodal values.
+
+    f_nodal: (d, nv) or flat (n_u,).  Constrained rows of b are zero (homogeneous data).
+    """
+    f = np.asarray(f_nodal, dtype=np.float64).reshape(level.dim, level.nv)
+    bu = np.concatenate([ops["Mv_full"] @ f[c] for c in range(level.dim)])
+    bu[ops["umask"]] = 0.0
+    return np.concatenate([bu, np.zeros(level.n_p)])

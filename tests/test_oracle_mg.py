@@ -1,0 +1,96 @@
+"""Pins of the oracle's multigrid cycle, coarse solve and outer Krylov loop (CPU only)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import workloads as W
+from oracle.assemble import assemble, load_vector_nodal
+from oracle.krylov import fgmres
+from oracle.mesh import Hierarchy, Level
+from oracle.mg import CoarseSolver, Multigrid
+
+
+def _bordered_direct(lev, K, b):
+    if not lev.has_pressure_kernel():
+        return spla.spsolve(K.tocsc(), b)
+    e = np.concatenate([np.zeros(lev.n_u), np.ones(lev.n_p)])
+    Kb = sp.bmat([[K, sp.csr_matrix(e[:, None])], [sp.csr_matrix(e[None, :]), None]], format="csc")
+    return spla.spsolve(Kb, np.concatenate([b, [0.0]]))[:-1]
+
+
+def _problem(dim, n, levels, seed=0, perturb=False, gamma_rho=0.0, faces=0x3F, **kw):
+    V = (W.perturbed_vertices(dim, (n,) * dim, seed=seed) if perturb else W.lattice_vertices(dim, (n,) * dim))
+    H = Hierarchy(dim, 2, (n,) * dim, levels, V, faces)
+    mg = Multigrid(H, gamma_rho=gamma_rho, **kw)
+    lev = H.levels[-1]
+    f = W.fourier_forcing(dim, 2, (n,) * dim, seed=seed)
+    b = load_vector_nodal(lev, mg.ops[-1], f)
+    return H, mg, lev, b
+
+
+def test_coarse_bordered_solve_picks_mean_free_pressure():
+    lev = Level(2, 2, (2, 2), W.lattice_vertices(2, (2, 2)))
+    K = assemble(lev)["K"]
+    cs = CoarseSolver(lev, K)
+    rng = np.random.default_rng(0)
+    x_true = rng.standard_normal(lev.size) * ~lev.constrained()
+    x_true[lev.n_u:] -= x_true[lev.n_u:].mean()
+    x = cs.solve(K @ x_true)
+    np.testing.assert_allclose(x, x_true, atol=1e-11)
+
+
+@pytest.mark.parametrize("dim,n,levels,perturb", [(2, 8, 3, False), (2, 8, 3, True), (3, 4, 2, True)])
+def test_fgmres_vcycle_matches_direct_solve(dim, n, levels, perturb):
+    H, mg, lev, b = _problem(dim, n, levels, perturb=perturb, kA=2, kS=2, m=2)
+    x, its, hist = fgmres(lambda v: mg.K @ v, mg.precondition, b, rtol=1e-12)
+    xd = _bordered_direct(lev, mg.K, b)
+    x[lev.n_u:] -= x[lev.n_u:].mean()
+    xd[lev.n_u:] -= xd[lev.n_u:].mean()
+    assert np.linalg.norm(b - mg.K @ x) <= 1e-12 * np.linalg.norm(b) * 1.01
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-9
+    assert its <= 15
+
+
+def test_level_independent_iteration_counts():
+    # q and FGMRES iteration counts stay flat under h-refinement (Sec. 4.3.3)
+    counts, rates = [], []
+    # (coarsest mesh 2x2; levels 4..6 are past the pre-asymptotic range)
+    for levels in (4, 5, 6):
+        n = 2 ** levels
+        H, mg, lev, b = _problem(2, n, levels, kA=1, kS=1, m=2)
+        _, its, _ = fgmres(lambda v: mg.K @ v, mg.precondition, b, rtol=1e-10)
+        _, _, q = mg.stationary(b)
+        counts.append(its)
+        rates.append(q)
+    assert max(counts) - min(counts) <= 1, counts
+    assert max(rates) - min(rates) < 0.05 and max(rates) < 0.35, rates
+
+
+def test_rate_improves_with_smoothing_steps_and_v_close_to_w():
+    qs = {}
+    for m in (1, 2, 4):
+        for cyc in ("V", "W"):
+            H, mg, lev, b = _problem(2, 16, 4, kA=1, kS=1, m=m, cycle=cyc)
+            qs[(m, cyc)] = mg.stationary(b)[2]
+    assert qs[(1, "V")] > qs[(2, "V")] > qs[(4, "V")]
+    for m in (1, 2, 4):
+        assert abs(qs[(m, "V")] - qs[(m, "W")]) < 0.5 * qs[(m, "W")] + 0.02
+
+
+def test_generalized_stokes_rates_independent_of_gamma():
+    # Sec. 4.6: the mass term gamma*rho does not deteriorate the rates
+    qs = []
+    for g in (0.0, 1.0, 100.0):
+        H, mg, lev, b = _problem(2, 16, 4, gamma_rho=g, kA=2, kS=2, m=2)
+        qs.append(mg.stationary(b)[2])
+    assert max(qs) < 0.25, qs
+
+
+def test_partial_dirichlet_has_no_pressure_kernel():
+    # do-nothing outflow at x = 1: K is nonsingular and the coarse solve is not bordered
+    H, mg, lev, b = _problem(2, 8, 3, faces=0x3F & ~0x2, kA=2, kS=2, m=2)
+    assert not lev.has_pressure_kernel() and not mg.coarse.bordered
+    x, its, _ = fgmres(lambda v: mg.K @ v, mg.precondition, b, rtol=1e-11)
+    xd = spla.spsolve(mg.K.tocsc(), b)
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-8
