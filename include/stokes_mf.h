@@ -1,0 +1,160 @@
+/*
+ * stokes_mf.h -- C ABI of the GB300 matrix-free monolithic multigrid library for
+ * Q_k-Q_{k-1} Taylor-Hood discretisations of the (generalized) Stokes system
+ *
+ *     [ A  B^T ] [u]   [f]        a(u,v) = int mu grad u : grad v + gamma*rho u.v
+ *     [ B  -C  ] [p] = [g],       b(v,q) = -int q div v,   C = 0
+ *
+ * (paper Sec. 1, Eq. LinearSystem; Sec. 2, Eqs. a(u,v), b(v,q), Kx=f).
+ *
+ * Conventions shared by every entry point:
+ *  - Meshes are structured boxes of n[0] x n[1] (x n[2]) quadrilateral / hexahedral
+ *    cells; level l of the hierarchy has n / 2^(L-l) cells per direction (Sec. 3.1).
+ *    Cells are bi/trilinear images of (0,1)^d (Sec. 2).
+ *  - Vector layout (every vector argument): [u_1 | ... | u_d | p]; each velocity
+ *    component is lexicographic over the (k n_x + 1) x (k n_y + 1) (x (k n_z + 1))
+ *    node lattice with x fastest, the pressure over the ((k-1) n + 1)^d lattice.
+ *    Nodes are the tensor-product Gauss-Lobatto points of each cell.
+ *  - Dirichlet velocity DoFs stay in the vector; their rows and columns of K are
+ *    the identity.  Right-hand sides must be zero there (lift inhomogeneous data).
+ *  - Vector pointers are DEVICE pointers owned by the caller unless the entry point
+ *    says HOST.  precision = 64 means double*, 32 means float*.
+ *  - stream is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls
+ *    are stream-ordered and asynchronous unless they return host scalars.
+ *  - Every call returns a status; on error, stokes_last_error(ctx) (or
+ *    stokes_global_last_error() when no context exists) holds a message.  No C++
+ *    exception crosses this boundary.  A context is not thread-safe.
+ */
+#ifndef STOKES_MF_H
+#define STOKES_MF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define STOKES_MAX_LEVELS 12
+
+typedef enum {
+  STOKES_OK = 0,
+  STOKES_EINVAL = 1,      /* bad argument (sizes, k, null pointers, unknown option) */
+  STOKES_ENOMEM = 2,      /* device allocation failed */
+  STOKES_ECUDA = 3,       /* a CUDA call failed */
+  STOKES_ENOTCONV = 4,    /* iteration limit reached before the tolerance */
+  STOKES_EBREAKDOWN = 5,  /* NaN/Inf or residual growth > 1e6 r0 detected */
+  STOKES_ETIMEOUT = 6     /* a bounded device-side wait expired */
+} stokes_status;
+
+typedef struct stokes_ctx stokes_ctx;
+
+/* Mesh of the finest level.  vertices (HOST, nullable): (n+1)^d vertex coordinates,
+ * x fastest, coordinates interleaved ((n_z+1)(n_y+1)(n_x+1) x d doubles); coarse
+ * levels use every 2^(L-l)-th vertex.  NULL = the Cartesian box [lo, hi].
+ * dirichlet_faces: bit 2a = face x_a = lo, bit 2a+1 = face x_a = hi; other faces
+ * carry the natural (do-nothing) condition.  0x3F (3D) / 0xF (2D) = all faces. */
+typedef struct {
+  int dim;
+  int n[3];
+  int n_levels;
+  double lo[3];
+  double hi[3];
+  const double *vertices;
+  unsigned int dirichlet_faces;
+} stokes_mesh;
+
+/* Smoother and solver options (Algorithm 2 inputs k_A, k_S; Sec. 4.1 knobs). */
+typedef struct {
+  int kA;               /* Chebyshev degree of A^-1_hat (number of A applications) */
+  int kS;               /* Chebyshev degree of S^-1_hat */
+  int m;                /* pre- and post-smoothing steps */
+  int cycle;            /* 0 = V-cycle, 1 = W-cycle (Algorithm 1, gamma = 1 / 2) */
+  int schur_diag;       /* 0 = local diagonal (Eq. diag loc), 1 = pressure mass (Eq. diag p) */
+  int vcycle_fp32;      /* 1: stokes_solve preconditions with the FP32 cycle, 0: FP64 */
+  int gmres_restart;    /* FGMRES restart length */
+  int eig_iters;        /* Lanczos steps for lambda_max estimates */
+  double eig_safety;    /* beta = eig_safety * Lanczos estimate */
+  unsigned long long seed; /* SplitMix64 seed of the Lanczos start vectors */
+} stokes_opts;
+
+/* Fill *o with kA = kS = 3, m = 2, V-cycle, local Schur diagonal, FP32 cycle,
+ * restart 30, 40 Lanczos steps, safety 1.1, seed 0x5EED. */
+void stokes_default_opts(stokes_opts *o);
+
+/* Build the level hierarchy, geometry, 1D tables, Jacobi/Schur diagonals, the
+ * lambda_max estimates (Lanczos, FP64), sigma/tau (Lemma 1) and the factorised
+ * coarse matrix (Sec. 3.1-3.3, Algorithm 2).  k in {2,3,4}; dim in {2,3}; every
+ * n[a] divisible by 2^(n_levels-1); mu > 0, gamma_rho >= 0.  mu_cell (HOST,
+ * nullable): per-cell viscosity of the finest level (n_cells doubles, x fastest);
+ * coarse cells take the mean of their 2^d children.  Synchronises the stream.
+ * On success *out owns all device memory until stokes_destroy. */
+int stokes_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
+                 const double *mu_cell, const stokes_opts *opts, void *stream,
+                 stokes_ctx **out);
+
+/* Sizes of level `level` (0 = coarsest, n_levels-1 = finest). */
+int stokes_sizes(const stokes_ctx *ctx, int level, long long *n_u, long long *n_p);
+
+/* y = K x on `level` (Sec. 3.1: Kx = sum_tau P_tau K_tau P_tau^T x by sum
+ * factorisation).  x, y: device vectors of n_u + n_p entries; must not alias. */
+int stokes_vmult(stokes_ctx *ctx, int level, int precision, const void *x, void *y, void *stream);
+
+/* Block applications on `level`: blocks is a bit set of 1 = A u, 2 = B^T p (both into
+ * yu), 4 = B u (into yp).  Outputs are overwritten; unused pointers may be NULL.
+ * Rows of constrained velocity DoFs of yu are zero (no identity term). */
+int stokes_apply_blocks(stokes_ctx *ctx, int level, int precision, int blocks, const void *u,
+                        const void *p, void *yu, void *yp, void *stream);
+
+/* b = [Z M_v f ; 0]: right-hand side of a forcing given by its velocity nodal values
+ * f (n_u entries).  Constrained rows are zero. */
+int stokes_mass_rhs(stokes_ctx *ctx, int level, int precision, const void *f, void *b, void *stream);
+
+/* `steps` steps of the inexact symmetric Uzawa smoother in compact form
+ * x <- x + K_hat^{-1}(b - K x) (Sec. 3.3.1) on a level >= 1; x in/out. */
+int stokes_smooth(stokes_ctx *ctx, int level, int precision, int steps, const void *b, void *x,
+                  void *stream);
+
+/* Grid transfer between fine_level and fine_level-1 (Sec. 3.2): direction 0 =
+ * restriction out = P^T in (fine -> coarse), 1 = prolongation out = P in (coarse ->
+ * fine).  Constrained velocity DoFs are removed on both sides. */
+int stokes_transfer(stokes_ctx *ctx, int fine_level, int precision, int direction, const void *in,
+                    void *out, void *stream);
+
+/* Coarse direct solve on level 0 (Sec. 4.1): x = K_0^{-1} b; under full Dirichlet
+ * data the bordered system fixes sum(p) = 0. */
+int stokes_coarse_solve(stokes_ctx *ctx, int precision, const void *b, void *x, void *stream);
+
+/* One multigrid cycle on the finest level, x <- MG(x, b) (Algorithm 1). */
+int mg_vcycle(stokes_ctx *ctx, int precision, const void *b, void *x, void *stream);
+
+/* FP64 flexible GMRES on the finest level, right-preconditioned by one cycle per
+ * iteration (FP32 or FP64 per opts.vcycle_fp32), from the initial guess in x, to
+ * ||b - K x||_2 <= rtol ||b||_2.  b, x: device double vectors.  Synchronises the
+ * stream.  Under full Dirichlet data the returned pressure has zero mean.
+ * iters, final_rel_res: HOST outputs (nullable).  STOKES_ENOTCONV after maxit. */
+int stokes_solve(stokes_ctx *ctx, const double *b, double *x, double rtol, int maxit, int *iters,
+                 double *final_rel_res, void *stream);
+
+/* stokes_solve with HOST vectors: copies b in, solves from x = 0, copies x out. */
+int stokes_solve_host(stokes_ctx *ctx, const double *b_host, double *x_host, double rtol, int maxit,
+                      int *iters, double *final_rel_res, void *stream);
+
+/* Smoother parameters of a level >= 1 (Algorithm 2): beta of D_A^-1 A and of
+ * D_S^-1 S_tilde (safety factor included), sigma and tau (Lemma 1).  HOST outputs. */
+int stokes_get_level_params(const stokes_ctx *ctx, int level, double *beta_A, double *beta_S,
+                            double *sigma, double *tau);
+
+/* Copy the FP64 Jacobi diagonal D_A (n_u) and the Schur diagonal approximation
+ * D_S (n_p) of a level into device buffers (either may be NULL). */
+int stokes_get_diagonals(stokes_ctx *ctx, int level, double *DA, double *DS, void *stream);
+
+/* Number of kernel launches this context issued since setup (a counter kept by the
+ * library for reporting; not thread-safe). */
+long long stokes_launch_count(const stokes_ctx *ctx);
+
+const char *stokes_last_error(const stokes_ctx *ctx);
+const char *stokes_global_last_error(void);
+void stokes_destroy(stokes_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STOKES_MF_H */

@@ -1,0 +1,248 @@
+"""GB300 matrix-free monolithic multigrid for Q_k-Q_{k-1} Taylor-Hood (generalized) Stokes.
+
+Python face of the C ABI in include/stokes_mf.h.  Every computation runs in the CUDA
+library libstokes_mf.so; this module only marshals torch tensors (device memory and
+streams) into the C calls.  If the library is missing, constructing a solver raises.
+
+    from paper_2205_15770_gb300 import StokesMG
+    S = StokesMG(dim=3, n=(32, 32, 32), n_levels=5, k=2, vertices=V, gamma_rho=100.0)
+    b = S.mass_rhs(f)                      # f: velocity nodal forcing, torch.float64 on cuda
+    x, iters, rel = S.solve(b, rtol=1e-8)
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib as L
+
+__all__ = ["StokesMG", "StokesError", "ALL_FACES"]
+
+ALL_FACES = {2: 0xF, 3: 0x3F}
+BLOCK_A, BLOCK_BT, BLOCK_B = 1, 2, 4
+
+
+class StokesError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{L.STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _ptr(t, dtype):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA torch tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"expected dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
+class StokesMG:
+    """One hierarchy + smoother setup (Algorithm 2) + coarse factorisation on the current CUDA device."""
+
+    def __init__(self, dim, n, n_levels, k=2, mu=1.0, gamma_rho=0.0, vertices=None, lo=(0.0, 0.0, 0.0),
+                 hi=(1.0, 1.0, 1.0), dirichlet_faces=None, mu_cell=None, kA=3, kS=3, m=2, cycle="V",
+                 schur_diag="loc", vcycle_fp32=True, restart=30, eig_iters=40, eig_safety=1.1, seed=0x5EED):
+        self._lib = L.load()
+        torch = _torch()
+        self.dim, self.k, self.n_levels = dim, k, n_levels
+        mesh = L.StokesMesh()
+        mesh.dim = dim
+        nn = list(n) + [1] * (3 - len(n))
+        for a in range(3):
+            mesh.n[a] = int(nn[a])
+            mesh.lo[a] = float(lo[a]) if a < len(lo) else 0.0
+            mesh.hi[a] = float(hi[a]) if a < len(hi) else 1.0
+        mesh.n_levels = n_levels
+        mesh.dirichlet_faces = ALL_FACES[dim] if dirichlet_faces is None else int(dirichlet_faces)
+        self._keep = []
+        if vertices is not None:
+            v = np.ascontiguousarray(np.asarray(vertices, dtype=np.float64).reshape(-1))
+            self._keep.append(v)
+            mesh.vertices = v.ctypes.data_as(C.POINTER(C.c_double))
+        mu_ptr = None
+        if mu_cell is not None:
+            mc = np.ascontiguousarray(np.asarray(mu_cell, dtype=np.float64).reshape(-1))
+            self._keep.append(mc)
+            mu_ptr = mc.ctypes.data_as(C.POINTER(C.c_double))
+        opts = L.StokesOpts()
+        self._lib.stokes_default_opts(C.byref(opts))
+        opts.kA, opts.kS, opts.m = kA, kS, m
+        opts.cycle = {"V": 0, "W": 1}[cycle]
+        opts.schur_diag = {"loc": 0, "p": 1}[schur_diag]
+        opts.vcycle_fp32 = 1 if vcycle_fp32 else 0
+        opts.gmres_restart = restart
+        opts.eig_iters = eig_iters
+        opts.eig_safety = eig_safety
+        opts.seed = seed
+        ctx = C.c_void_p()
+        st = self._lib.stokes_setup(C.byref(mesh), k, float(mu), float(gamma_rho), mu_ptr, C.byref(opts),
+                                    self._stream(), C.byref(ctx))
+        if st != 0:
+            raise StokesError(st, self._lib.stokes_global_last_error().decode())
+        self._ctx = ctx
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.sizes_all = [self.sizes(l) for l in range(n_levels)]
+
+    # --- plumbing ------------------------------------------------------------------------------
+    @staticmethod
+    def _stream():
+        torch = _torch()
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def _check(self, st):
+        if st != 0:
+            raise StokesError(st, self._lib.stokes_last_error(self._ctx).decode())
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._lib.stokes_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _level(self, level):
+        return self.n_levels - 1 if level is None else level
+
+    def sizes(self, level=None):
+        nu, npr = C.c_longlong(), C.c_longlong()
+        self._check(self._lib.stokes_sizes(self._ctx, self._level(level), C.byref(nu), C.byref(npr)))
+        return nu.value, npr.value
+
+    def size(self, level=None):
+        nu, npr = self.sizes(level)
+        return nu + npr
+
+    @staticmethod
+    def _prec(t):
+        torch = _torch()
+        if t.dtype == torch.float64:
+            return 64
+        if t.dtype == torch.float32:
+            return 32
+        raise TypeError("vectors must be float32 or float64")
+
+    def empty(self, level=None, dtype=None):
+        torch = _torch()
+        return torch.empty(self.size(level), dtype=dtype or torch.float64, device=self.device)
+
+    # --- operators ------------------------------------------------------------------------------
+    def vmult(self, x, y=None, level=None):
+        """y = K x (Sec. 3.1 matrix-free operator)."""
+        torch = _torch()
+        y = torch.empty_like(x) if y is None else y
+        pr = self._prec(x)
+        self._check(self._lib.stokes_vmult(self._ctx, self._level(level), pr, _ptr(x, x.dtype), _ptr(y, x.dtype),
+                                           self._stream()))
+        return y
+
+    def apply_blocks(self, blocks, u=None, p=None, level=None, dtype=None):
+        """Returns (yu, yp) with yu = [A u] + [B^T p], yp = B u according to the block bit set."""
+        torch = _torch()
+        lv = self._level(level)
+        nu, npr = self.sizes(lv)
+        ref = u if u is not None else p
+        dt = ref.dtype
+        yu = torch.empty(nu, dtype=dt, device=self.device) if blocks & 3 else None
+        yp = torch.empty(npr, dtype=dt, device=self.device) if blocks & 4 else None
+        self._check(self._lib.stokes_apply_blocks(
+            self._ctx, lv, self._prec(ref), blocks, _ptr(u, dt) if u is not None else None,
+            _ptr(p, dt) if p is not None else None, _ptr(yu, dt) if yu is not None else None,
+            _ptr(yp, dt) if yp is not None else None, self._stream()))
+        return yu, yp
+
+    def mass_rhs(self, f, level=None):
+        """b = [Z M_v f ; 0] for velocity nodal values f (n_u entries)."""
+        torch = _torch()
+        lv = self._level(level)
+        b = torch.empty(self.size(lv), dtype=f.dtype, device=self.device)
+        self._check(self._lib.stokes_mass_rhs(self._ctx, lv, self._prec(f), _ptr(f, f.dtype), _ptr(b, f.dtype),
+                                              self._stream()))
+        return b
+
+    def smooth(self, b, x, steps=1, level=None):
+        """x <- S^steps (x, b): inexact symmetric Uzawa smoother (in place)."""
+        self._check(self._lib.stokes_smooth(self._ctx, self._level(level), self._prec(x), steps, _ptr(b, x.dtype),
+                                            _ptr(x, x.dtype), self._stream()))
+        return x
+
+    def restrict(self, r_fine, fine_level):
+        torch = _torch()
+        out = torch.empty(self.size(fine_level - 1), dtype=r_fine.dtype, device=self.device)
+        self._check(self._lib.stokes_transfer(self._ctx, fine_level, self._prec(r_fine), 0, _ptr(r_fine, r_fine.dtype),
+                                              _ptr(out, r_fine.dtype), self._stream()))
+        return out
+
+    def prolongate(self, w_coarse, fine_level):
+        torch = _torch()
+        out = torch.empty(self.size(fine_level), dtype=w_coarse.dtype, device=self.device)
+        self._check(self._lib.stokes_transfer(self._ctx, fine_level, self._prec(w_coarse), 1,
+                                              _ptr(w_coarse, w_coarse.dtype), _ptr(out, w_coarse.dtype),
+                                              self._stream()))
+        return out
+
+    def coarse_solve(self, b):
+        torch = _torch()
+        x = torch.empty_like(b)
+        self._check(self._lib.stokes_coarse_solve(self._ctx, self._prec(b), _ptr(b, b.dtype), _ptr(x, b.dtype),
+                                                  self._stream()))
+        return x
+
+    def vcycle(self, b, x=None):
+        """x <- MG(x, b), one cycle of Algorithm 1 on the finest level (FP32 or FP64 by dtype)."""
+        torch = _torch()
+        x = torch.zeros_like(b) if x is None else x
+        self._check(self._lib.mg_vcycle(self._ctx, self._prec(b), _ptr(b, b.dtype), _ptr(x, b.dtype),
+                                        self._stream()))
+        return x
+
+    def solve(self, b, x=None, rtol=1e-8, maxit=200):
+        """FP64 FGMRES right-preconditioned by one cycle per iteration; returns (x, iterations, rel. residual)."""
+        torch = _torch()
+        x = torch.zeros_like(b) if x is None else x
+        it, rel = C.c_int(), C.c_double()
+        st = self._lib.stokes_solve(self._ctx, _ptr(b, torch.float64), _ptr(x, torch.float64), float(rtol),
+                                    int(maxit), C.byref(it), C.byref(rel), self._stream())
+        self._check(st)
+        return x, it.value, rel.value
+
+    def solve_host(self, b, rtol=1e-8, maxit=200, out=None):
+        """stokes_solve_host: numpy float64 b in (pinned or pageable host memory), numpy x out."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.empty_like(b) if out is None else out
+        it, rel = C.c_int(), C.c_double()
+        st = self._lib.stokes_solve_host(self._ctx, b.ctypes.data_as(C.POINTER(C.c_double)),
+                                         x.ctypes.data_as(C.POINTER(C.c_double)), float(rtol), int(maxit),
+                                         C.byref(it), C.byref(rel), self._stream())
+        self._check(st)
+        return x, it.value, rel.value
+
+    def level_params(self, level):
+        vals = [C.c_double() for _ in range(4)]
+        self._check(self._lib.stokes_get_level_params(self._ctx, level, *[C.byref(v) for v in vals]))
+        return dict(zip(("beta_A", "beta_S", "sigma", "tau"), (v.value for v in vals)))
+
+    def diagonals(self, level):
+        torch = _torch()
+        nu, npr = self.sizes(level)
+        DA = torch.empty(nu, dtype=torch.float64, device=self.device)
+        DS = torch.empty(npr, dtype=torch.float64, device=self.device)
+        self._check(self._lib.stokes_get_diagonals(self._ctx, level, _ptr(DA, torch.float64), _ptr(DS, torch.float64),
+                                                   self._stream()))
+        return DA, DS
+
+    @property
+    def launch_count(self):
+        return int(self._lib.stokes_launch_count(self._ctx))

@@ -1,0 +1,1159 @@
+// C ABI of the matrix-free monolithic multigrid library: context, setup (Algorithm 2),
+// smoother (Sec. 3.3.1), multigrid cycle (Algorithm 1), coarse solve (Sec. 4.1) and the
+// FP64 flexible-GMRES outer loop.  Host code orchestrates; every vector operation runs
+// in the kernels of apply.cuh, vec.cuh, transfer.cuh and kernels_misc.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/stokes_mf.h"
+#include "common.cuh"
+#include "host_tables.h"
+#include "transfer.cuh"
+#include "vec.cuh"
+
+namespace smf {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string &m) { g_last_error = m; }
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
+  set_error(std::string("CUDA error '") + cudaGetErrorString(e) + "' in " + what + " (" + file + ":" +
+            std::to_string(line) + ")");
+  return STOKES_ECUDA;
+}
+
+template <typename T>
+int launch_cell_apply(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, const T *u, const T *p, T *yu, T *yp,
+                      cudaStream_t s) {
+  switch (L.k) {
+    case 2: return launch_cell_apply_k<2, T>(L, tab, mode, u, p, yu, yp, s);
+    case 3: return launch_cell_apply_k<3, T>(L, tab, mode, u, p, yu, yp, s);
+    default: return launch_cell_apply_k<4, T>(L, tab, mode, u, p, yu, yp, s);
+  }
+}
+template <>
+int launch_cell_diag<double>(const LevelDesc<double> &L, const Tab1D<double> *tab, double *a, double *b, double *c,
+                             cudaStream_t s) {
+  switch (L.k) {
+    case 2: return launch_cell_diag_k<2, double>(L, tab, a, b, c, s);
+    case 3: return launch_cell_diag_k<3, double>(L, tab, a, b, c, s);
+    default: return launch_cell_diag_k<4, double>(L, tab, a, b, c, s);
+  }
+}
+
+// x = Kinv b on the coarse level: one warp per row, FP64 accumulation.
+template <typename T>
+__global__ void k_coarse_apply(const double *__restrict__ Kinv, int n0, const T *__restrict__ b, T *__restrict__ x) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n0) return;
+  const double *row = Kinv + (long long)warp * n0;
+  double s = 0.0;
+  for (int j = lane; j < n0; j += 32) s += row[j] * (double)b[j];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) x[warp] = (T)s;
+}
+
+// ------------------------------------------------------------------------------------------
+template <typename T>
+struct LevelRT {
+  LevelDesc<T> d{};
+  T *DAinv = nullptr, *DSinv = nullptr;
+  T *x = nullptr, *b = nullptr, *r = nullptr;                                   // full vectors
+  T *tu = nullptr, *ru = nullptr, *uhat = nullptr, *cx = nullptr, *cd = nullptr, *ct = nullptr;  // velocity
+  T *r2 = nullptr, *cx2 = nullptr, *cd2 = nullptr, *ct2 = nullptr, *au = nullptr;              // nested in S~
+  T *pt = nullptr, *rp = nullptr, *px = nullptr, *pd = nullptr, *ps = nullptr, *dp = nullptr;  // pressure
+};
+
+struct GraphSlot {
+  cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;
+};
+
+}  // namespace smf
+
+using namespace smf;
+
+struct stokes_ctx {
+  int dim = 0, k = 0, nl = 0;
+  stokes_opts o{};
+  double mu = 1, gamma_rho = 0;
+  bool pker = false;
+  std::vector<LevelRT<double>> L64;
+  std::vector<LevelRT<float>> L32;
+  std::vector<double *> DA, DS;    // FP64 diagonals per level (device)
+  Tab1D<double> *tab64 = nullptr;
+  Tab1D<float> *tab32 = nullptr;
+  TransferTab<double> *tt64 = nullptr;
+  TransferTab<float> *tt32 = nullptr;
+  std::vector<double> betaA, betaS;
+  double sigma = 1, tau = 1;
+  int n0 = 0;
+  double *Kinv = nullptr;
+  // Krylov / Lanczos work space (FP64, finest level size)
+  double *V = nullptr, *Z = nullptr, *w = nullptr, *hdev = nullptr, *partial = nullptr, *scal = nullptr;
+  double *lz0 = nullptr, *lz1 = nullptr, *lz2 = nullptr, *lz3 = nullptr, *sq = nullptr;
+  int restart = 30;
+  std::vector<void *> allocs;
+  std::string err;
+  long long launches = 0;
+  bool capturing = false;
+  long long cap_count = 0;
+  bool use_graphs = true;
+  GraphSlot g32, g64;
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+};
+
+namespace smf {
+
+template <typename T>
+static int dalloc(stokes_ctx *C, T **p, long long n) {
+  if (n <= 0) n = 1;
+  cudaError_t e = cudaMalloc((void **)p, (size_t)n * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error("device allocation of " + std::to_string((long long)n * sizeof(T)) + " bytes failed");
+    return STOKES_ENOMEM;
+  }
+  C->allocs.push_back((void *)*p);
+  SMF_CUDA_OK(cudaMemsetAsync(*p, 0, (size_t)n * sizeof(T), C->s));
+  return STOKES_OK;
+}
+
+template <typename T>
+std::vector<LevelRT<T>> &levels(stokes_ctx *C);
+template <>
+std::vector<LevelRT<double>> &levels<double>(stokes_ctx *C) { return C->L64; }
+template <>
+std::vector<LevelRT<float>> &levels<float>(stokes_ctx *C) { return C->L32; }
+template <typename T>
+const Tab1D<T> *tables(stokes_ctx *C);
+template <>
+const Tab1D<double> *tables<double>(stokes_ctx *C) { return C->tab64; }
+template <>
+const Tab1D<float> *tables<float>(stokes_ctx *C) { return C->tab32; }
+template <typename T>
+const TransferTab<T> *ttables(stokes_ctx *C);
+template <>
+const TransferTab<double> *ttables<double>(stokes_ctx *C) { return C->tt64; }
+template <>
+const TransferTab<float> *ttables<float>(stokes_ctx *C) { return C->tt32; }
+template <typename T>
+GraphSlot &graph_slot(stokes_ctx *C);
+template <>
+GraphSlot &graph_slot<double>(stokes_ctx *C) { return C->g64; }
+template <>
+GraphSlot &graph_slot<float>(stokes_ctx *C) { return C->g32; }
+
+// Chebyshev three-term recurrence coefficients (Sec. 3.3.1) for [alpha, beta] = [beta/2, beta].
+struct ChebCoef {
+  double c0;
+  int k;
+  double c1[17], c2[17];
+};
+static ChebCoef cheb_coef(int k, double beta) {
+  ChebCoef c{};
+  const double alpha = 0.5 * beta, theta = 0.5 * (beta + alpha), delta = 0.5 * (beta - alpha);
+  const double s1 = theta / delta;
+  double rho = 1.0 / s1;
+  c.c0 = 1.0 / theta;
+  c.k = k;
+  for (int j = 1; j <= k; ++j) {
+    const double rn = 1.0 / (2.0 * s1 - rho);
+    c.c1[j] = rn * rho;
+    c.c2[j] = 2.0 * rn / delta;
+    rho = rn;
+  }
+  return c;
+}
+
+static double lemma1_scaling(int k) {
+  // sigma = C_{k+1}(3) / (1 + C_{k+1}(3)), Chebyshev polynomial by its recurrence (Lemma 1)
+  double c0 = 1.0, c1 = 3.0;
+  for (int j = 1; j < k + 1; ++j) {
+    double c2 = 6.0 * c1 - c0;
+    c0 = c1;
+    c1 = c2;
+  }
+  return c1 / (1.0 + c1);
+}
+
+template <typename T>
+struct Runner {
+  stokes_ctx *C;
+  cudaStream_t s;
+  std::vector<LevelRT<T>> &L;
+  const Tab1D<T> *tab;
+  const TransferTab<T> *tt;
+  explicit Runner(stokes_ctx *c)
+      : C(c), s(c->s), L(levels<T>(c)), tab(tables<T>(c)), tt(ttables<T>(c)) {}
+
+  void note() {
+    if (C->capturing)
+      ++C->cap_count;
+    else
+      ++C->launches;
+  }
+  void zero(T *p, long long n) { cudaMemsetAsync(p, 0, (size_t)n * sizeof(T), s); }
+  long long nu(int l) const { return L[l].d.n_u; }
+  long long np(int l) const { return L[l].d.n_p; }
+
+  void apply(int l, int mode, const T *u, const T *p, T *yu, T *yp) {
+    if (yu) zero(yu, nu(l));
+    if (yp) zero(yp, np(l));
+    launch_cell_apply<T>(L[l].d, tab, mode, u, p, yu, yp, s);
+    note();
+  }
+  void vmult(int l, const T *x, T *y, bool identity) {
+    apply(l, kApplyA | kApplyBT | kApplyB, x, x + nu(l), y, y + nu(l));
+    if (identity) {
+      k_identity_rows<T><<<vec_blocks(nu(l)), kVecThreads, 0, s>>>(L[l].d, x, y);
+      note();
+    }
+  }
+  void sub(const T *a, const T *b, T *out, long long n) {
+    k_sub<T><<<vec_blocks(n), kVecThreads, 0, s>>>(a, b, out, n);
+    note();
+  }
+  void axpy(T *x, T a, const T *b, long long n) {
+    k_axpy<T><<<vec_blocks(n), kVecThreads, 0, s>>>(x, a, b, n);
+    note();
+  }
+
+  // out = base + fscale * scale * Cheb(M, D, k) r,  r = sr * (a - b)   (Sec. 3.3.1)
+  // velocity: M = A, D = D_A, (k, beta, scale) = (k_A, beta_A, sigma)
+  // pressure: M = S~ = B A^-1_hat B^T, D = D_S, (k_S, beta_S, tau)
+  void cheb(int l, bool velocity, bool nested, const T *a, const T *b, T sr, const T *base, T fscale, T *out) {
+    LevelRT<T> &R = L[l];
+    const int kd = velocity ? C->o.kA : C->o.kS;
+    const ChebCoef cc = cheb_coef(kd, velocity ? C->betaA[l] : C->betaS[l]);
+    const T scale = (T)(fscale * (velocity ? C->sigma : C->tau));
+    const T *Dinv = velocity ? R.DAinv : R.DSinv;
+    const long long n = velocity ? nu(l) : np(l);
+    T *rb, *xb, *db, *tb;
+    if (velocity) {
+      rb = nested ? R.r2 : R.ru;
+      xb = nested ? R.cx2 : R.cx;
+      db = nested ? R.cd2 : R.cd;
+      tb = nested ? R.ct2 : R.ct;
+    } else {
+      rb = R.rp;
+      xb = R.px;
+      db = R.pd;
+      tb = R.ps;
+    }
+    const int nb = vec_blocks(n);
+    if (kd == 0) {
+      k_cheb_init<T><<<nb, kVecThreads, 0, s>>>(a, b, sr, Dinv, (T)cc.c0, nullptr, db, xb, base, scale, out, n);
+      note();
+      return;
+    }
+    k_cheb_init<T><<<nb, kVecThreads, 0, s>>>(a, b, sr, Dinv, (T)cc.c0, rb, db, xb, nullptr, T(0), nullptr, n);
+    note();
+    for (int j = 1; j <= kd; ++j) {
+      if (velocity)
+        apply(l, kApplyA, xb, nullptr, tb, nullptr);
+      else
+        S_tilde(l, xb, tb);
+      const bool last = j == kd;
+      k_cheb_step<T><<<nb, kVecThreads, 0, s>>>(rb, tb, Dinv, (T)cc.c1[j], (T)cc.c2[j], db, xb, last ? base : nullptr,
+                                                scale, last ? out : nullptr, n);
+      note();
+    }
+  }
+  // y = B A^-1_hat B^T q
+  void S_tilde(int l, const T *q, T *y) {
+    LevelRT<T> &R = L[l];
+    apply(l, kApplyBT, nullptr, q, R.tu, nullptr);
+    cheb(l, true, true, R.tu, nullptr, T(1), nullptr, T(1), R.au);
+    apply(l, kApplyB, R.au, nullptr, nullptr, y);
+  }
+  // One inexact symmetric Uzawa step in compact form (Sec. 3.3.1, K_hat):
+  //   u_hat = u + A^-1_hat (f - A u - B^T p); dp = S^-1_hat (B u_hat - g);
+  //   u = u_hat - A^-1_hat B^T dp; p = p + dp
+  void smooth_step(int l, T *x, const T *bv) {
+    LevelRT<T> &R = L[l];
+    const long long n_u = nu(l), n_p = np(l);
+    T *u = x, *p = x + n_u;
+    const T *f = bv, *g = bv + n_u;
+    apply(l, kApplyA | kApplyBT, u, p, R.tu, nullptr);
+    cheb(l, true, false, f, R.tu, T(1), u, T(1), R.uhat);
+    apply(l, kApplyB, R.uhat, nullptr, nullptr, R.pt);
+    cheb(l, false, false, R.pt, g, T(1), nullptr, T(1), R.dp);
+    apply(l, kApplyBT, nullptr, R.dp, R.tu, nullptr);
+    cheb(l, true, false, R.tu, nullptr, T(1), R.uhat, T(-1), u);
+    axpy(p, T(1), R.dp, n_p);
+  }
+  void coarse(const T *b, T *x) {
+    const int n0 = C->n0;
+    k_coarse_apply<T><<<(n0 * 32 + 255) / 256, 256, 0, s>>>(C->Kinv, n0, b, x);
+    note();
+  }
+  void restrict_to(int lf, const T *in, T *out) {
+    const long long n = nu(lf - 1) + np(lf - 1);
+    k_restrict<T><<<vec_blocks(n), kVecThreads, 0, s>>>(L[lf].d, L[lf - 1].d, tt, in, out);
+    note();
+  }
+  void prolongate(int lf, const T *in, T *out, int add) {
+    const long long n = nu(lf) + np(lf);
+    k_prolongate<T><<<vec_blocks(n), kVecThreads, 0, s>>>(L[lf].d, L[lf - 1].d, tt, in, out, add);
+    note();
+  }
+  // Algorithm 1: MG(x_l, b_l) with gamma = 1 (V) or 2 (W); returns after the coarse solve on l = 0.
+  void cycle(int l, T *x, const T *b) {
+    if (l == 0) {
+      coarse(b, x);
+      return;
+    }
+    LevelRT<T> &R = L[l];
+    const long long n = nu(l) + np(l);
+    for (int i = 0; i < C->o.m; ++i) smooth_step(l, x, b);
+    vmult(l, x, R.r, false);
+    sub(b, R.r, R.r, n);
+    restrict_to(l, R.r, L[l - 1].b);
+    zero(L[l - 1].x, nu(l - 1) + np(l - 1));
+    const int gam = C->o.cycle == 1 ? 2 : 1;
+    for (int j = 0; j < gam; ++j) cycle(l - 1, L[l - 1].x, L[l - 1].b);
+    prolongate(l, L[l - 1].x, x, 1);
+    for (int i = 0; i < C->o.m; ++i) smooth_step(l, x, b);
+  }
+  // One cycle on the finest level using the internal top-level buffers (graph-captured).
+  int top_cycle() {
+    const int top = C->nl - 1;
+    if (!C->use_graphs) {
+      cycle(top, L[top].x, L[top].b);
+      return STOKES_OK;
+    }
+    GraphSlot &g = graph_slot<T>(C);
+    if (!g.exec) {
+      SMF_CUDA_OK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      C->capturing = true;
+      C->cap_count = 0;
+      cycle(top, L[top].x, L[top].b);
+      C->capturing = false;
+      cudaGraph_t graph;
+      SMF_CUDA_OK(cudaStreamEndCapture(s, &graph));
+      cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      SMF_CUDA_OK(e);
+      g.kernels = C->cap_count;
+    }
+    SMF_CUDA_OK(cudaGraphLaunch(g.exec, s));
+    C->launches += g.kernels;
+    return STOKES_OK;
+  }
+};
+
+// ---- FP64 reductions returning host scalars ------------------------------------------------
+static int dot64(stokes_ctx *C, const double *a, const double *b, long long n, double *out) {
+  k_mdot_partial<<<kRedBlocks, kVecThreads, 0, C->s>>>(a, n, 1, b, n, C->partial);
+  k_final_reduce<<<1, kVecThreads, 0, C->s>>>(C->partial, kRedBlocks, 1, C->scal);
+  C->launches += 2;
+  SMF_CUDA_OK(cudaMemcpyAsync(out, C->scal, sizeof(double), cudaMemcpyDeviceToHost, C->s));
+  SMF_CUDA_OK(cudaStreamSynchronize(C->s));
+  return STOKES_OK;
+}
+
+static int sum64(stokes_ctx *C, const double *a, long long n, double *dev_out) {
+  k_sum_partial<<<kRedBlocks, kVecThreads, 0, C->s>>>(a, n, C->partial);
+  k_final_reduce<<<1, kVecThreads, 0, C->s>>>(C->partial, kRedBlocks, 1, dev_out);
+  C->launches += 2;
+  return STOKES_OK;
+}
+
+// Largest Ritz value of plain Lanczos on D^{-1/2} M D^{-1/2} (Algorithm 2's lambda_max).
+// velocity: M = A on level l; pressure: M = S~.  Start vector: SplitMix64(seed) (velocity,
+// constrained entries zeroed) or SplitMix64(seed + 1) with the kernel direction D^{1/2} 1
+// projected out under full Dirichlet data.
+static int lanczos(stokes_ctx *C, int l, bool velocity, double *est) {
+  Runner<double> R(C);
+  LevelRT<double> &LV = C->L64[l];
+  const long long n = velocity ? LV.d.n_u : LV.d.n_p;
+  const int nb = vec_blocks(n);
+  double *v = C->lz0, *vprev = C->lz1, *w = C->lz2, *tmp = C->lz3, *sq = C->sq;
+  const double *Dg = velocity ? C->DA[l] : C->DS[l];
+  k_rsqrt<double><<<nb, kVecThreads, 0, C->s>>>(Dg, sq, n);
+  k_splitmix<<<nb, kVecThreads, 0, C->s>>>(C->o.seed + (velocity ? 0ull : 1ull), v, n);
+  C->launches += 2;
+  if (velocity) {
+    k_zero_constrained<double><<<nb, kVecThreads, 0, C->s>>>(LV.d, v);
+    ++C->launches;
+  } else if (C->pker) {
+    // z = sqrt(D_S) = 1 / sq
+    k_reciprocal<double><<<nb, kVecThreads, 0, C->s>>>(sq, tmp, n);
+    ++C->launches;
+    double vz, zz;
+    int st = dot64(C, v, tmp, n, &vz);
+    if (st) return st;
+    st = dot64(C, tmp, tmp, n, &zz);
+    if (st) return st;
+    k_axpy<double><<<nb, kVecThreads, 0, C->s>>>(v, -vz / zz, tmp, n);
+    ++C->launches;
+  }
+  double nrm2;
+  int st = dot64(C, v, v, n, &nrm2);
+  if (st) return st;
+  k_scale<double><<<nb, kVecThreads, 0, C->s>>>(v, 1.0 / std::sqrt(nrm2), v, n);
+  SMF_CUDA_OK(cudaMemsetAsync(vprev, 0, n * sizeof(double), C->s));
+  ++C->launches;
+  std::vector<double> al, be;
+  double bprev = 0.0;
+  const int steps = std::max(1, C->o.eig_iters);
+  for (int j = 0; j < steps; ++j) {
+    k_mul<double><<<nb, kVecThreads, 0, C->s>>>(sq, v, tmp, n);
+    ++C->launches;
+    if (velocity) {
+      R.apply(l, kApplyA, tmp, nullptr, w, nullptr);
+    } else {
+      R.S_tilde(l, tmp, w);
+    }
+    k_mul<double><<<nb, kVecThreads, 0, C->s>>>(sq, w, w, n);
+    k_axpy<double><<<nb, kVecThreads, 0, C->s>>>(w, -bprev, vprev, n);
+    C->launches += 2;
+    double a;
+    st = dot64(C, w, v, n, &a);
+    if (st) return st;
+    k_axpy<double><<<nb, kVecThreads, 0, C->s>>>(w, -a, v, n);
+    ++C->launches;
+    al.push_back(a);
+    double b2;
+    st = dot64(C, w, w, n, &b2);
+    if (st) return st;
+    const double b = std::sqrt(b2);
+    if (!std::isfinite(a) || !std::isfinite(b)) {
+      set_error("Lanczos produced a non-finite value");
+      return STOKES_EBREAKDOWN;
+    }
+    if (j == steps - 1 || b <= 1e-14 * std::max(std::fabs(a), 1.0)) break;
+    be.push_back(b);
+    std::swap(vprev, v);  // vprev <- v
+    k_scale<double><<<nb, kVecThreads, 0, C->s>>>(w, 1.0 / b, v, n);
+    ++C->launches;
+    bprev = b;
+  }
+  be.resize(al.size() > 0 ? al.size() - 1 : 0);
+  *est = tridiag_max_eig(al, be);
+  return STOKES_OK;
+}
+
+// Dense coarse matrix K_0 by applying the FP64 operator to unit vectors, then the inverse of
+// the (bordered) matrix by Gauss-Jordan with partial pivoting, all on the device.
+static int setup_coarse(stokes_ctx *C) {
+  Runner<double> R(C);
+  LevelRT<double> &L0 = C->L64[0];
+  const long long n0 = L0.d.n_u + L0.d.n_p;
+  if (n0 > 20000) {
+    set_error("coarse level has " + std::to_string(n0) + " DoFs; the dense direct solve allows at most 20000");
+    return STOKES_EINVAL;
+  }
+  C->n0 = (int)n0;
+  double *K0 = nullptr, *e = nullptr, *M = nullptr, *fac = nullptr;
+  int *err = nullptr;
+  int st;
+  if ((st = dalloc(C, &K0, n0 * n0))) return st;
+  if ((st = dalloc(C, &e, n0))) return st;
+  const int bord = C->pker ? 1 : 0;
+  const int nb = (int)n0 + bord;
+  if ((st = dalloc(C, &M, (long long)nb * 2 * nb))) return st;
+  if ((st = dalloc(C, &fac, nb))) return st;
+  if ((st = dalloc(C, &err, 1))) return st;
+  if ((st = dalloc(C, &C->Kinv, n0 * n0))) return st;
+  for (long long j = 0; j < n0; ++j) {
+    k_unit<<<vec_blocks(n0), kVecThreads, 0, C->s>>>(e, n0, j);
+    ++C->launches;
+    R.vmult(0, e, K0 + j * n0, true);
+  }
+  k_build_augmented<<<vec_blocks((long long)nb * 2 * nb), kVecThreads, 0, C->s>>>(K0, (int)n0, L0.d.n_u, bord, M);
+  ++C->launches;
+  for (int k = 0; k < nb; ++k) {
+    k_gj_pivot<<<1, 1024, 0, C->s>>>(M, nb, k, fac, err);
+    dim3 g((2 * nb + 255) / 256, nb);
+    k_gj_elim<<<g, 256, 0, C->s>>>(M, nb, k, fac);
+    C->launches += 2;
+  }
+  k_extract_inverse<<<vec_blocks(n0 * n0), kVecThreads, 0, C->s>>>(M, nb, (int)n0, C->Kinv);
+  ++C->launches;
+  int herr = 0;
+  SMF_CUDA_OK(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, C->s));
+  SMF_CUDA_OK(cudaStreamSynchronize(C->s));
+  if (herr) {
+    set_error("coarse matrix is singular");
+    return STOKES_EBREAKDOWN;
+  }
+  return STOKES_OK;
+}
+
+template <typename T>
+static int alloc_level_buffers(stokes_ctx *C, LevelRT<T> &R) {
+  const long long nu = R.d.n_u, np = R.d.n_p, n = nu + np;
+  int st;
+  T **full[] = {&R.x, &R.b, &R.r};
+  for (auto p : full)
+    if ((st = dalloc(C, p, n))) return st;
+  T **vel[] = {&R.DAinv, &R.tu, &R.ru, &R.uhat, &R.cx, &R.cd, &R.ct, &R.r2, &R.cx2, &R.cd2, &R.ct2, &R.au};
+  for (auto p : vel)
+    if ((st = dalloc(C, p, nu))) return st;
+  T **pre[] = {&R.DSinv, &R.pt, &R.rp, &R.px, &R.pd, &R.ps, &R.dp};
+  for (auto p : pre)
+    if ((st = dalloc(C, p, np))) return st;
+  return STOKES_OK;
+}
+
+struct StreamGuard {
+  stokes_ctx *C;
+  cudaStream_t user;
+  StreamGuard(stokes_ctx *c, void *u) : C(c), user((cudaStream_t)u) {
+    cudaEventRecord(C->ev_in, user);
+    cudaStreamWaitEvent(C->s, C->ev_in, 0);
+  }
+  ~StreamGuard() {
+    cudaEventRecord(C->ev_out, C->s);
+    cudaStreamWaitEvent(user, C->ev_out, 0);
+  }
+};
+
+static int finish(stokes_ctx *C, int st) {
+  if (st != STOKES_OK) {
+    C->err = g_last_error;
+    return st;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cuda_fail(e, "kernel launch", __FILE__, __LINE__);
+    C->err = g_last_error;
+    return STOKES_ECUDA;
+  }
+  return STOKES_OK;
+}
+
+static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho, const double *mu_cell,
+                    const stokes_opts *opts, stokes_ctx *C) {
+  const int dim = mesh->dim, nl = mesh->n_levels;
+  C->dim = dim;
+  C->k = k;
+  C->nl = nl;
+  C->mu = mu;
+  C->gamma_rho = gamma_rho;
+  if (opts)
+    C->o = *opts;
+  else
+    stokes_default_opts(&C->o);
+  if (C->o.kA < 0 || C->o.kA > 16 || C->o.kS < 0 || C->o.kS > 16 || C->o.m < 0 || C->o.gmres_restart < 1 ||
+      C->o.schur_diag < 0 || C->o.schur_diag > 1 || C->o.cycle < 0 || C->o.cycle > 1) {
+    set_error("invalid stokes_opts (kA, kS in [0,16], m >= 0, restart >= 1, schur_diag in {0,1}, cycle in {0,1})");
+    return STOKES_EINVAL;
+  }
+  const unsigned full = dim == 3 ? 0x3Fu : 0xFu;
+  const unsigned faces = mesh->dirichlet_faces & full;
+  C->pker = faces == full;
+  const char *env = getenv("STOKES_NO_GRAPHS");
+  C->use_graphs = !(env && env[0] == '1');
+  C->restart = C->o.gmres_restart;
+  int st;
+  SMF_CUDA_OK(cudaStreamCreateWithFlags(&C->s, cudaStreamNonBlocking));
+  SMF_CUDA_OK(cudaEventCreateWithFlags(&C->ev_in, cudaEventDisableTiming));
+  SMF_CUDA_OK(cudaEventCreateWithFlags(&C->ev_out, cudaEventDisableTiming));
+
+  // tables
+  Tab1D<double> t64;
+  build_tables(k, t64);
+  Tab1D<float> t32;
+  {
+    const double *src = reinterpret_cast<const double *>(&t64);
+    float *dst = reinterpret_cast<float *>(&t32);
+    for (size_t i = 0; i < sizeof(t64) / sizeof(double); ++i) dst[i] = (float)src[i];
+  }
+  TransferTab<double> tt64;
+  build_transfer(k, tt64);
+  TransferTab<float> tt32;
+  {
+    const double *src = reinterpret_cast<const double *>(&tt64);
+    float *dst = reinterpret_cast<float *>(&tt32);
+    for (size_t i = 0; i < sizeof(tt64) / sizeof(double); ++i) dst[i] = (float)src[i];
+  }
+  if ((st = dalloc(C, &C->tab64, 1))) return st;
+  if ((st = dalloc(C, &C->tab32, 1))) return st;
+  if ((st = dalloc(C, &C->tt64, 1))) return st;
+  if ((st = dalloc(C, &C->tt32, 1))) return st;
+  SMF_CUDA_OK(cudaMemcpyAsync(C->tab64, &t64, sizeof(t64), cudaMemcpyHostToDevice, C->s));
+  SMF_CUDA_OK(cudaMemcpyAsync(C->tab32, &t32, sizeof(t32), cudaMemcpyHostToDevice, C->s));
+  SMF_CUDA_OK(cudaMemcpyAsync(C->tt64, &tt64, sizeof(tt64), cudaMemcpyHostToDevice, C->s));
+  SMF_CUDA_OK(cudaMemcpyAsync(C->tt32, &tt32, sizeof(tt32), cudaMemcpyHostToDevice, C->s));
+
+  // level hierarchy (host copies of geometry and viscosity, coarse from fine)
+  C->L64.resize(nl);
+  C->L32.resize(nl);
+  C->DA.resize(nl, nullptr);
+  C->DS.resize(nl, nullptr);
+  C->betaA.assign(nl, 0.0);
+  C->betaS.assign(nl, 0.0);
+  const int nf[3] = {mesh->n[0], mesh->n[1], dim == 3 ? mesh->n[2] : 1};
+  std::vector<double> mu_fine;
+  if (mu_cell) mu_fine.assign(mu_cell, mu_cell + (long long)nf[0] * nf[1] * nf[2]);
+  std::vector<std::vector<double>> mu_levels(nl);
+  for (int l = nl - 1; l >= 0; --l) {
+    const int s = 1 << (nl - 1 - l);
+    int n[3] = {nf[0] / s, nf[1] / s, dim == 3 ? nf[2] / s : 1};
+    if (mu_cell) {
+      if (l < nl - 1) {  // mean of the 2^d children (fine level l+1 has 2n cells per direction)
+        std::vector<double> &fm = mu_levels[l + 1];
+        std::vector<double> cm((size_t)n[0] * n[1] * n[2], 0.0);
+        const int fx = 2 * n[0], fy = 2 * n[1];
+        for (int cz = 0; cz < n[2]; ++cz)
+          for (int cy = 0; cy < n[1]; ++cy)
+            for (int cx = 0; cx < n[0]; ++cx) {
+              double sum = 0.0;
+              for (int dz = 0; dz < (dim == 3 ? 2 : 1); ++dz)
+                for (int dy = 0; dy < 2; ++dy)
+                  for (int dx = 0; dx < 2; ++dx)
+                    sum += fm[((size_t)(2 * cz + dz) * fy + (2 * cy + dy)) * fx + (2 * cx + dx)];
+              cm[((size_t)cz * n[1] + cy) * n[0] + cx] = sum / (dim == 3 ? 8.0 : 4.0);
+            }
+        mu_levels[l] = cm;
+      } else {
+        mu_levels[l] = mu_fine;
+      }
+    }
+    LevelDesc<double> d{};
+    d.dim = dim;
+    d.k = k;
+    for (int a = 0; a < 3; ++a) {
+      d.n[a] = n[a];
+      d.N[a] = a < dim ? k * n[a] + 1 : 1;
+      d.Pn[a] = a < dim ? (k - 1) * n[a] + 1 : 1;
+    }
+    d.nv = (long long)d.N[0] * d.N[1] * d.N[2];
+    d.n_u = dim * d.nv;
+    d.n_p = (long long)d.Pn[0] * d.Pn[1] * d.Pn[2];
+    d.n_cells = (long long)n[0] * n[1] * n[2];
+    d.faces = faces;
+    d.cartesian = mesh->vertices ? 0 : 1;
+    for (int a = 0; a < 3; ++a) d.h[a] = a < dim ? (mesh->hi[a] - mesh->lo[a]) / n[a] : 1.0;
+    d.mu = mu;
+    d.gamma_rho = gamma_rho;
+    LevelDesc<float> f{};
+    f.dim = d.dim;
+    f.k = d.k;
+    for (int a = 0; a < 3; ++a) {
+      f.n[a] = d.n[a];
+      f.N[a] = d.N[a];
+      f.Pn[a] = d.Pn[a];
+      f.h[a] = (float)d.h[a];
+    }
+    f.nv = d.nv;
+    f.n_u = d.n_u;
+    f.n_p = d.n_p;
+    f.n_cells = d.n_cells;
+    f.faces = d.faces;
+    f.cartesian = d.cartesian;
+    f.mu = (float)mu;
+    f.gamma_rho = (float)gamma_rho;
+    if (mesh->vertices) {
+      const long long nvert = (long long)(n[0] + 1) * (n[1] + 1) * (dim == 3 ? n[2] + 1 : 1);
+      std::vector<double> hv((size_t)nvert * dim);
+      std::vector<float> hf((size_t)nvert * dim);
+      for (int vz = 0; vz < (dim == 3 ? n[2] + 1 : 1); ++vz)
+        for (int vy = 0; vy <= n[1]; ++vy)
+          for (int vx = 0; vx <= n[0]; ++vx) {
+            const long long fi = ((long long)(vz * s) * (nf[1] + 1) + vy * s) * (nf[0] + 1) + vx * s;
+            const long long ci = ((long long)vz * (n[1] + 1) + vy) * (n[0] + 1) + vx;
+            for (int a = 0; a < dim; ++a) {
+              hv[ci * dim + a] = mesh->vertices[fi * dim + a];
+              hf[ci * dim + a] = (float)hv[ci * dim + a];
+            }
+          }
+      double *dv;
+      float *fv;
+      if ((st = dalloc(C, &dv, nvert * dim))) return st;
+      if ((st = dalloc(C, &fv, nvert * dim))) return st;
+      SMF_CUDA_OK(cudaMemcpyAsync(dv, hv.data(), hv.size() * sizeof(double), cudaMemcpyHostToDevice, C->s));
+      SMF_CUDA_OK(cudaMemcpyAsync(fv, hf.data(), hf.size() * sizeof(float), cudaMemcpyHostToDevice, C->s));
+      SMF_CUDA_OK(cudaStreamSynchronize(C->s));
+      d.vert = dv;
+      f.vert = fv;
+    }
+    if (mu_cell) {
+      std::vector<double> &m = mu_levels[l];
+      std::vector<float> mf(m.begin(), m.end());
+      double *dm;
+      float *fm;
+      if ((st = dalloc(C, &dm, (long long)m.size()))) return st;
+      if ((st = dalloc(C, &fm, (long long)m.size()))) return st;
+      SMF_CUDA_OK(cudaMemcpyAsync(dm, m.data(), m.size() * sizeof(double), cudaMemcpyHostToDevice, C->s));
+      SMF_CUDA_OK(cudaMemcpyAsync(fm, mf.data(), mf.size() * sizeof(float), cudaMemcpyHostToDevice, C->s));
+      SMF_CUDA_OK(cudaStreamSynchronize(C->s));
+      d.mu_cell = dm;
+      f.mu_cell = fm;
+    }
+    C->L64[l].d = d;
+    C->L32[l].d = f;
+    if ((st = alloc_level_buffers(C, C->L64[l]))) return st;
+    if ((st = alloc_level_buffers(C, C->L32[l]))) return st;
+  }
+
+  // Krylov / Lanczos work space
+  const LevelDesc<double> &top = C->L64[nl - 1].d;
+  const long long N = top.n_u + top.n_p;
+  if ((st = dalloc(C, &C->V, (long long)(C->restart + 1) * N))) return st;
+  if ((st = dalloc(C, &C->Z, (long long)C->restart * N))) return st;
+  if ((st = dalloc(C, &C->w, N))) return st;
+  if ((st = dalloc(C, &C->hdev, 3 * (C->restart + 2)))) return st;
+  if ((st = dalloc(C, &C->partial, (long long)kRedBlocks * (C->restart + 2)))) return st;
+  if ((st = dalloc(C, &C->scal, 4))) return st;
+  double **lz[] = {&C->lz0, &C->lz1, &C->lz2, &C->lz3, &C->sq};
+  for (auto p : lz)
+    if ((st = dalloc(C, p, N))) return st;
+
+  // smoother setup per level (Algorithm 2), FP64
+  C->sigma = lemma1_scaling(C->o.kA);
+  C->tau = lemma1_scaling(C->o.kS);
+  for (int l = 1; l < nl; ++l) {
+    LevelRT<double> &R = C->L64[l];
+    const LevelDesc<double> &d = R.d;
+    double *dAs, *dSloc, *dMp;
+    if ((st = dalloc(C, &dAs, d.nv))) return st;
+    if ((st = dalloc(C, &dSloc, d.n_p))) return st;
+    if ((st = dalloc(C, &dMp, d.n_p))) return st;
+    if ((st = dalloc(C, &C->DA[l], d.n_u))) return st;
+    launch_cell_diag<double>(d, C->tab64, dAs, dSloc, dMp, C->s);
+    ++C->launches;
+    k_expand_diag<double><<<vec_blocks(d.n_u), kVecThreads, 0, C->s>>>(d, dAs, C->DA[l]);
+    k_reciprocal<double><<<vec_blocks(d.n_u), kVecThreads, 0, C->s>>>(C->DA[l], R.DAinv, d.n_u);
+    C->DS[l] = C->o.schur_diag == 0 ? dSloc : dMp;
+    k_reciprocal<double><<<vec_blocks(d.n_p), kVecThreads, 0, C->s>>>(C->DS[l], R.DSinv, d.n_p);
+    C->launches += 3;
+    double est;
+    if ((st = lanczos(C, l, true, &est))) return st;
+    C->betaA[l] = C->o.eig_safety * est;
+    if ((st = lanczos(C, l, false, &est))) return st;
+    C->betaS[l] = C->o.eig_safety * est;
+    LevelRT<float> &F = C->L32[l];
+    k_convert<double, float><<<vec_blocks(d.n_u), kVecThreads, 0, C->s>>>(R.DAinv, F.DAinv, d.n_u);
+    k_convert<double, float><<<vec_blocks(d.n_p), kVecThreads, 0, C->s>>>(R.DSinv, F.DSinv, d.n_p);
+    C->launches += 2;
+  }
+  if ((st = setup_coarse(C))) return st;
+  SMF_CUDA_OK(cudaStreamSynchronize(C->s));
+  SMF_CUDA_OK(cudaGetLastError());
+  return STOKES_OK;
+}
+
+static bool check_level(stokes_ctx *C, int level) {
+  if (!C || level < 0 || level >= C->nl) {
+    set_error("level out of range");
+    if (C) C->err = g_last_error;
+    return false;
+  }
+  return true;
+}
+
+// FP64 flexible GMRES (restarted), right-preconditioned by one multigrid cycle per iteration.
+static int fgmres(stokes_ctx *C, const double *b, double *x, double rtol, int maxit, int *iters, double *final_rel) {
+  Runner<double> R64(C);
+  Runner<float> R32(C);
+  const int top = C->nl - 1;
+  const long long n_u = C->L64[top].d.n_u, n_p = C->L64[top].d.n_p, N = n_u + n_p;
+  const int nb = vec_blocks(N);
+  const int m = C->restart;
+  int st;
+  double bn2;
+  if ((st = dot64(C, b, b, N, &bn2))) return st;
+  const double bnorm = std::sqrt(bn2);
+  if (iters) *iters = 0;
+  if (bnorm == 0.0) {
+    SMF_CUDA_OK(cudaMemsetAsync(x, 0, N * sizeof(double), C->s));
+    if (final_rel) *final_rel = 0.0;
+    return STOKES_OK;
+  }
+  int it = 0;
+  double rel = 1.0, beta0 = -1.0;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hcol(2 * (m + 2));
+  int status = STOKES_OK;
+  while (true) {
+    R64.vmult(top, x, C->w, true);
+    R64.sub(b, C->w, C->V, N);
+    double beta2;
+    if ((st = dot64(C, C->V, C->V, N, &beta2))) return st;
+    const double beta = std::sqrt(beta2);
+    if (beta0 < 0) beta0 = beta;
+    rel = beta / bnorm;
+    if (!std::isfinite(beta) || beta > 1e6 * beta0) {
+      set_error("FGMRES breakdown: residual is not finite or grew by 1e6");
+      status = STOKES_EBREAKDOWN;
+      break;
+    }
+    if (rel <= rtol) break;
+    if (it >= maxit) {
+      set_error("FGMRES reached maxit before rtol");
+      status = STOKES_ENOTCONV;
+      break;
+    }
+    k_scale<double><<<nb, kVecThreads, 0, C->s>>>(C->V, 1.0 / beta, C->V, N);
+    ++C->launches;
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jd = 0;
+    for (int j = 0; j < m; ++j) {
+      double *vj = C->V + (long long)j * N, *zj = C->Z + (long long)j * N;
+      // z_j = MG(0, v_j) in FP32 or FP64
+      if (C->o.vcycle_fp32) {
+        LevelRT<float> &T32 = C->L32[top];
+        k_convert<double, float><<<nb, kVecThreads, 0, C->s>>>(vj, T32.b, N);
+        ++C->launches;
+        SMF_CUDA_OK(cudaMemsetAsync(T32.x, 0, N * sizeof(float), C->s));
+        if ((st = R32.top_cycle())) return st;
+        k_convert<float, double><<<nb, kVecThreads, 0, C->s>>>(T32.x, zj, N);
+        ++C->launches;
+      } else {
+        LevelRT<double> &T64 = C->L64[top];
+        SMF_CUDA_OK(cudaMemcpyAsync(T64.b, vj, N * sizeof(double), cudaMemcpyDeviceToDevice, C->s));
+        SMF_CUDA_OK(cudaMemsetAsync(T64.x, 0, N * sizeof(double), C->s));
+        if ((st = R64.top_cycle())) return st;
+        SMF_CUDA_OK(cudaMemcpyAsync(zj, T64.x, N * sizeof(double), cudaMemcpyDeviceToDevice, C->s));
+      }
+      R64.vmult(top, zj, C->w, true);
+      // classical Gram-Schmidt with one re-orthogonalisation (CGS2)
+      for (int pass = 0; pass < 2; ++pass) {
+        k_mdot_partial<<<kRedBlocks, kVecThreads, 0, C->s>>>(C->V, N, j + 1, C->w, N, C->partial);
+        k_final_reduce<<<j + 1, kVecThreads, 0, C->s>>>(C->partial, kRedBlocks, j + 1, C->hdev + pass * (m + 2));
+        k_maxpy<<<nb, kVecThreads, 0, C->s>>>(C->V, N, j + 1, C->hdev + pass * (m + 2), C->w, N, -1.0);
+        C->launches += 3;
+      }
+      k_mdot_partial<<<kRedBlocks, kVecThreads, 0, C->s>>>(C->w, N, 1, C->w, N, C->partial);
+      k_final_reduce<<<1, kVecThreads, 0, C->s>>>(C->partial, kRedBlocks, 1, C->hdev + 2 * (m + 2));
+      k_scale_by_inv_sqrt<<<nb, kVecThreads, 0, C->s>>>(C->w, C->hdev + 2 * (m + 2), C->V + (long long)(j + 1) * N, N);
+      C->launches += 3;
+      SMF_CUDA_OK(cudaMemcpyAsync(hcol.data(), C->hdev, (2 * (m + 2) + 1) * sizeof(double), cudaMemcpyDeviceToHost,
+                                  C->s));
+      SMF_CUDA_OK(cudaStreamSynchronize(C->s));
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hcol[i] + hcol[(m + 2) + i];
+      const double hn = std::sqrt(hcol[2 * (m + 2)]);
+      H[(size_t)(j + 1) * m + j] = hn;
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * H[(size_t)i * m + j] + sn[i] * H[(size_t)(i + 1) * m + j];
+        H[(size_t)(i + 1) * m + j] = -sn[i] * H[(size_t)i * m + j] + cs[i] * H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = t;
+      }
+      const double den = std::hypot(H[(size_t)j * m + j], H[(size_t)(j + 1) * m + j]);
+      cs[j] = H[(size_t)j * m + j] / den;
+      sn[j] = H[(size_t)(j + 1) * m + j] / den;
+      H[(size_t)j * m + j] = den;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++it;
+      jd = j + 1;
+      if (!std::isfinite(g[j + 1])) break;
+      if (std::fabs(g[j + 1]) <= rtol * bnorm || it >= maxit) break;
+    }
+    // y = H^{-1} g (upper triangular), x += Z y
+    std::vector<double> y(jd);
+    for (int i = jd - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int c = i + 1; c < jd; ++c) s -= H[(size_t)i * m + c] * y[c];
+      y[i] = s / H[(size_t)i * m + i];
+    }
+    SMF_CUDA_OK(cudaMemcpyAsync(C->hdev, y.data(), jd * sizeof(double), cudaMemcpyHostToDevice, C->s));
+    k_maxpy<<<nb, kVecThreads, 0, C->s>>>(C->Z, N, jd, C->hdev, x, N, 1.0);
+    ++C->launches;
+    SMF_CUDA_OK(cudaStreamSynchronize(C->s));
+  }
+  // zero-mean pressure under full Dirichlet data (the constant pressure spans the kernel)
+  if (C->pker && status != STOKES_EBREAKDOWN) {
+    sum64(C, x + n_u, n_p, C->scal + 1);
+    k_add_scalar<double><<<vec_blocks(n_p), kVecThreads, 0, C->s>>>(x + n_u, C->scal + 1, -1.0 / (double)n_p, n_p);
+    ++C->launches;
+  }
+  SMF_CUDA_OK(cudaStreamSynchronize(C->s));
+  if (iters) *iters = it;
+  if (final_rel) *final_rel = rel;
+  return status;
+}
+
+}  // namespace smf
+
+// ================================ C ABI ========================================================
+extern "C" {
+
+void stokes_default_opts(stokes_opts *o) {
+  if (!o) return;
+  o->kA = 3;
+  o->kS = 3;
+  o->m = 2;
+  o->cycle = 0;
+  o->schur_diag = 0;
+  o->vcycle_fp32 = 1;
+  o->gmres_restart = 30;
+  o->eig_iters = 40;
+  o->eig_safety = 1.1;
+  o->seed = 0x5EEDull;
+}
+
+int stokes_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho, const double *mu_cell,
+                 const stokes_opts *opts, void *stream, stokes_ctx **out) {
+  if (!out) {
+    set_error("out is NULL");
+    return STOKES_EINVAL;
+  }
+  *out = nullptr;
+  if (!mesh || (mesh->dim != 2 && mesh->dim != 3) || k < 2 || k > kMaxDeg || mesh->n_levels < 1 ||
+      mesh->n_levels > STOKES_MAX_LEVELS || !(mu > 0) || !(gamma_rho >= 0)) {
+    set_error("invalid mesh / k / mu / gamma_rho (dim in {2,3}, k in {2,3,4}, 1 <= n_levels <= 12, mu > 0, gamma >= 0)");
+    return STOKES_EINVAL;
+  }
+  for (int a = 0; a < mesh->dim; ++a) {
+    const int s = 1 << (mesh->n_levels - 1);
+    if (mesh->n[a] < 1 || mesh->n[a] % s != 0 || !(mesh->hi[a] > mesh->lo[a])) {
+      set_error("n[a] must be a positive multiple of 2^(n_levels-1) and hi > lo");
+      return STOKES_EINVAL;
+    }
+  }
+  if (mu_cell) {
+    const long long nc = (long long)mesh->n[0] * mesh->n[1] * (mesh->dim == 3 ? mesh->n[2] : 1);
+    for (long long i = 0; i < nc; ++i)
+      if (!(mu_cell[i] > 0)) {
+        set_error("mu_cell entries must be positive");
+        return STOKES_EINVAL;
+      }
+  }
+  stokes_ctx *C = new (std::nothrow) stokes_ctx();
+  if (!C) {
+    set_error("host allocation failed");
+    return STOKES_ENOMEM;
+  }
+  cudaStream_t user = (cudaStream_t)stream;
+  cudaStreamSynchronize(user);
+  int st = do_setup(mesh, k, mu, gamma_rho, mu_cell, opts, C);
+  if (st == STOKES_OK) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) st = cuda_fail(e, "setup kernels", __FILE__, __LINE__);
+  }
+  if (st != STOKES_OK) {
+    stokes_destroy(C);
+    return st;
+  }
+  *out = C;
+  return STOKES_OK;
+}
+
+int stokes_sizes(const stokes_ctx *C, int level, long long *n_u, long long *n_p) {
+  if (!C || level < 0 || level >= C->nl) {
+    set_error("level out of range");
+    return STOKES_EINVAL;
+  }
+  if (n_u) *n_u = C->L64[level].d.n_u;
+  if (n_p) *n_p = C->L64[level].d.n_p;
+  return STOKES_OK;
+}
+
+int stokes_vmult(stokes_ctx *C, int level, int precision, const void *x, void *y, void *stream) {
+  if (!check_level(C, level) || !x || !y || (precision != 32 && precision != 64)) {
+    set_error("invalid stokes_vmult arguments");
+    if (C) C->err = "invalid stokes_vmult arguments";
+    return STOKES_EINVAL;
+  }
+  StreamGuard sg(C, stream);
+  if (precision == 64)
+    Runner<double>(C).vmult(level, (const double *)x, (double *)y, true);
+  else
+    Runner<float>(C).vmult(level, (const float *)x, (float *)y, true);
+  return finish(C, STOKES_OK);
+}
+
+int stokes_apply_blocks(stokes_ctx *C, int level, int precision, int blocks, const void *u, const void *p, void *yu,
+                        void *yp, void *stream) {
+  if (!check_level(C, level) || (precision != 32 && precision != 64) || blocks <= 0 || blocks > 7 ||
+      ((blocks & 1) && (!u || !yu)) || ((blocks & 2) && (!p || !yu)) || ((blocks & 4) && (!u || !yp))) {
+    set_error("invalid stokes_apply_blocks arguments");
+    if (C) C->err = "invalid stokes_apply_blocks arguments";
+    return STOKES_EINVAL;
+  }
+  StreamGuard sg(C, stream);
+  const bool wu = blocks & 3, wp = blocks & 4;
+  if (precision == 64)
+    Runner<double>(C).apply(level, blocks, (const double *)u, (const double *)p, wu ? (double *)yu : nullptr,
+                            wp ? (double *)yp : nullptr);
+  else
+    Runner<float>(C).apply(level, blocks, (const float *)u, (const float *)p, wu ? (float *)yu : nullptr,
+                           wp ? (float *)yp : nullptr);
+  return finish(C, STOKES_OK);
+}
+
+int stokes_mass_rhs(stokes_ctx *C, int level, int precision, const void *f, void *b, void *stream) {
+  if (!check_level(C, level) || !f || !b || (precision != 32 && precision != 64)) {
+    set_error("invalid stokes_mass_rhs arguments");
+    if (C) C->err = "invalid stokes_mass_rhs arguments";
+    return STOKES_EINVAL;
+  }
+  StreamGuard sg(C, stream);
+  if (precision == 64) {
+    Runner<double> R(C);
+    R.apply(level, kApplyMass, (const double *)f, nullptr, (double *)b, nullptr);
+    cudaMemsetAsync((double *)b + R.nu(level), 0, R.np(level) * sizeof(double), C->s);
+  } else {
+    Runner<float> R(C);
+    R.apply(level, kApplyMass, (const float *)f, nullptr, (float *)b, nullptr);
+    cudaMemsetAsync((float *)b + R.nu(level), 0, R.np(level) * sizeof(float), C->s);
+  }
+  return finish(C, STOKES_OK);
+}
+
+int stokes_smooth(stokes_ctx *C, int level, int precision, int steps, const void *b, void *x, void *stream) {
+  if (!check_level(C, level) || level < 1 || steps < 0 || !b || !x || (precision != 32 && precision != 64)) {
+    set_error("invalid stokes_smooth arguments (level must be >= 1)");
+    if (C) C->err = g_last_error;
+    return STOKES_EINVAL;
+  }
+  StreamGuard sg(C, stream);
+  for (int i = 0; i < steps; ++i) {
+    if (precision == 64)
+      Runner<double>(C).smooth_step(level, (double *)x, (const double *)b);
+    else
+      Runner<float>(C).smooth_step(level, (float *)x, (const float *)b);
+  }
+  return finish(C, STOKES_OK);
+}
+
+int stokes_transfer(stokes_ctx *C, int fine_level, int precision, int direction, const void *in, void *out,
+                    void *stream) {
+  if (!check_level(C, fine_level) || fine_level < 1 || !in || !out || (direction != 0 && direction != 1) ||
+      (precision != 32 && precision != 64)) {
+    set_error("invalid stokes_transfer arguments");
+    if (C) C->err = g_last_error;
+    return STOKES_EINVAL;
+  }
+  StreamGuard sg(C, stream);
+  if (precision == 64) {
+    Runner<double> R(C);
+    if (direction == 0)
+      R.restrict_to(fine_level, (const double *)in, (double *)out);
+    else
+      R.prolongate(fine_level, (const double *)in, (double *)out, 0);
+  } else {
+    Runner<float> R(C);
+    if (direction == 0)
+      R.restrict_to(fine_level, (const float *)in, (float *)out);
+    else
+      R.prolongate(fine_level, (const float *)in, (float *)out, 0);
+  }
+  return finish(C, STOKES_OK);
+}
+
+int stokes_coarse_solve(stokes_ctx *C, int precision, const void *b, void *x, void *stream) {
+  if (!C || !b || !x || (precision != 32 && precision != 64)) {
+    set_error("invalid stokes_coarse_solve arguments");
+    if (C) C->err = g_last_error;
+    return STOKES_EINVAL;
+  }
+  StreamGuard sg(C, stream);
+  if (precision == 64)
+    Runner<double>(C).coarse((const double *)b, (double *)x);
+  else
+    Runner<float>(C).coarse((const float *)b, (float *)x);
+  return finish(C, STOKES_OK);
+}
+
+int mg_vcycle(stokes_ctx *C, int precision, const void *b, void *x, void *stream) {
+  if (!C || !b || !x || (precision != 32 && precision != 64)) {
+    set_error("invalid mg_vcycle arguments");
+    if (C) C->err = g_last_error;
+    return STOKES_EINVAL;
+  }
+  StreamGuard sg(C, stream);
+  const int top = C->nl - 1;
+  int st;
+  if (precision == 64) {
+    Runner<double> R(C);
+    const long long N = R.nu(top) + R.np(top);
+    cudaMemcpyAsync(C->L64[top].b, b, N * sizeof(double), cudaMemcpyDeviceToDevice, C->s);
+    cudaMemcpyAsync(C->L64[top].x, x, N * sizeof(double), cudaMemcpyDeviceToDevice, C->s);
+    st = R.top_cycle();
+    cudaMemcpyAsync(x, C->L64[top].x, N * sizeof(double), cudaMemcpyDeviceToDevice, C->s);
+  } else {
+    Runner<float> R(C);
+    const long long N = R.nu(top) + R.np(top);
+    cudaMemcpyAsync(C->L32[top].b, b, N * sizeof(float), cudaMemcpyDeviceToDevice, C->s);
+    cudaMemcpyAsync(C->L32[top].x, x, N * sizeof(float), cudaMemcpyDeviceToDevice, C->s);
+    st = R.top_cycle();
+    cudaMemcpyAsync(x, C->L32[top].x, N * sizeof(float), cudaMemcpyDeviceToDevice, C->s);
+  }
+  return finish(C, st);
+}
+
+int stokes_solve(stokes_ctx *C, const double *b, double *x, double rtol, int maxit, int *iters, double *final_rel_res,
+                 void *stream) {
+  if (!C || !b || !x || !(rtol > 0) || maxit < 0) {
+    set_error("invalid stokes_solve arguments");
+    if (C) C->err = g_last_error;
+    return STOKES_EINVAL;
+  }
+  StreamGuard sg(C, stream);
+  int st = fgmres(C, b, x, rtol, maxit, iters, final_rel_res);
+  return finish(C, st);
+}
+
+int stokes_solve_host(stokes_ctx *C, const double *b_host, double *x_host, double rtol, int maxit, int *iters,
+                      double *final_rel_res, void *stream) {
+  if (!C || !b_host || !x_host) {
+    set_error("invalid stokes_solve_host arguments");
+    if (C) C->err = g_last_error;
+    return STOKES_EINVAL;
+  }
+  const int top = C->nl - 1;
+  const long long N = C->L64[top].d.n_u + C->L64[top].d.n_p;
+  StreamGuard sg(C, stream);
+  double *db = C->lz0, *dx = C->lz1;
+  cudaMemcpyAsync(db, b_host, N * sizeof(double), cudaMemcpyHostToDevice, C->s);
+  cudaMemsetAsync(dx, 0, N * sizeof(double), C->s);
+  int st = fgmres(C, db, dx, rtol, maxit, iters, final_rel_res);
+  cudaMemcpyAsync(x_host, dx, N * sizeof(double), cudaMemcpyDeviceToHost, C->s);
+  cudaStreamSynchronize(C->s);
+  return finish(C, st);
+}
+
+int stokes_get_level_params(const stokes_ctx *C, int level, double *beta_A, double *beta_S, double *sigma,
+                            double *tau) {
+  if (!C || level < 1 || level >= C->nl) {
+    set_error("level out of range (parameters exist on levels >= 1)");
+    return STOKES_EINVAL;
+  }
+  if (beta_A) *beta_A = C->betaA[level];
+  if (beta_S) *beta_S = C->betaS[level];
+  if (sigma) *sigma = C->sigma;
+  if (tau) *tau = C->tau;
+  return STOKES_OK;
+}
+
+int stokes_get_diagonals(stokes_ctx *C, int level, double *DA, double *DS, void *stream) {
+  if (!C || level < 1 || level >= C->nl) {
+    set_error("level out of range (diagonals exist on levels >= 1)");
+    if (C) C->err = g_last_error;
+    return STOKES_EINVAL;
+  }
+  StreamGuard sg(C, stream);
+  if (DA) cudaMemcpyAsync(DA, C->DA[level], C->L64[level].d.n_u * sizeof(double), cudaMemcpyDeviceToDevice, C->s);
+  if (DS) cudaMemcpyAsync(DS, C->DS[level], C->L64[level].d.n_p * sizeof(double), cudaMemcpyDeviceToDevice, C->s);
+  return finish(C, STOKES_OK);
+}
+
+long long stokes_launch_count(const stokes_ctx *C) { return C ? C->launches : 0; }
+
+const char *stokes_last_error(const stokes_ctx *C) { return C ? C->err.c_str() : g_last_error.c_str(); }
+const char *stokes_global_last_error(void) { return g_last_error.c_str(); }
+
+void stokes_destroy(stokes_ctx *C) {
+  if (!C) return;
+  if (C->s) cudaStreamSynchronize(C->s);
+  if (C->g32.exec) cudaGraphExecDestroy(C->g32.exec);
+  if (C->g64.exec) cudaGraphExecDestroy(C->g64.exec);
+  for (void *p : C->allocs) cudaFree(p);
+  if (C->ev_in) cudaEventDestroy(C->ev_in);
+  if (C->ev_out) cudaEventDestroy(C->ev_out);
+  if (C->s) cudaStreamDestroy(C->s);
+  delete C;
+}
+
+}  // extern "C"

@@ -1,0 +1,3 @@
+// Cell-kernel instantiations for velocity degree k = 2 (split per degree for parallel builds).
+#include "apply_launch.cuh"
+SMF_INSTANTIATE_K(2)

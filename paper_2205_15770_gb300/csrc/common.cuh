@@ -1,0 +1,84 @@
+// Shared definitions of the CUDA library: level descriptors, 1D tables, helpers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+
+namespace smf {
+
+constexpr int kMaxDeg = 4;            // highest velocity degree k supported
+constexpr int kMaxN1 = kMaxDeg + 1;   // nodes / Gauss points per direction
+
+// Operator block selection for the cell kernel (bit set).
+enum ApplyMode : int {
+  kApplyA = 1,     // yu += A u  (mu grad:grad + gamma*rho mass)
+  kApplyBT = 2,    // yu += B^T p
+  kApplyB = 4,     // yp += B u
+  kApplyMass = 8,  // yu += M_v u (plain velocity mass, no mu / gamma; right-hand sides)
+};
+
+// 1D tables of one velocity degree k on the reference interval, (k+1) Gauss points.
+// Row index = Gauss point q, column = node / function m.
+template <typename T>
+struct Tab1D {
+  T S[kMaxN1 * kMaxN1];    // S[q*(k+1)+m]  = l_m(x_q)       velocity Lagrange basis at Gauss points
+  T Sd[kMaxN1 * kMaxN1];   // Sd[q*(k+1)+m] = l_m'(x_q)      its derivative
+  T D[kMaxN1 * kMaxN1];    // D[q*nq+m]     = g_m'(x_q)      collocation derivative (Lagrange through Gauss points)
+  T Pv[kMaxN1 * kMaxDeg];  // Pv[q*k+m]     = pressure basis (degree k-1) at Gauss points
+  T w[kMaxN1];             // Gauss weights on [0,1]
+  T x[kMaxN1];             // Gauss points on [0,1]
+};
+
+// Transfer tables: for child h in {0,1}, fine local node a, coarse local node m:
+// weight of coarse basis m at the fine node (reference coordinate (h + t_a)/2).
+template <typename T>
+struct TransferTab {
+  T vel[2 * kMaxN1 * kMaxN1];   // [(h*(k+1)+a)*(k+1)+m]
+  T pre[2 * kMaxDeg * kMaxDeg]; // [(h*k+a)*k+m]   (degree k-1, k nodes)
+};
+
+// Device-side description of one level of the structured hierarchy.
+template <typename T>
+struct LevelDesc {
+  int dim, k;
+  int n[3];          // cells per direction (n[2] = 1 in 2D)
+  int N[3];          // velocity nodes per direction (k n + 1; 1 in unused dim)
+  int Pn[3];         // pressure nodes per direction
+  long long nv;      // nodes per velocity component
+  long long n_u, n_p;
+  long long n_cells;
+  unsigned faces;    // Dirichlet face bits
+  int cartesian;     // 1: axis-aligned uniform cells of size h (no vertex array)
+  T h[3];            // Cartesian cell sizes
+  const T *vert;     // (n+1)^d x d vertex coordinates (null if cartesian)
+  const T *mu_cell;  // per-cell viscosity (null: constant mu)
+  T mu, gamma_rho;
+};
+
+__host__ __device__ inline bool vel_constrained(const int N[3], unsigned faces, int dim, int gx, int gy,
+                                                int gz) {
+  if ((faces & 1u) && gx == 0) return true;
+  if ((faces & 2u) && gx == N[0] - 1) return true;
+  if ((faces & 4u) && gy == 0) return true;
+  if ((faces & 8u) && gy == N[1] - 1) return true;
+  if (dim == 3) {
+    if ((faces & 16u) && gz == 0) return true;
+    if ((faces & 32u) && gz == N[2] - 1) return true;
+  }
+  return false;
+}
+
+constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+#define SMF_CUDA_OK(expr)                                        \
+  do {                                                           \
+    cudaError_t _e = (expr);                                     \
+    if (_e != cudaSuccess) return ::smf::cuda_fail(_e, #expr, __FILE__, __LINE__); \
+  } while (0)
+
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+void set_error(const std::string &msg);
+
+}  // namespace smf

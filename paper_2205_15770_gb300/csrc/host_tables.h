@@ -1,0 +1,25 @@
+#pragma once
+#include <vector>
+
+#include "common.cuh"
+
+namespace smf {
+void gauss_legendre01(int n, double *x, double *w);
+void gauss_lobatto01(int deg, double *x);
+double lagrange(const double *nodes, int n, int i, double x);
+double lagrange_deriv(const double *nodes, int n, int i, double x);
+void build_tables(int k, Tab1D<double> &t);
+void build_transfer(int k, TransferTab<double> &tt);
+double tridiag_max_eig(const std::vector<double> &a, const std::vector<double> &b);
+
+template <typename T>
+int launch_cell_apply(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, const T *u, const T *p, T *yu, T *yp,
+                      cudaStream_t s);
+template <typename T>
+int launch_cell_diag(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dSloc, T *dMp, cudaStream_t s);
+template <int K, typename T>
+int launch_cell_apply_k(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, const T *u, const T *p, T *yu, T *yp,
+                        cudaStream_t s);
+template <int K, typename T>
+int launch_cell_diag_k(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dSloc, T *dMp, cudaStream_t s);
+}  // namespace smf

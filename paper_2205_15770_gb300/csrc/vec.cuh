@@ -1,0 +1,185 @@
+// Vector kernels: Chebyshev-Jacobi recurrence (Sec. 3.3.1), residuals, precision
+// conversion, FP64 reductions for the Krylov loop and Lanczos, SplitMix64 start vectors.
+#pragma once
+#include "common.cuh"
+
+namespace smf {
+
+constexpr int kVecThreads = 256;
+constexpr int kRedBlocks = 304;  // 2 x 152 SMs; fixed so that reductions are deterministic
+
+inline int vec_blocks(long long n) {
+  long long b = (n + kVecThreads - 1) / kVecThreads;
+  if (b > 152 * 32) b = 152 * 32;
+  return (int)(b < 1 ? 1 : b);
+}
+
+#define SMF_GRID_LOOP(i, n) \
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
+
+// out = a - b
+template <typename T>
+__global__ void k_sub(const T *__restrict__ a, const T *__restrict__ b, T *__restrict__ out, long long n) {
+  SMF_GRID_LOOP(i, n) out[i] = a[i] - b[i];
+}
+
+// out = a + s * b
+template <typename T>
+__global__ void k_axpy_out(const T *__restrict__ a, T s, const T *__restrict__ b, T *__restrict__ out, long long n) {
+  SMF_GRID_LOOP(i, n) out[i] = a[i] + s * b[i];
+}
+
+// x += s * b
+template <typename T>
+__global__ void k_axpy(T *__restrict__ x, T s, const T *__restrict__ b, long long n) {
+  SMF_GRID_LOOP(i, n) x[i] += s * b[i];
+}
+
+template <typename T>
+__global__ void k_scale(const T *__restrict__ a, T s, T *__restrict__ out, long long n) {
+  SMF_GRID_LOOP(i, n) out[i] = s * a[i];
+}
+
+template <typename T>
+__global__ void k_mul(const T *__restrict__ a, const T *__restrict__ b, T *__restrict__ out, long long n) {
+  SMF_GRID_LOOP(i, n) out[i] = a[i] * b[i];
+}
+
+template <typename T>
+__global__ void k_add_scalar(T *__restrict__ x, const double *__restrict__ sum, double scale, long long n) {
+  const T s = (T)(sum[0] * scale);
+  SMF_GRID_LOOP(i, n) x[i] += s;
+}
+
+template <typename Tin, typename Tout>
+__global__ void k_convert(const Tin *__restrict__ a, Tout *__restrict__ out, long long n) {
+  SMF_GRID_LOOP(i, n) out[i] = (Tout)a[i];
+}
+
+// Chebyshev start from x = 0 (Sec. 3.3.1): r = sr * (a - b) (b may be null),
+// d = x = c0 * Dinv * r; r is stored if r_out != null.  With final_out != null the
+// degree-0 result is also written as final_out = base + fscale * x.
+template <typename T>
+__global__ void k_cheb_init(const T *__restrict__ a, const T *__restrict__ b, T sr, const T *__restrict__ Dinv,
+                            T c0, T *__restrict__ r_out, T *__restrict__ d, T *__restrict__ x,
+                            const T *__restrict__ base, T fscale, T *__restrict__ final_out, long long n) {
+  SMF_GRID_LOOP(i, n) {
+    T r = b ? sr * (a[i] - b[i]) : sr * a[i];
+    if (r_out) r_out[i] = r;
+    T v = c0 * Dinv[i] * r;
+    d[i] = v;
+    x[i] = v;
+    if (final_out) final_out[i] = (base ? base[i] : T(0)) + fscale * v;
+  }
+}
+
+// One Chebyshev step: d = c1 d + c2 Dinv (r - t); x += d.  With final_out != null,
+// final_out = base + fscale * x_new (base may be null).
+template <typename T>
+__global__ void k_cheb_step(const T *__restrict__ r, const T *__restrict__ t, const T *__restrict__ Dinv, T c1, T c2,
+                            T *__restrict__ d, T *__restrict__ x, const T *__restrict__ base, T fscale,
+                            T *__restrict__ final_out, long long n) {
+  SMF_GRID_LOOP(i, n) {
+    T dn = c1 * d[i] + c2 * Dinv[i] * (r[i] - t[i]);
+    T xn = x[i] + dn;
+    d[i] = dn;
+    x[i] = xn;
+    if (final_out) final_out[i] = (base ? base[i] : T(0)) + fscale * xn;
+  }
+}
+
+// y_i = x_i on constrained velocity DoFs (identity rows of K).
+template <typename T>
+__global__ void k_identity_rows(const LevelDesc<T> L, const T *__restrict__ x, T *__restrict__ y) {
+  SMF_GRID_LOOP(i, L.n_u) {
+    long long node = i % L.nv;
+    int gx = (int)(node % L.N[0]);
+    long long r = node / L.N[0];
+    int gy = (int)(r % L.N[1]);
+    int gz = (int)(r / L.N[1]);
+    if (vel_constrained(L.N, L.faces, L.dim, gx, gy, gz)) y[i] = x[i];
+  }
+}
+
+// zero constrained velocity entries
+template <typename T>
+__global__ void k_zero_constrained(const LevelDesc<T> L, T *__restrict__ y) {
+  SMF_GRID_LOOP(i, L.n_u) {
+    long long node = i % L.nv;
+    int gx = (int)(node % L.N[0]);
+    long long r = node / L.N[0];
+    int gy = (int)(r % L.N[1]);
+    int gz = (int)(r / L.N[1]);
+    if (vel_constrained(L.N, L.faces, L.dim, gx, gy, gz)) y[i] = T(0);
+  }
+}
+
+// D_A over the full velocity vector from the scalar per-node diagonal; 1 on constrained DoFs.
+template <typename T>
+__global__ void k_expand_diag(const LevelDesc<T> L, const T *__restrict__ dAs, T *__restrict__ DA) {
+  SMF_GRID_LOOP(i, L.n_u) {
+    long long node = i % L.nv;
+    int gx = (int)(node % L.N[0]);
+    long long r = node / L.N[0];
+    int gy = (int)(r % L.N[1]);
+    int gz = (int)(r / L.N[1]);
+    DA[i] = vel_constrained(L.N, L.faces, L.dim, gx, gy, gz) ? T(1) : dAs[node];
+  }
+}
+
+template <typename T>
+__global__ void k_reciprocal(const T *__restrict__ a, T *__restrict__ out, long long n) {
+  SMF_GRID_LOOP(i, n) out[i] = T(1) / a[i];
+}
+
+template <typename T>
+__global__ void k_rsqrt(const T *__restrict__ a, T *__restrict__ out, long long n) {
+  SMF_GRID_LOOP(i, n) out[i] = T(1) / sqrt(a[i]);
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014): z = seed + (i+1)*0x9E3779B97F4A7C15, output mix,
+// mapped to 2*(z>>11)*2^-53 - 1 in [-1, 1).  mask_level (optional) zeroes constrained velocity DoFs.
+__device__ __forceinline__ double splitmix64_uniform(unsigned long long seed, long long i) {
+  unsigned long long z = seed + (unsigned long long)(i + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z = z ^ (z >> 31);
+  return 2.0 * ((double)(z >> 11) * 0x1.0p-53) - 1.0;
+}
+
+__global__ void k_splitmix(unsigned long long seed, double *__restrict__ out, long long n);
+
+// ---- deterministic FP64 reductions ---------------------------------------------------
+template <typename T>
+__device__ __forceinline__ double block_reduce_sum(double v, double *sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  v = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+  if (wid == 0)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  return v;
+}
+
+// partial[j * gridDim.x + blockIdx.x] = sum_i V[j*ldv + i] * w[i]   (j < nvec); V null -> sum w[i]^2 not used
+__global__ void k_mdot_partial(const double *__restrict__ V, long long ldv, int nvec, const double *__restrict__ w,
+                               long long n, double *__restrict__ partial);
+__global__ void k_sum_partial(const double *__restrict__ a, long long n, double *__restrict__ partial);
+__global__ void k_final_reduce(const double *__restrict__ partial, int nparts, int nvec, double *__restrict__ out);
+// w -= sum_j h[j] V[j]
+__global__ void k_maxpy(const double *__restrict__ V, long long ldv, int nvec, const double *__restrict__ h,
+                        double *__restrict__ w, long long n, double sign);
+// dense coarse solve (setup): unit vectors, augmented bordered matrix, Gauss-Jordan steps
+__global__ void k_unit(double *__restrict__ e, long long n, long long j);
+__global__ void k_build_augmented(const double *__restrict__ K0, int n0, long long n_u, int bordered,
+                                  double *__restrict__ M);
+__global__ void k_gj_pivot(double *__restrict__ M, int nb, int k, double *__restrict__ fac, int *__restrict__ err);
+__global__ void k_gj_elim(double *__restrict__ M, int nb, int k, const double *__restrict__ fac);
+__global__ void k_extract_inverse(const double *__restrict__ M, int nb, int n0, double *__restrict__ Kinv);
+// out = w / norm where norm = sqrt(*nrm2)
+__global__ void k_scale_by_inv_sqrt(const double *__restrict__ w, const double *__restrict__ nrm2,
+                                    double *__restrict__ out, long long n);
+
+}  // namespace smf

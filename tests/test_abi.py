@@ -1,0 +1,93 @@
+"""The C-ABI library builds, loads and exports every entry point of include/stokes_mf.h (CPU only).
+
+No compute call is made here: argument validation that returns before any CUDA work
+is exercised, nothing else.
+"""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "stokes_mf.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_ ]*?\**\s*\b([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "while", "for", "return", "sizeof")))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2205_15770_gb300 import build, _lib
+    build.build()
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("stokes_setup", "stokes_vmult", "mg_vcycle", "stokes_solve", "stokes_destroy",
+                     "stokes_sizes", "stokes_last_error"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_2205_15770_gb300 import _lib
+    names = _declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in _lib.SIGNATURES, f"binding lacks {n}"
+
+
+def test_invalid_arguments_are_rejected_before_any_device_work(lib):
+    from paper_2205_15770_gb300 import _lib
+    ctx = C.c_void_p()
+    opts = _lib.StokesOpts()
+    lib.stokes_default_opts(C.byref(opts))
+    assert (opts.kA, opts.kS, opts.m, opts.gmres_restart, opts.eig_iters) == (3, 3, 2, 30, 40)
+    mesh = _lib.StokesMesh()
+    mesh.dim = 3
+    for a in range(3):
+        mesh.n[a] = 6
+        mesh.hi[a] = 1.0
+    mesh.n_levels = 3  # 6 is not divisible by 4
+    mesh.dirichlet_faces = 0x3F
+    assert lib.stokes_setup(C.byref(mesh), 2, 1.0, 0.0, None, C.byref(opts), None, C.byref(ctx)) == 1
+    assert b"multiple" in lib.stokes_global_last_error()
+    mesh.n_levels = 2
+    assert lib.stokes_setup(C.byref(mesh), 5, 1.0, 0.0, None, C.byref(opts), None, C.byref(ctx)) == 1
+    assert lib.stokes_setup(C.byref(mesh), 2, -1.0, 0.0, None, C.byref(opts), None, C.byref(ctx)) == 1
+    assert lib.stokes_setup(None, 2, 1.0, 0.0, None, C.byref(opts), None, C.byref(ctx)) == 1
+    mu = np.full(216, 1.0)
+    mu[7] = 0.0
+    assert lib.stokes_setup(C.byref(mesh), 2, 1.0, 0.0, mu.ctypes.data_as(C.POINTER(C.c_double)),
+                            C.byref(opts), None, C.byref(ctx)) == 1
+    assert ctx.value is None
+    assert lib.stokes_vmult(None, 0, 64, None, None, None) == 1
+    assert lib.stokes_solve(None, None, None, 1e-8, 10, None, None, None) == 1
+    lib.stokes_destroy(None)
+
+
+def test_package_fails_loudly_without_library(tmp_path, monkeypatch):
+    from paper_2205_15770_gb300 import _lib
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(OSError):
+        _lib.load(str(tmp_path / "missing.so"))
+
+
+def test_sampled_oracle_rows_match_assembled_operator():
+    import workloads as W
+    from oracle.assemble import assemble
+    from oracle.mesh import Level
+    from oracle.sampled import apply_rows
+    V = W.perturbed_vertices(3, (3, 4, 2), seed=2, amplitude=0.3)
+    lev = Level(3, 2, (3, 4, 2), V, dirichlet_faces=0x3F & ~0x2)
+    ops = assemble(lev, mu=0.7, gamma_rho=5.0)
+    x = W.random_vector(lev.size, 1)
+    rows = np.random.default_rng(0).choice(lev.size, 60, replace=False)
+    np.testing.assert_allclose(apply_rows(lev, x, rows, 0.7, 5.0), (ops["K"] @ x)[rows], rtol=1e-12, atol=1e-12)
