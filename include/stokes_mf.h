@@ -146,6 +146,14 @@ int stokes_get_level_params(const stokes_ctx *ctx, int level, double *beta_A, do
  * D_S (n_p) of a level into device buffers (either may be NULL). */
 int stokes_get_diagonals(stokes_ctx *ctx, int level, double *DA, double *DS, void *stream);
 
+/* Measurement helper: launch the cell kernel of `blocks` (as in stokes_apply_blocks) on
+ * `level` reps times back to back on the library's internal stream, between two CUDA
+ * events recorded on that stream, using internal buffers as input and output (no
+ * allocation, no memset between launches).  *avg_ms (HOST) = elapsed / reps.
+ * Synchronises the stream. */
+int stokes_time_apply(stokes_ctx *ctx, int level, int precision, int blocks, int reps, double *avg_ms,
+                      void *stream);
+
 /* Number of kernel launches this context issued since setup (a counter kept by the
  * library for reporting; not thread-safe). */
 long long stokes_launch_count(const stokes_ctx *ctx);

@@ -243,6 +243,13 @@ class StokesMG:
                                                    self._stream()))
         return DA, DS
 
+    def time_apply(self, blocks, level=None, precision=32, reps=100):
+        """Average duration (ms) of the cell kernel for `blocks`, timed with CUDA events on the launching stream."""
+        ms = C.c_double()
+        self._check(self._lib.stokes_time_apply(self._ctx, self._level(level), precision, blocks, reps, C.byref(ms),
+                                                self._stream()))
+        return ms.value
+
     @property
     def launch_count(self):
         return int(self._lib.stokes_launch_count(self._ctx))

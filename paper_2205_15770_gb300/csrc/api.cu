@@ -1139,6 +1139,38 @@ int stokes_get_diagonals(stokes_ctx *C, int level, double *DA, double *DS, void 
   return finish(C, STOKES_OK);
 }
 
+int stokes_time_apply(stokes_ctx *C, int level, int precision, int blocks, int reps, double *avg_ms, void *stream) {
+  if (!check_level(C, level) || (precision != 32 && precision != 64) || blocks <= 0 || blocks > 15 || reps < 1 ||
+      !avg_ms) {
+    set_error("invalid stokes_time_apply arguments");
+    if (C) C->err = g_last_error;
+    return STOKES_EINVAL;
+  }
+  StreamGuard sg(C, stream);
+  cudaEvent_t e0, e1;
+  SMF_CUDA_OK(cudaEventCreate(&e0));
+  SMF_CUDA_OK(cudaEventCreate(&e1));
+  SMF_CUDA_OK(cudaEventRecord(e0, C->s));
+  for (int r = 0; r < reps; ++r) {
+    if (precision == 64) {
+      LevelRT<double> &R = C->L64[level];
+      launch_cell_apply<double>(R.d, C->tab64, blocks, R.x, R.x + R.d.n_u, R.r, R.r + R.d.n_u, C->s);
+    } else {
+      LevelRT<float> &R = C->L32[level];
+      launch_cell_apply<float>(R.d, C->tab32, blocks, R.x, R.x + R.d.n_u, R.r, R.r + R.d.n_u, C->s);
+    }
+    ++C->launches;
+  }
+  SMF_CUDA_OK(cudaEventRecord(e1, C->s));
+  SMF_CUDA_OK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  SMF_CUDA_OK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *avg_ms = (double)ms / reps;
+  return finish(C, STOKES_OK);
+}
+
 long long stokes_launch_count(const stokes_ctx *C) { return C ? C->launches : 0; }
 
 const char *stokes_last_error(const stokes_ctx *C) { return C ? C->err.c_str() : g_last_error.c_str(); }
