@@ -54,16 +54,17 @@ def flops_per_cell_A(k, trilinear, dim=3):
 
     Per component: forward interpolation d sweeps and collocation gradient d sweeps, backward
     the transposes (4 d (k+1)^d (k+1) multiply-adds), the point operation (d^2 multiply-adds
-    plus 5 flops per point).  Trilinear geometry per point: Jacobian from 2^d vertices
-    (2^d (d^2 MAC + d(d-1) mul)), adjugate, determinant, G = w adj adj^T / det, C = w adj
-    (~298 flops in 3D).  Cartesian cells: geometry is a constant.
+    plus 5 flops per point).  Trilinear geometry (3D, as the column kernel evaluates it): per
+    (x, y) node column 78 flops to set up the edge vectors of the Jacobian, per point 83 flops
+    (two Jacobian columns linear in zeta, adjugate, determinant, w/det, G = w adj adj^T / det,
+    w det).  Cartesian cells: geometry is a constant.
     """
     n1 = k + 1
     npt = n1 ** dim
     per_comp = 2 * (4 * dim * npt * n1 + dim * dim * npt) + 5 * npt
     geo = 0
     if trilinear:
-        geo = npt * ((2 ** dim) * (2 * dim * dim + dim * (dim - 1)) + 27 + 5 + 1 + 63 + 9 + 1)
+        geo = n1 ** (dim - 1) * 78 + npt * 83
     return dim * per_comp + geo
 
 
@@ -199,7 +200,7 @@ def traffic_record(kernel_src_sha):
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("apply.cuh", "common.cuh"):
+    for f in ("apply.cuh", "apply_col.cuh", "common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2205_15770_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 

@@ -98,8 +98,11 @@ int stokes_sizes(const stokes_ctx *ctx, int level, long long *n_u, long long *n_
 int stokes_vmult(stokes_ctx *ctx, int level, int precision, const void *x, void *y, void *stream);
 
 /* Block applications on `level`: blocks is a bit set of 1 = A u, 2 = B^T p (both into
- * yu), 4 = B u (into yp).  Outputs are overwritten; unused pointers may be NULL.
- * Rows of constrained velocity DoFs of yu are zero (no identity term). */
+ * yu), 4 = B u (into yp); or exactly 8 = Z M_v u (velocity mass, constrained rows zero, every
+ * entry of u read) or 16 = M_v Z u (its transpose: constrained entries of u read as 0, every
+ * row written), Z = identity on free velocity DoFs, 0 on constrained ones.  Outputs are
+ * overwritten; unused pointers may be NULL.  For blocks 1-7, rows of constrained velocity DoFs
+ * of yu are zero (no identity term) and constrained entries of u are ignored. */
 int stokes_apply_blocks(stokes_ctx *ctx, int level, int precision, int blocks, const void *u,
                         const void *p, void *yu, void *yp, void *stream);
 
@@ -136,6 +139,19 @@ int stokes_solve(stokes_ctx *ctx, const double *b, double *x, double rtol, int m
 /* stokes_solve with HOST vectors: copies b in, solves from x = 0, copies x out. */
 int stokes_solve_host(stokes_ctx *ctx, const double *b_host, double *x_host, double rtol, int maxit,
                       int *iters, double *final_rel_res, void *stream);
+
+/* Replace the per-cell viscosity of the finest level (HOST, n_cells positive doubles, x
+ * fastest) and rebuild everything that depends on it (coarse viscosities = mean of the 2^d
+ * children, diagonals, lambda_max estimates, coarse inverse).  Synchronises the stream; the
+ * context pointer stays valid.  No counterpart in the paper (the paper's mu is constant). */
+int stokes_set_viscosity(stokes_ctx *ctx, const double *mu_cell, void *stream);
+
+/* Adjoint viscosity gradient on the finest level: dJ_dmu[c] = - sum over velocity components of
+ * int_c grad lam_i . grad u_i dx, i.e. -lam^T (dK/dmu_c) u, for the solution u of K(mu) u = b
+ * and the adjoint lam of K lam = dJ/du (K is symmetric).  u, lam: device double vectors of
+ * n_u + n_p entries (velocity part used; constrained entries read as 0); dJ_dmu: device, n_cells
+ * doubles (x fastest).  No counterpart in the paper (constant mu there). */
+int stokes_cell_grad(stokes_ctx *ctx, const double *u, const double *lam, double *dJ_dmu, void *stream);
 
 /* Smoother parameters of a level >= 1 (Algorithm 2): beta of D_A^-1 A and of
  * D_S^-1 S_tilde (safety factor included), sigma and tau (Lemma 1).  HOST outputs. */

@@ -54,6 +54,7 @@ class StokesMG:
         self._lib = L.load()
         torch = _torch()
         self.dim, self.k, self.n_levels = dim, k, n_levels
+        self._n = tuple(int(v) for v in n[:dim])
         mesh = L.StokesMesh()
         mesh.dim = dim
         nn = list(n) + [1] * (3 - len(n))
@@ -155,7 +156,7 @@ class StokesMG:
         nu, npr = self.sizes(lv)
         ref = u if u is not None else p
         dt = ref.dtype
-        yu = torch.empty(nu, dtype=dt, device=self.device) if blocks & 3 else None
+        yu = torch.empty(nu, dtype=dt, device=self.device) if blocks & (1 | 2 | 8 | 16) else None
         yp = torch.empty(npr, dtype=dt, device=self.device) if blocks & 4 else None
         self._check(self._lib.stokes_apply_blocks(
             self._ctx, lv, self._prec(ref), blocks, _ptr(u, dt) if u is not None else None,
@@ -229,6 +230,28 @@ class StokesMG:
         self._check(st)
         return x, it.value, rel.value
 
+    def mass(self, u, full_rows=True, level=None):
+        """Velocity mass: full_rows -> M_v Z u (every row, constrained u read as 0); else Z M_v u."""
+        yu, _ = self.apply_blocks(16 if full_rows else 8, u=u, level=level)
+        return yu
+
+    def set_viscosity(self, mu_cell):
+        """Replace the per-cell viscosity of the finest level and rebuild the hierarchy's setup."""
+        mc = np.ascontiguousarray(np.asarray(mu_cell, dtype=np.float64).reshape(-1))
+        self._check(self._lib.stokes_set_viscosity(self._ctx, mc.ctypes.data_as(C.POINTER(C.c_double)),
+                                                   self._stream()))
+
+    def cell_grad(self, x, lam):
+        """dJ/dmu_c = -lam^T (dK/dmu_c) x per finest-level cell (adjoint viscosity gradient)."""
+        torch = _torch()
+        n = 1
+        for v in self._n:
+            n *= v
+        g = torch.empty(n, dtype=torch.float64, device=self.device)
+        self._check(self._lib.stokes_cell_grad(self._ctx, _ptr(x, torch.float64), _ptr(lam, torch.float64),
+                                               _ptr(g, torch.float64), self._stream()))
+        return g
+
     def level_params(self, level):
         vals = [C.c_double() for _ in range(4)]
         self._check(self._lib.stokes_get_level_params(self._ctx, level, *[C.byref(v) for v in vals]))
@@ -253,3 +276,52 @@ class StokesMG:
     @property
     def launch_count(self):
         return int(self._lib.stokes_launch_count(self._ctx))
+
+
+class StokesSolveFunction:
+    """torch.autograd.Function for x = K(mu)^{-1} (Z M_v f) with adjoint gradients.
+
+    forward(mu_cell, f): FP64 FGMRES solve on a StokesMG whose finest-level per-cell viscosity is
+    mu_cell (rebuilt through set_viscosity when mu changes).  backward(dJ/dx): one adjoint solve
+    K lam = dJ/dx with the same multigrid (K is symmetric), then
+        dJ/dmu_c = -lam^T (dK/dmu_c) x          (stokes_cell_grad)
+        dJ/df    = (Z M_v)^T lam_u = M_v Z lam_u  (velocity mass, every row)
+    Use through ``stokes_solve_fn(solver, mu_cell, f, rtol)``.
+    """
+
+
+def _make_function():
+    import torch
+
+    class _Fn(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, mu_cell, f, solver, rtol):
+            solver.set_viscosity(mu_cell.detach().cpu().numpy())
+            b = solver.mass_rhs(f.detach())
+            x, _, _ = solver.solve(b, rtol=rtol)
+            ctx.solver, ctx.rtol = solver, rtol
+            ctx.save_for_backward(x)
+            return x
+
+        @staticmethod
+        def backward(ctx, gx):
+            (x,) = ctx.saved_tensors
+            S = ctx.solver
+            lam, _, _ = S.solve(gx.detach().contiguous().clone(), rtol=ctx.rtol)
+            gmu = S.cell_grad(x, lam)
+            nu, _ = S.sizes()
+            gf = S.mass(lam[:nu].contiguous(), full_rows=True)  # (Z M_v)^T lam_u = M_v Z lam_u
+            return gmu, gf, None, None
+
+    return _Fn
+
+
+_FN = None
+
+
+def stokes_solve_fn(solver, mu_cell, f, rtol=1e-12):
+    """Differentiable solve: returns x(mu_cell, f) with gradients w.r.t. mu_cell and f."""
+    global _FN
+    if _FN is None:
+        _FN = _make_function()
+    return _FN.apply(mu_cell, f, solver, rtol)

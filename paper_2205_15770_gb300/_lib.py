@@ -45,6 +45,8 @@ SIGNATURES = {
     "stokes_get_level_params": (C.c_int, [P, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                           C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "stokes_get_diagonals": (C.c_int, [P, C.c_int, P, P, P]),
+    "stokes_cell_grad": (C.c_int, [P, P, P, P, P]),
+    "stokes_set_viscosity": (C.c_int, [P, C.POINTER(C.c_double), P]),
     "stokes_time_apply": (C.c_int, [P, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), P]),
     "stokes_launch_count": (C.c_longlong, [P]),
     "stokes_last_error": (C.c_char_p, [P]),

@@ -17,6 +17,14 @@
 namespace smf {
 
 static thread_local std::string g_last_error;
+bool pdl_on() {
+  static int v = -1;
+  if (v < 0) {
+    const char *e = getenv("STOKES_NO_PDL");
+    v = (e && e[0] == '1') ? 0 : 1;
+  }
+  return v == 1;
+}
 void set_error(const std::string &m) { g_last_error = m; }
 int cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
   set_error(std::string("CUDA error '") + cudaGetErrorString(e) + "' in " + what + " (" + file + ":" +
@@ -46,6 +54,7 @@ int launch_cell_diag<double>(const LevelDesc<double> &L, const Tab1D<double> *ta
 // x = Kinv b on the coarse level: one warp per row, FP64 accumulation.
 template <typename T>
 __global__ void k_coarse_apply(const double *__restrict__ Kinv, int n0, const T *__restrict__ b, T *__restrict__ x) {
+  pdl_enter();
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= n0) return;
   const double *row = Kinv + (long long)warp * n0;
@@ -60,7 +69,7 @@ template <typename T>
 struct LevelRT {
   LevelDesc<T> d{};
   T *DAinv = nullptr, *DSinv = nullptr;
-  T *x = nullptr, *b = nullptr, *r = nullptr;                                   // full vectors
+  T *x = nullptr, *b = nullptr, *r = nullptr, *kx = nullptr;                   // full vectors
   T *tu = nullptr, *ru = nullptr, *uhat = nullptr, *cx = nullptr, *cd = nullptr, *ct = nullptr;  // velocity
   T *r2 = nullptr, *cx2 = nullptr, *cd2 = nullptr, *ct2 = nullptr, *au = nullptr;              // nested in S~
   T *pt = nullptr, *rp = nullptr, *px = nullptr, *pd = nullptr, *ps = nullptr, *dp = nullptr;  // pressure
@@ -101,9 +110,13 @@ struct stokes_ctx {
   bool capturing = false;
   long long cap_count = 0;
   bool use_graphs = true;
-  GraphSlot g32, g64;
+  GraphSlot g32[2], g64[2];  // [x_zero]
   cudaStream_t s = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // setup inputs, kept for stokes_set_viscosity
+  stokes_mesh mesh{};
+  std::vector<double> mesh_vertices;
+  double mu_const = 1.0;
 };
 
 namespace smf {
@@ -141,11 +154,11 @@ const TransferTab<double> *ttables<double>(stokes_ctx *C) { return C->tt64; }
 template <>
 const TransferTab<float> *ttables<float>(stokes_ctx *C) { return C->tt32; }
 template <typename T>
-GraphSlot &graph_slot(stokes_ctx *C);
+GraphSlot &graph_slot(stokes_ctx *C, bool x_zero);
 template <>
-GraphSlot &graph_slot<double>(stokes_ctx *C) { return C->g64; }
+GraphSlot &graph_slot<double>(stokes_ctx *C, bool x_zero) { return C->g64[x_zero ? 1 : 0]; }
 template <>
-GraphSlot &graph_slot<float>(stokes_ctx *C) { return C->g32; }
+GraphSlot &graph_slot<float>(stokes_ctx *C, bool x_zero) { return C->g32[x_zero ? 1 : 0]; }
 
 // Chebyshev three-term recurrence coefficients (Sec. 3.3.1) for [alpha, beta] = [beta/2, beta].
 struct ChebCoef {
@@ -199,33 +212,48 @@ struct Runner {
   void zero(T *p, long long n) { cudaMemsetAsync(p, 0, (size_t)n * sizeof(T), s); }
   long long nu(int l) const { return L[l].d.n_u; }
   long long np(int l) const { return L[l].d.n_p; }
+  template <typename... KA, typename... A>
+  void vec(void (*k)(KA...), long long n, A... args) {
+    launch_kernel(k, dim3(vec_blocks(n)), dim3(kVecThreads), 0, s, args...);
+    note();
+  }
+  // Packed launch: kv processes 16-byte packs (VW elements), k1 single elements; kv is chosen
+  // when every pointer in `ptrs` is 16-byte aligned.
+  static constexpr int VW = 16 / sizeof(T);
+  template <typename K1, typename KV, typename... A>
+  void vecp(K1 k1, KV kv, std::initializer_list<const void *> ptrs, long long n, A... args) {
+    if (all_aligned(16, ptrs))
+      launch_kernel(kv, dim3(vec_blocks((n + VW - 1) / VW)), dim3(kVecThreads), 0, s, args...);
+    else
+      launch_kernel(k1, dim3(vec_blocks(n)), dim3(kVecThreads), 0, s, args...);
+    note();
+  }
 
+  // Public form: outputs are zeroed, then accumulated by the cell kernel.
   void apply(int l, int mode, const T *u, const T *p, T *yu, T *yp) {
     if (yu) zero(yu, nu(l));
     if (yp) zero(yp, np(l));
+    apply_nz(l, mode, u, p, yu, yp);
+  }
+  // Cycle form: the outputs are already zero (work buffers are zeroed by the kernel that
+  // consumes them, so the captured cycle contains kernels only).
+  void apply_nz(int l, int mode, const T *u, const T *p, T *yu, T *yp) {
     launch_cell_apply<T>(L[l].d, tab, mode, u, p, yu, yp, s);
     note();
   }
   void vmult(int l, const T *x, T *y, bool identity) {
     apply(l, kApplyA | kApplyBT | kApplyB, x, x + nu(l), y, y + nu(l));
-    if (identity) {
-      k_identity_rows<T><<<vec_blocks(nu(l)), kVecThreads, 0, s>>>(L[l].d, x, y);
-      note();
-    }
+    if (identity) vec(k_identity_rows<T>, nu(l), L[l].d, x, y);
   }
-  void sub(const T *a, const T *b, T *out, long long n) {
-    k_sub<T><<<vec_blocks(n), kVecThreads, 0, s>>>(a, b, out, n);
-    note();
-  }
-  void axpy(T *x, T a, const T *b, long long n) {
-    k_axpy<T><<<vec_blocks(n), kVecThreads, 0, s>>>(x, a, b, n);
-    note();
-  }
+  void sub(const T *a, const T *b, T *out, long long n) { vec(k_sub<T>, n, a, b, out, n); }
 
-  // out = base + fscale * scale * Cheb(M, D, k) r,  r = sr * (a - b)   (Sec. 3.3.1)
+  // Chebyshev-Jacobi application (Sec. 3.3.1) from a zero start on r = sr (a - b):
+  //   f = base + fscale * scale * Cheb(M, D, k) r, written to out and/or accumulated into acc.
   // velocity: M = A, D = D_A, (k, beta, scale) = (k_A, beta_A, sigma)
   // pressure: M = S~ = B A^-1_hat B^T, D = D_S, (k_S, beta_S, tau)
-  void cheb(int l, bool velocity, bool nested, const T *a, const T *b, T sr, const T *base, T fscale, T *out) {
+  // za / zb: buffers zeroed after a / b are read (apply targets).
+  void cheb(int l, bool velocity, bool nested, const T *a, const T *b, T *za, T *zb, T sr, const T *base, T fscale,
+            T *out, T *acc) {
     LevelRT<T> &R = L[l];
     const int kd = velocity ? C->o.kA : C->o.kS;
     const ChebCoef cc = cheb_coef(kd, velocity ? C->betaA[l] : C->betaS[l]);
@@ -244,94 +272,100 @@ struct Runner {
       db = R.pd;
       tb = R.ps;
     }
-    const int nb = vec_blocks(n);
     if (kd == 0) {
-      k_cheb_init<T><<<nb, kVecThreads, 0, s>>>(a, b, sr, Dinv, (T)cc.c0, nullptr, db, xb, base, scale, out, n);
-      note();
+      vecp(k_cheb_init<T, 1>, k_cheb_init<T, VW>, {a, b, Dinv, db, xb, base, out, acc, za, zb}, n, a, b, sr, Dinv,
+           (T)cc.c0, (T *)nullptr, db, xb, base, scale, out, acc, za, zb, n);
       return;
     }
-    k_cheb_init<T><<<nb, kVecThreads, 0, s>>>(a, b, sr, Dinv, (T)cc.c0, rb, db, xb, nullptr, T(0), nullptr, n);
-    note();
+    vecp(k_cheb_init<T, 1>, k_cheb_init<T, VW>, {a, b, Dinv, rb, db, xb, za, zb}, n, a, b, sr, Dinv, (T)cc.c0, rb, db,
+         xb, (const T *)nullptr, T(0), (T *)nullptr, (T *)nullptr, za, zb, n);
     for (int j = 1; j <= kd; ++j) {
       if (velocity)
-        apply(l, kApplyA, xb, nullptr, tb, nullptr);
+        apply_nz(l, kApplyA, xb, nullptr, tb, nullptr);
       else
         S_tilde(l, xb, tb);
       const bool last = j == kd;
-      k_cheb_step<T><<<nb, kVecThreads, 0, s>>>(rb, tb, Dinv, (T)cc.c1[j], (T)cc.c2[j], db, xb, last ? base : nullptr,
-                                                scale, last ? out : nullptr, n);
-      note();
+      const T *bs = last ? base : nullptr;
+      T *fo = last ? out : nullptr, *ac = last ? acc : nullptr;
+      vecp(k_cheb_step<T, 1>, k_cheb_step<T, VW>, {rb, tb, Dinv, db, xb, bs, fo, ac}, n, (const T *)rb, tb, Dinv,
+           (T)cc.c1[j], (T)cc.c2[j], db, xb, bs, scale, fo, ac, n);
     }
   }
-  // y = B A^-1_hat B^T q
+  // y = B A^-1_hat B^T q   (y zero on entry)
   void S_tilde(int l, const T *q, T *y) {
     LevelRT<T> &R = L[l];
-    apply(l, kApplyBT, nullptr, q, R.tu, nullptr);
-    cheb(l, true, true, R.tu, nullptr, T(1), nullptr, T(1), R.au);
-    apply(l, kApplyB, R.au, nullptr, nullptr, y);
+    apply_nz(l, kApplyBT, nullptr, q, R.tu, nullptr);
+    cheb(l, true, true, R.tu, nullptr, R.tu, nullptr, T(1), nullptr, T(1), R.au, nullptr);
+    apply_nz(l, kApplyB, R.au, nullptr, nullptr, y);
   }
   // One inexact symmetric Uzawa step in compact form (Sec. 3.3.1, K_hat):
   //   u_hat = u + A^-1_hat (f - A u - B^T p); dp = S^-1_hat (B u_hat - g);
   //   u = u_hat - A^-1_hat B^T dp; p = p + dp
-  void smooth_step(int l, T *x, const T *bv) {
+  // x_zero: x is known to be zero on entry (first step on a coarse level), so A u + B^T p = 0.
+  void smooth_step(int l, T *x, const T *bv, bool x_zero) {
     LevelRT<T> &R = L[l];
-    const long long n_u = nu(l), n_p = np(l);
+    const long long n_u = nu(l);
     T *u = x, *p = x + n_u;
     const T *f = bv, *g = bv + n_u;
-    apply(l, kApplyA | kApplyBT, u, p, R.tu, nullptr);
-    cheb(l, true, false, f, R.tu, T(1), u, T(1), R.uhat);
-    apply(l, kApplyB, R.uhat, nullptr, nullptr, R.pt);
-    cheb(l, false, false, R.pt, g, T(1), nullptr, T(1), R.dp);
-    apply(l, kApplyBT, nullptr, R.dp, R.tu, nullptr);
-    cheb(l, true, false, R.tu, nullptr, T(1), R.uhat, T(-1), u);
-    axpy(p, T(1), R.dp, n_p);
+    if (!x_zero) apply_nz(l, kApplyA | kApplyBT, u, p, R.tu, nullptr);
+    cheb(l, true, false, f, x_zero ? nullptr : R.tu, nullptr, x_zero ? nullptr : R.tu, T(1), u, T(1), R.uhat,
+         nullptr);
+    apply_nz(l, kApplyB, R.uhat, nullptr, nullptr, R.pt);
+    cheb(l, false, false, R.pt, g, R.pt, nullptr, T(1), nullptr, T(1), R.dp, p);
+    apply_nz(l, kApplyBT, nullptr, R.dp, R.tu, nullptr);
+    cheb(l, true, false, R.tu, nullptr, R.tu, nullptr, T(1), R.uhat, T(-1), u, nullptr);
   }
   void coarse(const T *b, T *x) {
     const int n0 = C->n0;
-    k_coarse_apply<T><<<(n0 * 32 + 255) / 256, 256, 0, s>>>(C->Kinv, n0, b, x);
+    launch_kernel(k_coarse_apply<T>, dim3((n0 * 32 + 255) / 256), dim3(256), 0, s, (const double *)C->Kinv, n0, b, x);
     note();
   }
-  void restrict_to(int lf, const T *in, T *out) {
+  void restrict_to(int lf, const T *in, T *out, T *zero_c) {
     const long long n = nu(lf - 1) + np(lf - 1);
-    k_restrict<T><<<vec_blocks(n), kVecThreads, 0, s>>>(L[lf].d, L[lf - 1].d, tt, in, out);
-    note();
+    if (n < 32768)
+      vec(k_restrict<T, 8>, n * 8, L[lf].d, L[lf - 1].d, tt, in, out, zero_c);
+    else
+      vec(k_restrict<T, 1>, n, L[lf].d, L[lf - 1].d, tt, in, out, zero_c);
   }
   void prolongate(int lf, const T *in, T *out, int add) {
     const long long n = nu(lf) + np(lf);
-    k_prolongate<T><<<vec_blocks(n), kVecThreads, 0, s>>>(L[lf].d, L[lf - 1].d, tt, in, out, add);
-    note();
+    vec(k_prolongate<T>, n, L[lf].d, L[lf - 1].d, tt, in, out, add);
   }
   // Algorithm 1: MG(x_l, b_l) with gamma = 1 (V) or 2 (W); returns after the coarse solve on l = 0.
-  void cycle(int l, T *x, const T *b) {
+  void cycle(int l, T *x, const T *b, bool x_zero) {
     if (l == 0) {
       coarse(b, x);
       return;
     }
     LevelRT<T> &R = L[l];
     const long long n = nu(l) + np(l);
-    for (int i = 0; i < C->o.m; ++i) smooth_step(l, x, b);
-    vmult(l, x, R.r, false);
-    sub(b, R.r, R.r, n);
-    restrict_to(l, R.r, L[l - 1].b);
-    zero(L[l - 1].x, nu(l - 1) + np(l - 1));
+    for (int i = 0; i < C->o.m; ++i) smooth_step(l, x, b, x_zero && i == 0);
+    if (C->o.m == 0 && x_zero) {
+      vec(k_convert_zero<T, T, 1>, n, b, R.r, (T *)nullptr, n);  // r = b - K 0
+    } else {
+      apply_nz(l, kApplyA | kApplyBT | kApplyB, x, x + nu(l), R.kx, R.kx + nu(l));
+      vecp(k_residual<T, 1>, k_residual<T, VW>, {b, R.kx, R.r}, n, b, R.kx, R.r, n);
+    }
+    restrict_to(l, R.r, L[l - 1].b, L[l - 1].x);
     const int gam = C->o.cycle == 1 ? 2 : 1;
-    for (int j = 0; j < gam; ++j) cycle(l - 1, L[l - 1].x, L[l - 1].b);
+    for (int j = 0; j < gam; ++j) cycle(l - 1, L[l - 1].x, L[l - 1].b, j == 0);
     prolongate(l, L[l - 1].x, x, 1);
-    for (int i = 0; i < C->o.m; ++i) smooth_step(l, x, b);
+    for (int i = 0; i < C->o.m; ++i) smooth_step(l, x, b, false);
   }
-  // One cycle on the finest level using the internal top-level buffers (graph-captured).
-  int top_cycle() {
+  // One cycle on the finest level on the internal top-level buffers, replayed from a captured
+  // graph (one graph per precision and per "x is zero on entry").
+  int top_cycle(bool x_zero) {
     const int top = C->nl - 1;
     if (!C->use_graphs) {
-      cycle(top, L[top].x, L[top].b);
+      cycle(top, L[top].x, L[top].b, x_zero);
       return STOKES_OK;
     }
-    GraphSlot &g = graph_slot<T>(C);
+    GraphSlot &g = graph_slot<T>(C, x_zero);
     if (!g.exec) {
       SMF_CUDA_OK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
       C->capturing = true;
       C->cap_count = 0;
-      cycle(top, L[top].x, L[top].b);
+      cycle(top, L[top].x, L[top].b, x_zero);
       C->capturing = false;
       cudaGraph_t graph;
       SMF_CUDA_OK(cudaStreamEndCapture(s, &graph));
@@ -407,6 +441,7 @@ static int lanczos(stokes_ctx *C, int l, bool velocity, double *est) {
     if (velocity) {
       R.apply(l, kApplyA, tmp, nullptr, w, nullptr);
     } else {
+      SMF_CUDA_OK(cudaMemsetAsync(w, 0, n * sizeof(double), C->s));
       R.S_tilde(l, tmp, w);
     }
     k_mul<double><<<nb, kVecThreads, 0, C->s>>>(sq, w, w, n);
@@ -489,7 +524,7 @@ template <typename T>
 static int alloc_level_buffers(stokes_ctx *C, LevelRT<T> &R) {
   const long long nu = R.d.n_u, np = R.d.n_p, n = nu + np;
   int st;
-  T **full[] = {&R.x, &R.b, &R.r};
+  T **full[] = {&R.x, &R.b, &R.r, &R.kx};
   for (auto p : full)
     if ((st = dalloc(C, p, n))) return st;
   T **vel[] = {&R.DAinv, &R.tu, &R.ru, &R.uhat, &R.cx, &R.cd, &R.ct, &R.r2, &R.cx2, &R.cd2, &R.ct2, &R.au};
@@ -531,6 +566,13 @@ static int finish(stokes_ctx *C, int st) {
 static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho, const double *mu_cell,
                     const stokes_opts *opts, stokes_ctx *C) {
   const int dim = mesh->dim, nl = mesh->n_levels;
+  C->mesh = *mesh;
+  if (mesh->vertices) {
+    const long long nvert = (long long)(mesh->n[0] + 1) * (mesh->n[1] + 1) * (dim == 3 ? mesh->n[2] + 1 : 1);
+    C->mesh_vertices.assign(mesh->vertices, mesh->vertices + nvert * dim);
+    C->mesh.vertices = C->mesh_vertices.data();
+  }
+  C->mu_const = mu;
   C->dim = dim;
   C->k = k;
   C->nl = nl;
@@ -581,6 +623,11 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
   SMF_CUDA_OK(cudaMemcpyAsync(C->tab32, &t32, sizeof(t32), cudaMemcpyHostToDevice, C->s));
   SMF_CUDA_OK(cudaMemcpyAsync(C->tt64, &tt64, sizeof(tt64), cudaMemcpyHostToDevice, C->s));
   SMF_CUDA_OK(cudaMemcpyAsync(C->tt32, &tt32, sizeof(tt32), cudaMemcpyHostToDevice, C->s));
+  {
+    const int e = k == 2 ? upload_col_tables<2>(t64, C->s) : (k == 3 ? upload_col_tables<3>(t64, C->s)
+                                                                     : upload_col_tables<4>(t64, C->s));
+    if (e) SMF_CUDA_OK((cudaError_t)e);
+  }
 
   // level hierarchy (host copies of geometry and viscosity, coarse from fine)
   C->L64.resize(nl);
@@ -771,9 +818,17 @@ static int fgmres(stokes_ctx *C, const double *b, double *x, double rtol, int ma
   double rel = 1.0, beta0 = -1.0;
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hcol(2 * (m + 2));
   int status = STOKES_OK;
+  double xn2;
+  if ((st = dot64(C, x, x, N, &xn2))) return st;
+  bool x_is_zero = xn2 == 0.0;
   while (true) {
-    R64.vmult(top, x, C->w, true);
-    R64.sub(b, C->w, C->V, N);
+    if (x_is_zero) {  // r = b - K 0
+      SMF_CUDA_OK(cudaMemcpyAsync(C->V, b, N * sizeof(double), cudaMemcpyDeviceToDevice, C->s));
+      x_is_zero = false;
+    } else {
+      R64.vmult(top, x, C->w, true);
+      R64.sub(b, C->w, C->V, N);
+    }
     double beta2;
     if ((st = dot64(C, C->V, C->V, N, &beta2))) return st;
     const double beta = std::sqrt(beta2);
@@ -801,18 +856,16 @@ static int fgmres(stokes_ctx *C, const double *b, double *x, double rtol, int ma
       // z_j = MG(0, v_j) in FP32 or FP64
       if (C->o.vcycle_fp32) {
         LevelRT<float> &T32 = C->L32[top];
-        k_convert<double, float><<<nb, kVecThreads, 0, C->s>>>(vj, T32.b, N);
-        ++C->launches;
-        SMF_CUDA_OK(cudaMemsetAsync(T32.x, 0, N * sizeof(float), C->s));
-        if ((st = R32.top_cycle())) return st;
-        k_convert<float, double><<<nb, kVecThreads, 0, C->s>>>(T32.x, zj, N);
-        ++C->launches;
+        R32.vec(k_convert_zero<double, float, 1>, N, (const double *)vj, T32.b, T32.x, N);
+        if ((st = R32.top_cycle(true))) return st;
+        R32.vec(k_convert_zero<float, double, 1>, N, (const float *)T32.x, zj, (double *)nullptr, N);
       } else {
         LevelRT<double> &T64 = C->L64[top];
-        SMF_CUDA_OK(cudaMemcpyAsync(T64.b, vj, N * sizeof(double), cudaMemcpyDeviceToDevice, C->s));
-        SMF_CUDA_OK(cudaMemsetAsync(T64.x, 0, N * sizeof(double), C->s));
-        if ((st = R64.top_cycle())) return st;
-        SMF_CUDA_OK(cudaMemcpyAsync(zj, T64.x, N * sizeof(double), cudaMemcpyDeviceToDevice, C->s));
+        R64.vecp(k_convert_zero<double, double, 1>, k_convert_zero<double, double, 2>, {vj, T64.b, T64.x}, N,
+                 (const double *)vj, T64.b, T64.x, N);
+        if ((st = R64.top_cycle(true))) return st;
+        R64.vecp(k_convert_zero<double, double, 1>, k_convert_zero<double, double, 2>, {T64.x, zj}, N,
+                 (const double *)T64.x, zj, (double *)nullptr, N);
       }
       R64.vmult(top, zj, C->w, true);
       // classical Gram-Schmidt with one re-orthogonalisation (CGS2)
@@ -965,14 +1018,15 @@ int stokes_vmult(stokes_ctx *C, int level, int precision, const void *x, void *y
 
 int stokes_apply_blocks(stokes_ctx *C, int level, int precision, int blocks, const void *u, const void *p, void *yu,
                         void *yp, void *stream) {
-  if (!check_level(C, level) || (precision != 32 && precision != 64) || blocks <= 0 || blocks > 7 ||
-      ((blocks & 1) && (!u || !yu)) || ((blocks & 2) && (!p || !yu)) || ((blocks & 4) && (!u || !yp))) {
+  const bool mass = blocks == kApplyMass || blocks == kApplyMassAll;
+  if (!check_level(C, level) || (precision != 32 && precision != 64) || blocks <= 0 || (blocks > 7 && !mass) ||
+      ((blocks & (1 | 8 | 16)) && (!u || !yu)) || ((blocks & 2) && (!p || !yu)) || ((blocks & 4) && (!u || !yp))) {
     set_error("invalid stokes_apply_blocks arguments");
     if (C) C->err = "invalid stokes_apply_blocks arguments";
     return STOKES_EINVAL;
   }
   StreamGuard sg(C, stream);
-  const bool wu = blocks & 3, wp = blocks & 4;
+  const bool wu = blocks & (1 | 2 | 8 | 16), wp = blocks & 4;
   if (precision == 64)
     Runner<double>(C).apply(level, blocks, (const double *)u, (const double *)p, wu ? (double *)yu : nullptr,
                             wp ? (double *)yp : nullptr);
@@ -1010,9 +1064,9 @@ int stokes_smooth(stokes_ctx *C, int level, int precision, int steps, const void
   StreamGuard sg(C, stream);
   for (int i = 0; i < steps; ++i) {
     if (precision == 64)
-      Runner<double>(C).smooth_step(level, (double *)x, (const double *)b);
+      Runner<double>(C).smooth_step(level, (double *)x, (const double *)b, false);
     else
-      Runner<float>(C).smooth_step(level, (float *)x, (const float *)b);
+      Runner<float>(C).smooth_step(level, (float *)x, (const float *)b, false);
   }
   return finish(C, STOKES_OK);
 }
@@ -1029,13 +1083,13 @@ int stokes_transfer(stokes_ctx *C, int fine_level, int precision, int direction,
   if (precision == 64) {
     Runner<double> R(C);
     if (direction == 0)
-      R.restrict_to(fine_level, (const double *)in, (double *)out);
+      R.restrict_to(fine_level, (const double *)in, (double *)out, nullptr);
     else
       R.prolongate(fine_level, (const double *)in, (double *)out, 0);
   } else {
     Runner<float> R(C);
     if (direction == 0)
-      R.restrict_to(fine_level, (const float *)in, (float *)out);
+      R.restrict_to(fine_level, (const float *)in, (float *)out, nullptr);
     else
       R.prolongate(fine_level, (const float *)in, (float *)out, 0);
   }
@@ -1070,14 +1124,14 @@ int mg_vcycle(stokes_ctx *C, int precision, const void *b, void *x, void *stream
     const long long N = R.nu(top) + R.np(top);
     cudaMemcpyAsync(C->L64[top].b, b, N * sizeof(double), cudaMemcpyDeviceToDevice, C->s);
     cudaMemcpyAsync(C->L64[top].x, x, N * sizeof(double), cudaMemcpyDeviceToDevice, C->s);
-    st = R.top_cycle();
+    st = R.top_cycle(false);
     cudaMemcpyAsync(x, C->L64[top].x, N * sizeof(double), cudaMemcpyDeviceToDevice, C->s);
   } else {
     Runner<float> R(C);
     const long long N = R.nu(top) + R.np(top);
     cudaMemcpyAsync(C->L32[top].b, b, N * sizeof(float), cudaMemcpyDeviceToDevice, C->s);
     cudaMemcpyAsync(C->L32[top].x, x, N * sizeof(float), cudaMemcpyDeviceToDevice, C->s);
-    st = R.top_cycle();
+    st = R.top_cycle(false);
     cudaMemcpyAsync(x, C->L32[top].x, N * sizeof(float), cudaMemcpyDeviceToDevice, C->s);
   }
   return finish(C, st);
@@ -1139,6 +1193,54 @@ int stokes_get_diagonals(stokes_ctx *C, int level, double *DA, double *DS, void 
   return finish(C, STOKES_OK);
 }
 
+int stokes_cell_grad(stokes_ctx *C, const double *u, const double *lam, double *dJ_dmu, void *stream) {
+  if (!C || !u || !lam || !dJ_dmu) {
+    set_error("invalid stokes_cell_grad arguments");
+    if (C) C->err = g_last_error;
+    return STOKES_EINVAL;
+  }
+  StreamGuard sg(C, stream);
+  const LevelDesc<double> &d = C->L64[C->nl - 1].d;
+  switch (d.k) {
+    case 2: launch_cell_grad_k<2, double>(d, C->tab64, u, lam, dJ_dmu, C->s); break;
+    case 3: launch_cell_grad_k<3, double>(d, C->tab64, u, lam, dJ_dmu, C->s); break;
+    default: launch_cell_grad_k<4, double>(d, C->tab64, u, lam, dJ_dmu, C->s); break;
+  }
+  ++C->launches;
+  return finish(C, STOKES_OK);
+}
+
+int stokes_set_viscosity(stokes_ctx *C, const double *mu_cell, void *stream) {
+  if (!C || !mu_cell) {
+    set_error("invalid stokes_set_viscosity arguments");
+    if (C) C->err = g_last_error;
+    return STOKES_EINVAL;
+  }
+  const long long nc = (long long)C->mesh.n[0] * C->mesh.n[1] * (C->dim == 3 ? C->mesh.n[2] : 1);
+  for (long long i = 0; i < nc; ++i)
+    if (!(mu_cell[i] > 0)) {
+      set_error("mu_cell entries must be positive");
+      C->err = g_last_error;
+      return STOKES_EINVAL;
+    }
+  cudaStreamSynchronize((cudaStream_t)stream);
+  if (C->s) cudaStreamSynchronize(C->s);
+  // rebuild every mu-dependent part (level viscosities, diagonals, eigenvalue estimates,
+  // coarse inverse, captured graphs) in a fresh context, then take over its contents
+  stokes_ctx *T = nullptr;
+  stokes_mesh mesh = C->mesh;
+  const int st = stokes_setup(&mesh, C->k, C->mu_const, C->gamma_rho, mu_cell, &C->o, stream, &T);
+  if (st != STOKES_OK) {
+    C->err = g_last_error;
+    return st;
+  }
+  const long long launches = C->launches;
+  std::swap(*C, *T);
+  C->launches += launches;
+  stokes_destroy(T);
+  return STOKES_OK;
+}
+
 int stokes_time_apply(stokes_ctx *C, int level, int precision, int blocks, int reps, double *avg_ms, void *stream) {
   if (!check_level(C, level) || (precision != 32 && precision != 64) || blocks <= 0 || blocks > 15 || reps < 1 ||
       !avg_ms) {
@@ -1179,8 +1281,10 @@ const char *stokes_global_last_error(void) { return g_last_error.c_str(); }
 void stokes_destroy(stokes_ctx *C) {
   if (!C) return;
   if (C->s) cudaStreamSynchronize(C->s);
-  if (C->g32.exec) cudaGraphExecDestroy(C->g32.exec);
-  if (C->g64.exec) cudaGraphExecDestroy(C->g64.exec);
+  for (int i = 0; i < 2; ++i) {
+    if (C->g32[i].exec) cudaGraphExecDestroy(C->g32[i].exec);
+    if (C->g64[i].exec) cudaGraphExecDestroy(C->g64[i].exec);
+  }
   for (void *p : C->allocs) cudaFree(p);
   if (C->ev_in) cudaEventDestroy(C->ev_in);
   if (C->ev_out) cudaEventDestroy(C->ev_out);

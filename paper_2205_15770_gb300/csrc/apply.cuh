@@ -158,6 +158,7 @@ __global__ void __launch_bounds__(CellShape<DIM, K>::THREADS)
     stokes_cell_apply(const LevelDesc<T> L, const Tab1D<T> *__restrict__ tab, const int mode,
                       const T *__restrict__ u, const T *__restrict__ p, T *__restrict__ yu,
                       T *__restrict__ yp) {
+  pdl_enter();
   using CS = CellShape<DIM, K>;
   constexpr int NQ = CS::NQ, NV = CS::NV, NPR = CS::NPR, NP = CS::NP, NPP = CS::NPP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -201,8 +202,9 @@ __global__ void __launch_bounds__(CellShape<DIM, K>::THREADS)
   const T mu = L.mu_cell ? (valid ? L.mu_cell[cell] : T(0)) : L.mu;
 
   const bool needP = mode & kApplyBT;
-  const bool needU = mode & (kApplyA | kApplyB | kApplyMass);
-  const bool outU = mode & (kApplyA | kApplyBT | kApplyMass);
+  const bool massOp = mode & (kApplyMass | kApplyMassAll);
+  const bool needU = (mode & (kApplyA | kApplyB)) || massOp;
+  const bool outU = (mode & (kApplyA | kApplyBT)) || massOp;
   const bool outP = mode & kApplyB;
 
   // ---- pressure at the Gauss points ------------------------------------------------
@@ -239,7 +241,9 @@ __global__ void __launch_bounds__(CellShape<DIM, K>::THREADS)
     T gr[3] = {T(0), T(0), T(0)};
     T uq = T(0);
     if (needU) {
-      bufA[t] = vfree ? u[c * L.nv + vidx] : T(0);
+      // b = Z M_v f reads every node of f (boundary values couple into free rows); its transpose
+      // M_v Z reads the free nodes only and writes every row
+      bufA[t] = ((mode & kApplyMass) ? valid : vfree) ? u[c * L.nv + vidx] : T(0);
       __syncthreads();
       if (DIM == 3) {
         bufB[t] = contract<0, NQ, NV, NV, NV, NV, false>(t, bufA, st->S);
@@ -279,7 +283,7 @@ __global__ void __launch_bounds__(CellShape<DIM, K>::THREADS)
         }
         mv = L.gamma_rho * g.wdet * uq;
       }
-      if (mode & kApplyMass) mv += g.wdet * uq;
+      if (massOp) mv += g.wdet * uq;
       if (mode & kApplyBT) {
 #pragma unroll
         for (int b = 0; b < DIM; ++b) f[b] -= pq * g.C[b * DIM + c];
@@ -305,7 +309,7 @@ __global__ void __launch_bounds__(CellShape<DIM, K>::THREADS)
         __syncthreads();
         val = contract<0, NV, NV, 1, NQ, NV, true>(t, bufB, st->S);
       }
-      if (vfree) atomicAdd(&yu[c * L.nv + vidx], val);
+      if ((mode & kApplyMassAll) ? valid : vfree) atomicAdd(&yu[c * L.nv + vidx], val);
     }
     __syncthreads();
   }
@@ -442,6 +446,98 @@ __global__ void stokes_cell_diagonals(const LevelDesc<T> L, const Tab1D<T> *__re
     const long long gi = lattice_index<DIM, T>(L.Pn, (K - 1) * cx + px, (K - 1) * cy + py, (K - 1) * cz + pz);
     atomicAdd(&dSloc[gi], sLoc[t]);
     atomicAdd(&dMp[gi], mp);
+  }
+}
+
+}  // namespace smf
+
+namespace smf {
+
+// Per-cell viscosity gradient of the adjoint method (no counterpart in the paper; the paper
+// has constant mu): with K(mu) x = b and K lambda = dJ/dx,
+//   dJ/dmu_c = -lambda^T (dK/dmu_c) x = - sum_comp int_c grad lambda_comp . grad u_comp dx,
+// evaluated by the same sum-factorised gradients as the operator (w adj adj^T / det at each
+// Gauss point).  Constrained velocity DoFs read as 0 (the identity rows of K do not depend on
+// mu).  One value per cell, no scatter.
+template <int DIM, int K, typename T, bool CART>
+__global__ void __launch_bounds__(CellShape<DIM, K>::THREADS)
+    stokes_cell_grad_mu(const LevelDesc<T> L, const Tab1D<T> *__restrict__ tab, const T *__restrict__ u,
+                        const T *__restrict__ lam, T *__restrict__ g_out) {
+  pdl_enter();
+  using CS = CellShape<DIM, K>;
+  constexpr int NQ = CS::NQ, NV = CS::NV, NP = CS::NP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *sm = reinterpret_cast<T *>(smem_raw);
+  Tab1D<T> *st = reinterpret_cast<Tab1D<T> *>(sm);
+  T *cellmem = sm + sizeof(Tab1D<T>) / sizeof(T);
+  const int lc = threadIdx.x / NP;
+  const int t = threadIdx.x - lc * NP;
+  const long long cell = (long long)blockIdx.x * CS::CPB + lc;
+  const bool valid = cell < L.n_cells;
+  T *bufA = cellmem + lc * CS::PER_CELL;
+  T *bufB = bufA + NP;
+  T *verts = bufA + CS::BUFS * NP;
+  int cx = 0, cy = 0, cz = 0;
+  if (valid) {
+    cx = (int)(cell % L.n[0]);
+    const long long r = cell / L.n[0];
+    cy = (int)(r % L.n[1]);
+    cz = (int)(r / L.n[1]);
+  }
+  load_tables(tab, sm);
+  if (!CART && t < CS::NVERT * DIM) {
+    const int v = t / DIM, a = t - (t / DIM) * DIM;
+    const int vx = v & 1, vy = (v >> 1) & 1, vz = (v >> 2) & 1;
+    long long gv = DIM == 3 ? ((long long)(cz + vz) * (L.n[1] + 1) + (cy + vy)) * (L.n[0] + 1) + (cx + vx)
+                            : (long long)(cy + vy) * (L.n[0] + 1) + (cx + vx);
+    verts[t] = valid ? L.vert[gv * DIM + a] : T(0);
+  }
+  __syncthreads();
+  const int qx = t % NQ, qy = (t / NQ) % NQ, qz = DIM == 3 ? t / (NQ * NQ) : 0;
+  PointGeo<DIM, T> geo;
+  point_geometry<DIM, K, T, CART>(L, st->x, st->w, verts, qx, qy, qz, geo);
+  const int ix = t % NV, iy = (t / NV) % NV, iz = DIM == 3 ? t / (NV * NV) : 0;
+  const int gx = K * cx + ix, gy = K * cy + iy, gz = K * cz + iz;
+  const long long vidx = lattice_index<DIM, T>(L.N, gx, gy, gz);
+  const bool vfree = valid && !vel_constrained(L.N, L.faces, DIM, gx, gy, gz);
+  T acc = T(0);
+  for (int c = 0; c < DIM; ++c) {
+    T gr[2][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
+    for (int f = 0; f < 2; ++f) {
+      const T *src = f == 0 ? u : lam;
+      bufA[t] = vfree ? src[c * L.nv + vidx] : T(0);
+      __syncthreads();
+      if (DIM == 3) {
+        bufB[t] = contract<0, NQ, NV, NV, NV, NV, false>(t, bufA, st->S);
+        __syncthreads();
+        bufA[t] = contract<1, NQ, NQ, NV, NV, NV, false>(t, bufB, st->S);
+        __syncthreads();
+        bufB[t] = contract<2, NQ, NQ, NQ, NV, NV, false>(t, bufA, st->S);
+        __syncthreads();
+        gr[f][0] = contract<0, NQ, NQ, NQ, NQ, NQ, false>(t, bufB, st->D);
+        gr[f][1] = contract<1, NQ, NQ, NQ, NQ, NQ, false>(t, bufB, st->D);
+        gr[f][2] = contract<2, NQ, NQ, NQ, NQ, NQ, false>(t, bufB, st->D);
+      } else {
+        bufB[t] = contract<0, NQ, NV, 1, NV, NV, false>(t, bufA, st->S);
+        __syncthreads();
+        bufA[t] = contract<1, NQ, NQ, 1, NV, NV, false>(t, bufB, st->S);
+        __syncthreads();
+        gr[f][0] = contract<0, NQ, NQ, 1, NQ, NQ, false>(t, bufA, st->D);
+        gr[f][1] = contract<1, NQ, NQ, 1, NQ, NQ, false>(t, bufA, st->D);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) acc += gr[1][a] * geo.G[a * DIM + b] * gr[0][b];
+  }
+  bufA[t] = acc;
+  __syncthreads();
+  if (t == 0 && valid) {
+    T s = T(0);
+    for (int q = 0; q < NP; ++q) s += bufA[q];
+    g_out[cell] = -s;
   }
 }
 

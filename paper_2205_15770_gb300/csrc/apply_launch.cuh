@@ -1,9 +1,21 @@
 // Launchers of the cell kernels for one polynomial degree K (included by apply_kK.cu).
 #pragma once
+#include <cstdlib>
 #include "apply.cuh"
+#include "apply_col.cuh"
 #include "host_tables.h"
 
 namespace smf {
+
+// STOKES_GENERIC_KERNEL=1 routes 3D applications to the point-per-thread kernel (for A/B runs).
+static inline bool getenv_generic() {
+  static int v = -1;
+  if (v < 0) {
+    const char *e = getenv("STOKES_GENERIC_KERNEL");
+    v = (e && e[0] == '1') ? 1 : 0;
+  }
+  return v == 1;
+}
 
 template <int DIM, int K, typename T, bool CART>
 static int launch_apply_dim(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, const T *u, const T *p, T *yu,
@@ -11,13 +23,38 @@ static int launch_apply_dim(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode
   using CS = CellShape<DIM, K>;
   const long long blocks = (L.n_cells + CS::CPB - 1) / CS::CPB;
   const size_t smem = sizeof(Tab1D<T>) + (size_t)CS::CPB * CS::PER_CELL * sizeof(T);
-  stokes_cell_apply<DIM, K, T, CART><<<(unsigned)blocks, CS::THREADS, smem, s>>>(L, tab, mode, u, p, yu, yp);
+  launch_kernel(stokes_cell_apply<DIM, K, T, CART>, dim3((unsigned)blocks), dim3(CS::THREADS), smem, s, L, tab, mode, u,
+                p, yu, yp);
   return 0;
+}
+
+template <int K, typename T, int MODE, bool CART>
+static int launch_col(const LevelDesc<T> &L, const T *u, const T *p, T *yu, T *yp, cudaStream_t s) {
+  using CS = ColShape<K>;
+  const long long blocks = (L.n_cells + CS::CPB - 1) / CS::CPB;
+  launch_kernel(stokes_cell_apply_col<K, T, MODE, CART>, dim3((unsigned)blocks), dim3(CS::THREADS), 0, s, L, u, p, yu,
+                yp);
+  return 0;
+}
+
+template <int K, typename T, int MODE>
+static int launch_col_mode(const LevelDesc<T> &L, const T *u, const T *p, T *yu, T *yp, cudaStream_t s) {
+  return L.cartesian ? launch_col<K, T, MODE, true>(L, u, p, yu, yp, s) : launch_col<K, T, MODE, false>(L, u, p, yu, yp, s);
 }
 
 template <int K, typename T>
 int launch_cell_apply_k(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, const T *u, const T *p, T *yu, T *yp,
                         cudaStream_t s) {
+  if (L.dim == 3 && !getenv_generic()) {
+    switch (mode) {
+      case kApplyA: return launch_col_mode<K, T, kApplyA>(L, u, p, yu, yp, s);
+      case kApplyBT: return launch_col_mode<K, T, kApplyBT>(L, u, p, yu, yp, s);
+      case kApplyB: return launch_col_mode<K, T, kApplyB>(L, u, p, yu, yp, s);
+      case kApplyA | kApplyBT: return launch_col_mode<K, T, kApplyA | kApplyBT>(L, u, p, yu, yp, s);
+      case kApplyA | kApplyBT | kApplyB: return launch_col_mode<K, T, kApplyA | kApplyBT | kApplyB>(L, u, p, yu, yp, s);
+      default: break;
+    }
+  }
   if (L.dim == 3)
     return L.cartesian ? launch_apply_dim<3, K, T, true>(L, tab, mode, u, p, yu, yp, s)
                        : launch_apply_dim<3, K, T, false>(L, tab, mode, u, p, yu, yp, s);
@@ -30,6 +67,25 @@ static int launch_diag_dim(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T
   using CS = CellShape<DIM, K>;
   stokes_cell_diagonals<DIM, K, T, CART><<<(unsigned)L.n_cells, CS::NP, 0, s>>>(L, tab, dAs, dSloc, dMp);
   return 0;
+}
+
+template <int DIM, int K, typename T, bool CART>
+static int launch_grad_dim(const LevelDesc<T> &L, const Tab1D<T> *tab, const T *u, const T *lam, T *g, cudaStream_t s) {
+  using CS = CellShape<DIM, K>;
+  const long long blocks = (L.n_cells + CS::CPB - 1) / CS::CPB;
+  const size_t smem = sizeof(Tab1D<T>) + (size_t)CS::CPB * CS::PER_CELL * sizeof(T);
+  launch_kernel(stokes_cell_grad_mu<DIM, K, T, CART>, dim3((unsigned)blocks), dim3(CS::THREADS), smem, s, L, tab, u,
+                lam, g);
+  return 0;
+}
+
+template <int K, typename T>
+int launch_cell_grad_k(const LevelDesc<T> &L, const Tab1D<T> *tab, const T *u, const T *lam, T *g, cudaStream_t s) {
+  if (L.dim == 3)
+    return L.cartesian ? launch_grad_dim<3, K, T, true>(L, tab, u, lam, g, s)
+                       : launch_grad_dim<3, K, T, false>(L, tab, u, lam, g, s);
+  return L.cartesian ? launch_grad_dim<2, K, T, true>(L, tab, u, lam, g, s)
+                     : launch_grad_dim<2, K, T, false>(L, tab, u, lam, g, s);
 }
 
 template <int K, typename T>
@@ -52,4 +108,7 @@ int launch_cell_diag_k(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dS
                                                 cudaStream_t);                                                  \
   template int launch_cell_diag_k<KK, double>(const LevelDesc<double> &, const Tab1D<double> *, double *,      \
                                                double *, double *, cudaStream_t);                              \
+  template int upload_col_tables<KK>(const Tab1D<double> &, cudaStream_t);                                     \
+  template int launch_cell_grad_k<KK, double>(const LevelDesc<double> &, const Tab1D<double> *, const double *,  \
+                                               const double *, double *, cudaStream_t);                        \
   }

@@ -16,7 +16,8 @@ enum ApplyMode : int {
   kApplyA = 1,     // yu += A u  (mu grad:grad + gamma*rho mass)
   kApplyBT = 2,    // yu += B^T p
   kApplyB = 4,     // yp += B u
-  kApplyMass = 8,  // yu += M_v u (plain velocity mass, no mu / gamma; right-hand sides)
+  kApplyMass = 8,      // yu += Z M_v u (right-hand sides b = Z M_v f; every node of u is read)
+  kApplyMassAll = 16,  // yu += M_v Z u (its transpose: free nodes of u read, every row written)
 };
 
 // 1D tables of one velocity degree k on the reference interval, (k+1) Gauss points.
@@ -68,6 +69,35 @@ __host__ __device__ inline bool vel_constrained(const int N[3], unsigned faces, 
     if ((faces & 32u) && gz == N[2] - 1) return true;
   }
   return false;
+}
+
+// Programmatic dependent launch: let the next kernel in the stream start launching, then wait
+// until every kernel this one depends on has completed and its writes are visible.  Both are
+// no-ops when the kernel was launched without the programmatic-serialization attribute.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Host side: launch with the programmatic-stream-serialization attribute (PDL) unless
+// STOKES_NO_PDL=1.  Every kernel of the library begins with pdl_enter().
+bool pdl_on();
+template <typename... KArgs, typename... Args>
+inline void launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                          Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  if (pdl_on()) {
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+  }
+  cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
 }
 
 constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }

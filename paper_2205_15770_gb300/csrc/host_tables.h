@@ -21,5 +21,9 @@ template <int K, typename T>
 int launch_cell_apply_k(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, const T *u, const T *p, T *yu, T *yp,
                         cudaStream_t s);
 template <int K, typename T>
+int launch_cell_grad_k(const LevelDesc<T> &L, const Tab1D<T> *tab, const T *u, const T *lam, T *g, cudaStream_t s);
+template <int K>
+int upload_col_tables(const Tab1D<double> &t, cudaStream_t s);
+template <int K, typename T>
 int launch_cell_diag_k(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dSloc, T *dMp, cudaStream_t s);
 }  // namespace smf

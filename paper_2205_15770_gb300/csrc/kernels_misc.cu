@@ -5,11 +5,13 @@
 namespace smf {
 
 __global__ void k_splitmix(unsigned long long seed, double *__restrict__ out, long long n) {
+  pdl_enter();
   SMF_GRID_LOOP(i, n) out[i] = splitmix64_uniform(seed, i);
 }
 
 __global__ void k_mdot_partial(const double *__restrict__ V, long long ldv, int nvec, const double *__restrict__ w,
                                long long n, double *__restrict__ partial) {
+  pdl_enter();
   __shared__ double sh[32];
   for (int j = 0; j < nvec; ++j) {
     const double *v = V + (long long)j * ldv;
@@ -21,6 +23,7 @@ __global__ void k_mdot_partial(const double *__restrict__ V, long long ldv, int 
 }
 
 __global__ void k_sum_partial(const double *__restrict__ a, long long n, double *__restrict__ partial) {
+  pdl_enter();
   __shared__ double sh[32];
   double s = 0.0;
   SMF_GRID_LOOP(i, n) s += a[i];
@@ -30,6 +33,7 @@ __global__ void k_sum_partial(const double *__restrict__ a, long long n, double 
 
 // out[j] = sum_b partial[j*nparts + b]; one block per j
 __global__ void k_final_reduce(const double *__restrict__ partial, int nparts, int nvec, double *__restrict__ out) {
+  pdl_enter();
   __shared__ double sh[32];
   const int j = blockIdx.x;
   double s = 0.0;
@@ -40,6 +44,7 @@ __global__ void k_final_reduce(const double *__restrict__ partial, int nparts, i
 
 __global__ void k_maxpy(const double *__restrict__ V, long long ldv, int nvec, const double *__restrict__ h,
                         double *__restrict__ w, long long n, double sign) {
+  pdl_enter();
   SMF_GRID_LOOP(i, n) {
     double s = 0.0;
     for (int j = 0; j < nvec; ++j) s += h[j] * V[(long long)j * ldv + i];
@@ -49,11 +54,13 @@ __global__ void k_maxpy(const double *__restrict__ V, long long ldv, int nvec, c
 
 __global__ void k_scale_by_inv_sqrt(const double *__restrict__ w, const double *__restrict__ nrm2,
                                     double *__restrict__ out, long long n) {
+  pdl_enter();
   const double s = 1.0 / sqrt(nrm2[0]);
   SMF_GRID_LOOP(i, n) out[i] = s * w[i];
 }
 
 __global__ void k_unit(double *__restrict__ e, long long n, long long j) {
+  pdl_enter();
   SMF_GRID_LOOP(i, n) e[i] = (i == j) ? 1.0 : 0.0;
 }
 

@@ -56,6 +56,7 @@ __device__ __forceinline__ int inj_col(int G, int deg, int nc, const T *tab, int
 template <typename T>
 __global__ void k_prolongate(const LevelDesc<T> F, const LevelDesc<T> C, const TransferTab<T> *__restrict__ tt,
                              const T *__restrict__ in, T *__restrict__ out, int add) {
+  pdl_enter();
   const int dim = F.dim, k = F.k;
   SMF_GRID_LOOP(i, F.n_u + F.n_p) {
     const bool vel = i < F.n_u;
@@ -103,37 +104,47 @@ __global__ void k_prolongate(const LevelDesc<T> F, const LevelDesc<T> C, const T
   }
 }
 
-// out (coarse) = P^T in (fine).
-template <typename T>
+// out (coarse) = P^T in (fine); zero_c (coarse-sized, may be null) is zeroed on the way.
+// LANES consecutive lanes share one coarse DoF: the (up to (4k+1)^d) fine terms of its support
+// are split across them and combined with warp shuffles (LANES = 8 on small coarse levels,
+// where there are too few DoFs to fill the GPU; 1 on large ones).
+template <typename T, int LANES>
 __global__ void k_restrict(const LevelDesc<T> F, const LevelDesc<T> C, const TransferTab<T> *__restrict__ tt,
-                           const T *__restrict__ in, T *__restrict__ out) {
+                           const T *__restrict__ in, T *__restrict__ out, T *__restrict__ zero_c) {
+  pdl_enter();
   const int dim = F.dim, k = F.k;
-  SMF_GRID_LOOP(i, C.n_u + C.n_p) {
-    const bool vel = i < C.n_u;
-    const int deg = vel ? k : k - 1;
-    const T *tab = vel ? tt->vel : tt->pre;
-    const int *Nc = vel ? C.N : C.Pn;
-    const long long j = vel ? i % C.nv : i - C.n_u;
-    const int comp = vel ? (int)(i / C.nv) : 0;
-    int G[3] = {(int)(j % Nc[0]), (int)((j / Nc[0]) % Nc[1]), dim == 3 ? (int)(j / ((long long)Nc[0] * Nc[1])) : 0};
-    if (vel && vel_constrained(C.N, C.faces, dim, G[0], G[1], G[2])) {
-      out[i] = T(0);
-      continue;
-    }
-    int g[3][kMaxAxis];
-    T w[3][kMaxAxis];
-    int cnt[3] = {1, 1, 1};
-    for (int a = 0; a < dim; ++a) cnt[a] = inj_col(G[a], deg, C.n[a], tab, g[a], w[a]);
-    if (dim == 2) {
-      g[2][0] = 0;
-      w[2][0] = T(1);
-    }
+  const long long total = (C.n_u + C.n_p) * LANES;
+  const int sub = threadIdx.x & (LANES - 1);
+  // grid-stride over (DoF, lane) pairs; the loop condition depends only on the warp's first
+  // index, so all 32 lanes iterate together and the full-mask shuffles below are converged
+  for (long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x; gid - (threadIdx.x & 31) < total;
+       gid += (long long)gridDim.x * blockDim.x) {
+    const long long i = gid / LANES;
+    const bool active = i < C.n_u + C.n_p;
     T s = T(0);
-    for (int c2 = 0; c2 < cnt[2]; ++c2)
-      for (int c1 = 0; c1 < cnt[1]; ++c1) {
-        const T w12 = w[2][c2] * w[1][c1];
-        for (int c0 = 0; c0 < cnt[0]; ++c0) {
-          const T ww = w12 * w[0][c0];
+    bool constrained = false;
+    if (active) {
+      const bool vel = i < C.n_u;
+      const int deg = vel ? k : k - 1;
+      const T *tab = vel ? tt->vel : tt->pre;
+      const int *Nc = vel ? C.N : C.Pn;
+      const long long j = vel ? i % C.nv : i - C.n_u;
+      const int comp = vel ? (int)(i / C.nv) : 0;
+      int G[3] = {(int)(j % Nc[0]), (int)((j / Nc[0]) % Nc[1]), dim == 3 ? (int)(j / ((long long)Nc[0] * Nc[1])) : 0};
+      constrained = vel && vel_constrained(C.N, C.faces, dim, G[0], G[1], G[2]);
+      if (!constrained) {
+        int g[3][kMaxAxis];
+        T w[3][kMaxAxis];
+        int cnt[3] = {1, 1, 1};
+        for (int a = 0; a < dim; ++a) cnt[a] = inj_col(G[a], deg, C.n[a], tab, g[a], w[a]);
+        if (dim == 2) {
+          g[2][0] = 0;
+          w[2][0] = T(1);
+        }
+        const int nterms = cnt[0] * cnt[1] * cnt[2];
+        for (int t = sub; t < nterms; t += LANES) {
+          const int c0 = t % cnt[0], c1 = (t / cnt[0]) % cnt[1], c2 = t / (cnt[0] * cnt[1]);
+          const T ww = w[2][c2] * w[1][c1] * w[0][c0];
           if (vel) {
             if (vel_constrained(F.N, F.faces, dim, g[0][c0], g[1][c1], g[2][c2])) continue;
             const long long fi = dim == 3 ? ((long long)g[2][c2] * F.N[1] + g[1][c1]) * F.N[0] + g[0][c0]
@@ -146,7 +157,13 @@ __global__ void k_restrict(const LevelDesc<T> F, const LevelDesc<T> C, const Tra
           }
         }
       }
-    out[i] = s;
+    }
+#pragma unroll
+    for (int o = LANES / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, LANES);
+    if (active && sub == 0) {
+      out[i] = s;
+      if (zero_c) zero_c[i] = T(0);
+    }
   }
 }
 

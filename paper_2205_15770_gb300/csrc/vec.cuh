@@ -1,6 +1,8 @@
 // Vector kernels: Chebyshev-Jacobi recurrence (Sec. 3.3.1), residuals, precision
 // conversion, FP64 reductions for the Krylov loop and Lanczos, SplitMix64 start vectors.
 #pragma once
+#include <initializer_list>
+
 #include "common.cuh"
 
 namespace smf {
@@ -14,83 +16,238 @@ inline int vec_blocks(long long n) {
   return (int)(b < 1 ? 1 : b);
 }
 
+// Host: true if every non-null pointer is aligned to `bytes`.
+inline bool all_aligned(size_t bytes, std::initializer_list<const void *> ptrs) {
+  for (const void *p : ptrs)
+    if (p && (reinterpret_cast<uintptr_t>(p) % bytes) != 0) return false;
+  return true;
+}
+
 #define SMF_GRID_LOOP(i, n) \
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
 
 // out = a - b
 template <typename T>
 __global__ void k_sub(const T *__restrict__ a, const T *__restrict__ b, T *__restrict__ out, long long n) {
+  pdl_enter();
   SMF_GRID_LOOP(i, n) out[i] = a[i] - b[i];
 }
 
 // out = a + s * b
 template <typename T>
 __global__ void k_axpy_out(const T *__restrict__ a, T s, const T *__restrict__ b, T *__restrict__ out, long long n) {
+  pdl_enter();
   SMF_GRID_LOOP(i, n) out[i] = a[i] + s * b[i];
 }
 
 // x += s * b
 template <typename T>
 __global__ void k_axpy(T *__restrict__ x, T s, const T *__restrict__ b, long long n) {
+  pdl_enter();
   SMF_GRID_LOOP(i, n) x[i] += s * b[i];
 }
 
 template <typename T>
 __global__ void k_scale(const T *__restrict__ a, T s, T *__restrict__ out, long long n) {
+  pdl_enter();
   SMF_GRID_LOOP(i, n) out[i] = s * a[i];
 }
 
 template <typename T>
 __global__ void k_mul(const T *__restrict__ a, const T *__restrict__ b, T *__restrict__ out, long long n) {
+  pdl_enter();
   SMF_GRID_LOOP(i, n) out[i] = a[i] * b[i];
 }
 
 template <typename T>
 __global__ void k_add_scalar(T *__restrict__ x, const double *__restrict__ sum, double scale, long long n) {
+  pdl_enter();
   const T s = (T)(sum[0] * scale);
   SMF_GRID_LOOP(i, n) x[i] += s;
 }
 
 template <typename Tin, typename Tout>
 __global__ void k_convert(const Tin *__restrict__ a, Tout *__restrict__ out, long long n) {
+  pdl_enter();
   SMF_GRID_LOOP(i, n) out[i] = (Tout)a[i];
 }
 
-// Chebyshev start from x = 0 (Sec. 3.3.1): r = sr * (a - b) (b may be null),
-// d = x = c0 * Dinv * r; r is stored if r_out != null.  With final_out != null the
-// degree-0 result is also written as final_out = base + fscale * x.
-template <typename T>
+// ---- packed (16-byte) element access for the cycle's vector kernels -------------------------
+template <typename T, int V>
+struct alignas(sizeof(T) * V) Pack {
+  T v[V];
+};
+template <int V, typename T>
+__device__ __forceinline__ Pack<T, V> ldp(const T *p, long long j) {
+  return *reinterpret_cast<const Pack<T, V> *>(p + j * V);
+}
+template <int V, typename T>
+__device__ __forceinline__ void stp(T *p, long long j, const Pack<T, V> &v) {
+  *reinterpret_cast<Pack<T, V> *>(p + j * V) = v;
+}
+template <int V, typename T>
+__device__ __forceinline__ Pack<T, V> ldp_or0(const T *p, long long j) {
+  Pack<T, V> r;
+  if (p) {
+    r = ldp<V>(p, j);
+  } else {
+#pragma unroll
+    for (int k = 0; k < V; ++k) r.v[k] = T(0);
+  }
+  return r;
+}
+// Elements [0, n) as n/V packs plus a scalar tail handled by the first threads of the grid.
+#define SMF_PACK_LOOP(j, n, V) SMF_GRID_LOOP(j, (n) / (V))
+#define SMF_TAIL_LOOP(i, n, V)                                                                       \
+  for (long long i = ((n) / (V)) * (V) + (long long)blockIdx.x * blockDim.x + threadIdx.x; i < (n); \
+       i += (long long)gridDim.x * blockDim.x)
+
+// Chebyshev start from x = 0 (Sec. 3.3.1): r = sr * (a - b) (a or b may be null),
+// d = x = c0 * Dinv * r; r is stored if r_out != null.  za / zb (may alias a / b) are zeroed
+// after they are read: apply targets are kept zero between uses, so the cycle needs no memset.
+// With final_out / acc_out the degree-0 result f = base + fscale * x is written / accumulated.
+template <typename T, int V>
+__device__ __forceinline__ void cheb_init_pack(const Pack<T, V> &A, const Pack<T, V> &B, T sr, const Pack<T, V> &Di,
+                                               T c0, Pack<T, V> &R, Pack<T, V> &X) {
+#pragma unroll
+  for (int k = 0; k < V; ++k) {
+    R.v[k] = sr * (A.v[k] - B.v[k]);
+    X.v[k] = c0 * Di.v[k] * R.v[k];
+  }
+}
+template <typename T, int V>
 __global__ void k_cheb_init(const T *__restrict__ a, const T *__restrict__ b, T sr, const T *__restrict__ Dinv,
-                            T c0, T *__restrict__ r_out, T *__restrict__ d, T *__restrict__ x,
-                            const T *__restrict__ base, T fscale, T *__restrict__ final_out, long long n) {
-  SMF_GRID_LOOP(i, n) {
-    T r = b ? sr * (a[i] - b[i]) : sr * a[i];
+                            T c0, T *__restrict__ r_out, T *__restrict__ d, T *__restrict__ x, const T *__restrict__ base,
+                            T fscale, T *__restrict__ final_out, T *__restrict__ acc_out, T *za, T *zb, long long n) {
+  pdl_enter();
+  SMF_PACK_LOOP(j, n, V) {
+    const Pack<T, V> A = ldp_or0<V>(a, j), B = ldp_or0<V>(b, j), Di = ldp<V>(Dinv, j);
+    const Pack<T, V> Bs = ldp_or0<V>(base, j), Ac = ldp_or0<V>(acc_out, j);
+    Pack<T, V> R, X, Z;
+    cheb_init_pack(A, B, sr, Di, c0, R, X);
+#pragma unroll
+    for (int k = 0; k < V; ++k) Z.v[k] = T(0);
+    if (za) stp<V>(za, j, Z);
+    if (zb) stp<V>(zb, j, Z);
+    if (r_out) stp<V>(r_out, j, R);
+    stp<V>(d, j, X);
+    stp<V>(x, j, X);
+    if (final_out || acc_out) {
+      Pack<T, V> F, Anew;
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        F.v[k] = Bs.v[k] + fscale * X.v[k];
+        Anew.v[k] = Ac.v[k] + F.v[k];
+      }
+      if (final_out) stp<V>(final_out, j, F);
+      if (acc_out) stp<V>(acc_out, j, Anew);
+    }
+  }
+  SMF_TAIL_LOOP(i, n, V) {
+    const T av = a ? a[i] : T(0), bv = b ? b[i] : T(0);
+    if (za) za[i] = T(0);
+    if (zb) zb[i] = T(0);
+    const T r = sr * (av - bv);
     if (r_out) r_out[i] = r;
-    T v = c0 * Dinv[i] * r;
+    const T v = c0 * Dinv[i] * r;
     d[i] = v;
     x[i] = v;
-    if (final_out) final_out[i] = (base ? base[i] : T(0)) + fscale * v;
+    const T f = (base ? base[i] : T(0)) + fscale * v;
+    if (final_out) final_out[i] = f;
+    if (acc_out) acc_out[i] += f;
   }
 }
 
-// One Chebyshev step: d = c1 d + c2 Dinv (r - t); x += d.  With final_out != null,
-// final_out = base + fscale * x_new (base may be null).
-template <typename T>
-__global__ void k_cheb_step(const T *__restrict__ r, const T *__restrict__ t, const T *__restrict__ Dinv, T c1, T c2,
+// One Chebyshev step: d = c1 d + c2 Dinv (r - t); x += d; t is zeroed after it is read.  With
+// final_out / acc_out, f = base + fscale * x_new is written / accumulated.
+template <typename T, int V>
+__global__ void k_cheb_step(const T *__restrict__ r, T *__restrict__ t, const T *__restrict__ Dinv, T c1, T c2,
                             T *__restrict__ d, T *__restrict__ x, const T *__restrict__ base, T fscale,
-                            T *__restrict__ final_out, long long n) {
-  SMF_GRID_LOOP(i, n) {
-    T dn = c1 * d[i] + c2 * Dinv[i] * (r[i] - t[i]);
-    T xn = x[i] + dn;
+                            T *__restrict__ final_out, T *__restrict__ acc_out, long long n) {
+  pdl_enter();
+  SMF_PACK_LOOP(j, n, V) {
+    const Pack<T, V> R = ldp<V>(r, j), Tt = ldp<V>(t, j), Di = ldp<V>(Dinv, j), Dd = ldp<V>(d, j), X = ldp<V>(x, j);
+    const Pack<T, V> Bs = ldp_or0<V>(base, j), Ac = ldp_or0<V>(acc_out, j);
+    Pack<T, V> Dn, Xn, Z;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      Dn.v[k] = c1 * Dd.v[k] + c2 * Di.v[k] * (R.v[k] - Tt.v[k]);
+      Xn.v[k] = X.v[k] + Dn.v[k];
+      Z.v[k] = T(0);
+    }
+    stp<V>(t, j, Z);
+    stp<V>(d, j, Dn);
+    stp<V>(x, j, Xn);
+    if (final_out || acc_out) {
+      Pack<T, V> F, Anew;
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        F.v[k] = Bs.v[k] + fscale * Xn.v[k];
+        Anew.v[k] = Ac.v[k] + F.v[k];
+      }
+      if (final_out) stp<V>(final_out, j, F);
+      if (acc_out) stp<V>(acc_out, j, Anew);
+    }
+  }
+  SMF_TAIL_LOOP(i, n, V) {
+    const T tv = t[i];
+    t[i] = T(0);
+    const T dn = c1 * d[i] + c2 * Dinv[i] * (r[i] - tv);
+    const T xn = x[i] + dn;
     d[i] = dn;
     x[i] = xn;
-    if (final_out) final_out[i] = (base ? base[i] : T(0)) + fscale * xn;
+    const T f = (base ? base[i] : T(0)) + fscale * xn;
+    if (final_out) final_out[i] = f;
+    if (acc_out) acc_out[i] += f;
+  }
+}
+
+// r = b - kx; kx is zeroed after it is read (residual of Algorithm 1).
+template <typename T, int V>
+__global__ void k_residual(const T *__restrict__ b, T *__restrict__ kx, T *__restrict__ r, long long n) {
+  pdl_enter();
+  SMF_PACK_LOOP(j, n, V) {
+    const Pack<T, V> B = ldp<V>(b, j), K = ldp<V>(kx, j);
+    Pack<T, V> R, Z;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      R.v[k] = B.v[k] - K.v[k];
+      Z.v[k] = T(0);
+    }
+    stp<V>(r, j, R);
+    stp<V>(kx, j, Z);
+  }
+  SMF_TAIL_LOOP(i, n, V) {
+    r[i] = b[i] - kx[i];
+    kx[i] = T(0);
+  }
+}
+
+// out = (Tout) a; zero (may be null) is zeroed.
+template <typename Tin, typename Tout, int V>
+__global__ void k_convert_zero(const Tin *__restrict__ a, Tout *__restrict__ out, Tout *__restrict__ zero, long long n) {
+  pdl_enter();
+  SMF_PACK_LOOP(j, n, V) {
+    const Pack<Tin, V> A = ldp<V>(a, j);
+    Pack<Tout, V> O, Z;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      O.v[k] = (Tout)A.v[k];
+      Z.v[k] = Tout(0);
+    }
+    stp<V>(out, j, O);
+    if (zero) stp<V>(zero, j, Z);
+  }
+  SMF_TAIL_LOOP(i, n, V) {
+    out[i] = (Tout)a[i];
+    if (zero) zero[i] = Tout(0);
   }
 }
 
 // y_i = x_i on constrained velocity DoFs (identity rows of K).
 template <typename T>
 __global__ void k_identity_rows(const LevelDesc<T> L, const T *__restrict__ x, T *__restrict__ y) {
+  pdl_enter();
   SMF_GRID_LOOP(i, L.n_u) {
     long long node = i % L.nv;
     int gx = (int)(node % L.N[0]);
@@ -104,6 +261,7 @@ __global__ void k_identity_rows(const LevelDesc<T> L, const T *__restrict__ x, T
 // zero constrained velocity entries
 template <typename T>
 __global__ void k_zero_constrained(const LevelDesc<T> L, T *__restrict__ y) {
+  pdl_enter();
   SMF_GRID_LOOP(i, L.n_u) {
     long long node = i % L.nv;
     int gx = (int)(node % L.N[0]);
@@ -117,6 +275,7 @@ __global__ void k_zero_constrained(const LevelDesc<T> L, T *__restrict__ y) {
 // D_A over the full velocity vector from the scalar per-node diagonal; 1 on constrained DoFs.
 template <typename T>
 __global__ void k_expand_diag(const LevelDesc<T> L, const T *__restrict__ dAs, T *__restrict__ DA) {
+  pdl_enter();
   SMF_GRID_LOOP(i, L.n_u) {
     long long node = i % L.nv;
     int gx = (int)(node % L.N[0]);
@@ -129,11 +288,13 @@ __global__ void k_expand_diag(const LevelDesc<T> L, const T *__restrict__ dAs, T
 
 template <typename T>
 __global__ void k_reciprocal(const T *__restrict__ a, T *__restrict__ out, long long n) {
+  pdl_enter();
   SMF_GRID_LOOP(i, n) out[i] = T(1) / a[i];
 }
 
 template <typename T>
 __global__ void k_rsqrt(const T *__restrict__ a, T *__restrict__ out, long long n) {
+  pdl_enter();
   SMF_GRID_LOOP(i, n) out[i] = T(1) / sqrt(a[i]);
 }
 

@@ -218,3 +218,34 @@ def test_zero_rhs_returns_zero():
     b = torch.zeros(S.size(), dtype=torch.float64, device="cuda")
     x, its, rel = S.solve(b)
     assert its == 0 and rel == 0.0 and torch.count_nonzero(x).item() == 0
+
+
+def test_point_and_column_kernels_agree(tmp_path):
+    # The 3D operator runs in the column kernel by default; STOKES_GENERIC_KERNEL=1 selects the
+    # point-per-thread kernel.  Both must give the same FP64 result to rounding.
+    import subprocess
+    import sys
+    import os
+    case = CASES["3d_q2_pert"]
+    H = oracle_hierarchy(case)
+    lev = H.levels[-1]
+    x = random_full(lev, 99)
+    np.save(tmp_path / "x.npy", x)
+    code = (
+        "import sys, numpy as np, torch; sys.path.insert(0, %r); sys.path.insert(0, %r)\n"
+        "from parity_cases import CASES, gpu_solver\n"
+        "S = gpu_solver(CASES['3d_q2_pert'])\n"
+        "x = torch.as_tensor(np.load(%r), device='cuda')\n"
+        "np.save(%r, S.vmult(x).cpu().numpy())\n"
+        "np.save(%r, S.vmult(x.float()).double().cpu().numpy())\n"
+    ) % (os.path.dirname(os.path.dirname(os.path.abspath(__file__))), os.path.dirname(os.path.abspath(__file__)),
+         str(tmp_path / "x.npy"), str(tmp_path / "y64.npy"), str(tmp_path / "y32.npy"))
+    env = dict(os.environ, STOKES_GENERIC_KERNEL="1")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    _, _, _, S = _pair("3d_q2_pert")
+    y_col = _n(S.vmult(_t(x)))
+    y_pt = np.load(tmp_path / "y64.npy")
+    assert rel_err(y_col, y_pt) < 1e-13
+    y_col32 = _n(S.vmult(_t(x, torch.float32)))
+    assert rel_err(y_col32, np.load(tmp_path / "y32.npy")) < 2e-6
