@@ -31,11 +31,16 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "MDoF/s Stokes vmult; solve time/MDoF to 1e-8 residual, FP32-MG vs FP64-MG"
+# Smoother degrees (k_A, k_S) and smoothing steps m: the paper sweeps them for the best residual
+# reduction per second (Sec. 4.3.3, 4.5); on GB300 the sweep of `--smoother-sweep` puts
+# (k_A, k_S, m) = (1, 2, 2) first in time-to-1e-8 (the paper's 3D favourite (1, 1, 2) second).
 WL = dict(dim=3, k=2, n=(32, 32, 32), levels=5, amplitude=0.1, seed=0, gammas=(0.0, 1e2, 1e4), rtol=1e-8,
-          kA=3, kS=3, m=2, restart=30)
+          kA=1, kS=2, m=2, restart=30)
 WORKLOAD_NAME = ("3D generalized Stokes Q2-Q1, unit cube 32^3 hexes, smooth trilinear vertex perturbation "
                  "0.1h (seed 0), 5 levels, mu=rho=1, gamma in {0,1e2,1e4}, FGMRES(30)+FP32 V-cycle "
-                 "(kA=kS=3, m=2), rtol 1e-8")
+                 "(Chebyshev kA=1, kS=2, m=2), rtol 1e-8")
+SWEEP = [(3, 3, 2), (1, 1, 2), (2, 1, 2), (1, 2, 2), (2, 2, 1), (1, 1, 1), (3, 2, 1), (2, 2, 2), (0, 0, 4),
+         (1, 0, 2), (0, 1, 2)]
 L2_FLUSH_BYTES = 256 << 20
 FALLBACK_HBM_GBS = 6800.0
 
@@ -328,6 +333,11 @@ def run_ours(args):
     traffic = traffic_record(kernel_source_sha())
     avg64 = S.time_apply(1, precision=64, reps=10)
 
+    # --- batched multi-mesh solves (16 unit-cube meshes of uneven size, seeded) -----------------
+    batched = run_batched(args) if not args.no_extras else None
+    # --- adjoint (32^3 Cartesian, mu = exp(g)): forward + adjoint solve + viscosity gradient ----
+    adjoint = run_adjoint() if not args.no_extras else None
+
     # --- end to end through the host-buffer C call ----------------------------------------------
     bh = [torch.empty(N, dtype=torch.float64).pin_memory() for _ in S32]
     xh = [torch.empty(N, dtype=torch.float64).pin_memory() for _ in S32]
@@ -372,6 +382,9 @@ def run_ours(args):
                 "d2h_bytes_per_step": solves * N * 8},
         "gpu_launches": int(launches),
         "clocks": clk,
+        "launch_shapes_fp32": S32[0].launch_shapes(32),
+        "batched": batched,
+        "adjoint": adjoint,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
@@ -390,6 +403,121 @@ def run_ours(args):
         S.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_batched(args):
+    """16 independent Q2-Q1 solves on unit-cube meshes of 8^3..40^3 cells (seeded sizes, gamma in
+    {0, 1e3}, 4-mode Fourier forcing): one batched solve (one graph launch per FGMRES iteration
+    for all members) against the same members solved one after another."""
+    import torch
+    import workloads as W
+    from paper_2205_15770_gb300 import StokesBatch
+    recipe = W.batch_meshes(16, seed=0)
+    members = [dict(dim=3, n=(r["n"],) * 3, n_levels=r["levels"], gamma_rho=r["gamma"]) for r in recipe]
+    Bt = StokesBatch(members, kA=WL["kA"], kS=WL["kS"], m=WL["m"], restart=WL["restart"])
+    bs = []
+    for r, mv in zip(recipe, Bt.members):
+        f = torch.as_tensor(W.fourier_forcing(3, 2, (r["n"],) * 3, seed=r["forcing_seed"]).reshape(-1), device="cuda")
+        bs.append(mv.mass_rhs(f))
+    xs = [torch.zeros_like(b) for b in bs]
+    dofs_total = sum(int(b.numel()) for b in bs)
+    for _ in range(2):
+        for x in xs:
+            x.zero_()
+        Bt.solve(bs, xs, rtol=WL["rtol"])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record()
+    for _ in range(reps):
+        for x in xs:
+            x.zero_()
+        _, its, rels = Bt.solve(bs, xs, rtol=WL["rtol"])
+    e1.record()
+    e1.synchronize()
+    batch_ms = e0.elapsed_time(e1) / reps
+    e0.record()
+    for _ in range(reps):
+        for mv, b, x in zip(Bt.members, bs, xs):
+            x.zero_()
+            mv.solve(b, x, rtol=WL["rtol"])
+    e1.record()
+    e1.synchronize()
+    seq_ms = e0.elapsed_time(e1) / reps
+    Bt.close()
+    return {"meshes": len(members), "sizes": [r["n"] for r in recipe], "gammas": [r["gamma"] for r in recipe],
+            "dofs_total": dofs_total, "batch_ms": round(batch_ms, 3), "sequential_ms": round(seq_ms, 3),
+            "speedup_vs_sequential": round(seq_ms / batch_ms, 3),
+            "batch_mdof_s": round(dofs_total / (batch_ms / 1e3) / 1e6, 3), "iterations": its,
+            "max_rel_residual": max(rels)}
+
+
+def run_adjoint():
+    """Forward + adjoint FP64-MG solves and the per-cell viscosity gradient on 32^3 Cartesian hexes,
+    mu_c = exp(g_c) (seeded Gaussian field, correlation length 0.2), J = 0.5 ||u - u_obs||^2."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2205_15770_gb300 import StokesMG, stokes_solve_fn
+    n = 32
+    mu = np.exp(W.gaussian_field_cells(n, seed=0)).reshape(-1)
+    mu_obs = np.exp(W.gaussian_field_cells(n, seed=1)).reshape(-1)
+    f = torch.as_tensor(W.fourier_forcing(3, 2, (n,) * 3, seed=0).reshape(-1), device="cuda")
+    S = StokesMG(dim=3, n=(n,) * 3, n_levels=5, k=2, vcycle_fp32=False)
+    u_obs = stokes_solve_fn(S, torch.as_tensor(mu_obs, device="cuda"), f, 1e-10).detach()
+    nu = S.sizes()[0]
+    S.set_viscosity(mu)
+    b = S.mass_rhs(f)
+    x, _, _ = S.solve(b, rtol=1e-10)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    e[0].record()
+    x, it_f, _ = S.solve(b, rtol=1e-10)
+    e[1].record()
+    gx = torch.zeros_like(x)
+    gx[:nu] = x[:nu] - u_obs[:nu]
+    lam, it_a, _ = S.solve(gx, rtol=1e-10)
+    e[2].record()
+    gmu = S.cell_grad(x, lam)
+    gf = S.mass(lam[:nu].contiguous(), full_rows=True)
+    e[3].record()
+    e[3].synchronize()
+    S.close()
+    return {"mesh": "32^3 Cartesian, Q2-Q1, FP64 MG, rtol 1e-10", "forward_ms": round(e[0].elapsed_time(e[1]), 3),
+            "adjoint_ms": round(e[1].elapsed_time(e[2]), 3), "gradients_ms": round(e[2].elapsed_time(e[3]), 3),
+            "iterations": [it_f, it_a], "max_abs_dJ_dmu": float(gmu.abs().max()),
+            "max_abs_dJ_df": float(gf.abs().max())}
+
+
+def run_smoother_sweep(args):
+    """Time-to-1e-8 of the workload's three FP32-MG solves for each (k_A, k_S, m) in SWEEP."""
+    import torch
+    from paper_2205_15770_gb300 import StokesMG
+    V = perturbed_vertices()
+    f = torch.as_tensor(forcing(), device="cuda")
+    for kA, kS, m in SWEEP:
+        tot, its = 0.0, []
+        for g in WL["gammas"]:
+            S = StokesMG(dim=3, n=WL["n"], n_levels=WL["levels"], k=WL["k"], vertices=V, gamma_rho=g, kA=kA, kS=kS,
+                         m=m)
+            b = S.mass_rhs(f)
+            x = torch.zeros_like(b)
+            for _ in range(2):
+                x.zero_()
+                S.solve(b, x, rtol=WL["rtol"], maxit=100)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(3):
+                x.zero_()
+                _, it, _ = S.solve(b, x, rtol=WL["rtol"], maxit=100)
+            e1.record()
+            e1.synchronize()
+            tot += e0.elapsed_time(e1) / 3
+            its.append(it)
+            S.close()
+        print(json.dumps({"kA": kA, "kS": kS, "m": m, "ms_per_solve": round(tot / len(WL["gammas"]), 3),
+                          "iterations": its}), flush=True)
 
 
 def run_kernel_only(args):
@@ -439,8 +567,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed steps by cudaProfilerStart/Stop (for ncu --profile-from-start off)")
+    ap.add_argument("--smoother-sweep", action="store_true",
+                    help="time-to-1e-8 of the workload for a list of (k_A, k_S, m); prints one JSON line each")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only launch the dominant kernel inside a profiler range (for ncu --set full)")
     ap.add_argument("--_oracle-sample", nargs=2, type=int, default=None, dest="oracle_sample")
@@ -450,7 +581,9 @@ def main():
         return
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")
-    if args.kernel_only:
+    if args.smoother_sweep:
+        run_smoother_sweep(args)
+    elif args.kernel_only:
         run_kernel_only(args)
     elif args.impl == "reference":
         run_reference(args)

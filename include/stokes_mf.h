@@ -45,6 +45,7 @@ typedef enum {
 } stokes_status;
 
 typedef struct stokes_ctx stokes_ctx;
+typedef struct stokes_batch stokes_batch;
 
 /* Mesh of the finest level.  vertices (HOST, nullable): (n+1)^d vertex coordinates,
  * x fastest, coordinates interleaved ((n_z+1)(n_y+1)(n_x+1) x d doubles); coarse
@@ -169,6 +170,36 @@ int stokes_get_diagonals(stokes_ctx *ctx, int level, double *DA, double *DS, voi
  * Synchronises the stream. */
 int stokes_time_apply(stokes_ctx *ctx, int level, int precision, int blocks, int reps, double *avg_ms,
                       void *stream);
+
+/* Batched solves of independent meshes (no counterpart in the paper; a layer on its method).
+ * stokes_setup_batch builds one context per mesh (meshes[i], k[i], mu[i], gamma_rho[i], shared
+ * opts; every mesh with its own hierarchy and coarse level).  Synchronises the stream. */
+int stokes_setup_batch(int n_meshes, const stokes_mesh *meshes, const int *k, const double *mu,
+                       const double *gamma_rho, const stokes_opts *opts, void *stream,
+                       stokes_batch **out);
+
+/* The context of batch member `mesh` (owned by the batch; for sizes, right-hand sides, vmult). */
+int stokes_batch_context(stokes_batch *batch, int mesh, stokes_ctx **ctx);
+
+/* Solve every member: b[i], x[i] are device double vectors of member i (x[i] = initial guess
+ * in, solution out).  FP64 FGMRES of all members in lockstep; the FP32 cycles of one iteration of
+ * all members run as one CUDA-graph launch with one parallel branch per member.  iters,
+ * final_rel_res: HOST arrays of n_meshes entries (nullable).  Synchronises the stream.  Returns
+ * the first non-OK member status (STOKES_ENOTCONV / STOKES_EBREAKDOWN). */
+int stokes_solve_batch(stokes_batch *batch, const double *const *b, double *const *x, double rtol,
+                       int maxit, int *iters, double *final_rel_res, void *stream);
+
+const char *stokes_batch_last_error(const stokes_batch *batch);
+void stokes_destroy_batch(stokes_batch *batch);
+
+/* Launch shape of the 3D cell kernel that setup's autotuner chose for `level` and `precision`:
+ * 1 or 4 = column kernel with that many warps per CTA, -1 = point-per-thread kernel,
+ * 0 = not tuned (2D, or STOKES_NO_AUTOTUNE=1).  HOST output. */
+int stokes_get_launch_shape(const stokes_ctx *ctx, int level, int precision, int *shape);
+
+/* Override the launch shape of `level` / `precision` (values as above; 0 is not accepted).
+ * Captured cycle graphs of the context are dropped and recaptured on next use. */
+int stokes_set_launch_shape(stokes_ctx *ctx, int level, int precision, int shape);
 
 /* Number of kernel launches this context issued since setup (a counter kept by the
  * library for reporting; not thread-safe). */

@@ -17,7 +17,7 @@ import numpy as np
 
 from . import _lib as L
 
-__all__ = ["StokesMG", "StokesError", "ALL_FACES"]
+__all__ = ["StokesMG", "StokesBatch", "StokesError", "ALL_FACES", "stokes_solve_fn"]
 
 ALL_FACES = {2: 0xF, 3: 0x3F}
 BLOCK_A, BLOCK_BT, BLOCK_B = 1, 2, 4
@@ -273,9 +273,127 @@ class StokesMG:
                                                 self._stream()))
         return ms.value
 
+    def launch_shapes(self, precision=32):
+        """Autotuned 3D cell-kernel launch shape per level (warps per CTA, -1 = point kernel)."""
+        out = []
+        for l in range(self.n_levels):
+            v = C.c_int()
+            self._check(self._lib.stokes_get_launch_shape(self._ctx, l, precision, C.byref(v)))
+            out.append(v.value)
+        return out
+
+    def set_launch_shape(self, level, shape, precision=32):
+        """Override the autotuned launch shape (1 or 4 warps per CTA column kernel, -1 point kernel)."""
+        self._check(self._lib.stokes_set_launch_shape(self._ctx, level, precision, shape))
+
     @property
     def launch_count(self):
         return int(self._lib.stokes_launch_count(self._ctx))
+
+
+class StokesBatch:
+    """Independent meshes solved together (stokes_setup_batch / stokes_solve_batch).
+
+    members: list of dicts with keys dim, n, n_levels and optionally k, mu, gamma_rho,
+    vertices, lo, hi, dirichlet_faces.  Options (kA, kS, m, ...) are shared.
+    """
+
+    def __init__(self, members, kA=3, kS=3, m=2, cycle="V", schur_diag="loc", vcycle_fp32=True, restart=30,
+                 eig_iters=40, eig_safety=1.1, seed=0x5EED):
+        self._lib = L.load()
+        torch = _torch()
+        nm = len(members)
+        meshes = (L.StokesMesh * nm)()
+        self._keep = []
+        ks = (C.c_int * nm)()
+        mus = (C.c_double * nm)()
+        gs = (C.c_double * nm)()
+        for i, mb in enumerate(members):
+            ms = meshes[i]
+            dim = mb["dim"]
+            ms.dim = dim
+            nn = list(mb["n"]) + [1] * (3 - len(mb["n"]))
+            lo = mb.get("lo", (0.0, 0.0, 0.0))
+            hi = mb.get("hi", (1.0, 1.0, 1.0))
+            for a in range(3):
+                ms.n[a] = int(nn[a])
+                ms.lo[a] = float(lo[a])
+                ms.hi[a] = float(hi[a])
+            ms.n_levels = mb["n_levels"]
+            ms.dirichlet_faces = mb.get("dirichlet_faces", ALL_FACES[dim])
+            if mb.get("vertices") is not None:
+                v = np.ascontiguousarray(np.asarray(mb["vertices"], dtype=np.float64).reshape(-1))
+                self._keep.append(v)
+                ms.vertices = v.ctypes.data_as(C.POINTER(C.c_double))
+            ks[i] = mb.get("k", 2)
+            mus[i] = mb.get("mu", 1.0)
+            gs[i] = mb.get("gamma_rho", 0.0)
+        opts = L.StokesOpts()
+        self._lib.stokes_default_opts(C.byref(opts))
+        opts.kA, opts.kS, opts.m = kA, kS, m
+        opts.cycle = {"V": 0, "W": 1}[cycle]
+        opts.schur_diag = {"loc": 0, "p": 1}[schur_diag]
+        opts.vcycle_fp32 = 1 if vcycle_fp32 else 0
+        opts.gmres_restart = restart
+        opts.eig_iters = eig_iters
+        opts.eig_safety = eig_safety
+        opts.seed = seed
+        bt = C.c_void_p()
+        st = self._lib.stokes_setup_batch(nm, meshes, ks, mus, gs, C.byref(opts), StokesMG._stream(), C.byref(bt))
+        if st != 0:
+            raise StokesError(st, self._lib.stokes_global_last_error().decode())
+        self._bt = bt
+        self.n_meshes = nm
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.members = []
+        for i in range(nm):
+            ctx = C.c_void_p()
+            self._check(self._lib.stokes_batch_context(bt, i, C.byref(ctx)))
+            self.members.append(_MemberView(self._lib, ctx, members[i]["n_levels"], members[i]["dim"],
+                                            members[i]["n"], self.device))
+
+    def _check(self, st):
+        if st != 0:
+            raise StokesError(st, self._lib.stokes_batch_last_error(self._bt).decode())
+
+    def solve(self, bs, xs=None, rtol=1e-8, maxit=200):
+        """Solve all members; bs, xs: lists of float64 CUDA tensors.  Returns (xs, iterations, rel residuals)."""
+        torch = _torch()
+        xs = [torch.zeros_like(b) for b in bs] if xs is None else xs
+        nm = self.n_meshes
+        bp = (C.c_void_p * nm)(*[_ptr(b, torch.float64).value for b in bs])
+        xp = (C.c_void_p * nm)(*[_ptr(x, torch.float64).value for x in xs])
+        its = (C.c_int * nm)()
+        rel = (C.c_double * nm)()
+        self._check(self._lib.stokes_solve_batch(self._bt, bp, xp, float(rtol), int(maxit), its, rel,
+                                                 StokesMG._stream()))
+        return xs, list(its), list(rel)
+
+    def close(self):
+        if getattr(self, "_bt", None):
+            self._lib.stokes_destroy_batch(self._bt)
+            self._bt = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _MemberView(StokesMG):
+    """A batch member's context seen through the StokesMG interface (owned by the batch)."""
+
+    def __init__(self, lib, ctx, n_levels, dim, n, device):  # noqa: D401 - no setup here
+        self._lib = lib
+        self._ctx = ctx
+        self.n_levels = n_levels
+        self.dim = dim
+        self._n = tuple(int(v) for v in n[:dim])
+        self.device = device
+
+    def close(self):
+        self._ctx = None
 
 
 class StokesSolveFunction:

@@ -48,6 +48,15 @@ SIGNATURES = {
     "stokes_cell_grad": (C.c_int, [P, P, P, P, P]),
     "stokes_set_viscosity": (C.c_int, [P, C.POINTER(C.c_double), P]),
     "stokes_time_apply": (C.c_int, [P, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), P]),
+    "stokes_get_launch_shape": (C.c_int, [P, C.c_int, C.c_int, C.POINTER(C.c_int)]),
+    "stokes_setup_batch": (C.c_int, [C.c_int, C.POINTER(StokesMesh), C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double), C.POINTER(StokesOpts), P, C.POINTER(P)]),
+    "stokes_batch_context": (C.c_int, [P, C.c_int, C.POINTER(P)]),
+    "stokes_solve_batch": (C.c_int, [P, C.POINTER(P), C.POINTER(P), C.c_double, C.c_int, C.POINTER(C.c_int),
+                                     C.POINTER(C.c_double), P]),
+    "stokes_batch_last_error": (C.c_char_p, [P]),
+    "stokes_destroy_batch": (None, [P]),
+    "stokes_set_launch_shape": (C.c_int, [P, C.c_int, C.c_int, C.c_int]),
     "stokes_launch_count": (C.c_longlong, [P]),
     "stokes_last_error": (C.c_char_p, [P]),
     "stokes_global_last_error": (C.c_char_p, []),

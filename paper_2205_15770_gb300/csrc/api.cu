@@ -34,11 +34,11 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
 
 template <typename T>
 int launch_cell_apply(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, const T *u, const T *p, T *yu, T *yp,
-                      cudaStream_t s) {
+                      cudaStream_t s, int shape) {
   switch (L.k) {
-    case 2: return launch_cell_apply_k<2, T>(L, tab, mode, u, p, yu, yp, s);
-    case 3: return launch_cell_apply_k<3, T>(L, tab, mode, u, p, yu, yp, s);
-    default: return launch_cell_apply_k<4, T>(L, tab, mode, u, p, yu, yp, s);
+    case 2: return launch_cell_apply_k<2, T>(L, tab, mode, u, p, yu, yp, s, shape);
+    case 3: return launch_cell_apply_k<3, T>(L, tab, mode, u, p, yu, yp, s, shape);
+    default: return launch_cell_apply_k<4, T>(L, tab, mode, u, p, yu, yp, s, shape);
   }
 }
 template <>
@@ -68,6 +68,7 @@ __global__ void k_coarse_apply(const double *__restrict__ Kinv, int n0, const T 
 template <typename T>
 struct LevelRT {
   LevelDesc<T> d{};
+  int shape = 0;  // 3D cell-kernel launch shape chosen by the autotuner (see launch_cell_apply_k)
   T *DAinv = nullptr, *DSinv = nullptr;
   T *x = nullptr, *b = nullptr, *r = nullptr, *kx = nullptr;                   // full vectors
   T *tu = nullptr, *ru = nullptr, *uhat = nullptr, *cx = nullptr, *cd = nullptr, *ct = nullptr;  // velocity
@@ -238,7 +239,7 @@ struct Runner {
   // Cycle form: the outputs are already zero (work buffers are zeroed by the kernel that
   // consumes them, so the captured cycle contains kernels only).
   void apply_nz(int l, int mode, const T *u, const T *p, T *yu, T *yp) {
-    launch_cell_apply<T>(L[l].d, tab, mode, u, p, yu, yp, s);
+    launch_cell_apply<T>(L[l].d, tab, mode, u, p, yu, yp, s, L[l].shape);
     note();
   }
   void vmult(int l, const T *x, T *y, bool identity) {
@@ -563,6 +564,49 @@ static int finish(stokes_ctx *C, int st) {
   return STOKES_OK;
 }
 
+// Autotuner of the 3D cell-kernel launch shape, per level and precision: the velocity-block
+// apply is timed (CUDA events on the context stream) for the column kernel with 1 and 4
+// warps per CTA and for the point-per-thread kernel.  Candidates are interleaved over several
+// rounds and each keeps its best round, so clock ramps and one-off effects do not bias the
+// choice; the default shape (4 warps) is kept unless another is faster by more than 3 %.
+template <typename T>
+static int autotune_level(stokes_ctx *C, LevelRT<T> &R, const Tab1D<T> *tab) {
+  if (R.d.dim != 3) return STOKES_OK;
+  const int cands[3] = {4, 1, -1};
+  const int reps = sizeof(T) == 8 ? 3 : 20, rounds = 3;
+  cudaEvent_t e0, e1;
+  SMF_CUDA_OK(cudaEventCreate(&e0));
+  SMF_CUDA_OK(cudaEventCreate(&e1));
+  float best[3] = {1e30f, 1e30f, 1e30f};
+  for (int w = 0; w < 3; ++w)
+    for (int c : cands) {
+      R.shape = c;
+      launch_cell_apply<T>(R.d, tab, kApplyA, R.x, nullptr, R.r, nullptr, C->s, R.shape);
+    }
+  for (int round = 0; round < rounds; ++round)
+    for (int ci = 0; ci < 3; ++ci) {
+      R.shape = cands[ci];
+      cudaEventRecord(e0, C->s);
+      for (int r = 0; r < reps; ++r)
+        launch_cell_apply<T>(R.d, tab, kApplyA, R.x, nullptr, R.r, nullptr, C->s, R.shape);
+      cudaEventRecord(e1, C->s);
+      SMF_CUDA_OK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best[ci] = std::min(best[ci], ms);
+      C->launches += reps;
+    }
+  C->launches += 9;
+  int choice = 0;
+  for (int ci = 1; ci < 3; ++ci)
+    if (best[ci] < 0.97f * best[choice]) choice = ci;
+  R.shape = cands[choice];
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  SMF_CUDA_OK(cudaMemsetAsync(R.r, 0, (R.d.n_u + R.d.n_p) * sizeof(T), C->s));
+  return STOKES_OK;
+}
+
 static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho, const double *mu_cell,
                     const stokes_opts *opts, stokes_ctx *C) {
   const int dim = mesh->dim, nl = mesh->n_levels;
@@ -738,6 +782,17 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
     C->L32[l].d = f;
     if ((st = alloc_level_buffers(C, C->L64[l]))) return st;
     if ((st = alloc_level_buffers(C, C->L32[l]))) return st;
+  }
+
+  // launch-shape autotuning (STOKES_NO_AUTOTUNE=1 keeps the default shape)
+  {
+    const char *na = getenv("STOKES_NO_AUTOTUNE");
+    if (!(na && na[0] == '1')) {
+      for (int l = 0; l < nl; ++l) {
+        if ((st = autotune_level<double>(C, C->L64[l], C->tab64))) return st;
+        if ((st = autotune_level<float>(C, C->L32[l], C->tab32))) return st;
+      }
+    }
   }
 
   // Krylov / Lanczos work space
@@ -923,6 +978,277 @@ static int fgmres(stokes_ctx *C, const double *b, double *x, double rtol, int ma
   SMF_CUDA_OK(cudaStreamSynchronize(C->s));
   if (iters) *iters = it;
   if (final_rel) *final_rel = rel;
+  return status;
+}
+
+
+// ---- batched multi-mesh solves (layer on top of the paper's method) -------------------------
+// A batch owns one context per mesh.  One FP32 V-cycle of every mesh is captured into a single
+// CUDA graph with one parallel branch per mesh (each branch on that mesh's stream); the FP64
+// FGMRES iterations of all meshes advance in lockstep, each mesh's FP64 work on its own stream,
+// with one host synchronisation per iteration for the whole batch.
+struct BatchState {
+  stokes_ctx *C = nullptr;
+  const double *b = nullptr;
+  double *x = nullptr;
+  double bnorm = 0, beta0 = -1, rel = 1;
+  int it = 0, j = 0, status = STOKES_OK;
+  bool done = false, need_start = true, x_zero = false;
+  std::vector<double> H, cs, sn, g;
+  double *hhost = nullptr;  // pinned: h columns + norms
+};
+
+}  // namespace smf
+
+struct stokes_batch {
+  std::vector<stokes_ctx *> ctx;
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraphExec_t graph = nullptr;
+  long long graph_kernels = 0;
+  std::vector<double *> pinned;
+  std::string err;
+};
+
+namespace smf {
+
+static int batch_capture(stokes_batch *Bt) {
+  SMF_CUDA_OK(cudaStreamBeginCapture(Bt->s, cudaStreamCaptureModeThreadLocal));
+  SMF_CUDA_OK(cudaEventRecord(Bt->fork, Bt->s));
+  long long kernels = 0;
+  for (size_t i = 0; i < Bt->ctx.size(); ++i) {
+    stokes_ctx *C = Bt->ctx[i];
+    SMF_CUDA_OK(cudaStreamWaitEvent(C->s, Bt->fork, 0));
+    Runner<float> R(C);
+    const int top = C->nl - 1;
+    C->capturing = true;
+    C->cap_count = 0;
+    R.cycle(top, C->L32[top].x, C->L32[top].b, true);
+    C->capturing = false;
+    kernels += C->cap_count;
+    SMF_CUDA_OK(cudaEventRecord(Bt->join[i], C->s));
+    SMF_CUDA_OK(cudaStreamWaitEvent(Bt->s, Bt->join[i], 0));
+  }
+  cudaGraph_t graph;
+  SMF_CUDA_OK(cudaStreamEndCapture(Bt->s, &graph));
+  cudaError_t e = cudaGraphInstantiate(&Bt->graph, graph, 0);
+  cudaGraphDestroy(graph);
+  SMF_CUDA_OK(e);
+  Bt->graph_kernels = kernels;
+  return STOKES_OK;
+}
+
+// launch a device-side dot product into dev_out (no host sync)
+static void dot64_async(stokes_ctx *C, const double *a, const double *b, long long n, double *dev_out) {
+  k_mdot_partial<<<kRedBlocks, kVecThreads, 0, C->s>>>(a, n, 1, b, n, C->partial);
+  k_final_reduce<<<1, kVecThreads, 0, C->s>>>(C->partial, kRedBlocks, 1, dev_out);
+  C->launches += 2;
+}
+
+static int batch_solve(stokes_batch *Bt, const double *const *b, double *const *x, double rtol, int maxit, int *iters,
+                       double *final_rel) {
+  const int nm = (int)Bt->ctx.size();
+  std::vector<BatchState> S(nm);
+  for (int i = 0; i < nm; ++i) {
+    BatchState &st = S[i];
+    st.C = Bt->ctx[i];
+    st.b = b[i];
+    st.x = x[i];
+    const int m = st.C->restart;
+    st.H.assign((size_t)(m + 1) * m, 0.0);
+    st.cs.assign(m, 0.0);
+    st.sn.assign(m, 0.0);
+    st.g.assign(m + 1, 0.0);
+    st.hhost = Bt->pinned[i];
+    const int top = st.C->nl - 1;
+    const long long N = st.C->L64[top].d.n_u + st.C->L64[top].d.n_p;
+    dot64_async(st.C, st.b, st.b, N, st.C->scal);
+    dot64_async(st.C, st.x, st.x, N, st.C->scal + 1);
+    SMF_CUDA_OK(cudaMemcpyAsync(st.hhost, st.C->scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st.C->s));
+  }
+  for (int i = 0; i < nm; ++i) {
+    SMF_CUDA_OK(cudaStreamSynchronize(S[i].C->s));
+    S[i].bnorm = std::sqrt(S[i].hhost[0]);
+    S[i].x_zero = S[i].hhost[1] == 0.0;
+    if (S[i].bnorm == 0.0) {
+      const int top = S[i].C->nl - 1;
+      const long long N = S[i].C->L64[top].d.n_u + S[i].C->L64[top].d.n_p;
+      SMF_CUDA_OK(cudaMemsetAsync(S[i].x, 0, N * sizeof(double), S[i].C->s));
+      S[i].done = true;
+      S[i].rel = 0.0;
+    }
+  }
+  while (true) {
+    // (a) restart-cycle start: r = b - K x, beta = ||r||
+    bool any_start = false;
+    for (auto &st : S) {
+      if (st.done || !st.need_start) continue;
+      any_start = true;
+      stokes_ctx *C = st.C;
+      Runner<double> R64(C);
+      const int top = C->nl - 1;
+      const long long N = R64.nu(top) + R64.np(top);
+      if (st.x_zero) {
+        SMF_CUDA_OK(cudaMemcpyAsync(C->V, st.b, N * sizeof(double), cudaMemcpyDeviceToDevice, C->s));
+        st.x_zero = false;
+      } else {
+        R64.vmult(top, st.x, C->w, true);
+        R64.sub(st.b, C->w, C->V, N);
+      }
+      dot64_async(C, C->V, C->V, N, C->scal);
+      SMF_CUDA_OK(cudaMemcpyAsync(st.hhost, C->scal, sizeof(double), cudaMemcpyDeviceToHost, C->s));
+    }
+    if (any_start) {
+      for (auto &st : S) {
+        if (st.done || !st.need_start) continue;
+        SMF_CUDA_OK(cudaStreamSynchronize(st.C->s));
+        const double beta = std::sqrt(st.hhost[0]);
+        if (st.beta0 < 0) st.beta0 = beta;
+        st.rel = beta / st.bnorm;
+        st.need_start = false;
+        if (!std::isfinite(beta) || beta > 1e6 * st.beta0) {
+          st.status = STOKES_EBREAKDOWN;
+          st.done = true;
+        } else if (st.rel <= rtol) {
+          st.done = true;
+        } else if (st.it >= maxit) {
+          st.status = STOKES_ENOTCONV;
+          st.done = true;
+        } else {
+          stokes_ctx *C = st.C;
+          const int top = C->nl - 1;
+          const long long N = C->L64[top].d.n_u + C->L64[top].d.n_p;
+          k_scale<double><<<vec_blocks(N), kVecThreads, 0, C->s>>>(C->V, 1.0 / beta, C->V, N);
+          ++C->launches;
+          std::fill(st.H.begin(), st.H.end(), 0.0);
+          std::fill(st.g.begin(), st.g.end(), 0.0);
+          st.g[0] = beta;
+          st.j = 0;
+        }
+      }
+    }
+    int nactive = 0;
+    for (auto &st : S) nactive += st.done ? 0 : 1;
+    if (nactive == 0) break;
+    // (b) one Arnoldi step for every active mesh; the FP32 cycles of all meshes in one graph
+    for (auto &st : S) {
+      if (st.done) continue;
+      stokes_ctx *C = st.C;
+      const int top = C->nl - 1;
+      const long long N = C->L64[top].d.n_u + C->L64[top].d.n_p;
+      Runner<float> R32(C);
+      R32.vec(k_convert_zero<double, float, 1>, N, (const double *)(C->V + (long long)st.j * N), C->L32[top].b,
+              C->L32[top].x, N);
+    }
+    if (nactive == nm) {
+      if (!Bt->graph) {
+        int st = batch_capture(Bt);
+        if (st) return st;
+      }
+      // the batch stream waits for every member's input conversion before the graph starts
+      for (int i = 0; i < nm; ++i) {
+        SMF_CUDA_OK(cudaEventRecord(Bt->join[i], Bt->ctx[i]->s));
+        SMF_CUDA_OK(cudaStreamWaitEvent(Bt->s, Bt->join[i], 0));
+      }
+      SMF_CUDA_OK(cudaGraphLaunch(Bt->graph, Bt->s));
+      for (auto *C : Bt->ctx) C->launches += Bt->graph_kernels / nm;
+      SMF_CUDA_OK(cudaEventRecord(Bt->fork, Bt->s));
+      for (auto *C : Bt->ctx) SMF_CUDA_OK(cudaStreamWaitEvent(C->s, Bt->fork, 0));
+    } else {
+      for (auto &st : S) {
+        if (st.done) continue;
+        int e = Runner<float>(st.C).top_cycle(true);
+        if (e) return e;
+      }
+    }
+    for (auto &st : S) {
+      if (st.done) continue;
+      stokes_ctx *C = st.C;
+      Runner<double> R64(C);
+      Runner<float> R32(C);
+      const int top = C->nl - 1;
+      const long long N = R64.nu(top) + R64.np(top);
+      const int m = C->restart, j = st.j;
+      double *zj = C->Z + (long long)j * N;
+      R32.vec(k_convert_zero<float, double, 1>, N, (const float *)C->L32[top].x, zj, (double *)nullptr, N);
+      R64.vmult(top, zj, C->w, true);
+      const int nb = vec_blocks(N);
+      for (int pass = 0; pass < 2; ++pass) {
+        k_mdot_partial<<<kRedBlocks, kVecThreads, 0, C->s>>>(C->V, N, j + 1, C->w, N, C->partial);
+        k_final_reduce<<<j + 1, kVecThreads, 0, C->s>>>(C->partial, kRedBlocks, j + 1, C->hdev + pass * (m + 2));
+        k_maxpy<<<nb, kVecThreads, 0, C->s>>>(C->V, N, j + 1, C->hdev + pass * (m + 2), C->w, N, -1.0);
+        C->launches += 3;
+      }
+      k_mdot_partial<<<kRedBlocks, kVecThreads, 0, C->s>>>(C->w, N, 1, C->w, N, C->partial);
+      k_final_reduce<<<1, kVecThreads, 0, C->s>>>(C->partial, kRedBlocks, 1, C->hdev + 2 * (m + 2));
+      k_scale_by_inv_sqrt<<<nb, kVecThreads, 0, C->s>>>(C->w, C->hdev + 2 * (m + 2), C->V + (long long)(j + 1) * N, N);
+      C->launches += 3;
+      SMF_CUDA_OK(cudaMemcpyAsync(st.hhost, C->hdev, (2 * (m + 2) + 1) * sizeof(double), cudaMemcpyDeviceToHost, C->s));
+    }
+    for (auto &st : S) {
+      if (st.done) continue;
+      stokes_ctx *C = st.C;
+      SMF_CUDA_OK(cudaStreamSynchronize(C->s));
+      const int m = C->restart, j = st.j;
+      std::vector<double> &H = st.H;
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = st.hhost[i] + st.hhost[(m + 2) + i];
+      H[(size_t)(j + 1) * m + j] = std::sqrt(st.hhost[2 * (m + 2)]);
+      for (int i = 0; i < j; ++i) {
+        const double t = st.cs[i] * H[(size_t)i * m + j] + st.sn[i] * H[(size_t)(i + 1) * m + j];
+        H[(size_t)(i + 1) * m + j] = -st.sn[i] * H[(size_t)i * m + j] + st.cs[i] * H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = t;
+      }
+      const double den = std::hypot(H[(size_t)j * m + j], H[(size_t)(j + 1) * m + j]);
+      st.cs[j] = H[(size_t)j * m + j] / den;
+      st.sn[j] = H[(size_t)(j + 1) * m + j] / den;
+      H[(size_t)j * m + j] = den;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      st.g[j + 1] = -st.sn[j] * st.g[j];
+      st.g[j] = st.cs[j] * st.g[j];
+      ++st.it;
+      ++st.j;
+      const bool end_cycle = !std::isfinite(st.g[st.j]) || std::fabs(st.g[st.j]) <= rtol * st.bnorm ||
+                             st.it >= maxit || st.j == m;
+      if (end_cycle) {
+        const int jd = st.j;
+        std::vector<double> y(jd);
+        for (int i = jd - 1; i >= 0; --i) {
+          double sum = st.g[i];
+          for (int c = i + 1; c < jd; ++c) sum -= H[(size_t)i * m + c] * y[c];
+          y[i] = sum / H[(size_t)i * m + i];
+        }
+        const int top = C->nl - 1;
+        const long long N = C->L64[top].d.n_u + C->L64[top].d.n_p;
+        for (int i = 0; i < jd; ++i) st.hhost[i] = y[i];
+        SMF_CUDA_OK(cudaMemcpyAsync(C->hdev, st.hhost, jd * sizeof(double), cudaMemcpyHostToDevice, C->s));
+        k_maxpy<<<vec_blocks(N), kVecThreads, 0, C->s>>>(C->Z, N, jd, C->hdev, st.x, N, 1.0);
+        ++C->launches;
+        st.need_start = true;
+      }
+    }
+  }
+  for (int i = 0; i < nm; ++i) {
+    BatchState &st = S[i];
+    stokes_ctx *C = st.C;
+    const int top = C->nl - 1;
+    const long long n_u = C->L64[top].d.n_u, n_p = C->L64[top].d.n_p;
+    if (C->pker && st.status != STOKES_EBREAKDOWN && st.bnorm > 0) {
+      sum64(C, st.x + n_u, n_p, C->scal + 1);
+      k_add_scalar<double><<<vec_blocks(n_p), kVecThreads, 0, C->s>>>(st.x + n_u, C->scal + 1, -1.0 / (double)n_p,
+                                                                       n_p);
+      ++C->launches;
+    }
+  }
+  int status = STOKES_OK;
+  for (int i = 0; i < nm; ++i) {
+    SMF_CUDA_OK(cudaStreamSynchronize(S[i].C->s));
+    if (iters) iters[i] = S[i].it;
+    if (final_rel) final_rel[i] = S[i].rel;
+    if (S[i].status != STOKES_OK && status == STOKES_OK) status = S[i].status;
+  }
+  if (status == STOKES_ENOTCONV) set_error("a batch member reached maxit before rtol");
+  if (status == STOKES_EBREAKDOWN) set_error("FGMRES breakdown in a batch member");
   return status;
 }
 
@@ -1256,10 +1582,10 @@ int stokes_time_apply(stokes_ctx *C, int level, int precision, int blocks, int r
   for (int r = 0; r < reps; ++r) {
     if (precision == 64) {
       LevelRT<double> &R = C->L64[level];
-      launch_cell_apply<double>(R.d, C->tab64, blocks, R.x, R.x + R.d.n_u, R.r, R.r + R.d.n_u, C->s);
+      launch_cell_apply<double>(R.d, C->tab64, blocks, R.x, R.x + R.d.n_u, R.r, R.r + R.d.n_u, C->s, R.shape);
     } else {
       LevelRT<float> &R = C->L32[level];
-      launch_cell_apply<float>(R.d, C->tab32, blocks, R.x, R.x + R.d.n_u, R.r, R.r + R.d.n_u, C->s);
+      launch_cell_apply<float>(R.d, C->tab32, blocks, R.x, R.x + R.d.n_u, R.r, R.r + R.d.n_u, C->s, R.shape);
     }
     ++C->launches;
   }
@@ -1271,6 +1597,134 @@ int stokes_time_apply(stokes_ctx *C, int level, int precision, int blocks, int r
   cudaEventDestroy(e1);
   *avg_ms = (double)ms / reps;
   return finish(C, STOKES_OK);
+}
+
+int stokes_setup_batch(int n_meshes, const stokes_mesh *meshes, const int *k, const double *mu,
+                       const double *gamma_rho, const stokes_opts *opts, void *stream, stokes_batch **out) {
+  if (!out || n_meshes < 1 || !meshes || !k || !mu || !gamma_rho) {
+    set_error("invalid stokes_setup_batch arguments");
+    return STOKES_EINVAL;
+  }
+  *out = nullptr;
+  stokes_batch *Bt = new (std::nothrow) stokes_batch();
+  if (!Bt) {
+    set_error("host allocation failed");
+    return STOKES_ENOMEM;
+  }
+  for (int i = 0; i < n_meshes; ++i) {
+    stokes_ctx *C = nullptr;
+    const int st = stokes_setup(&meshes[i], k[i], mu[i], gamma_rho[i], nullptr, opts, stream, &C);
+    if (st != STOKES_OK) {
+      const std::string e = g_last_error;
+      stokes_destroy_batch(Bt);
+      set_error("batch member " + std::to_string(i) + ": " + e);
+      return st;
+    }
+    Bt->ctx.push_back(C);
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&Bt->s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&Bt->fork, cudaEventDisableTiming);
+  Bt->join.resize(n_meshes, nullptr);
+  for (int i = 0; i < n_meshes && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&Bt->join[i], cudaEventDisableTiming);
+  for (int i = 0; i < n_meshes && e == cudaSuccess; ++i) {
+    double *h = nullptr;
+    e = cudaMallocHost((void **)&h, (size_t)(3 * (Bt->ctx[i]->restart + 2) + 4) * sizeof(double));
+    Bt->pinned.push_back(h);
+  }
+  if (e != cudaSuccess) {
+    const int st = cuda_fail(e, "batch streams/events", __FILE__, __LINE__);
+    stokes_destroy_batch(Bt);
+    return st;
+  }
+  *out = Bt;
+  return STOKES_OK;
+}
+
+int stokes_batch_context(stokes_batch *Bt, int mesh, stokes_ctx **ctx) {
+  if (!Bt || !ctx || mesh < 0 || mesh >= (int)Bt->ctx.size()) {
+    set_error("invalid stokes_batch_context arguments");
+    return STOKES_EINVAL;
+  }
+  *ctx = Bt->ctx[mesh];
+  return STOKES_OK;
+}
+
+int stokes_solve_batch(stokes_batch *Bt, const double *const *b, double *const *x, double rtol, int maxit, int *iters,
+                       double *final_rel_res, void *stream) {
+  if (!Bt || !b || !x || !(rtol > 0) || maxit < 0) {
+    set_error("invalid stokes_solve_batch arguments");
+    if (Bt) Bt->err = g_last_error;
+    return STOKES_EINVAL;
+  }
+  for (size_t i = 0; i < Bt->ctx.size(); ++i)
+    if (!b[i] || !x[i]) {
+      set_error("null vector in stokes_solve_batch");
+      Bt->err = g_last_error;
+      return STOKES_EINVAL;
+    }
+  cudaStream_t user = (cudaStream_t)stream;
+  cudaEvent_t ev;
+  cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  cudaEventRecord(ev, user);
+  for (auto *C : Bt->ctx) cudaStreamWaitEvent(C->s, ev, 0);
+  int st = batch_solve(Bt, b, x, rtol, maxit, iters, final_rel_res);
+  for (auto *C : Bt->ctx) {
+    cudaEventRecord(C->ev_out, C->s);
+    cudaStreamWaitEvent(user, C->ev_out, 0);
+  }
+  cudaEventDestroy(ev);
+  if (st == STOKES_OK) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) st = cuda_fail(e, "batch kernels", __FILE__, __LINE__);
+  }
+  if (st != STOKES_OK) Bt->err = g_last_error;
+  return st;
+}
+
+const char *stokes_batch_last_error(const stokes_batch *Bt) { return Bt ? Bt->err.c_str() : g_last_error.c_str(); }
+
+void stokes_destroy_batch(stokes_batch *Bt) {
+  if (!Bt) return;
+  if (Bt->s) cudaStreamSynchronize(Bt->s);
+  if (Bt->graph) cudaGraphExecDestroy(Bt->graph);
+  for (auto *C : Bt->ctx) stokes_destroy(C);
+  for (auto *h : Bt->pinned)
+    if (h) cudaFreeHost(h);
+  for (auto e : Bt->join)
+    if (e) cudaEventDestroy(e);
+  if (Bt->fork) cudaEventDestroy(Bt->fork);
+  if (Bt->s) cudaStreamDestroy(Bt->s);
+  delete Bt;
+}
+
+int stokes_get_launch_shape(const stokes_ctx *C, int level, int precision, int *shape) {
+  if (!C || level < 0 || level >= C->nl || !shape || (precision != 32 && precision != 64)) {
+    set_error("invalid stokes_get_launch_shape arguments");
+    return STOKES_EINVAL;
+  }
+  *shape = precision == 64 ? C->L64[level].shape : C->L32[level].shape;
+  return STOKES_OK;
+}
+
+int stokes_set_launch_shape(stokes_ctx *C, int level, int precision, int shape) {
+  if (!C || level < 0 || level >= C->nl || (precision != 32 && precision != 64) ||
+      !(shape == 1 || shape == 4 || shape == -1)) {
+    set_error("invalid stokes_set_launch_shape arguments (shape in {1,4,-1})");
+    if (C) C->err = g_last_error;
+    return STOKES_EINVAL;
+  }
+  if (precision == 64)
+    C->L64[level].shape = shape;
+  else
+    C->L32[level].shape = shape;
+  // captured cycles baked the previous shape in: drop them so the next call recaptures
+  for (int i = 0; i < 2; ++i) {
+    if (C->g32[i].exec) cudaGraphExecDestroy(C->g32[i].exec);
+    if (C->g64[i].exec) cudaGraphExecDestroy(C->g64[i].exec);
+    C->g32[i].exec = nullptr;
+    C->g64[i].exec = nullptr;
+  }
+  return STOKES_OK;
 }
 
 long long stokes_launch_count(const stokes_ctx *C) { return C ? C->launches : 0; }

@@ -21,9 +21,8 @@ struct ColShape {
   static constexpr int NPR = K;               // pressure nodes per direction
   static constexpr int TPC = NV * NV;         // threads per cell
   static constexpr int CPW = 32 / TPC;        // cells per warp
-  static constexpr int WARPS = 4;             // warps per CTA
-  static constexpr int THREADS = 32 * WARPS;
-  static constexpr int CPB = CPW * WARPS;     // cells per CTA
+  static constexpr int MAX_WARPS = 4;         // warps per CTA: 1 or 4 (template parameter, autotuned)
+  static constexpr int MAX_THREADS = 32 * MAX_WARPS;
 };
 
 // Uniform 1D tables of this translation unit's degree (one copy per TU / degree).
@@ -73,8 +72,8 @@ __device__ __forceinline__ T sel3(int c, T a, T b, T d) {
   return c == 0 ? a : (c == 1 ? b : d);
 }
 
-template <int K, typename T, int MODE, bool CART>
-__global__ void __launch_bounds__(ColShape<K>::THREADS)
+template <int K, typename T, int MODE, bool CART, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS)
     stokes_cell_apply_col(const LevelDesc<T> L, const T *__restrict__ u, const T *__restrict__ p,
                           T *__restrict__ yu, T *__restrict__ yp) {
   pdl_enter();
@@ -94,7 +93,7 @@ __global__ void __launch_bounds__(ColShape<K>::THREADS)
   const int tl = lane - (lane / TPC) * TPC;
   const int ix = pad ? 0 : tl % NV, iy = pad ? 0 : tl / NV;
   const int base = sub * TPC;
-  const long long cell = ((long long)blockIdx.x * CS::WARPS + warp) * CS::CPW + sub;
+  const long long cell = ((long long)blockIdx.x * WARPS + warp) * CS::CPW + sub;
   const bool valid = !pad && cell < L.n_cells;
   int cx = 0, cy = 0, cz = 0;
   if (valid) {

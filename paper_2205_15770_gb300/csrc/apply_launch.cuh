@@ -28,30 +28,41 @@ static int launch_apply_dim(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode
   return 0;
 }
 
-template <int K, typename T, int MODE, bool CART>
-static int launch_col(const LevelDesc<T> &L, const T *u, const T *p, T *yu, T *yp, cudaStream_t s) {
+template <int K, typename T, int MODE, bool CART, int WARPS>
+static int launch_col_w(const LevelDesc<T> &L, const T *u, const T *p, T *yu, T *yp, cudaStream_t s) {
   using CS = ColShape<K>;
-  const long long blocks = (L.n_cells + CS::CPB - 1) / CS::CPB;
-  launch_kernel(stokes_cell_apply_col<K, T, MODE, CART>, dim3((unsigned)blocks), dim3(CS::THREADS), 0, s, L, u, p, yu,
-                yp);
+  const long long cpb = (long long)CS::CPW * WARPS;
+  const long long blocks = (L.n_cells + cpb - 1) / cpb;
+  launch_kernel(stokes_cell_apply_col<K, T, MODE, CART, WARPS>, dim3((unsigned)blocks), dim3(32 * WARPS), 0, s, L, u,
+                p, yu, yp);
   return 0;
 }
 
-template <int K, typename T, int MODE>
-static int launch_col_mode(const LevelDesc<T> &L, const T *u, const T *p, T *yu, T *yp, cudaStream_t s) {
-  return L.cartesian ? launch_col<K, T, MODE, true>(L, u, p, yu, yp, s) : launch_col<K, T, MODE, false>(L, u, p, yu, yp, s);
+template <int K, typename T, int MODE, bool CART>
+static int launch_col(const LevelDesc<T> &L, const T *u, const T *p, T *yu, T *yp, cudaStream_t s, int shape) {
+  return shape == 1 ? launch_col_w<K, T, MODE, CART, 1>(L, u, p, yu, yp, s)
+                    : launch_col_w<K, T, MODE, CART, 4>(L, u, p, yu, yp, s);
 }
 
+template <int K, typename T, int MODE>
+static int launch_col_mode(const LevelDesc<T> &L, const T *u, const T *p, T *yu, T *yp, cudaStream_t s, int shape) {
+  return L.cartesian ? launch_col<K, T, MODE, true>(L, u, p, yu, yp, s, shape)
+                     : launch_col<K, T, MODE, false>(L, u, p, yu, yp, s, shape);
+}
+
+// shape: 3D launch shape chosen by the autotuner (1 / 4 warps per CTA column kernel, -1 point
+// kernel, 0 default = column kernel with 4 warps).
 template <int K, typename T>
 int launch_cell_apply_k(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, const T *u, const T *p, T *yu, T *yp,
-                        cudaStream_t s) {
-  if (L.dim == 3 && !getenv_generic()) {
+                        cudaStream_t s, int shape) {
+  if (L.dim == 3 && !getenv_generic() && shape >= 0) {
     switch (mode) {
-      case kApplyA: return launch_col_mode<K, T, kApplyA>(L, u, p, yu, yp, s);
-      case kApplyBT: return launch_col_mode<K, T, kApplyBT>(L, u, p, yu, yp, s);
-      case kApplyB: return launch_col_mode<K, T, kApplyB>(L, u, p, yu, yp, s);
-      case kApplyA | kApplyBT: return launch_col_mode<K, T, kApplyA | kApplyBT>(L, u, p, yu, yp, s);
-      case kApplyA | kApplyBT | kApplyB: return launch_col_mode<K, T, kApplyA | kApplyBT | kApplyB>(L, u, p, yu, yp, s);
+      case kApplyA: return launch_col_mode<K, T, kApplyA>(L, u, p, yu, yp, s, shape);
+      case kApplyBT: return launch_col_mode<K, T, kApplyBT>(L, u, p, yu, yp, s, shape);
+      case kApplyB: return launch_col_mode<K, T, kApplyB>(L, u, p, yu, yp, s, shape);
+      case kApplyA | kApplyBT: return launch_col_mode<K, T, kApplyA | kApplyBT>(L, u, p, yu, yp, s, shape);
+      case kApplyA | kApplyBT | kApplyB:
+        return launch_col_mode<K, T, kApplyA | kApplyBT | kApplyB>(L, u, p, yu, yp, s, shape);
       default: break;
     }
   }
@@ -102,10 +113,11 @@ int launch_cell_diag_k(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dS
 #define SMF_INSTANTIATE_K(KK)                                                                                  \
   namespace smf {                                                                                              \
   template int launch_cell_apply_k<KK, float>(const LevelDesc<float> &, const Tab1D<float> *, int,             \
-                                               const float *, const float *, float *, float *, cudaStream_t);  \
+                                               const float *, const float *, float *, float *, cudaStream_t,   \
+                                               int);                                                           \
   template int launch_cell_apply_k<KK, double>(const LevelDesc<double> &, const Tab1D<double> *, int,          \
                                                 const double *, const double *, double *, double *,            \
-                                                cudaStream_t);                                                  \
+                                                cudaStream_t, int);                                             \
   template int launch_cell_diag_k<KK, double>(const LevelDesc<double> &, const Tab1D<double> *, double *,      \
                                                double *, double *, cudaStream_t);                              \
   template int upload_col_tables<KK>(const Tab1D<double> &, cudaStream_t);                                     \

@@ -14,12 +14,12 @@ double tridiag_max_eig(const std::vector<double> &a, const std::vector<double> &
 
 template <typename T>
 int launch_cell_apply(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, const T *u, const T *p, T *yu, T *yp,
-                      cudaStream_t s);
+                      cudaStream_t s, int shape);
 template <typename T>
 int launch_cell_diag(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dSloc, T *dMp, cudaStream_t s);
 template <int K, typename T>
 int launch_cell_apply_k(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, const T *u, const T *p, T *yu, T *yp,
-                        cudaStream_t s);
+                        cudaStream_t s, int shape);
 template <int K, typename T>
 int launch_cell_grad_k(const LevelDesc<T> &L, const Tab1D<T> *tab, const T *u, const T *lam, T *g, cudaStream_t s);
 template <int K>

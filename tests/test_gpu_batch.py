@@ -1,0 +1,80 @@
+"""Batched solves of independent meshes (one graph launch per iteration for all members) and the
+launch-shape autotuner, against single-mesh solves and the CPU oracle."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def test_batch_matches_single_solves_and_oracle_residuals():
+    from oracle.assemble import assemble, load_vector_nodal
+    from oracle.mesh import Hierarchy
+    from paper_2205_15770_gb300 import StokesBatch, StokesMG
+    members = [
+        dict(dim=3, n=(4, 4, 4), n_levels=2, gamma_rho=0.0),
+        dict(dim=3, n=(8, 8, 8), n_levels=3, gamma_rho=1e3),
+        dict(dim=3, n=(6, 6, 6), n_levels=2, gamma_rho=0.0),
+        dict(dim=2, n=(8, 8), n_levels=3, gamma_rho=10.0,
+             vertices=W.perturbed_vertices(2, (8, 8), seed=3)),
+    ]
+    Bt = StokesBatch(members, kA=2, kS=2, m=2)
+    bs, refs = [], []
+    for i, mb in enumerate(members):
+        f = W.fourier_forcing(mb["dim"], 2, mb["n"], seed=10 + i).reshape(-1)
+        V = mb.get("vertices")
+        H = Hierarchy(mb["dim"], 2, mb["n"], mb["n_levels"],
+                      V if V is not None else W.lattice_vertices(mb["dim"], mb["n"]))
+        lev = H.levels[-1]
+        ops = assemble(lev, 1.0, mb["gamma_rho"])
+        b = load_vector_nodal(lev, ops, f)
+        bs.append(torch.as_tensor(b, device="cuda"))
+        refs.append((lev, ops, b))
+    xs, its, rels = Bt.solve(bs, rtol=1e-10)
+    for i, mb in enumerate(members):
+        lev, ops, b = refs[i]
+        x = xs[i].cpu().numpy()
+        assert np.linalg.norm(b - ops["K"] @ x) <= 1.01e-10 * np.linalg.norm(b), i
+        S = StokesMG(dim=mb["dim"], n=mb["n"], n_levels=mb["n_levels"], gamma_rho=mb["gamma_rho"],
+                     vertices=mb.get("vertices"), kA=2, kS=2, m=2)
+        xs1, its1, _ = S.solve(bs[i], rtol=1e-10)
+        assert its[i] == its1, (i, its, its1)
+        assert np.abs(xs1.cpu().numpy() - x).max() <= 1e-8 * np.abs(x).max(), i
+
+
+def test_batch_zero_rhs_member():
+    from paper_2205_15770_gb300 import StokesBatch
+    members = [dict(dim=3, n=(4, 4, 4), n_levels=2), dict(dim=3, n=(4, 4, 4), n_levels=2, gamma_rho=5.0)]
+    Bt = StokesBatch(members)
+    N = Bt.members[0].size()
+    b0 = torch.zeros(N, dtype=torch.float64, device="cuda")
+    b1 = Bt.members[1].mass_rhs(torch.as_tensor(W.fourier_forcing(3, 2, (4, 4, 4), seed=1).reshape(-1),
+                                                device="cuda"))
+    xs, its, rels = Bt.solve([b0, b1], rtol=1e-9)
+    assert its[0] == 0 and rels[0] == 0.0 and torch.count_nonzero(xs[0]).item() == 0
+    assert rels[1] <= 1e-9 and its[1] > 0
+
+
+def test_autotuned_launch_shapes_are_valid():
+    from paper_2205_15770_gb300 import StokesMG
+    S = StokesMG(dim=3, n=(16, 16, 16), n_levels=4, k=2)
+    for prec in (32, 64):
+        shapes = S.launch_shapes(prec)
+        assert len(shapes) == 4 and all(s in (1, 4, -1) for s in shapes), shapes
+
+
+def test_every_launch_shape_gives_the_same_operator():
+    from paper_2205_15770_gb300 import StokesMG
+    V = W.perturbed_vertices(3, (8, 8, 8), seed=4)
+    S = StokesMG(dim=3, n=(8, 8, 8), n_levels=2, k=2, vertices=V, gamma_rho=3.0)
+    x = torch.as_tensor(W.random_vector(S.size(), 9), device="cuda")
+    ref = None
+    for shape in (4, 1, -1):
+        S.set_launch_shape(1, shape, precision=64)
+        y = S.vmult(x).cpu().numpy()
+        if ref is None:
+            ref = y
+        assert np.abs(y - ref).max() <= 1e-13 * np.abs(ref).max(), shape

@@ -24,6 +24,7 @@ __all__ = [
     "velocity_lattice",
     "gaussian_field_cells",
     "random_vector",
+    "batch_meshes",
 ]
 
 
@@ -146,3 +147,23 @@ def random_vector(size, seed, dtype=np.float64):
     """Uniform(-1, 1) entries, seeded."""
     rng = np.random.default_rng(seed)
     return rng.uniform(-1.0, 1.0, size=size).astype(dtype)
+
+
+def batch_meshes(count=16, seed=0, sizes=(8, 16, 24, 32, 40), gammas=(0.0, 1e3)):
+    """Seeded recipe of a batch of independent unit-cube meshes of uneven size.
+
+    Each member: n cells per direction drawn from `sizes`, gamma drawn from `gammas`, a forcing
+    seed, and the number of levels that coarsens n by halving down to 2, 3 or 5 cells.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.choice(sizes))
+        g = float(rng.choice(gammas))
+        levels = 1
+        m = n
+        while m % 2 == 0 and m // 2 >= 2:
+            m //= 2
+            levels += 1
+        out.append({"n": n, "levels": levels, "coarse_n": m, "gamma": g, "forcing_seed": int(seed * 1000 + i)})
+    return out
