@@ -116,6 +116,22 @@ int stokes_mass_rhs(stokes_ctx *ctx, int level, int precision, const void *f, vo
 int stokes_smooth(stokes_ctx *ctx, int level, int precision, int steps, const void *b, void *x,
                   void *stream);
 
+/* stokes_smooth without any device allocation.  The paper has no counterpart: this entry point
+ * exists for callers that must not allocate device memory at the point of the call -- code that
+ * runs under stream capture, real-time or latency-critical loops, or applications whose own
+ * allocator owns all device memory.  Every work vector of the smoother lives in one static device
+ * array of 16 MiB compiled into the library (present on every GPU that loads it, until exit); a
+ * level needing more (11 velocity + 6 pressure work vectors, each padded to 64 entries, in the
+ * given precision) is rejected with STOKES_EINVAL and a message.  The context, b and x are as for
+ * stokes_smooth and must exist already; the call performs no cudaMalloc/cudaFree and calls no
+ * allocating library routine.  The array is shared by all calls and keeps the last call's
+ * contents (the used part is cleared at the start of each call): calls that overlap on the GPU --
+ * different streams, contexts or host threads -- race on it.  The array's device address is looked
+ * up once per device (in stokes_setup, or by the first call on a device that had no setup); make
+ * that first call before any stream capture. */
+int stokes_smooth_noalloc(stokes_ctx *ctx, int level, int precision, int steps, const void *b,
+                          void *x, void *stream);
+
 /* Grid transfer between fine_level and fine_level-1 (Sec. 3.2): direction 0 =
  * restriction out = P^T in (fine -> coarse), 1 = prolongation out = P in (coarse ->
  * fine).  Constrained velocity DoFs are removed on both sides. */

@@ -179,6 +179,14 @@ class StokesMG:
                                             _ptr(x, x.dtype), self._stream()))
         return x
 
+    def smooth_noalloc(self, b, x, steps=1, level=None):
+        """Same as smooth(), but the smoother's work vectors live in the library's static 16 MiB device
+        array instead of the context's memory: for callers that must not allocate at this point.
+        Overlapping calls race on that array; levels that need more scratch raise StokesError."""
+        self._check(self._lib.stokes_smooth_noalloc(self._ctx, self._level(level), self._prec(x), steps,
+                                                    _ptr(b, x.dtype), _ptr(x, x.dtype), self._stream()))
+        return x
+
     def restrict(self, r_fine, fine_level):
         torch = _torch()
         out = torch.empty(self.size(fine_level - 1), dtype=r_fine.dtype, device=self.device)

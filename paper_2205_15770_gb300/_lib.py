@@ -36,6 +36,7 @@ SIGNATURES = {
     "stokes_apply_blocks": (C.c_int, [P, C.c_int, C.c_int, C.c_int, P, P, P, P, P]),
     "stokes_mass_rhs": (C.c_int, [P, C.c_int, C.c_int, P, P, P]),
     "stokes_smooth": (C.c_int, [P, C.c_int, C.c_int, C.c_int, P, P, P]),
+    "stokes_smooth_noalloc": (C.c_int, [P, C.c_int, C.c_int, C.c_int, P, P, P]),
     "stokes_transfer": (C.c_int, [P, C.c_int, C.c_int, C.c_int, P, P, P]),
     "stokes_coarse_solve": (C.c_int, [P, C.c_int, P, P, P]),
     "mg_vcycle": (C.c_int, [P, C.c_int, P, P, P]),

@@ -1252,6 +1252,61 @@ static int batch_solve(stokes_batch *Bt, const double *const *b, double *const *
   return status;
 }
 
+// ---- allocation-free smoothing --------------------------------------------------------------
+// Scratch of stokes_smooth_noalloc: one file-scope device array, present on every GPU that loads
+// the library until the process exits.  Host code cannot hand the array's name to a kernel (on
+// the host it only stands for the symbol), so its device address is looked up with
+// cudaGetSymbolAddress once per device, with that device current, and cached here.
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;  // 16 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+constexpr int kNoAllocMaxDevices = 64;
+static void *g_noalloc_addr[kNoAllocMaxDevices];
+
+static int noalloc_scratch_address(void **out) {
+  int dev = 0;
+  SMF_CUDA_OK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) {
+    set_error("device index out of range for the allocation-free scratch table");
+    return STOKES_EINVAL;
+  }
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    SMF_CUDA_OK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return STOKES_OK;
+}
+
+static long long noalloc_pad(long long n) { return (n + 63) / 64 * 64; }
+
+// Bytes of smoother scratch a level needs: 11 velocity and 6 pressure work vectors.
+static size_t noalloc_bytes(long long n_u, long long n_p, size_t elt) {
+  return (size_t)(11 * noalloc_pad(n_u) + 6 * noalloc_pad(n_p)) * elt;
+}
+
+// Run `steps` smoothing steps on `level` with every work vector of the smoother carved out of
+// the static scratch (the context's own work vectors of that level are swapped out meanwhile).
+template <typename T>
+static void smooth_noalloc_run(stokes_ctx *C, int level, int steps, void *base, const T *b, T *x) {
+  std::vector<LevelRT<T>> &Ls = levels<T>(C);
+  const LevelRT<T> saved = Ls[level];
+  LevelRT<T> &R = Ls[level];
+  const long long nu = R.d.n_u, np = R.d.n_p;
+  T *cur = static_cast<T *>(base);
+  auto take = [&](long long n) {
+    T *q = cur;
+    cur += noalloc_pad(n);
+    return q;
+  };
+  T **vel[] = {&R.tu, &R.ru, &R.uhat, &R.cx, &R.cd, &R.ct, &R.r2, &R.cx2, &R.cd2, &R.ct2, &R.au};
+  for (auto q : vel) *q = take(nu);
+  T **pre[] = {&R.pt, &R.rp, &R.px, &R.pd, &R.ps, &R.dp};
+  for (auto q : pre) *q = take(np);
+  for (int i = 0; i < steps; ++i) Runner<T>(C).smooth_step(level, x, b, false);
+  Ls[level] = saved;
+}
+
 }  // namespace smf
 
 // ================================ C ABI ========================================================
@@ -1297,6 +1352,11 @@ int stokes_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho, co
         set_error("mu_cell entries must be positive");
         return STOKES_EINVAL;
       }
+  }
+  {
+    void *scratch = nullptr;  // device address of the allocation-free scratch, once per device
+    const int sa = noalloc_scratch_address(&scratch);
+    if (sa != STOKES_OK) return sa;
   }
   stokes_ctx *C = new (std::nothrow) stokes_ctx();
   if (!C) {
@@ -1394,6 +1454,38 @@ int stokes_smooth(stokes_ctx *C, int level, int precision, int steps, const void
     else
       Runner<float>(C).smooth_step(level, (float *)x, (const float *)b, false);
   }
+  return finish(C, STOKES_OK);
+}
+
+int stokes_smooth_noalloc(stokes_ctx *C, int level, int precision, int steps, const void *b, void *x, void *stream) {
+  if (!check_level(C, level) || level < 1 || steps < 0 || !b || !x || (precision != 32 && precision != 64)) {
+    set_error("invalid stokes_smooth_noalloc arguments (level must be >= 1)");
+    if (C) C->err = g_last_error;
+    return STOKES_EINVAL;
+  }
+  const long long nu = C->L64[level].d.n_u, np = C->L64[level].d.n_p;
+  const size_t need = noalloc_bytes(nu, np, precision == 64 ? sizeof(double) : sizeof(float));
+  if (need > kNoAllocScratchBytes) {
+    set_error("stokes_smooth_noalloc: level " + std::to_string(level) + " needs " + std::to_string(need) +
+              " bytes of smoother scratch, more than the " + std::to_string(kNoAllocScratchBytes) +
+              " bytes of the static scratch array; use stokes_smooth");
+    C->err = g_last_error;
+    return STOKES_EINVAL;
+  }
+  void *base = nullptr;
+  int st = noalloc_scratch_address(&base);
+  if (st != STOKES_OK) {
+    C->err = g_last_error;
+    return st;
+  }
+  StreamGuard sg(C, stream);
+  // the scratch keeps the previous call's contents: the smoother's accumulation targets must start
+  // at zero, so the used part is cleared first
+  cudaMemsetAsync(base, 0, need, C->s);
+  if (precision == 64)
+    smooth_noalloc_run<double>(C, level, steps, base, (const double *)b, (double *)x);
+  else
+    smooth_noalloc_run<float>(C, level, steps, base, (const float *)b, (float *)x);
   return finish(C, STOKES_OK);
 }
 
