@@ -170,6 +170,21 @@ int stokes_set_viscosity(stokes_ctx *ctx, const double *mu_cell, void *stream);
  * doubles (x fastest).  No counterpart in the paper (constant mu there). */
 int stokes_cell_grad(stokes_ctx *ctx, const double *u, const double *lam, double *dJ_dmu, void *stream);
 
+/* Lifting of inhomogeneous Dirichlet data on the finest level: b -= Z K_full u_D, where uD
+ * (device, n_u + n_p doubles) holds the Dirichlet values on constrained velocity DoFs (zero
+ * elsewhere) and K_full reads them (Z zeroes the rows of constrained DoFs).  Solving K x0 = b
+ * and adding uD gives the solution with u = u_D on the Dirichlet faces (Sec. 1: nonzero u_D in
+ * the paper's experiments). */
+int stokes_lift_rhs(stokes_ctx *ctx, const double *uD, double *b, void *stream);
+
+/* The paper's solver driver (Sec. 4.1): x <- MG(x, b) iterated as a stationary method with the
+ * FP64 cycle of opts (V or W), from the x given, until ||b - K x||_2 <= reduction ||b - K x0||_2
+ * or max_iter cycles.  HOST outputs (nullable): iters, res_history (max_iter + 1 entries: the
+ * residual norms r^0..r^iters), rate = q = (r^j / r^{j-3})^{1/3} at the last cycle j (NaN if
+ * j < 3).  STOKES_ENOTCONV if the reduction was not reached, STOKES_EBREAKDOWN on divergence. */
+int stokes_mg_iterate(stokes_ctx *ctx, const double *b, double *x, int max_iter, double reduction,
+                      int *iters, double *res_history, double *rate, void *stream);
+
 /* Smoother parameters of a level >= 1 (Algorithm 2): beta of D_A^-1 A and of
  * D_S^-1 S_tilde (safety factor included), sigma and tau (Lemma 1).  HOST outputs. */
 int stokes_get_level_params(const stokes_ctx *ctx, int level, double *beta_A, double *beta_S,

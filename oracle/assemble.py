@@ -142,3 +142,16 @@ def load_vector_nodal(level, ops, f_nodal):
     bu = np.concatenate([ops["Mv_full"] @ f[c] for c in range(level.dim)])
     bu[ops["umask"]] = 0.0
     return np.concatenate([bu, np.zeros(level.n_p)])
+
+
+def lift(level, ops, uD):
+    """Z K_full u_D: the operator applied to Dirichlet values without the constraint masking,
+    with the rows of constrained DoFs zeroed (inhomogeneous data by lifting: solve
+    K x0 = b - Z K_full u_D, then x = x0 + u_D)."""
+    d = level.dim
+    A_full = sp.block_diag([ops["As_full"]] * d, format="csr")
+    Bf = ops["B_full"]
+    K_full = sp.bmat([[A_full, Bf.T], [Bf, None]], format="csr")
+    y = K_full @ uD
+    y[level.constrained()] = 0.0
+    return y

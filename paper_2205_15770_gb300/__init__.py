@@ -260,6 +260,25 @@ class StokesMG:
                                                _ptr(g, torch.float64), self._stream()))
         return g
 
+    def lift_rhs(self, uD, b):
+        """b -= Z K_full u_D in place (inhomogeneous Dirichlet data by lifting); returns b."""
+        torch = _torch()
+        self._check(self._lib.stokes_lift_rhs(self._ctx, _ptr(uD, torch.float64), _ptr(b, torch.float64),
+                                              self._stream()))
+        return b
+
+    def mg_iterate(self, b, x=None, max_iter=15, reduction=1e-10):
+        """Stationary multigrid iteration (FP64 cycle); returns (x, iterations, residual history, rate q)."""
+        torch = _torch()
+        x = torch.zeros_like(b) if x is None else x
+        it, q = C.c_int(), C.c_double()
+        hist = (C.c_double * (max_iter + 1))()
+        st = self._lib.stokes_mg_iterate(self._ctx, _ptr(b, torch.float64), _ptr(x, torch.float64), int(max_iter),
+                                         float(reduction), C.byref(it), hist, C.byref(q), self._stream())
+        if st not in (0, 4):
+            self._check(st)
+        return x, it.value, list(hist)[: it.value + 1], q.value
+
     def level_params(self, level):
         vals = [C.c_double() for _ in range(4)]
         self._check(self._lib.stokes_get_level_params(self._ctx, level, *[C.byref(v) for v in vals]))

@@ -48,6 +48,9 @@ SIGNATURES = {
     "stokes_get_diagonals": (C.c_int, [P, C.c_int, P, P, P]),
     "stokes_cell_grad": (C.c_int, [P, P, P, P, P]),
     "stokes_set_viscosity": (C.c_int, [P, C.POINTER(C.c_double), P]),
+    "stokes_lift_rhs": (C.c_int, [P, P, P, P]),
+    "stokes_mg_iterate": (C.c_int, [P, P, P, C.c_int, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double), P]),
     "stokes_time_apply": (C.c_int, [P, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), P]),
     "stokes_get_launch_shape": (C.c_int, [P, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "stokes_setup_batch": (C.c_int, [C.c_int, C.POINTER(StokesMesh), C.POINTER(C.c_int), C.POINTER(C.c_double),

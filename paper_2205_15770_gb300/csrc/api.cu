@@ -1659,6 +1659,76 @@ int stokes_set_viscosity(stokes_ctx *C, const double *mu_cell, void *stream) {
   return STOKES_OK;
 }
 
+int stokes_lift_rhs(stokes_ctx *C, const double *uD, double *b, void *stream) {
+  if (!C || !uD || !b) {
+    set_error("invalid stokes_lift_rhs arguments");
+    if (C) C->err = g_last_error;
+    return STOKES_EINVAL;
+  }
+  StreamGuard sg(C, stream);
+  Runner<double> R(C);
+  const int top = C->nl - 1;
+  LevelRT<double> &L = C->L64[top];
+  const long long nu = L.d.n_u, n = nu + L.d.n_p;
+  // kx = [A B^T; B 0] u_D with the Dirichlet values read (rows of constrained DoFs stay zero)
+  R.zero(L.kx, n);
+  launch_cell_apply<double>(L.d, C->tab64, kApplyA | kApplyBT | kApplyB | kApplyUnmasked, uD, uD + nu, L.kx,
+                            L.kx + nu, C->s, -1);
+  ++C->launches;
+  R.vec(k_axpy<double>, n, b, -1.0, (const double *)L.kx, n);
+  R.zero(L.kx, n);
+  return finish(C, STOKES_OK);
+}
+
+int stokes_mg_iterate(stokes_ctx *C, const double *b, double *x, int max_iter, double reduction, int *iters,
+                      double *res_history, double *rate, void *stream) {
+  if (!C || !b || !x || max_iter < 0 || !(reduction > 0)) {
+    set_error("invalid stokes_mg_iterate arguments");
+    if (C) C->err = g_last_error;
+    return STOKES_EINVAL;
+  }
+  StreamGuard sg(C, stream);
+  Runner<double> R(C);
+  const int top = C->nl - 1;
+  LevelRT<double> &L = C->L64[top];
+  const long long N = L.d.n_u + L.d.n_p;
+  std::vector<double> res;
+  auto resnorm = [&](double *out) -> int {
+    R.vmult(top, x, C->w, true);
+    R.sub(b, C->w, C->w, N);
+    double r2;
+    int st = dot64(C, C->w, C->w, N, &r2);
+    *out = std::sqrt(r2);
+    return st;
+  };
+  double r;
+  int st = resnorm(&r);
+  if (st) return finish(C, st);
+  res.push_back(r);
+  int it = 0;
+  while (it < max_iter && res.back() > reduction * res[0]) {
+    // x <- MG(x, b), FP64 cycle (Algorithm 1 iterated as a stationary method, Sec. 4.1)
+    SMF_CUDA_OK(cudaMemcpyAsync(L.b, b, N * sizeof(double), cudaMemcpyDeviceToDevice, C->s));
+    SMF_CUDA_OK(cudaMemcpyAsync(L.x, x, N * sizeof(double), cudaMemcpyDeviceToDevice, C->s));
+    if ((st = R.top_cycle(false))) return finish(C, st);
+    SMF_CUDA_OK(cudaMemcpyAsync(x, L.x, N * sizeof(double), cudaMemcpyDeviceToDevice, C->s));
+    if ((st = resnorm(&r))) return finish(C, st);
+    res.push_back(r);
+    ++it;
+    if (!std::isfinite(r) || r > 1e6 * res[0]) {
+      set_error("stationary multigrid diverged");
+      C->err = g_last_error;
+      if (iters) *iters = it;
+      return STOKES_EBREAKDOWN;
+    }
+  }
+  if (iters) *iters = it;
+  if (res_history)
+    for (size_t i = 0; i < res.size(); ++i) res_history[i] = res[i];
+  if (rate) *rate = it >= 3 ? std::pow(res[it] / res[it - 3], 1.0 / 3.0) : std::nan("");
+  return finish(C, res.back() <= reduction * res[0] ? STOKES_OK : STOKES_ENOTCONV);
+}
+
 int stokes_time_apply(stokes_ctx *C, int level, int precision, int blocks, int reps, double *avg_ms, void *stream) {
   if (!check_level(C, level) || (precision != 32 && precision != 64) || blocks <= 0 || blocks > 15 || reps < 1 ||
       !avg_ms) {

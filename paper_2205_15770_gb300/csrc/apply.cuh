@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(CellShape<DIM, K>::THREADS)
     if (needU) {
       // b = Z M_v f reads every node of f (boundary values couple into free rows); its transpose
       // M_v Z reads the free nodes only and writes every row
-      bufA[t] = ((mode & kApplyMass) ? valid : vfree) ? u[c * L.nv + vidx] : T(0);
+      bufA[t] = ((mode & (kApplyMass | kApplyUnmasked)) ? valid : vfree) ? u[c * L.nv + vidx] : T(0);
       __syncthreads();
       if (DIM == 3) {
         bufB[t] = contract<0, NQ, NV, NV, NV, NV, false>(t, bufA, st->S);

@@ -18,6 +18,7 @@ enum ApplyMode : int {
   kApplyB = 4,     // yp += B u
   kApplyMass = 8,      // yu += Z M_v u (right-hand sides b = Z M_v f; every node of u is read)
   kApplyMassAll = 16,  // yu += M_v Z u (its transpose: free nodes of u read, every row written)
+  kApplyUnmasked = 32, // with A / BT / B: read u at constrained nodes too (K_full u_D for lifting)
 };
 
 // 1D tables of one velocity degree k on the reference interval, (k+1) Gauss points.
