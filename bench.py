@@ -520,6 +520,127 @@ def run_smoother_sweep(args):
                           "iterations": its}), flush=True)
 
 
+def cavity_lid(S, dim, n):
+    """Dirichlet vector of the lid-driven cavity: u = (1, 0[, 0]) on the top face (y = 1 in 2D,
+    z = 1 in 3D) without its edges, 0 on the other walls (Sec. 4.3 / 4.5)."""
+    import numpy as np
+    import torch
+    N = 2 * n + 1
+    nv = N ** dim
+    uD = np.zeros(S.size())
+    idx = np.arange(nv)
+    gx = idx % N
+    top = (idx // (N ** (dim - 1))) == N - 1
+    inner = (gx > 0) & (gx < N - 1)
+    if dim == 3:
+        gy = (idx // N) % N
+        inner &= (gy > 0) & (gy < N - 1)
+    uD[:nv][top & inner] = 1.0
+    return torch.as_tensor(uD, device="cuda")
+
+
+def run_paper_sweep(args):
+    """The paper's rate study on the GPU (Sec. 4.1 protocol, Sec. 4.3.3 / 4.5 settings): stationary
+    FP64 multigrid from x = 0 on the lid-driven cavity, 2D Q2-Q1 128^2 (148,739 DoFs, 7 levels) and
+    3D Q2-Q1 16^3 (112,724 DoFs, 4 levels), mu = 1, f = 0, local Schur diagonal; for every
+    (k_A, k_S) in {0..3}^2, m in {1, 2} and V / W cycles: q = (r^j / r^{j-3})^(1/3) after at most 15
+    cycles or a 1e-10 reduction, T_iter (ms per cycle) and T(0.1) = T_iter log(0.1) / log(q)."""
+    import math
+    import torch
+    from paper_2205_15770_gb300 import StokesMG
+    cases = [(2, 128, 7), (3, 16, 4)]
+    for dim, n, levels in cases:
+        for cyc in ("V", "W"):
+            for m in (1, 2):
+                for kA in range(4):
+                    for kS in range(4):
+                        S = StokesMG(dim=dim, n=(n,) * dim, n_levels=levels, k=2, kA=kA, kS=kS, m=m, cycle=cyc,
+                                     vcycle_fp32=False)
+                        uD = cavity_lid(S, dim, n)
+                        b = S.lift_rhs(uD, torch.zeros_like(uD))
+                        x = torch.zeros_like(b)
+                        S.mg_iterate(b, x.zero_(), max_iter=2, reduction=1e-10, allow_divergence=True)
+                        torch.cuda.synchronize()
+                        t0 = time.perf_counter()
+                        _, it, hist, q = S.mg_iterate(b, x.zero_(), max_iter=15, reduction=1e-10,
+                                                      allow_divergence=True)
+                        torch.cuda.synchronize()
+                        t_iter = (time.perf_counter() - t0) / max(it, 1) * 1e3
+                        ok = bool(hist) and 0 < q < 1
+                        t01 = t_iter * math.log(0.1) / math.log(q) if ok else None
+                        print(json.dumps({"dim": dim, "dofs": S.size(), "cycle": cyc, "m": m, "kA": kA, "kS": kS,
+                                          "iterations": it, "q": round(q, 4) if ok else None,
+                                          "converged": bool(hist) and hist[-1] <= 1e-10 * hist[0],
+                                          "T_iter_ms": round(t_iter, 3),
+                                          "T_0.1_ms": round(t01, 3) if t01 else None}), flush=True)
+                        S.close()
+
+
+def run_channel(args):
+    """Q_k-Q_{k-1} channel [0,4] x [0,1]^2 on 64^3 cells (aspect 4:1:1), parabolic inflow
+    u = 16 y(1-y) z(1-z) on x = 0, no-slip walls, do-nothing outflow at x = 4, mu = 1e-3, 6 levels.
+    For k = 2, 3, 4: vmult throughput (FP32 / FP64, MDoF/s) through stokes_vmult, the full-operator
+    cell kernel's duration, and its HBM fraction for the algorithmic bytes (x read once, y written
+    once); for k = 3 one FP32-MG FGMRES solve of the lifted problem to 1e-8."""
+    import torch
+    from paper_2205_15770_gb300 import StokesMG
+    peaks, src = measured_peaks()
+    hbm = (peaks or {}).get("hbm_gbs", FALLBACK_HBM_GBS)
+    out = {"workload": "channel [0,4]x[0,1]^2, 64^3 hexes, mu 1e-3, inflow 16y(1-y)z(1-z), do-nothing outflow",
+           "hbm_peak_gbs": hbm, "hbm_peak_source": src, "k": {}}
+    for k in (2, 3, 4):
+        S = StokesMG(dim=3, n=(64, 64, 64), n_levels=6, k=k, mu=1e-3, hi=(4.0, 1.0, 1.0), dirichlet_faces=0x3D,
+                     kA=WL["kA"], kS=WL["kS"], m=WL["m"])
+        N = S.size()
+        row = {"dofs": N}
+        for prec, dt in ((32, torch.float32), (64, torch.float64)):
+            x = torch.randn(N, dtype=dt, device="cuda")
+            y = torch.empty_like(x)
+            for _ in range(2):
+                S.vmult(x, y)
+            reps = 20 if prec == 32 else 4
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                S.vmult(x, y)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            kern = S.time_apply(7, precision=prec, reps=reps)
+            bytes_alg = 2 * N * (4 if prec == 32 else 8)
+            row[f"fp{prec}"] = {"vmult_ms": round(ms, 3), "mdof_s": round(N / (ms / 1e3) / 1e6, 1),
+                                "kernel_ms": round(kern, 3),
+                                "hbm_frac_of_kernel": round(bytes_alg / (kern / 1e3) / 1e9 / hbm, 4)}
+        if k == 3:
+            nodes = S.velocity_nodes()
+            nu, _ = S.sizes()
+            nv = nu // 3
+            uD = torch.zeros(N, dtype=torch.float64, device="cuda")
+            inflow = nodes[:, 0] == 0.0
+            yy, zz = nodes[:, 1], nodes[:, 2]
+            uD[:nv] = torch.where(inflow, 16 * yy * (1 - yy) * zz * (1 - zz), torch.zeros_like(yy))
+            b = S.lift_rhs(uD, torch.zeros_like(uD))
+            xs = torch.zeros_like(b)
+            S.solve(b, xs, rtol=WL["rtol"])
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            xs.zero_()
+            e0.record()
+            _, its, rel = S.solve(b, xs, rtol=WL["rtol"])
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            row["solve"] = {"ms": round(ms, 2), "iterations": its, "rel_residual": rel,
+                            "mdof_s": round(N / (ms / 1e3) / 1e6, 2),
+                            "max_u": float((xs[:nv] + uD[:nv]).max())}
+        out["k"][k] = row
+        S.close()
+        del S
+        torch.cuda.empty_cache()
+    print(json.dumps(out))
+
+
 def run_kernel_only(args):
     """Set up one FP32 context of the workload (gamma = 1e2) and launch the dominant kernel (A-block
     cell apply, FP32, finest level) a few times inside a cudaProfilerStart/Stop range; for ncu."""
@@ -570,6 +691,10 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed steps by cudaProfilerStart/Stop (for ncu --profile-from-start off)")
+    ap.add_argument("--channel", action="store_true",
+                    help="64^3 channel (Q2..Q4): vmult throughput, HBM fraction, Q3 solve of the lifted problem")
+    ap.add_argument("--paper-sweep", action="store_true",
+                    help="the paper's (k_A, k_S, m) rate study on the lid-driven cavities (stationary FP64 MG)")
     ap.add_argument("--smoother-sweep", action="store_true",
                     help="time-to-1e-8 of the workload for a list of (k_A, k_S, m); prints one JSON line each")
     ap.add_argument("--kernel-only", action="store_true",
@@ -581,7 +706,11 @@ def main():
         return
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")
-    if args.smoother_sweep:
+    if args.channel:
+        run_channel(args)
+    elif args.paper_sweep:
+        run_paper_sweep(args)
+    elif args.smoother_sweep:
         run_smoother_sweep(args)
     elif args.kernel_only:
         run_kernel_only(args)

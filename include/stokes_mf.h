@@ -170,6 +170,12 @@ int stokes_set_viscosity(stokes_ctx *ctx, const double *mu_cell, void *stream);
  * doubles (x fastest).  No counterpart in the paper (constant mu there). */
 int stokes_cell_grad(stokes_ctx *ctx, const double *u, const double *lam, double *dJ_dmu, void *stream);
 
+/* Physical coordinates of the velocity nodes of `level` (the Gauss-Lobatto nodes of every cell
+ * mapped by its bi/trilinear map), for building nodal data (forcing, Dirichlet values): xyz is a
+ * device array of nv x dim doubles, interleaved, in the lattice order of one velocity component
+ * (nv = n_u / dim). */
+int stokes_velocity_nodes(stokes_ctx *ctx, int level, double *xyz, void *stream);
+
 /* Lifting of inhomogeneous Dirichlet data on the finest level: b -= Z K_full u_D, where uD
  * (device, n_u + n_p doubles) holds the Dirichlet values on constrained velocity DoFs (zero
  * elsewhere) and K_full reads them (Z zeroes the rows of constrained DoFs).  Solving K x0 = b

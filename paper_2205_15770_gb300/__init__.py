@@ -260,6 +260,15 @@ class StokesMG:
                                                _ptr(g, torch.float64), self._stream()))
         return g
 
+    def velocity_nodes(self, level=None):
+        """(nv, dim) float64 CUDA tensor of the physical velocity-node coordinates of a level."""
+        torch = _torch()
+        lv = self._level(level)
+        nu, _ = self.sizes(lv)
+        xyz = torch.empty(nu, dtype=torch.float64, device=self.device)
+        self._check(self._lib.stokes_velocity_nodes(self._ctx, lv, _ptr(xyz, torch.float64), self._stream()))
+        return xyz.view(nu // self.dim, self.dim)
+
     def lift_rhs(self, uD, b):
         """b -= Z K_full u_D in place (inhomogeneous Dirichlet data by lifting); returns b."""
         torch = _torch()
@@ -267,14 +276,19 @@ class StokesMG:
                                               self._stream()))
         return b
 
-    def mg_iterate(self, b, x=None, max_iter=15, reduction=1e-10):
-        """Stationary multigrid iteration (FP64 cycle); returns (x, iterations, residual history, rate q)."""
+    def mg_iterate(self, b, x=None, max_iter=15, reduction=1e-10, allow_divergence=False):
+        """Stationary multigrid iteration (FP64 cycle); returns (x, iterations, residual history, rate q).
+
+        Not reaching the reduction in max_iter cycles is not an error (the paper's protocol); a
+        diverging iteration raises StokesError unless allow_divergence, in which case q = inf."""
         torch = _torch()
         x = torch.zeros_like(b) if x is None else x
         it, q = C.c_int(), C.c_double()
         hist = (C.c_double * (max_iter + 1))()
         st = self._lib.stokes_mg_iterate(self._ctx, _ptr(b, torch.float64), _ptr(x, torch.float64), int(max_iter),
                                          float(reduction), C.byref(it), hist, C.byref(q), self._stream())
+        if st == 5 and allow_divergence:
+            return x, it.value, [], float("inf")
         if st not in (0, 4):
             self._check(st)
         return x, it.value, list(hist)[: it.value + 1], q.value

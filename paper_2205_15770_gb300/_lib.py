@@ -48,6 +48,7 @@ SIGNATURES = {
     "stokes_get_diagonals": (C.c_int, [P, C.c_int, P, P, P]),
     "stokes_cell_grad": (C.c_int, [P, P, P, P, P]),
     "stokes_set_viscosity": (C.c_int, [P, C.POINTER(C.c_double), P]),
+    "stokes_velocity_nodes": (C.c_int, [P, C.c_int, P, P]),
     "stokes_lift_rhs": (C.c_int, [P, P, P, P]),
     "stokes_mg_iterate": (C.c_int, [P, P, P, C.c_int, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_double),
                                     C.POINTER(C.c_double), P]),

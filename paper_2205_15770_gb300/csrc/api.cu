@@ -64,6 +64,46 @@ __global__ void k_coarse_apply(const double *__restrict__ Kinv, int n0, const T 
   if (lane == 0) x[warp] = (T)s;
 }
 
+// x[i * stride] += s
+__global__ void k_add_strided(double *x, long long stride, double s, long long n) {
+  pdl_enter();
+  SMF_GRID_LOOP(i, n) x[i * stride] += s;
+}
+
+// Physical coordinates of the velocity nodes of a level: node (g_x, g_y[, g_z]) lies in cell
+// min(g / k, n - 1) at reference coordinate = Gauss-Lobatto node (g - k c); the cell map is the
+// bi/trilinear map through its vertices (or the Cartesian box).  out: nv x dim, interleaved.
+__global__ void k_velocity_nodes(const LevelDesc<double> L, const Tab1D<double> *__restrict__ tab, double *out) {
+  pdl_enter();
+  const int dim = L.dim, k = L.k;
+  SMF_GRID_LOOP(i, L.nv) {
+    const int g[3] = {(int)(i % L.N[0]), (int)((i / L.N[0]) % L.N[1]), dim == 3 ? (int)(i / ((long long)L.N[0] * L.N[1])) : 0};
+    int c[3] = {0, 0, 0};
+    double xi[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) {
+      c[a] = min(g[a] / k, L.n[a] - 1);
+      xi[a] = tab->nodes[g[a] - k * c[a]];
+    }
+    for (int a = 0; a < dim; ++a) {
+      double v = 0.0;
+      if (L.cartesian) {
+        v = (c[a] + xi[a]) * L.h[a];
+      } else {
+        for (int vtx = 0; vtx < (1 << dim); ++vtx) {
+          const int vb[3] = {vtx & 1, (vtx >> 1) & 1, (vtx >> 2) & 1};
+          double wgt = 1.0;
+          for (int d = 0; d < dim; ++d) wgt *= vb[d] ? xi[d] : 1.0 - xi[d];
+          const long long gv = dim == 3
+                                   ? ((long long)(c[2] + vb[2]) * (L.n[1] + 1) + (c[1] + vb[1])) * (L.n[0] + 1) + (c[0] + vb[0])
+                                   : (long long)(c[1] + vb[1]) * (L.n[0] + 1) + (c[0] + vb[0]);
+          v += wgt * L.vert[gv * dim + a];
+        }
+      }
+      out[i * dim + a] = v;
+    }
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 template <typename T>
 struct LevelRT {
@@ -1657,6 +1697,26 @@ int stokes_set_viscosity(stokes_ctx *C, const double *mu_cell, void *stream) {
   C->launches += launches;
   stokes_destroy(T);
   return STOKES_OK;
+}
+
+int stokes_velocity_nodes(stokes_ctx *C, int level, double *xyz, void *stream) {
+  if (!check_level(C, level) || !xyz) {
+    set_error("invalid stokes_velocity_nodes arguments");
+    if (C) C->err = g_last_error;
+    return STOKES_EINVAL;
+  }
+  StreamGuard sg(C, stream);
+  LevelDesc<double> d = C->L64[level].d;
+  // the Cartesian box offset is applied on the host side of the descriptor
+  Runner<double> R(C);
+  R.vec(k_velocity_nodes, d.nv, d, (const Tab1D<double> *)C->tab64, xyz);
+  if (d.cartesian) {
+    for (int a = 0; a < C->dim; ++a)
+      if (C->mesh.lo[a] != 0.0)
+        launch_kernel(k_add_strided, dim3(vec_blocks(d.nv)), dim3(kVecThreads), 0, C->s, xyz + a, (long long)C->dim,
+                      C->mesh.lo[a], d.nv);
+  }
+  return finish(C, STOKES_OK);
 }
 
 int stokes_lift_rhs(stokes_ctx *C, const double *uD, double *b, void *stream) {

@@ -31,6 +31,7 @@ struct Tab1D {
   T Pv[kMaxN1 * kMaxDeg];  // Pv[q*k+m]     = pressure basis (degree k-1) at Gauss points
   T w[kMaxN1];             // Gauss weights on [0,1]
   T x[kMaxN1];             // Gauss points on [0,1]
+  T nodes[kMaxN1];         // velocity Gauss-Lobatto nodes on [0,1]
 };
 
 // Transfer tables: for child h in {0,1}, fine local node a, coarse local node m:

@@ -92,6 +92,7 @@ void build_tables(int k, Tab1D<double> &t) {
   gauss_lobatto01(k - 1, xp);
   for (int i = 0; i < kMaxN1 * kMaxN1; ++i) t.S[i] = t.Sd[i] = t.D[i] = 0.0;
   for (int i = 0; i < kMaxN1 * kMaxDeg; ++i) t.Pv[i] = 0.0;
+  for (int m = 0; m < kMaxN1; ++m) t.nodes[m] = m < nv ? xv[m] : 0.0;
   for (int q = 0; q < nq; ++q) {
     t.x[q] = xg[q];
     t.w[q] = wg[q];
