@@ -230,9 +230,17 @@ const char *stokes_batch_last_error(const stokes_batch *batch);
 void stokes_destroy_batch(stokes_batch *batch);
 
 /* Launch shape of the 3D cell kernel that setup's autotuner chose for `level` and `precision`:
- * 1 or 4 = column kernel with that many warps per CTA, -1 = point-per-thread kernel,
- * 0 = not tuned (2D, or STOKES_NO_AUTOTUNE=1).  HOST output. */
+ * 1 or 4 = column kernel with that many warps per CTA, 3 = column kernel with the three velocity
+ * components on the three warps of a CTA (shorter per-warp chain for small levels), -1 =
+ * point-per-thread kernel, 0 = not tuned (2D, or STOKES_NO_AUTOTUNE=1).  HOST output. */
 int stokes_get_launch_shape(const stokes_ctx *ctx, int level, int precision, int *shape);
+
+/* 1 if smoothing on `level` / `precision` runs in the fused form (k_A = 1, 3D, column kernel: the
+ * Chebyshev-Jacobi and Uzawa vector updates of Sec. 3.3.1 evaluated inside the cell-kernel
+ * gathers, 5 + 3 k_S launches per step), 0 if in the unfused form (separate vector kernels).
+ * Setup times both forms per level and keeps the faster (STOKES_NO_AUTOTUNE=1: fused wherever
+ * eligible; STOKES_NO_FUSE=1: never).  Level 0 (direct solve) reports 0.  HOST output. */
+int stokes_get_smoother_fusion(stokes_ctx *ctx, int level, int precision, int *fused);
 
 /* Override the launch shape of `level` / `precision` (values as above; 0 is not accepted).
  * Captured cycle graphs of the context are dropped and recaptured on next use. */

@@ -315,7 +315,8 @@ class StokesMG:
         return ms.value
 
     def launch_shapes(self, precision=32):
-        """Autotuned 3D cell-kernel launch shape per level (warps per CTA, -1 = point kernel)."""
+        """Autotuned 3D cell-kernel launch shape per level (1 / 4 warps per CTA, 3 = components split over
+        3 warps, -1 = point kernel)."""
         out = []
         for l in range(self.n_levels):
             v = C.c_int()
@@ -323,8 +324,18 @@ class StokesMG:
             out.append(v.value)
         return out
 
+    def fused_levels(self, precision=32):
+        """Per level: True where smoothing runs in the fused form (stokes_get_smoother_fusion)."""
+        out = []
+        for l in range(self.n_levels):
+            v = C.c_int()
+            self._check(self._lib.stokes_get_smoother_fusion(self._ctx, l, precision, C.byref(v)))
+            out.append(bool(v.value))
+        return out
+
     def set_launch_shape(self, level, shape, precision=32):
-        """Override the autotuned launch shape (1 or 4 warps per CTA column kernel, -1 point kernel)."""
+        """Override the autotuned launch shape (1 or 4 warps per CTA column kernel, 3 component split,
+        -1 point kernel)."""
         self._check(self._lib.stokes_set_launch_shape(self._ctx, level, precision, shape))
 
     @property

@@ -41,6 +41,15 @@ int launch_cell_apply(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, cons
     default: return launch_cell_apply_k<4, T>(L, tab, mode, u, p, yu, yp, s, shape);
   }
 }
+template <typename T>
+int launch_cell_apply_fused(const LevelDesc<T> &L, int mode, const T *u, const T *p, T *yu, T *yp, cudaStream_t s,
+                            int shape, const Fuse<T> &F) {
+  switch (L.k) {
+    case 2: return launch_cell_apply_fused_k<2, T>(L, mode, u, p, yu, yp, s, shape, F);
+    case 3: return launch_cell_apply_fused_k<3, T>(L, mode, u, p, yu, yp, s, shape, F);
+    default: return launch_cell_apply_fused_k<4, T>(L, mode, u, p, yu, yp, s, shape, F);
+  }
+}
 template <>
 int launch_cell_diag<double>(const LevelDesc<double> &L, const Tab1D<double> *tab, double *a, double *b, double *c,
                              cudaStream_t s) {
@@ -109,6 +118,8 @@ template <typename T>
 struct LevelRT {
   LevelDesc<T> d{};
   int shape = 0;  // 3D cell-kernel launch shape chosen by the autotuner (see launch_cell_apply_k)
+  XferTabs<T> xf{};  // 1D transfer matrices between this level and the next coarser one
+  bool fuse = true;  // fused smoothing on this level (set by the setup's timing, when eligible)
   T *DAinv = nullptr, *DSinv = nullptr;
   T *x = nullptr, *b = nullptr, *r = nullptr, *kx = nullptr;                   // full vectors
   T *tu = nullptr, *ru = nullptr, *uhat = nullptr, *cx = nullptr, *cd = nullptr, *ct = nullptr;  // velocity
@@ -135,8 +146,6 @@ struct stokes_ctx {
   std::vector<double *> DA, DS;    // FP64 diagonals per level (device)
   Tab1D<double> *tab64 = nullptr;
   Tab1D<float> *tab32 = nullptr;
-  TransferTab<double> *tt64 = nullptr;
-  TransferTab<float> *tt32 = nullptr;
   std::vector<double> betaA, betaS;
   double sigma = 1, tau = 1;
   int n0 = 0;
@@ -151,6 +160,7 @@ struct stokes_ctx {
   bool capturing = false;
   long long cap_count = 0;
   bool use_graphs = true;
+  bool fuse = true;  // fused smoothing where eligible (STOKES_NO_FUSE=1: the unfused path)
   GraphSlot g32[2], g64[2];  // [x_zero]
   cudaStream_t s = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -188,12 +198,6 @@ template <>
 const Tab1D<double> *tables<double>(stokes_ctx *C) { return C->tab64; }
 template <>
 const Tab1D<float> *tables<float>(stokes_ctx *C) { return C->tab32; }
-template <typename T>
-const TransferTab<T> *ttables(stokes_ctx *C);
-template <>
-const TransferTab<double> *ttables<double>(stokes_ctx *C) { return C->tt64; }
-template <>
-const TransferTab<float> *ttables<float>(stokes_ctx *C) { return C->tt32; }
 template <typename T>
 GraphSlot &graph_slot(stokes_ctx *C, bool x_zero);
 template <>
@@ -240,9 +244,8 @@ struct Runner {
   cudaStream_t s;
   std::vector<LevelRT<T>> &L;
   const Tab1D<T> *tab;
-  const TransferTab<T> *tt;
   explicit Runner(stokes_ctx *c)
-      : C(c), s(c->s), L(levels<T>(c)), tab(tables<T>(c)), tt(ttables<T>(c)) {}
+      : C(c), s(c->s), L(levels<T>(c)), tab(tables<T>(c)) {}
 
   void note() {
     if (C->capturing)
@@ -361,17 +364,230 @@ struct Runner {
     launch_kernel(k_coarse_apply<T>, dim3((n0 * 32 + 255) / 256), dim3(256), 0, s, (const double *)C->Kinv, n0, b, x);
     note();
   }
-  void restrict_to(int lf, const T *in, T *out, T *zero_c) {
+  template <int W>
+  void restrict_w(int lf, const T *in, T *out, T *zero_c) {
     const long long n = nu(lf - 1) + np(lf - 1);
     if (n < 32768)
-      vec(k_restrict<T, 8>, n * 8, L[lf].d, L[lf - 1].d, tt, in, out, zero_c);
+      vec(k_restrict<T, W, 8>, n * 8, L[lf].d, L[lf - 1].d, L[lf].xf, in, out, zero_c);
     else
-      vec(k_restrict<T, 1>, n, L[lf].d, L[lf - 1].d, tt, in, out, zero_c);
+      vec(k_restrict<T, W, 1>, n, L[lf].d, L[lf - 1].d, L[lf].xf, in, out, zero_c);
   }
-  void prolongate(int lf, const T *in, T *out, int add) {
+  void restrict_to(int lf, const T *in, T *out, T *zero_c) {
+    switch (L[lf].d.k) {
+      case 2: restrict_w<9>(lf, in, out, zero_c); break;
+      case 3: restrict_w<13>(lf, in, out, zero_c); break;
+      default: restrict_w<17>(lf, in, out, zero_c); break;
+    }
+  }
+  void prolongate(int lf, const T *in, T *out, int add, T *z0 = nullptr, T *z1 = nullptr) {
     const long long n = nu(lf) + np(lf);
-    vec(k_prolongate<T>, n, L[lf].d, L[lf - 1].d, tt, in, out, add);
+    switch (L[lf].d.k) {
+      case 2: vec(k_prolongate<T, 9>, n, L[lf].d, L[lf - 1].d, L[lf].xf, in, out, add, z0, z1); break;
+      case 3: vec(k_prolongate<T, 13>, n, L[lf].d, L[lf - 1].d, L[lf].xf, in, out, add, z0, z1); break;
+      default: vec(k_prolongate<T, 17>, n, L[lf].d, L[lf - 1].d, L[lf].xf, in, out, add, z0, z1); break;
+    }
   }
+  // ---- fused smoothing: k_A = 1, 3D column kernel ------------------------------------------
+  // The Chebyshev-Jacobi and Uzawa vector updates of smooth_step are folded into the gathers of
+  // the cell-kernel applications (Fuse descriptors), so a step is 5 + 3 k_S launches instead of
+  // 10 + 6 k_S.  Work buffers: two velocity pairs (TU: B^T / A|B^T target, T: A target) used
+  // alternately, the stored u_hat, and the pressure targets pt, ps_1..ps_kS.  Every buffer
+  // accumulated into is zero when the launch that accumulates starts; the launch that last
+  // reads it is followed by one whose owners zero it.  A step ends with the update
+  // u = u_hat - A^-1_hat B^T dp still pending; it is folded into the next gather of u (next
+  // step, residual) or written by k_fused_finish.
+  bool fused_ok(int l) const { return fused_eligible(l) && L[l].fuse; }
+  bool fused_eligible(int l) const {
+    return C->fuse && C->o.kA == 1 && C->o.kS >= 1 && C->o.kS <= 4 && L[l].d.dim == 3 && L[l].shape >= 0;
+  }
+  T *pairU(int l, int pr) { return pr == 0 ? L[l].tu : L[l].cx; }
+  T *pairT(int l, int pr) { return pr == 0 ? L[l].ct : L[l].ct2; }
+  T *psb(int l, int j) {
+    LevelRT<T> &R = L[l];
+    T *b[4] = {R.ps, R.rp, R.px, R.pd};
+    return b[j];
+  }
+  void fapply(int l, int mode, const T *u, const T *p, T *yu, T *yp, const Fuse<T> &F) {
+    launch_cell_apply_fused<T>(L[l].d, mode, u, p, yu, yp, s, L[l].shape, F);
+    note();
+  }
+  // Velocity Chebyshev with k_A = 1 from zero on r: x_1 = c0 D^-1 r, t = A x_1,
+  // x_2 = D^-1 (ra r + ta t)  (Sec. 3.3.1 recurrence with one step).
+  struct VelCoef {
+    double c0, ra, ta;
+  };
+  VelCoef vcoef(int l) const {
+    const ChebCoef cc = cheb_coef(1, C->betaA[l]);
+    return {cc.c0, (1 + cc.c1[1]) * cc.c0 + cc.c2[1], -cc.c2[1]};
+  }
+  // Pressure Chebyshev with k_S steps from zero on r, in the basis {r, t_1, ..., t_kS} scaled by
+  // D_S^-1: x_j = D_S^-1 (X[j][0] r + sum_i X[j][i] t_i), t_j = S~ x_j, j = 1..k_S+1.
+  void pcoef(int l, double X[6][6]) const {
+    const int k = C->o.kS;
+    const ChebCoef cc = cheb_coef(k, C->betaS[l]);
+    double x[6] = {cc.c0, 0, 0, 0, 0, 0}, d[6] = {cc.c0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < 6; ++i) X[1][i] = x[i];
+    for (int j = 1; j <= k; ++j) {
+      for (int i = 0; i < 6; ++i) d[i] *= cc.c1[j];
+      d[0] += cc.c2[j];
+      d[j] -= cc.c2[j];
+      for (int i = 0; i < 6; ++i) x[i] += d[i];
+      for (int i = 0; i < 6; ++i) X[j + 1][i] = x[i];
+    }
+  }
+  // The pending last line of the previous step as the velocity input, stored into u.
+  void set_pending(Fuse<T> &F, int l, int pend, T *u) {
+    const VelCoef vc = vcoef(l);
+    const double sg = C->sigma;
+    F.vb = L[l].uhat;
+    F.vd = L[l].DAinv;
+    F.vv[0] = pairU(l, pend);
+    F.vc[0] = (T)(-sg * vc.ra);
+    F.vv[1] = pairT(l, pend);
+    F.vc[1] = (T)(-sg * vc.ta);
+    F.nv = 2;
+    F.vstore = u;
+  }
+  void set_pzero(Fuse<T> &F, int l) {
+    F.pzero[0] = L[l].pt;
+    for (int j = 0; j < C->o.kS; ++j) F.pzero[1 + j] = psb(l, j);
+  }
+  // One inexact Uzawa step (same arithmetic as smooth_step, fused).  pend: in, the pair holding
+  // the previous step's pending update (-1: none); out, this step's.
+  void fused_step(int l, T *x, const T *bv, bool x_zero, int &pend) {
+    LevelRT<T> &R = L[l];
+    const long long n_u = nu(l);
+    T *u = x, *p = x + n_u;
+    const T *f = bv, *g = bv + n_u;
+    const VelCoef vc = vcoef(l);
+    const double sg = C->sigma, tau = C->tau;
+    const int kS = C->o.kS;
+    double X[6][6] = {};
+    pcoef(l, X);
+    int pr = pend >= 0 ? 1 - pend : 0;
+    if (!x_zero) {  // TU = A u + B^T p
+      Fuse<T> F;
+      const T *uin = u;
+      if (pend >= 0) {
+        set_pending(F, l, pend, u);
+        uin = nullptr;
+      }
+      set_pzero(F, l);
+      fapply(l, kApplyA | kApplyBT, uin, p, pairU(l, pr), nullptr, F);
+    }
+    {  // T = A x_1, x_1 = c0 D_A^-1 (f - TU)
+      Fuse<T> F;
+      F.vd = R.DAinv;
+      F.vv[0] = f;
+      F.vc[0] = (T)vc.c0;
+      F.nv = 1;
+      if (!x_zero) {
+        F.vv[1] = pairU(l, pr);
+        F.vc[1] = (T)(-vc.c0);
+        F.nv = 2;
+      }
+      if (pend >= 0) {
+        F.vzero[0] = pairU(l, pend);
+        F.vzero[1] = pairT(l, pend);
+      }
+      fapply(l, kApplyA, nullptr, nullptr, pairT(l, pr), nullptr, F);
+    }
+    pend = -1;
+    {  // u_hat = u + sigma x_2 (stored); pt = B u_hat
+      Fuse<T> F;
+      F.vd = R.DAinv;
+      int j = 0;
+      F.vv[j] = f;
+      F.vc[j++] = (T)(sg * vc.ra);
+      if (!x_zero) {
+        F.vv[j] = pairU(l, pr);
+        F.vc[j++] = (T)(-sg * vc.ra);
+        F.vb = u;
+      }
+      F.vv[j] = pairT(l, pr);
+      F.vc[j++] = (T)(sg * vc.ta);
+      F.nv = j;
+      F.vstore = R.uhat;
+      fapply(l, kApplyB, nullptr, nullptr, nullptr, R.pt, F);
+    }
+    // dp = tau Cheb(S~, D_S, k_S)(pt - g); each S~ x_j = B A^-1_hat B^T x_j
+    for (int j = 1; j <= kS + 1; ++j) {
+      const bool last = j == kS + 1;
+      const int prev = pr;
+      pr = 1 - pr;
+      const double sc = last ? tau : 1.0;
+      {  // TU = B^T x_j  (last: B^T dp, and p += dp)
+        Fuse<T> F;
+        F.pd = R.DSinv;
+        F.pv[0] = R.pt;
+        F.pc[0] = (T)(sc * X[j][0]);
+        F.pv[1] = g;
+        F.pc[1] = (T)(-sc * X[j][0]);
+        for (int i = 1; i < j; ++i) {
+          F.pv[1 + i] = psb(l, i - 1);
+          F.pc[1 + i] = (T)(sc * X[j][i]);
+        }
+        F.np = j + 1;
+        F.vzero[0] = pairU(l, prev);
+        F.vzero[1] = pairT(l, prev);
+        if (last) F.pacc = p;
+        fapply(l, kApplyBT, nullptr, nullptr, pairU(l, pr), nullptr, F);
+      }
+      {  // T = A (c0 D_A^-1 TU)
+        Fuse<T> F;
+        F.vd = R.DAinv;
+        F.vv[0] = pairU(l, pr);
+        F.vc[0] = (T)vc.c0;
+        F.nv = 1;
+        fapply(l, kApplyA, nullptr, nullptr, pairT(l, pr), nullptr, F);
+      }
+      if (!last) {  // t_j = B (sigma D_A^-1 (ra TU + ta T))
+        Fuse<T> F;
+        F.vd = R.DAinv;
+        F.vv[0] = pairU(l, pr);
+        F.vc[0] = (T)(sg * vc.ra);
+        F.vv[1] = pairT(l, pr);
+        F.vc[1] = (T)(sg * vc.ta);
+        F.nv = 2;
+        fapply(l, kApplyB, nullptr, nullptr, nullptr, psb(l, j - 1), F);
+      }
+    }
+    pend = pr;
+  }
+  // kx = K x with the pending update folded in (x stored), pressure work vectors zeroed.
+  void fused_residual_apply(int l, T *x, int pend) {
+    LevelRT<T> &R = L[l];
+    Fuse<T> F;
+    const T *uin = x;
+    if (pend >= 0) {
+      set_pending(F, l, pend, x);
+      uin = nullptr;
+    }
+    set_pzero(F, l);
+    fapply(l, kApplyA | kApplyBT | kApplyB, uin, x + nu(l), R.kx, R.kx + nu(l), F);
+  }
+  void fused_finish(int l, T *x, int pend) {
+    LevelRT<T> &R = L[l];
+    const VelCoef vc = vcoef(l);
+    const double sg = C->sigma;
+    ZeroList<T> z{};
+    z.p[0] = R.pt;
+    for (int j = 0; j < C->o.kS; ++j) z.p[1 + j] = psb(l, j);
+    z.n = 1 + C->o.kS;
+    vec(k_fused_finish<T>, std::max(nu(l), np(l)), (const T *)R.uhat, (const T *)R.DAinv, pairU(l, pend),
+        pairT(l, pend), (T)(-sg * vc.ra), (T)(-sg * vc.ta), x, nu(l), z, np(l));
+  }
+  // `steps` smoothing steps on level l (x_zero: x is zero on entry).
+  void smooth(int l, T *x, const T *b, int steps, bool x_zero) {
+    if (!fused_ok(l)) {
+      for (int i = 0; i < steps; ++i) smooth_step(l, x, b, x_zero && i == 0);
+      return;
+    }
+    int pend = -1;
+    for (int i = 0; i < steps; ++i) fused_step(l, x, b, x_zero && i == 0, pend);
+    if (pend >= 0) fused_finish(l, x, pend);
+  }
+
   // Algorithm 1: MG(x_l, b_l) with gamma = 1 (V) or 2 (W); returns after the coarse solve on l = 0.
   void cycle(int l, T *x, const T *b, bool x_zero) {
     if (l == 0) {
@@ -380,18 +596,35 @@ struct Runner {
     }
     LevelRT<T> &R = L[l];
     const long long n = nu(l) + np(l);
-    for (int i = 0; i < C->o.m; ++i) smooth_step(l, x, b, x_zero && i == 0);
+    const bool fz = fused_ok(l);
+    int pend = -1;
+    for (int i = 0; i < C->o.m; ++i) {
+      if (fz)
+        fused_step(l, x, b, x_zero && i == 0, pend);
+      else
+        smooth_step(l, x, b, x_zero && i == 0);
+    }
     if (C->o.m == 0 && x_zero) {
       vec(k_convert_zero<T, T, 1>, n, b, R.r, (T *)nullptr, n);  // r = b - K 0
     } else {
-      apply_nz(l, kApplyA | kApplyBT | kApplyB, x, x + nu(l), R.kx, R.kx + nu(l));
+      if (fz)
+        fused_residual_apply(l, x, pend);
+      else
+        apply_nz(l, kApplyA | kApplyBT | kApplyB, x, x + nu(l), R.kx, R.kx + nu(l));
       vecp(k_residual<T, 1>, k_residual<T, VW>, {b, R.kx, R.r}, n, b, R.kx, R.r, n);
     }
     restrict_to(l, R.r, L[l - 1].b, L[l - 1].x);
     const int gam = C->o.cycle == 1 ? 2 : 1;
     for (int j = 0; j < gam; ++j) cycle(l - 1, L[l - 1].x, L[l - 1].b, j == 0);
-    prolongate(l, L[l - 1].x, x, 1);
-    for (int i = 0; i < C->o.m; ++i) smooth_step(l, x, b, false);
+    prolongate(l, L[l - 1].x, x, 1, pend >= 0 ? pairU(l, pend) : nullptr, pend >= 0 ? pairT(l, pend) : nullptr);
+    pend = -1;
+    for (int i = 0; i < C->o.m; ++i) {
+      if (fz)
+        fused_step(l, x, b, false, pend);
+      else
+        smooth_step(l, x, b, false);
+    }
+    if (pend >= 0) fused_finish(l, x, pend);
   }
   // One cycle on the finest level on the internal top-level buffers, replayed from a captured
   // graph (one graph per precision and per "x is zero on entry").
@@ -577,6 +810,95 @@ static int alloc_level_buffers(stokes_ctx *C, LevelRT<T> &R) {
   return STOKES_OK;
 }
 
+// 1D injection matrices of the level pair (fine F, coarse Cd) per space and axis with the
+// Dirichlet masks folded in (a node constrained along an axis gets an empty row / column), as
+// padded (node, weight) rows of width 4k + 1 (the support of a coarse vertex function: two coarse
+// cells, four fine ones) for the transfer kernels.
+template <typename T>
+static int build_xfer(stokes_ctx *C, const LevelDesc<T> &F, const LevelDesc<T> &Cd, const TransferTab<double> &tt,
+                      XferTabs<T> &X) {
+  const int k = F.k, W = 4 * k + 1, dim = F.dim;
+  X.W = W;
+  for (int sp = 0; sp < 2; ++sp) {
+    const int deg = sp == 0 ? k : k - 1;
+    const double *tab = sp == 0 ? tt.vel : tt.pre;
+    for (int a = 0; a < 3; ++a) {
+      const int Nf = sp == 0 ? F.N[a] : F.Pn[a], Nc = sp == 0 ? Cd.N[a] : Cd.Pn[a];
+      std::vector<std::vector<std::pair<int, double>>> rows(Nf), cols(Nc);
+      if (a >= dim) {
+        rows[0].push_back({0, 1.0});
+        cols[0].push_back({0, 1.0});
+      } else {
+        const int nc = Cd.n[a];
+        auto free_node = [&](int g, int N) {
+          if (sp != 0) return true;
+          if (((F.faces >> (2 * a)) & 1u) && g == 0) return false;
+          if (((F.faces >> (2 * a + 1)) & 1u) && g == N - 1) return false;
+          return true;
+        };
+        for (int g = 0; g < Nf; ++g) {
+          if (!free_node(g, Nf)) continue;
+          int f = g / deg;
+          if (f > 2 * nc - 1) f = 2 * nc - 1;
+          const int aa = g - deg * f, c = f >> 1, h = f & 1;
+          for (int m = 0; m <= deg; ++m) {
+            const int G = deg * c + m;
+            const double w = tab[(h * (deg + 1) + aa) * (deg + 1) + m];
+            if (w == 0.0 || !free_node(G, Nc)) continue;
+            rows[g].push_back({G, w});
+            cols[G].push_back({g, w});
+          }
+        }
+      }
+      for (int dir = 0; dir < 2; ++dir) {
+        const auto &R = dir == 0 ? cols : rows;  // dir 0: restriction rows (per coarse node)
+        const int n = (int)R.size();
+        std::vector<int> cnt(n), idx((size_t)n * W, 0);
+        std::vector<T> w((size_t)n * W, T(0));
+        for (int r = 0; r < n; ++r) {
+          if ((int)R[r].size() > W) {
+            set_error("transfer table row wider than 4k+1");
+            return STOKES_EINVAL;
+          }
+          cnt[r] = (int)R[r].size();
+          for (size_t e = 0; e < R[r].size(); ++e) {
+            idx[(size_t)r * W + e] = R[r][e].first;
+            w[(size_t)r * W + e] = (T)R[r][e].second;
+          }
+        }
+        int *dc, *di;
+        T *dw;
+        int st;
+        if ((st = dalloc(C, &dc, n))) return st;
+        if ((st = dalloc(C, &di, (long long)n * W))) return st;
+        if ((st = dalloc(C, &dw, (long long)n * W))) return st;
+        SMF_CUDA_OK(cudaMemcpyAsync(dc, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice, C->s));
+        SMF_CUDA_OK(cudaMemcpyAsync(di, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice, C->s));
+        SMF_CUDA_OK(cudaMemcpyAsync(dw, w.data(), w.size() * sizeof(T), cudaMemcpyHostToDevice, C->s));
+        SMF_CUDA_OK(cudaStreamSynchronize(C->s));  // host vectors go out of scope
+        Xfer1D<T> &x = dir == 0 ? X.r[sp][a] : X.p[sp][a];
+        x.cnt = dc;
+        x.idx = di;
+        x.w = dw;
+      }
+    }
+  }
+  return STOKES_OK;
+}
+
+// Zero every smoother work vector of a level (accumulation targets must start at zero; the
+// unfused and fused smoothers leave different state vectors behind).
+template <typename T>
+static int zero_level_work(stokes_ctx *C, LevelRT<T> &R) {
+  const long long nu = R.d.n_u, np = R.d.n_p;
+  T *vel[] = {R.tu, R.ru, R.uhat, R.cx, R.cd, R.ct, R.r2, R.cx2, R.cd2, R.ct2, R.au};
+  for (T *p : vel) SMF_CUDA_OK(cudaMemsetAsync(p, 0, (size_t)nu * sizeof(T), C->s));
+  T *pre[] = {R.pt, R.rp, R.px, R.pd, R.ps, R.dp};
+  for (T *p : pre) SMF_CUDA_OK(cudaMemsetAsync(p, 0, (size_t)np * sizeof(T), C->s));
+  SMF_CUDA_OK(cudaMemsetAsync(R.kx, 0, (size_t)(nu + np) * sizeof(T), C->s));
+  return STOKES_OK;
+}
+
 struct StreamGuard {
   stokes_ctx *C;
   cudaStream_t user;
@@ -606,25 +928,27 @@ static int finish(stokes_ctx *C, int st) {
 
 // Autotuner of the 3D cell-kernel launch shape, per level and precision: the velocity-block
 // apply is timed (CUDA events on the context stream) for the column kernel with 1 and 4
-// warps per CTA and for the point-per-thread kernel.  Candidates are interleaved over several
+// warps per CTA, the column kernel with the velocity components split over 3 warps, and the
+// point-per-thread kernel.  Candidates are interleaved over several
 // rounds and each keeps its best round, so clock ramps and one-off effects do not bias the
 // choice; the default shape (4 warps) is kept unless another is faster by more than 3 %.
 template <typename T>
 static int autotune_level(stokes_ctx *C, LevelRT<T> &R, const Tab1D<T> *tab) {
   if (R.d.dim != 3) return STOKES_OK;
-  const int cands[3] = {4, 1, -1};
+  constexpr int NC = 4;
+  const int cands[NC] = {4, 1, 3, -1};
   const int reps = sizeof(T) == 8 ? 3 : 20, rounds = 3;
   cudaEvent_t e0, e1;
   SMF_CUDA_OK(cudaEventCreate(&e0));
   SMF_CUDA_OK(cudaEventCreate(&e1));
-  float best[3] = {1e30f, 1e30f, 1e30f};
+  float best[NC] = {1e30f, 1e30f, 1e30f, 1e30f};
   for (int w = 0; w < 3; ++w)
     for (int c : cands) {
       R.shape = c;
       launch_cell_apply<T>(R.d, tab, kApplyA, R.x, nullptr, R.r, nullptr, C->s, R.shape);
     }
   for (int round = 0; round < rounds; ++round)
-    for (int ci = 0; ci < 3; ++ci) {
+    for (int ci = 0; ci < NC; ++ci) {
       R.shape = cands[ci];
       cudaEventRecord(e0, C->s);
       for (int r = 0; r < reps; ++r)
@@ -636,15 +960,48 @@ static int autotune_level(stokes_ctx *C, LevelRT<T> &R, const Tab1D<T> *tab) {
       best[ci] = std::min(best[ci], ms);
       C->launches += reps;
     }
-  C->launches += 9;
+  C->launches += 3 * NC;
   int choice = 0;
-  for (int ci = 1; ci < 3; ++ci)
+  for (int ci = 1; ci < NC; ++ci)
     if (best[ci] < 0.97f * best[choice]) choice = ci;
   R.shape = cands[choice];
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   SMF_CUDA_OK(cudaMemsetAsync(R.r, 0, (R.d.n_u + R.d.n_p) * sizeof(T), C->s));
   return STOKES_OK;
+}
+
+// Fused or unfused smoothing per level: where the fused smoother is eligible, one smoothing step
+// of each kind is timed (CUDA events on the context stream, interleaved rounds, best round kept)
+// on the level's own buffers; the fused form is kept unless the unfused one is faster by more
+// than 3 %.  The fused form saves launches and vector passes but makes every cell-kernel gather
+// read several vectors, which costs more than it saves on the largest levels.
+template <typename T>
+static int autotune_fusion(stokes_ctx *C, int l) {
+  Runner<T> R(C);
+  LevelRT<T> &L = R.L[l];
+  if (!R.fused_eligible(l)) return STOKES_OK;
+  const int reps = sizeof(T) == 8 ? 1 : 4, rounds = sizeof(T) == 8 ? 2 : 3;
+  cudaEvent_t e0, e1;
+  SMF_CUDA_OK(cudaEventCreate(&e0));
+  SMF_CUDA_OK(cudaEventCreate(&e1));
+  float best[2] = {1e30f, 1e30f};
+  for (int round = -1; round < rounds; ++round)  // round -1: warm-up
+    for (int f = 0; f < 2; ++f) {
+      L.fuse = f == 1;
+      cudaEventRecord(e0, C->s);
+      for (int r = 0; r < reps; ++r) R.smooth(l, L.x, L.b, 1, false);
+      cudaEventRecord(e1, C->s);
+      SMF_CUDA_OK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (round >= 0) best[f] = std::min(best[f], ms);
+    }
+  L.fuse = !(best[0] < 0.97f * best[1]);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  SMF_CUDA_OK(cudaMemsetAsync(L.x, 0, (L.d.n_u + L.d.n_p) * sizeof(T), C->s));
+  return zero_level_work(C, L);
 }
 
 static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho, const double *mu_cell,
@@ -676,6 +1033,8 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
   C->pker = faces == full;
   const char *env = getenv("STOKES_NO_GRAPHS");
   C->use_graphs = !(env && env[0] == '1');
+  const char *nofuse = getenv("STOKES_NO_FUSE");
+  C->fuse = !(nofuse && nofuse[0] == '1');
   C->restart = C->o.gmres_restart;
   int st;
   SMF_CUDA_OK(cudaStreamCreateWithFlags(&C->s, cudaStreamNonBlocking));
@@ -693,20 +1052,10 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
   }
   TransferTab<double> tt64;
   build_transfer(k, tt64);
-  TransferTab<float> tt32;
-  {
-    const double *src = reinterpret_cast<const double *>(&tt64);
-    float *dst = reinterpret_cast<float *>(&tt32);
-    for (size_t i = 0; i < sizeof(tt64) / sizeof(double); ++i) dst[i] = (float)src[i];
-  }
   if ((st = dalloc(C, &C->tab64, 1))) return st;
   if ((st = dalloc(C, &C->tab32, 1))) return st;
-  if ((st = dalloc(C, &C->tt64, 1))) return st;
-  if ((st = dalloc(C, &C->tt32, 1))) return st;
   SMF_CUDA_OK(cudaMemcpyAsync(C->tab64, &t64, sizeof(t64), cudaMemcpyHostToDevice, C->s));
   SMF_CUDA_OK(cudaMemcpyAsync(C->tab32, &t32, sizeof(t32), cudaMemcpyHostToDevice, C->s));
-  SMF_CUDA_OK(cudaMemcpyAsync(C->tt64, &tt64, sizeof(tt64), cudaMemcpyHostToDevice, C->s));
-  SMF_CUDA_OK(cudaMemcpyAsync(C->tt32, &tt32, sizeof(tt32), cudaMemcpyHostToDevice, C->s));
   {
     const int e = k == 2 ? upload_col_tables<2>(t64, C->s) : (k == 3 ? upload_col_tables<3>(t64, C->s)
                                                                      : upload_col_tables<4>(t64, C->s));
@@ -824,6 +1173,12 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
     if ((st = alloc_level_buffers(C, C->L32[l]))) return st;
   }
 
+  // transfer matrices between consecutive levels
+  for (int l = 1; l < nl; ++l) {
+    if ((st = build_xfer(C, C->L64[l].d, C->L64[l - 1].d, tt64, C->L64[l].xf))) return st;
+    if ((st = build_xfer(C, C->L32[l].d, C->L32[l - 1].d, tt64, C->L32[l].xf))) return st;
+  }
+
   // launch-shape autotuning (STOKES_NO_AUTOTUNE=1 keeps the default shape)
   {
     const char *na = getenv("STOKES_NO_AUTOTUNE");
@@ -877,6 +1232,19 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
     C->launches += 2;
   }
   if ((st = setup_coarse(C))) return st;
+  for (int l = 0; l < nl; ++l) {
+    if ((st = zero_level_work(C, C->L64[l]))) return st;
+    if ((st = zero_level_work(C, C->L32[l]))) return st;
+  }
+  // fused or unfused smoothing per level (STOKES_NO_AUTOTUNE=1 keeps the fused form)
+  {
+    const char *na = getenv("STOKES_NO_AUTOTUNE");
+    if (!(na && na[0] == '1'))
+      for (int l = 1; l < nl; ++l) {
+        if ((st = autotune_fusion<float>(C, l))) return st;
+        if ((st = autotune_fusion<double>(C, l))) return st;
+      }
+  }
   SMF_CUDA_OK(cudaStreamSynchronize(C->s));
   SMF_CUDA_OK(cudaGetLastError());
   return STOKES_OK;
@@ -1343,7 +1711,7 @@ static void smooth_noalloc_run(stokes_ctx *C, int level, int steps, void *base, 
   for (auto q : vel) *q = take(nu);
   T **pre[] = {&R.pt, &R.rp, &R.px, &R.pd, &R.ps, &R.dp};
   for (auto q : pre) *q = take(np);
-  for (int i = 0; i < steps; ++i) Runner<T>(C).smooth_step(level, x, b, false);
+  Runner<T>(C).smooth(level, x, b, steps, false);
   Ls[level] = saved;
 }
 
@@ -1488,12 +1856,10 @@ int stokes_smooth(stokes_ctx *C, int level, int precision, int steps, const void
     return STOKES_EINVAL;
   }
   StreamGuard sg(C, stream);
-  for (int i = 0; i < steps; ++i) {
-    if (precision == 64)
-      Runner<double>(C).smooth_step(level, (double *)x, (const double *)b, false);
-    else
-      Runner<float>(C).smooth_step(level, (float *)x, (const float *)b, false);
-  }
+  if (precision == 64)
+    Runner<double>(C).smooth(level, (double *)x, (const double *)b, steps, false);
+  else
+    Runner<float>(C).smooth(level, (float *)x, (const float *)b, steps, false);
   return finish(C, STOKES_OK);
 }
 
@@ -1928,10 +2294,24 @@ int stokes_get_launch_shape(const stokes_ctx *C, int level, int precision, int *
   return STOKES_OK;
 }
 
+int stokes_get_smoother_fusion(stokes_ctx *C, int level, int precision, int *fused) {
+  if (!C || level < 0 || level >= C->nl || !fused || (precision != 32 && precision != 64)) {
+    set_error("invalid stokes_get_smoother_fusion arguments");
+    return STOKES_EINVAL;
+  }
+  if (level == 0)
+    *fused = 0;
+  else if (precision == 64)
+    *fused = Runner<double>(C).fused_ok(level) ? 1 : 0;
+  else
+    *fused = Runner<float>(C).fused_ok(level) ? 1 : 0;
+  return STOKES_OK;
+}
+
 int stokes_set_launch_shape(stokes_ctx *C, int level, int precision, int shape) {
   if (!C || level < 0 || level >= C->nl || (precision != 32 && precision != 64) ||
-      !(shape == 1 || shape == 4 || shape == -1)) {
-    set_error("invalid stokes_set_launch_shape arguments (shape in {1,4,-1})");
+      !(shape == 1 || shape == 3 || shape == 4 || shape == -1)) {
+    set_error("invalid stokes_set_launch_shape arguments (shape in {1,3,4,-1})");
     if (C) C->err = g_last_error;
     return STOKES_EINVAL;
   }
@@ -1939,6 +2319,14 @@ int stokes_set_launch_shape(stokes_ctx *C, int level, int precision, int shape) 
     C->L64[level].shape = shape;
   else
     C->L32[level].shape = shape;
+  // the shape decides between the fused and the unfused smoother on this level: start from
+  // zeroed work vectors
+  int st = precision == 64 ? zero_level_work(C, C->L64[level]) : zero_level_work(C, C->L32[level]);
+  if (st == STOKES_OK && cudaStreamSynchronize(C->s) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "set_launch_shape", __FILE__, __LINE__);
+  if (st != STOKES_OK) {
+    C->err = g_last_error;
+    return st;
+  }
   // captured cycles baked the previous shape in: drop them so the next call recaptures
   for (int i = 0; i < 2; ++i) {
     if (C->g32[i].exec) cudaGraphExecDestroy(C->g32[i].exec);

@@ -9,6 +9,11 @@
 //     constant for the third, so it is set up once per thread from the 8 vertices and then
 //     evaluated at the (k+1) Gauss points of the column with a few FMAs.
 // MODE is the block bit set (kApplyA / kApplyBT / kApplyB) fixed at compile time.
+// WARPS = 1 or 4: each warp takes its own cells and runs the three velocity components one
+// after another.  WARPS = 3 ("component split", for small levels where the kernel's duration is
+// the latency of one warp): the three warps of a CTA share the same cells, warp c handles
+// velocity component c (geometry and pressure interpolation are evaluated by each warp), and the
+// pressure test-function sums of the three warps meet in the atomic scatter.
 #pragma once
 #include "apply.cuh"
 
@@ -21,7 +26,7 @@ struct ColShape {
   static constexpr int NPR = K;               // pressure nodes per direction
   static constexpr int TPC = NV * NV;         // threads per cell
   static constexpr int CPW = 32 / TPC;        // cells per warp
-  static constexpr int MAX_WARPS = 4;         // warps per CTA: 1 or 4 (template parameter, autotuned)
+  static constexpr int MAX_WARPS = 4;         // warps per CTA: 1, 3 (component split) or 4 (autotuned)
   static constexpr int MAX_THREADS = 32 * MAX_WARPS;
 };
 
@@ -72,10 +77,12 @@ __device__ __forceinline__ T sel3(int c, T a, T b, T d) {
   return c == 0 ? a : (c == 1 ? b : d);
 }
 
-template <int K, typename T, int MODE, bool CART, int WARPS>
+// FUSED: the inputs are the combinations of a Fuse descriptor, evaluated while gathering, and the
+// owners of the gathered nodes perform its side effects (stores, zeroing, p += dp).
+template <int K, typename T, int MODE, bool CART, int WARPS, bool FUSED>
 __global__ void __launch_bounds__(32 * WARPS)
     stokes_cell_apply_col(const LevelDesc<T> L, const T *__restrict__ u, const T *__restrict__ p,
-                          T *__restrict__ yu, T *__restrict__ yp) {
+                          T *__restrict__ yu, T *__restrict__ yp, const Fuse<T> F) {
   pdl_enter();
   using CS = ColShape<K>;
   using CT = CTab<T>;
@@ -93,7 +100,10 @@ __global__ void __launch_bounds__(32 * WARPS)
   const int tl = lane - (lane / TPC) * TPC;
   const int ix = pad ? 0 : tl % NV, iy = pad ? 0 : tl / NV;
   const int base = sub * TPC;
-  const long long cell = ((long long)blockIdx.x * WARPS + warp) * CS::CPW + sub;
+  constexpr bool SPLIT = WARPS == 3;
+  const long long group = SPLIT ? (long long)blockIdx.x : (long long)blockIdx.x * WARPS + warp;
+  const long long cell = group * CS::CPW + sub;
+  const int c_begin = SPLIT ? warp : 0, c_end = SPLIT ? warp + 1 : 3;
   const bool valid = !pad && cell < L.n_cells;
   int cx = 0, cy = 0, cz = 0;
   if (valid) {
@@ -103,6 +113,9 @@ __global__ void __launch_bounds__(32 * WARPS)
     cz = (int)(r / L.n[1]);
   }
   auto lane_of = [&](int a, int b) { return base + b * NV + a; };
+  // ownership of the gathered nodes (each node has exactly one owning cell)
+  const bool own_xy = valid && (ix < K || cx == L.n[0] - 1) && (iy < K || cy == L.n[1] - 1);
+  const bool pown_xy = valid && (ix < K - 1 || cx == L.n[0] - 1) && (iy < K - 1 || cy == L.n[1] - 1);
 
   // per-thread rows of the x / y tables
   T Sx[NV], Sy[NV], Dx[NQ], Dy[NQ], StX[NQ], StY[NQ], DtX[NQ], DtY[NQ];
@@ -120,6 +133,42 @@ __global__ void __launch_bounds__(32 * WARPS)
     DtX[m] = CT::D(m * NQ + ix);
     DtY[m] = CT::D(m * NQ + iy);
   }
+
+  // ---- velocity loads, issued one component ahead of their use -----------------------------
+  // The gathers of component c+1 are in flight while component c is computed, and those of the
+  // first component while the geometry is evaluated, so the warp waits for memory once.
+  const int gx = K * cx + ix, gy = K * cy + iy;
+  constexpr int NR = FUSED ? kFuseVel + 2 : 1;  // raw values per node: vv[0..2], vd, vb (fused) or u
+  T raw[NR][NV];
+  bool frs[NV], owns[NV];
+#pragma unroll
+  for (int iz = 0; iz < NV; ++iz) {
+    const int gz = K * cz + iz;
+    frs[iz] = valid && !vel_constrained(L.N, L.faces, 3, gx, gy, gz);
+    owns[iz] = own_xy && (iz < K || cz == L.n[2] - 1);
+  }
+  const long long col0 = valid ? lattice_index<3, T>(L.N, gx, gy, K * cz) : 0;
+  const long long zstride = (long long)L.N[0] * L.N[1];
+  auto load_comp = [&](int c) {
+#pragma unroll
+    for (int iz = 0; iz < NV; ++iz) {
+      const long long gi = c * L.nv + col0 + iz * zstride;
+      if (!FUSED) {
+        raw[0][iz] = frs[iz] ? u[gi] : T(0);
+      } else {
+        const bool need = frs[iz] || owns[iz];
+        if (F.nv > 0) {
+#pragma unroll
+          for (int j = 0; j < kFuseVel; ++j) raw[j][iz] = (need && j < F.nv) ? F.vv[j][gi] : T(0);
+          raw[kFuseVel][iz] = (need && F.vd) ? F.vd[gi] : T(1);
+          raw[kFuseVel + 1][iz] = (need && F.vb) ? F.vb[gi] : T(0);
+        } else {
+          raw[0][iz] = need ? u[gi] : T(0);
+        }
+      }
+    }
+  };
+  if (NEED_U) load_comp(c_begin);
 
   // ---- geometry at the column's Gauss points (qx = ix, qy = iy, qz = 0..NQ-1) --------------
   T G[NQ][6];                 // w adj adj^T / det, symmetric: 00 01 02 11 12 22
@@ -225,10 +274,40 @@ __global__ void __launch_bounds__(32 * WARPS)
   if (DO_BT) {
     T pz[NPR];
     const bool pown = valid && ix < NPR && iy < NPR;
+    long long pgi[NPR];
 #pragma unroll
-    for (int iz = 0; iz < NPR; ++iz) {
-      const long long gi = lattice_index<3, T>(L.Pn, (K - 1) * cx + ix, (K - 1) * cy + iy, (K - 1) * cz + iz);
-      pz[iz] = pown ? p[gi] : T(0);
+    for (int iz = 0; iz < NPR; ++iz)
+      pgi[iz] = lattice_index<3, T>(L.Pn, (K - 1) * cx + ix, (K - 1) * cy + iy, (K - 1) * cz + iz);
+    if (FUSED) {
+      // loads first, then the side effects, once per node: its owning cell, and in the split
+      // shape only warp 0
+#pragma unroll
+      for (int iz = 0; iz < NPR; ++iz) {
+        T pv = T(0);
+        if (pown) {
+          if (F.np > 0) {
+            T sum = T(0);
+#pragma unroll
+            for (int j = 0; j < kFusePre; ++j)
+              if (j < F.np) sum += F.pc[j] * F.pv[j][pgi[iz]];
+            pv = F.pd[pgi[iz]] * sum;
+          } else {
+            pv = p[pgi[iz]];
+          }
+        }
+        pz[iz] = pv;
+      }
+#pragma unroll
+      for (int iz = 0; iz < NPR; ++iz)
+        if (pown && pown_xy && (iz < K - 1 || cz == L.n[2] - 1) && (!SPLIT || warp == 0)) {
+          if (F.pacc) F.pacc[pgi[iz]] += pz[iz];
+#pragma unroll
+          for (int j = 0; j < kFusePre; ++j)
+            if (F.pzero[j]) F.pzero[j][pgi[iz]] = T(0);
+        }
+    } else {
+#pragma unroll
+      for (int iz = 0; iz < NPR; ++iz) pz[iz] = pown ? p[pgi[iz]] : T(0);
     }
     T a[NQ];
 #pragma unroll
@@ -259,20 +338,40 @@ __global__ void __launch_bounds__(32 * WARPS)
   }
 
   // ---- velocity components -----------------------------------------------------------------
-  const int gx = K * cx + ix, gy = K * cy + iy;
   T qacc[NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) qacc[q] = T(0);
 #pragma unroll 1
-  for (int c = 0; c < 3; ++c) {
+  for (int c = c_begin; c < c_end; ++c) {
     T v[NQ], gxv[NQ], gyv[NQ], gzv[NQ];
     if (NEED_U) {
       T uz[NV];
+      {
+        T vals[NV];
 #pragma unroll
-      for (int iz = 0; iz < NV; ++iz) {
-        const int gz = K * cz + iz;
-        const bool fr = valid && !vel_constrained(L.N, L.faces, 3, gx, gy, gz);
-        uz[iz] = fr ? u[c * L.nv + lattice_index<3, T>(L.N, gx, gy, gz)] : T(0);
+        for (int iz = 0; iz < NV; ++iz) {
+          if (FUSED && F.nv > 0) {
+            T sum = F.vc[0] * raw[0][iz];
+#pragma unroll
+            for (int j = 1; j < kFuseVel; ++j)
+              if (j < F.nv) sum += F.vc[j] * raw[j][iz];
+            vals[iz] = raw[kFuseVel + 1][iz] + raw[kFuseVel][iz] * sum;
+          } else {
+            vals[iz] = raw[0][iz];
+          }
+          uz[iz] = frs[iz] ? vals[iz] : T(0);
+        }
+        if (FUSED) {
+#pragma unroll
+          for (int iz = 0; iz < NV; ++iz)
+            if (owns[iz]) {
+              const long long gi = c * L.nv + col0 + iz * zstride;
+              if (F.vstore) F.vstore[gi] = vals[iz];
+              if (F.vzero[0]) F.vzero[0][gi] = T(0);
+              if (F.vzero[1]) F.vzero[1][gi] = T(0);
+            }
+        }
+        if (c + 1 < c_end) load_comp(c + 1);
       }
       T a[NQ];
 #pragma unroll
@@ -314,6 +413,15 @@ __global__ void __launch_bounds__(32 * WARPS)
     } else {
 #pragma unroll
       for (int q = 0; q < NQ; ++q) v[q] = gxv[q] = gyv[q] = gzv[q] = T(0);
+      if (FUSED && (F.vzero[0] || F.vzero[1])) {
+#pragma unroll
+        for (int iz = 0; iz < NV; ++iz)
+          if (owns[iz]) {
+            const long long gi = c * L.nv + col0 + iz * zstride;
+            if (F.vzero[0]) F.vzero[0][gi] = T(0);
+            if (F.vzero[1]) F.vzero[1][gi] = T(0);
+          }
+      }
     }
     // column c of C = w adj at each point (selected without dynamic register indexing)
     T cc0[NQ], cc1[NQ], cc2[NQ];

@@ -28,41 +28,49 @@ static int launch_apply_dim(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode
   return 0;
 }
 
-template <int K, typename T, int MODE, bool CART, int WARPS>
-static int launch_col_w(const LevelDesc<T> &L, const T *u, const T *p, T *yu, T *yp, cudaStream_t s) {
+template <int K, typename T, int MODE, bool CART, int WARPS, bool FUSED>
+static int launch_col_w(const LevelDesc<T> &L, const T *u, const T *p, T *yu, T *yp, cudaStream_t s,
+                        const Fuse<T> &F) {
   using CS = ColShape<K>;
-  const long long cpb = (long long)CS::CPW * WARPS;
+  const long long cpb = (long long)CS::CPW * (WARPS == 3 ? 1 : WARPS);  // WARPS 3: one cell group, 3 components
   const long long blocks = (L.n_cells + cpb - 1) / cpb;
-  launch_kernel(stokes_cell_apply_col<K, T, MODE, CART, WARPS>, dim3((unsigned)blocks), dim3(32 * WARPS), 0, s, L, u,
-                p, yu, yp);
+  launch_kernel(stokes_cell_apply_col<K, T, MODE, CART, WARPS, FUSED>, dim3((unsigned)blocks), dim3(32 * WARPS), 0, s,
+                L, u, p, yu, yp, F);
   return 0;
 }
 
-template <int K, typename T, int MODE, bool CART>
-static int launch_col(const LevelDesc<T> &L, const T *u, const T *p, T *yu, T *yp, cudaStream_t s, int shape) {
-  return shape == 1 ? launch_col_w<K, T, MODE, CART, 1>(L, u, p, yu, yp, s)
-                    : launch_col_w<K, T, MODE, CART, 4>(L, u, p, yu, yp, s);
+template <int K, typename T, int MODE, bool CART, bool FUSED>
+static int launch_col(const LevelDesc<T> &L, const T *u, const T *p, T *yu, T *yp, cudaStream_t s, int shape,
+                      const Fuse<T> &F) {
+  switch (shape) {
+    case 1: return launch_col_w<K, T, MODE, CART, 1, FUSED>(L, u, p, yu, yp, s, F);
+    case 3: return launch_col_w<K, T, MODE, CART, 3, FUSED>(L, u, p, yu, yp, s, F);
+    default: return launch_col_w<K, T, MODE, CART, 4, FUSED>(L, u, p, yu, yp, s, F);
+  }
 }
 
-template <int K, typename T, int MODE>
-static int launch_col_mode(const LevelDesc<T> &L, const T *u, const T *p, T *yu, T *yp, cudaStream_t s, int shape) {
-  return L.cartesian ? launch_col<K, T, MODE, true>(L, u, p, yu, yp, s, shape)
-                     : launch_col<K, T, MODE, false>(L, u, p, yu, yp, s, shape);
+template <int K, typename T, int MODE, bool FUSED>
+static int launch_col_mode(const LevelDesc<T> &L, const T *u, const T *p, T *yu, T *yp, cudaStream_t s, int shape,
+                           const Fuse<T> &F) {
+  return L.cartesian ? launch_col<K, T, MODE, true, FUSED>(L, u, p, yu, yp, s, shape, F)
+                     : launch_col<K, T, MODE, false, FUSED>(L, u, p, yu, yp, s, shape, F);
 }
 
-// shape: 3D launch shape chosen by the autotuner (1 / 4 warps per CTA column kernel, -1 point
-// kernel, 0 default = column kernel with 4 warps).
+// shape: 3D launch shape chosen by the autotuner (1 / 4 warps per CTA column kernel, 3 = column
+// kernel with the velocity components split over the 3 warps of a CTA, -1 point kernel,
+// 0 default = column kernel with 4 warps).
 template <int K, typename T>
 int launch_cell_apply_k(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, const T *u, const T *p, T *yu, T *yp,
                         cudaStream_t s, int shape) {
   if (L.dim == 3 && !getenv_generic() && shape >= 0) {
+    const Fuse<T> F{};
     switch (mode) {
-      case kApplyA: return launch_col_mode<K, T, kApplyA>(L, u, p, yu, yp, s, shape);
-      case kApplyBT: return launch_col_mode<K, T, kApplyBT>(L, u, p, yu, yp, s, shape);
-      case kApplyB: return launch_col_mode<K, T, kApplyB>(L, u, p, yu, yp, s, shape);
-      case kApplyA | kApplyBT: return launch_col_mode<K, T, kApplyA | kApplyBT>(L, u, p, yu, yp, s, shape);
+      case kApplyA: return launch_col_mode<K, T, kApplyA, false>(L, u, p, yu, yp, s, shape, F);
+      case kApplyBT: return launch_col_mode<K, T, kApplyBT, false>(L, u, p, yu, yp, s, shape, F);
+      case kApplyB: return launch_col_mode<K, T, kApplyB, false>(L, u, p, yu, yp, s, shape, F);
+      case kApplyA | kApplyBT: return launch_col_mode<K, T, kApplyA | kApplyBT, false>(L, u, p, yu, yp, s, shape, F);
       case kApplyA | kApplyBT | kApplyB:
-        return launch_col_mode<K, T, kApplyA | kApplyBT | kApplyB>(L, u, p, yu, yp, s, shape);
+        return launch_col_mode<K, T, kApplyA | kApplyBT | kApplyB, false>(L, u, p, yu, yp, s, shape, F);
       default: break;
     }
   }
@@ -71,6 +79,23 @@ int launch_cell_apply_k(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, co
                        : launch_apply_dim<3, K, T, false>(L, tab, mode, u, p, yu, yp, s);
   return L.cartesian ? launch_apply_dim<2, K, T, true>(L, tab, mode, u, p, yu, yp, s)
                      : launch_apply_dim<2, K, T, false>(L, tab, mode, u, p, yu, yp, s);
+}
+
+// Fused application (3D column kernel only; shape >= 0): returns -1 for a mode without a fused
+// instantiation so that the caller can reject it.
+template <int K, typename T>
+int launch_cell_apply_fused_k(const LevelDesc<T> &L, int mode, const T *u, const T *p, T *yu, T *yp, cudaStream_t s,
+                              int shape, const Fuse<T> &F) {
+  if (L.dim != 3 || shape < 0) return -1;
+  switch (mode) {
+    case kApplyA: return launch_col_mode<K, T, kApplyA, true>(L, u, p, yu, yp, s, shape, F);
+    case kApplyBT: return launch_col_mode<K, T, kApplyBT, true>(L, u, p, yu, yp, s, shape, F);
+    case kApplyB: return launch_col_mode<K, T, kApplyB, true>(L, u, p, yu, yp, s, shape, F);
+    case kApplyA | kApplyBT: return launch_col_mode<K, T, kApplyA | kApplyBT, true>(L, u, p, yu, yp, s, shape, F);
+    case kApplyA | kApplyBT | kApplyB:
+      return launch_col_mode<K, T, kApplyA | kApplyBT | kApplyB, true>(L, u, p, yu, yp, s, shape, F);
+    default: return -1;
+  }
 }
 
 template <int DIM, int K, typename T, bool CART>
@@ -118,6 +143,11 @@ int launch_cell_diag_k(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dS
   template int launch_cell_apply_k<KK, double>(const LevelDesc<double> &, const Tab1D<double> *, int,          \
                                                 const double *, const double *, double *, double *,            \
                                                 cudaStream_t, int);                                             \
+  template int launch_cell_apply_fused_k<KK, float>(const LevelDesc<float> &, int, const float *, const float *, \
+                                                     float *, float *, cudaStream_t, int, const Fuse<float> &);   \
+  template int launch_cell_apply_fused_k<KK, double>(const LevelDesc<double> &, int, const double *,             \
+                                                      const double *, double *, double *, cudaStream_t, int,       \
+                                                      const Fuse<double> &);                                      \
   template int launch_cell_diag_k<KK, double>(const LevelDesc<double> &, const Tab1D<double> *, double *,      \
                                                double *, double *, cudaStream_t);                              \
   template int upload_col_tables<KK>(const Tab1D<double> &, cudaStream_t);                                     \

@@ -60,6 +60,33 @@ struct LevelDesc {
   T mu, gamma_rho;
 };
 
+// Vector updates of the smoother folded into a 3D cell-kernel application (Sec. 3.3.1:
+// Chebyshev-Jacobi recurrence and the inexact Uzawa step).  The kernel's input is not a stored
+// vector but a pointwise combination evaluated while gathering,
+//   velocity  u_in[i] = vb[i] + vd[i] * sum_{j < nv} vc[j] * vv[j][i]   (vb / vd may be null:
+//             0 / 1; nv == 0: u_in = u),
+//   pressure  p_in[i] = pd[i] * sum_{j < np} pc[j] * pv[j][i]           (np == 0: p_in = p),
+// and the one cell that owns a node (the cell whose local index along each axis is below the
+// last one, or the last cell along that axis) performs the side effects on that node:
+//   vstore[i] = u_in[i]; vzero[*][i] = 0; pacc[i] += p_in[i]; pzero[*][i] = 0.
+// Buffers written through these side effects are never read by the same launch.
+constexpr int kFuseVel = 3, kFusePre = 6;
+template <typename T>
+struct Fuse {
+  const T *vb = nullptr, *vd = nullptr;
+  const T *vv[kFuseVel] = {};
+  T vc[kFuseVel] = {};
+  int nv = 0;
+  T *vstore = nullptr;
+  T *vzero[2] = {};
+  const T *pd = nullptr;
+  const T *pv[kFusePre] = {};
+  T pc[kFusePre] = {};
+  int np = 0;
+  T *pacc = nullptr;
+  T *pzero[kFusePre] = {};
+};
+
 __host__ __device__ inline bool vel_constrained(const int N[3], unsigned faces, int dim, int gx, int gy,
                                                 int gz) {
   if ((faces & 1u) && gx == 0) return true;

@@ -20,6 +20,12 @@ int launch_cell_diag(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dSlo
 template <int K, typename T>
 int launch_cell_apply_k(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, const T *u, const T *p, T *yu, T *yp,
                         cudaStream_t s, int shape);
+template <typename T>
+int launch_cell_apply_fused(const LevelDesc<T> &L, int mode, const T *u, const T *p, T *yu, T *yp, cudaStream_t s,
+                            int shape, const Fuse<T> &F);
+template <int K, typename T>
+int launch_cell_apply_fused_k(const LevelDesc<T> &L, int mode, const T *u, const T *p, T *yu, T *yp, cudaStream_t s,
+                              int shape, const Fuse<T> &F);
 template <int K, typename T>
 int launch_cell_grad_k(const LevelDesc<T> &L, const Tab1D<T> *tab, const T *u, const T *lam, T *g, cudaStream_t s);
 template <int K>

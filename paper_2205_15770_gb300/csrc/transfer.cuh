@@ -1,161 +1,80 @@
 // Grid transfers (paper Sec. 3.2): prolongation = canonical injection of the coarse
 // Q_k x Q_{k-1} space into the fine one, restriction = its transpose.  On the structured
-// hierarchy the injection is a tensor product of 1D matrices: fine node g along an axis
-// lies in fine cell f (local node a), child h = f mod 2 of coarse cell c = f / 2, and takes
-// the coarse basis values at reference coordinate (h + t_a)/2.  Constrained velocity DoFs
-// are dropped on both sides (P_eff = Z_fine P Z_coarse).
+// hierarchy the injection is a tensor product of 1D matrices: fine node g along an axis lies in
+// fine cell f (local node a), child h = f mod 2 of coarse cell c = f / 2, and takes the coarse
+// basis values at reference coordinate (h + t_a)/2.  Constrained velocity DoFs are dropped on
+// both sides (P_eff = Z_fine P Z_coarse); a node is free iff it is free along every axis, so the
+// masks are tensor products too and are folded into the 1D weights.
 //
-// Both kernels are DoF-parallel and write every output once (no atomics):
-//   prolongation: each fine DoF gathers the (deg+1)^d coarse values of its coarse cell;
-//   restriction:  each coarse DoF gathers the fine DoFs in the support of its basis function.
+// The 1D matrices of a level pair are stored per axis and space as padded rows of
+// (node, weight) pairs without zeros: prolongation rows (per fine node, <= deg+1 entries) and
+// restriction rows (per coarse node, <= 4 deg + 1 entries), built on the host at setup.  Both
+// kernels are DoF-parallel, write every output once (no atomics) and sum the tensor-product
+// terms in nested loops.
 #pragma once
 #include "common.cuh"
 #include "vec.cuh"
 
 namespace smf {
 
-constexpr int kMaxAxis = 4 * kMaxDeg + 1;
-
-// Row of the 1D injection for fine node g (degree deg, nc coarse cells): coarse nodes G[m] with weights w[m].
+// One axis, one space: rows of up to W (node, weight) pairs.
 template <typename T>
-__device__ __forceinline__ int inj_row(int g, int deg, int nc, const T *tab, int *G, T *w) {
-  int f = g / deg;
-  if (f > 2 * nc - 1) f = 2 * nc - 1;
-  const int a = g - deg * f, c = f >> 1, h = f & 1;
-  for (int m = 0; m <= deg; ++m) {
-    G[m] = deg * c + m;
-    w[m] = tab[(h * (deg + 1) + a) * (deg + 1) + m];
-  }
-  return deg + 1;
-}
-
-// Column of the 1D injection for coarse node G: fine nodes g[j] with weights w[j] != 0.
+struct Xfer1D {
+  const int *cnt = nullptr;  // [rows]
+  const int *idx = nullptr;  // [rows * W]
+  const T *w = nullptr;      // [rows * W]
+};
+// All 1D matrices of a level pair: [space: 0 velocity, 1 pressure][axis]; row width W = 4k + 1.
 template <typename T>
-__device__ __forceinline__ int inj_col(int G, int deg, int nc, const T *tab, int *g, T *w) {
-  int c_lo = G / deg, c_hi = G / deg;
-  if (G % deg == 0) c_lo -= 1;
-  if (c_lo < 0) c_lo = 0;
-  if (c_hi > nc - 1) c_hi = nc - 1;
-  int cnt = 0;
-  for (int gi = 2 * deg * c_lo; gi <= 2 * deg * c_hi + 2 * deg; ++gi) {
-    int f = gi / deg;
-    if (f > 2 * nc - 1) f = 2 * nc - 1;
-    const int a = gi - deg * f, c = f >> 1, h = f & 1, m = G - deg * c;
-    if (m < 0 || m > deg) continue;
-    const T v = tab[(h * (deg + 1) + a) * (deg + 1) + m];
-    if (v != T(0)) {
-      g[cnt] = gi;
-      w[cnt] = v;
-      ++cnt;
-    }
-  }
-  return cnt;
-}
-
-// out (fine) = P in (coarse); add != 0: out += P in.  Covers velocity and pressure.
-template <typename T>
-__global__ void k_prolongate(const LevelDesc<T> F, const LevelDesc<T> C, const TransferTab<T> *__restrict__ tt,
-                             const T *__restrict__ in, T *__restrict__ out, int add) {
-  pdl_enter();
-  const int dim = F.dim, k = F.k;
-  SMF_GRID_LOOP(i, F.n_u + F.n_p) {
-    const bool vel = i < F.n_u;
-    const int deg = vel ? k : k - 1;
-    const T *tab = vel ? tt->vel : tt->pre;
-    const int *Nf = vel ? F.N : F.Pn;
-    const long long nodes = vel ? F.nv : F.n_p;
-    const long long j = vel ? i % F.nv : i - F.n_u;
-    const int comp = vel ? (int)(i / F.nv) : 0;
-    int g[3] = {(int)(j % Nf[0]), (int)((j / Nf[0]) % Nf[1]), dim == 3 ? (int)(j / ((long long)Nf[0] * Nf[1])) : 0};
-    (void)nodes;
-    if (vel && vel_constrained(F.N, F.faces, dim, g[0], g[1], g[2])) {
-      if (!add) out[i] = T(0);
-      continue;
-    }
-    int G[3][kMaxN1];
-    T w[3][kMaxN1];
-    int cnt[3] = {1, 1, 1};
-    for (int a = 0; a < dim; ++a) cnt[a] = inj_row(g[a], deg, C.n[a], tab, G[a], w[a]);
-    if (dim == 2) {
-      G[2][0] = 0;
-      w[2][0] = T(1);
-    }
-    T s = T(0);
-    for (int c2 = 0; c2 < cnt[2]; ++c2)
-      for (int c1 = 0; c1 < cnt[1]; ++c1) {
-        const T w12 = w[2][c2] * w[1][c1];
-        if (w12 == T(0)) continue;
-        for (int c0 = 0; c0 < cnt[0]; ++c0) {
-          const T ww = w12 * w[0][c0];
-          if (ww == T(0)) continue;
-          if (vel) {
-            if (vel_constrained(C.N, C.faces, dim, G[0][c0], G[1][c1], G[2][c2])) continue;
-            const long long ci = dim == 3 ? ((long long)G[2][c2] * C.N[1] + G[1][c1]) * C.N[0] + G[0][c0]
-                                          : (long long)G[1][c1] * C.N[0] + G[0][c0];
-            s += ww * in[comp * C.nv + ci];
-          } else {
-            const long long ci = dim == 3 ? ((long long)G[2][c2] * C.Pn[1] + G[1][c1]) * C.Pn[0] + G[0][c0]
-                                          : (long long)G[1][c1] * C.Pn[0] + G[0][c0];
-            s += ww * in[C.n_u + ci];
-          }
-        }
-      }
-    out[i] = add ? out[i] + s : s;
-  }
-}
+struct XferTabs {
+  Xfer1D<T> r[2][3];  // restriction: per coarse node, the fine nodes of its basis function's support
+  Xfer1D<T> p[2][3];  // prolongation: per fine node, the coarse nodes of its coarse cell
+  int W = 0;
+};
 
 // out (coarse) = P^T in (fine); zero_c (coarse-sized, may be null) is zeroed on the way.
-// LANES consecutive lanes share one coarse DoF: the (up to (4k+1)^d) fine terms of its support
-// are split across them and combined with warp shuffles (LANES = 8 on small coarse levels,
-// where there are too few DoFs to fill the GPU; 1 on large ones).
-template <typename T, int LANES>
-__global__ void k_restrict(const LevelDesc<T> F, const LevelDesc<T> C, const TransferTab<T> *__restrict__ tt,
-                           const T *__restrict__ in, T *__restrict__ out, T *__restrict__ zero_c) {
+// LANES consecutive lanes share one coarse DoF and split its (z, y) term pairs; the partial sums
+// are combined with shuffles (LANES > 1 on small coarse levels, where there are too few DoFs to
+// fill the GPU).
+template <typename T, int W, int LANES>
+__global__ void k_restrict(const LevelDesc<T> F, const LevelDesc<T> C, const XferTabs<T> X, const T *__restrict__ in,
+                           T *__restrict__ out, T *__restrict__ zero_c) {
   pdl_enter();
-  const int dim = F.dim, k = F.k;
   const long long total = (C.n_u + C.n_p) * LANES;
   const int sub = threadIdx.x & (LANES - 1);
-  // grid-stride over (DoF, lane) pairs; the loop condition depends only on the warp's first
-  // index, so all 32 lanes iterate together and the full-mask shuffles below are converged
+  // the loop condition depends only on the warp's first index, so all 32 lanes iterate together
+  // and the full-mask shuffles below are converged
   for (long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x; gid - (threadIdx.x & 31) < total;
        gid += (long long)gridDim.x * blockDim.x) {
     const long long i = gid / LANES;
     const bool active = i < C.n_u + C.n_p;
     T s = T(0);
-    bool constrained = false;
     if (active) {
       const bool vel = i < C.n_u;
-      const int deg = vel ? k : k - 1;
-      const T *tab = vel ? tt->vel : tt->pre;
-      const int *Nc = vel ? C.N : C.Pn;
+      const int sp = vel ? 0 : 1;
+      const int *Nc = vel ? C.N : C.Pn, *Nf = vel ? F.N : F.Pn;
       const long long j = vel ? i % C.nv : i - C.n_u;
-      const int comp = vel ? (int)(i / C.nv) : 0;
-      int G[3] = {(int)(j % Nc[0]), (int)((j / Nc[0]) % Nc[1]), dim == 3 ? (int)(j / ((long long)Nc[0] * Nc[1])) : 0};
-      constrained = vel && vel_constrained(C.N, C.faces, dim, G[0], G[1], G[2]);
-      if (!constrained) {
-        int g[3][kMaxAxis];
-        T w[3][kMaxAxis];
-        int cnt[3] = {1, 1, 1};
-        for (int a = 0; a < dim; ++a) cnt[a] = inj_col(G[a], deg, C.n[a], tab, g[a], w[a]);
-        if (dim == 2) {
-          g[2][0] = 0;
-          w[2][0] = T(1);
-        }
-        const int nterms = cnt[0] * cnt[1] * cnt[2];
-        for (int t = sub; t < nterms; t += LANES) {
-          const int c0 = t % cnt[0], c1 = (t / cnt[0]) % cnt[1], c2 = t / (cnt[0] * cnt[1]);
-          const T ww = w[2][c2] * w[1][c1] * w[0][c0];
-          if (vel) {
-            if (vel_constrained(F.N, F.faces, dim, g[0][c0], g[1][c1], g[2][c2])) continue;
-            const long long fi = dim == 3 ? ((long long)g[2][c2] * F.N[1] + g[1][c1]) * F.N[0] + g[0][c0]
-                                          : (long long)g[1][c1] * F.N[0] + g[0][c0];
-            s += ww * in[comp * F.nv + fi];
-          } else {
-            const long long fi = dim == 3 ? ((long long)g[2][c2] * F.Pn[1] + g[1][c1]) * F.Pn[0] + g[0][c0]
-                                          : (long long)g[1][c1] * F.Pn[0] + g[0][c0];
-            s += ww * in[F.n_u + fi];
-          }
-        }
+      const int G0 = (int)(j % Nc[0]), G1 = (int)((j / Nc[0]) % Nc[1]), G2 = (int)(j / ((long long)Nc[0] * Nc[1]));
+      const T *src = in + (vel ? (i / C.nv) * F.nv : F.n_u);
+      const Xfer1D<T> &ax = X.r[sp][0], &ay = X.r[sp][1], &az = X.r[sp][2];
+      const int n0 = ax.cnt[G0], n1 = ay.cnt[G1], n2 = az.cnt[G2];
+      int f0[W];
+      T w0[W];
+#pragma unroll
+      for (int a = 0; a < W; ++a) {
+        f0[a] = a < n0 ? ax.idx[G0 * W + a] : 0;
+        w0[a] = a < n0 ? ax.w[G0 * W + a] : T(0);
+      }
+      for (int t = sub; t < n1 * n2; t += LANES) {
+        const int a1 = t % n1, a2 = t / n1;
+        const int f1 = ay.idx[G1 * W + a1], f2 = az.idx[G2 * W + a2];
+        const T w21 = ay.w[G1 * W + a1] * az.w[G2 * W + a2];
+        const T *row = src + ((long long)f2 * Nf[1] + f1) * Nf[0];
+        T r = T(0);
+#pragma unroll
+        for (int a = 0; a < W; ++a)
+          if (a < n0) r += w0[a] * row[f0[a]];
+        s += w21 * r;
       }
     }
 #pragma unroll
@@ -164,6 +83,40 @@ __global__ void k_restrict(const LevelDesc<T> F, const LevelDesc<T> C, const Tra
       out[i] = s;
       if (zero_c) zero_c[i] = T(0);
     }
+  }
+}
+
+// out (fine) = P in (coarse); add != 0: out += P in.  Covers velocity and pressure.  z0 / z1
+// (fine velocity-sized, may be null) are zeroed on the way.
+template <typename T, int W>
+__global__ void k_prolongate(const LevelDesc<T> F, const LevelDesc<T> C, const XferTabs<T> X, const T *__restrict__ in,
+                             T *__restrict__ out, int add, T *__restrict__ z0, T *__restrict__ z1) {
+  pdl_enter();
+  SMF_GRID_LOOP(i, F.n_u + F.n_p) {
+    const bool vel = i < F.n_u;
+    if (vel) {
+      if (z0) z0[i] = T(0);
+      if (z1) z1[i] = T(0);
+    }
+    const int sp = vel ? 0 : 1;
+    const int *Nc = vel ? C.N : C.Pn, *Nf = vel ? F.N : F.Pn;
+    const long long j = vel ? i % F.nv : i - F.n_u;
+    const int g0 = (int)(j % Nf[0]), g1 = (int)((j / Nf[0]) % Nf[1]), g2 = (int)(j / ((long long)Nf[0] * Nf[1]));
+    const T *src = in + (vel ? (i / F.nv) * C.nv : C.n_u);
+    const Xfer1D<T> &ax = X.p[sp][0], &ay = X.p[sp][1], &az = X.p[sp][2];
+    const int n0 = ax.cnt[g0], n1 = ay.cnt[g1], n2 = az.cnt[g2];
+    T s = T(0);
+    for (int a2 = 0; a2 < n2; ++a2) {
+      const int G2 = az.idx[g2 * W + a2];
+      const T w2 = az.w[g2 * W + a2];
+      for (int a1 = 0; a1 < n1; ++a1) {
+        const T *row = src + ((long long)G2 * Nc[1] + ay.idx[g1 * W + a1]) * Nc[0];
+        T r = T(0);
+        for (int a0 = 0; a0 < n0; ++a0) r += ax.w[g0 * W + a0] * row[ax.idx[g0 * W + a0]];
+        s += w2 * ay.w[g1 * W + a1] * r;
+      }
+    }
+    out[i] = add ? out[i] + s : s;
   }
 }
 

@@ -202,6 +202,31 @@ __global__ void k_cheb_step(const T *__restrict__ r, T *__restrict__ t, const T 
   }
 }
 
+// End of a fused smoothing sequence: the last line of the compact Uzawa step,
+//   u[i] = uhat[i] + Dinv[i] (ca a[i] + cb b[i])   (i < n_u; a, b zeroed afterwards),
+// and the pressure work vectors pz[0..npz) zeroed (i < n_p).
+template <typename T>
+struct ZeroList {
+  T *p[kFusePre];
+  int n;
+};
+template <typename T>
+__global__ void k_fused_finish(const T *__restrict__ uhat, const T *__restrict__ Dinv, T *__restrict__ a,
+                               T *__restrict__ b, T ca, T cb, T *__restrict__ u, long long n_u, ZeroList<T> pz,
+                               long long n_p) {
+  pdl_enter();
+  const long long n = n_u > n_p ? n_u : n_p;
+  SMF_GRID_LOOP(i, n) {
+    if (i < n_u) {
+      u[i] = uhat[i] + Dinv[i] * (ca * a[i] + cb * b[i]);
+      a[i] = T(0);
+      b[i] = T(0);
+    }
+    if (i < n_p)
+      for (int j = 0; j < pz.n; ++j) pz.p[j][i] = T(0);
+  }
+}
+
 // r = b - kx; kx is zeroed after it is read (residual of Algorithm 1).
 template <typename T, int V>
 __global__ void k_residual(const T *__restrict__ b, T *__restrict__ kx, T *__restrict__ r, long long n) {

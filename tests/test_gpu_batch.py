@@ -63,7 +63,27 @@ def test_autotuned_launch_shapes_are_valid():
     S = StokesMG(dim=3, n=(16, 16, 16), n_levels=4, k=2)
     for prec in (32, 64):
         shapes = S.launch_shapes(prec)
-        assert len(shapes) == 4 and all(s in (1, 4, -1) for s in shapes), shapes
+        assert len(shapes) == 4 and all(s in (1, 3, 4, -1) for s in shapes), shapes
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+@pytest.mark.parametrize("blocks", [1, 2, 4, 3, 7])
+def test_every_launch_shape_gives_the_same_blocks(k, blocks):
+    from paper_2205_15770_gb300 import StokesMG
+    n = (4, 6, 2) if k < 4 else (2, 4, 2)
+    V = W.perturbed_vertices(3, n, seed=5)
+    S = StokesMG(dim=3, n=n, n_levels=1, k=k, vertices=V, gamma_rho=2.0)
+    nu, npr = S.sizes()
+    u = torch.as_tensor(W.random_vector(nu, 11), device="cuda")
+    p = torch.as_tensor(W.random_vector(npr, 12), device="cuda")
+    ref = None
+    for shape in (4, 1, 3, -1):
+        S.set_launch_shape(0, shape, precision=64)
+        yu, yp = S.apply_blocks(blocks, u=u, p=p)
+        y = torch.cat([t for t in (yu, yp) if t is not None]).cpu().numpy()
+        if ref is None:
+            ref = y
+        assert np.abs(y - ref).max() <= 1e-13 * np.abs(ref).max(), (shape, k, blocks)
 
 
 def test_every_launch_shape_gives_the_same_operator():
@@ -72,7 +92,7 @@ def test_every_launch_shape_gives_the_same_operator():
     S = StokesMG(dim=3, n=(8, 8, 8), n_levels=2, k=2, vertices=V, gamma_rho=3.0)
     x = torch.as_tensor(W.random_vector(S.size(), 9), device="cuda")
     ref = None
-    for shape in (4, 1, -1):
+    for shape in (4, 1, 3, -1):
         S.set_launch_shape(1, shape, precision=64)
         y = S.vmult(x).cpu().numpy()
         if ref is None:

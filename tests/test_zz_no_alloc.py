@@ -21,10 +21,11 @@ def _t(a, dtype):
 
 
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 2e-5)])
-def test_noalloc_smoothing_matches_stokes_smooth_on_two_calls(dtype, tol):
+@pytest.mark.parametrize("kA,kS", [(3, 3), (1, 2)])  # (1, 2): the fused smoother
+def test_noalloc_smoothing_matches_stokes_smooth_on_two_calls(dtype, tol, kA, kS):
     case = CASES["3d_q2_pert"]
     H = oracle_hierarchy(case)
-    S = gpu_solver(case)
+    S = gpu_solver(case, kA=kA, kS=kS)
     level = len(H.levels) - 1
     lev = H.levels[level]
     b = _t(random_full(lev, 21, constrained_zero=True), dtype)
