@@ -34,20 +34,28 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
 
 template <typename T>
 int launch_cell_apply(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, const T *u, const T *p, T *yu, T *yp,
-                      cudaStream_t s, int shape) {
+                      cudaStream_t s, int shape, const T *geo) {
   switch (L.k) {
-    case 2: return launch_cell_apply_k<2, T>(L, tab, mode, u, p, yu, yp, s, shape);
-    case 3: return launch_cell_apply_k<3, T>(L, tab, mode, u, p, yu, yp, s, shape);
-    default: return launch_cell_apply_k<4, T>(L, tab, mode, u, p, yu, yp, s, shape);
+    case 2: return launch_cell_apply_k<2, T>(L, tab, mode, u, p, yu, yp, s, shape, geo);
+    case 3: return launch_cell_apply_k<3, T>(L, tab, mode, u, p, yu, yp, s, shape, geo);
+    default: return launch_cell_apply_k<4, T>(L, tab, mode, u, p, yu, yp, s, shape, geo);
+  }
+}
+template <typename T>
+int launch_col_geometry(const LevelDesc<T> &L, T *geo, cudaStream_t s) {
+  switch (L.k) {
+    case 2: return launch_col_geometry_k<2, T>(L, geo, s);
+    case 3: return launch_col_geometry_k<3, T>(L, geo, s);
+    default: return launch_col_geometry_k<4, T>(L, geo, s);
   }
 }
 template <typename T>
 int launch_cell_apply_fused(const LevelDesc<T> &L, int mode, const T *u, const T *p, T *yu, T *yp, cudaStream_t s,
-                            int shape, const Fuse<T> &F) {
+                            int shape, const Fuse<T> &F, const T *geo) {
   switch (L.k) {
-    case 2: return launch_cell_apply_fused_k<2, T>(L, mode, u, p, yu, yp, s, shape, F);
-    case 3: return launch_cell_apply_fused_k<3, T>(L, mode, u, p, yu, yp, s, shape, F);
-    default: return launch_cell_apply_fused_k<4, T>(L, mode, u, p, yu, yp, s, shape, F);
+    case 2: return launch_cell_apply_fused_k<2, T>(L, mode, u, p, yu, yp, s, shape, F, geo);
+    case 3: return launch_cell_apply_fused_k<3, T>(L, mode, u, p, yu, yp, s, shape, F, geo);
+    default: return launch_cell_apply_fused_k<4, T>(L, mode, u, p, yu, yp, s, shape, F, geo);
   }
 }
 template <>
@@ -120,6 +128,7 @@ struct LevelRT {
   int shape = 0;  // 3D cell-kernel launch shape chosen by the autotuner (see launch_cell_apply_k)
   XferTabs<T> xf{};  // 1D transfer matrices between this level and the next coarser one
   bool fuse = true;  // fused smoothing on this level (set by the setup's timing, when eligible)
+  const T *geo = nullptr;  // FP64 3D trilinear: precomputed per-point geometry of the column kernel
   T *DAinv = nullptr, *DSinv = nullptr;
   T *x = nullptr, *b = nullptr, *r = nullptr, *kx = nullptr;                   // full vectors
   T *tu = nullptr, *ru = nullptr, *uhat = nullptr, *cx = nullptr, *cd = nullptr, *ct = nullptr;  // velocity
@@ -282,7 +291,7 @@ struct Runner {
   // Cycle form: the outputs are already zero (work buffers are zeroed by the kernel that
   // consumes them, so the captured cycle contains kernels only).
   void apply_nz(int l, int mode, const T *u, const T *p, T *yu, T *yp) {
-    launch_cell_apply<T>(L[l].d, tab, mode, u, p, yu, yp, s, L[l].shape);
+    launch_cell_apply<T>(L[l].d, tab, mode, u, p, yu, yp, s, L[l].shape, L[l].geo);
     note();
   }
   void vmult(int l, const T *x, T *y, bool identity) {
@@ -408,7 +417,7 @@ struct Runner {
     return b[j];
   }
   void fapply(int l, int mode, const T *u, const T *p, T *yu, T *yp, const Fuse<T> &F) {
-    launch_cell_apply_fused<T>(L[l].d, mode, u, p, yu, yp, s, L[l].shape, F);
+    launch_cell_apply_fused<T>(L[l].d, mode, u, p, yu, yp, s, L[l].shape, F, L[l].geo);
     note();
   }
   // Velocity Chebyshev with k_A = 1 from zero on r: x_1 = c0 D^-1 r, t = A x_1,
@@ -945,14 +954,14 @@ static int autotune_level(stokes_ctx *C, LevelRT<T> &R, const Tab1D<T> *tab) {
   for (int w = 0; w < 3; ++w)
     for (int c : cands) {
       R.shape = c;
-      launch_cell_apply<T>(R.d, tab, kApplyA, R.x, nullptr, R.r, nullptr, C->s, R.shape);
+      launch_cell_apply<T>(R.d, tab, kApplyA, R.x, nullptr, R.r, nullptr, C->s, R.shape, R.geo);
     }
   for (int round = 0; round < rounds; ++round)
     for (int ci = 0; ci < NC; ++ci) {
       R.shape = cands[ci];
       cudaEventRecord(e0, C->s);
       for (int r = 0; r < reps; ++r)
-        launch_cell_apply<T>(R.d, tab, kApplyA, R.x, nullptr, R.r, nullptr, C->s, R.shape);
+        launch_cell_apply<T>(R.d, tab, kApplyA, R.x, nullptr, R.r, nullptr, C->s, R.shape, R.geo);
       cudaEventRecord(e1, C->s);
       SMF_CUDA_OK(cudaEventSynchronize(e1));
       float ms = 0.f;
@@ -1097,6 +1106,7 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
       }
     }
     LevelDesc<double> d{};
+    double *geo_l = nullptr;
     d.dim = dim;
     d.k = k;
     for (int a = 0; a < 3; ++a) {
@@ -1153,6 +1163,18 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
       SMF_CUDA_OK(cudaStreamSynchronize(C->s));
       d.vert = dv;
       f.vert = fv;
+      // per-point geometry of the FP64 column kernel, precomputed once (the geometry is a quarter
+      // of the FP64 flops of an application; STOKES_GEO=none keeps it on the fly)
+      if (dim == 3) {
+        const char *gs = getenv("STOKES_GEO");
+        const bool g64 = !(gs && std::strcmp(gs, "none") == 0);
+        const long long per = 16LL * (k + 1) * (k + 1) * (k + 1), cells = d.n_cells;
+        if (g64 && cells * per * (long long)sizeof(double) <= (4LL << 30)) {
+          if ((st = dalloc(C, &geo_l, cells * per))) return st;
+          launch_col_geometry<double>(d, geo_l, C->s);
+          SMF_CUDA_OK(cudaGetLastError());
+        }
+      }
     }
     if (mu_cell) {
       std::vector<double> &m = mu_levels[l];
@@ -1169,6 +1191,7 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
     }
     C->L64[l].d = d;
     C->L32[l].d = f;
+    C->L64[l].geo = geo_l;
     if ((st = alloc_level_buffers(C, C->L64[l]))) return st;
     if ((st = alloc_level_buffers(C, C->L32[l]))) return st;
   }
@@ -2170,10 +2193,10 @@ int stokes_time_apply(stokes_ctx *C, int level, int precision, int blocks, int r
   for (int r = 0; r < reps; ++r) {
     if (precision == 64) {
       LevelRT<double> &R = C->L64[level];
-      launch_cell_apply<double>(R.d, C->tab64, blocks, R.x, R.x + R.d.n_u, R.r, R.r + R.d.n_u, C->s, R.shape);
+      launch_cell_apply<double>(R.d, C->tab64, blocks, R.x, R.x + R.d.n_u, R.r, R.r + R.d.n_u, C->s, R.shape, R.geo);
     } else {
       LevelRT<float> &R = C->L32[level];
-      launch_cell_apply<float>(R.d, C->tab32, blocks, R.x, R.x + R.d.n_u, R.r, R.r + R.d.n_u, C->s, R.shape);
+      launch_cell_apply<float>(R.d, C->tab32, blocks, R.x, R.x + R.d.n_u, R.r, R.r + R.d.n_u, C->s, R.shape, R.geo);
     }
     ++C->launches;
   }

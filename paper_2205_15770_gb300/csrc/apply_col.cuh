@@ -16,6 +16,7 @@
 // pressure test-function sums of the three warps meet in the atomic scatter.
 #pragma once
 #include "apply.cuh"
+#include "vec.cuh"
 
 namespace smf {
 
@@ -77,12 +78,115 @@ __device__ __forceinline__ T sel3(int c, T a, T b, T d) {
   return c == 0 ? a : (c == 1 ? b : d);
 }
 
+// Geometry of a column's Gauss points (qx = ix, qy = iy, qz = 0..NQ-1) of cell (cx, cy, cz):
+// G = w adj(J) adj(J)^T / det J (symmetric, 00 01 02 11 12 22), Cm = w adj(J) (when NEED_C),
+// Wd = w det J, w the tensor Gauss weight.  Trilinear cells: the first two Jacobian columns are
+// linear in zeta along the column and the third is constant, so they are set up once from the
+// 8 vertices and evaluated per point.
+template <int K, typename T, bool CART, bool NEED_C>
+__device__ __forceinline__ void col_geometry(const LevelDesc<T> &L, int ix, int iy, int cx, int cy, int cz,
+                                             T (&G)[K + 1][6], T (&Cm)[NEED_C ? K + 1 : 1][9], T (&Wd)[K + 1]) {
+  using CT = CTab<T>;
+  constexpr int NQ = K + 1;
+  {
+    const T wxy = CT::W(ix) * CT::W(iy);
+    if (CART) {
+      const T h0 = L.h[0], h1 = L.h[1], h2 = L.h[2];
+      const T a0 = h1 * h2, a1 = h0 * h2, a2 = h0 * h1, det = h0 * h1 * h2;
+#pragma unroll
+      for (int qz = 0; qz < NQ; ++qz) {
+        const T w = wxy * CT::W(qz);
+        G[qz][0] = w * a0 * a0 / det;
+        G[qz][1] = T(0);
+        G[qz][2] = T(0);
+        G[qz][3] = w * a1 * a1 / det;
+        G[qz][4] = T(0);
+        G[qz][5] = w * a2 * a2 / det;
+        Wd[qz] = w * det;
+        if (NEED_C) {
+#pragma unroll
+          for (int i = 0; i < 9; ++i) Cm[qz][i] = T(0);
+          Cm[qz][0] = w * a0;
+          Cm[qz][4] = w * a1;
+          Cm[qz][8] = w * a2;
+        }
+      }
+    } else {
+      // vertices X[v][a], v = vx + 2 vy + 4 vz
+      T X[8][3];
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        const long long gv =
+            ((long long)(cz + ((v >> 2) & 1)) * (L.n[1] + 1) + (cy + ((v >> 1) & 1))) * (L.n[0] + 1) + (cx + (v & 1));
+#pragma unroll
+        for (int a = 0; a < 3; ++a) X[v][a] = L.vert[gv * 3 + a];
+      }
+      const T xi = CT::W(NQ + ix), eta = CT::W(NQ + iy);
+      // column 0 (d/dxi) at zeta = 0 and 1: bilinear in eta of the x-edge differences
+      // column 1 (d/deta) at zeta = 0 and 1: in xi of the y-edge differences
+      // column 2 (d/dzeta): bilinear in (xi, eta) of the z-edge differences (constant in zeta)
+      T c0[2][3], c1[2][3], c2[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int z = 0; z < 2; ++z) {
+          const T e00 = X[4 * z + 1][a] - X[4 * z + 0][a], e10 = X[4 * z + 3][a] - X[4 * z + 2][a];
+          c0[z][a] = e00 + eta * (e10 - e00);
+          const T f00 = X[4 * z + 2][a] - X[4 * z + 0][a], f10 = X[4 * z + 3][a] - X[4 * z + 1][a];
+          c1[z][a] = f00 + xi * (f10 - f00);
+        }
+        const T g00 = X[4][a] - X[0][a], g10 = X[5][a] - X[1][a], g01 = X[6][a] - X[2][a], g11 = X[7][a] - X[3][a];
+        const T gl = g00 + xi * (g10 - g00), gh = g01 + xi * (g11 - g01);
+        c2[a] = gl + eta * (gh - gl);
+      }
+#pragma unroll
+      for (int qz = 0; qz < NQ; ++qz) {
+        const T zeta = CT::W(NQ + qz);
+        T J[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          J[a][0] = c0[0][a] + zeta * (c0[1][a] - c0[0][a]);
+          J[a][1] = c1[0][a] + zeta * (c1[1][a] - c1[0][a]);
+          J[a][2] = c2[a];
+        }
+        T adj[3][3];
+        adj[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+        adj[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+        adj[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+        adj[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+        adj[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+        adj[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+        adj[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+        adj[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+        adj[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        const T det = J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
+        const T w = wxy * CT::W(qz);
+        const T wd = w / det;
+        G[qz][0] = wd * (adj[0][0] * adj[0][0] + adj[0][1] * adj[0][1] + adj[0][2] * adj[0][2]);
+        G[qz][1] = wd * (adj[0][0] * adj[1][0] + adj[0][1] * adj[1][1] + adj[0][2] * adj[1][2]);
+        G[qz][2] = wd * (adj[0][0] * adj[2][0] + adj[0][1] * adj[2][1] + adj[0][2] * adj[2][2]);
+        G[qz][3] = wd * (adj[1][0] * adj[1][0] + adj[1][1] * adj[1][1] + adj[1][2] * adj[1][2]);
+        G[qz][4] = wd * (adj[1][0] * adj[2][0] + adj[1][1] * adj[2][1] + adj[1][2] * adj[2][2]);
+        G[qz][5] = wd * (adj[2][0] * adj[2][0] + adj[2][1] * adj[2][1] + adj[2][2] * adj[2][2]);
+        Wd[qz] = w * det;
+        if (NEED_C) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) Cm[qz][a * 3 + b] = w * adj[a][b];
+        }
+      }
+    }
+  }
+}
+
 // FUSED: the inputs are the combinations of a Fuse descriptor, evaluated while gathering, and the
 // owners of the gathered nodes perform its side effects (stores, zeroing, p += dp).
 template <int K, typename T, int MODE, bool CART, int WARPS, bool FUSED>
 __global__ void __launch_bounds__(32 * WARPS)
     stokes_cell_apply_col(const LevelDesc<T> L, const T *__restrict__ u, const T *__restrict__ p,
-                          T *__restrict__ yu, T *__restrict__ yp, const Fuse<T> F) {
+                          T *__restrict__ yu, T *__restrict__ yp, const Fuse<T> F,
+                          const T *__restrict__ geo) {
   pdl_enter();
   using CS = ColShape<K>;
   using CT = CTab<T>;
@@ -174,92 +278,115 @@ __global__ void __launch_bounds__(32 * WARPS)
   T G[NQ][6];                 // w adj adj^T / det, symmetric: 00 01 02 11 12 22
   T Cm[NEED_C ? NQ : 1][9];   // w adj
   T Wd[NQ];                   // w det
-  {
-    const T wxy = CT::W(ix) * CT::W(iy);
-    if (CART) {
-      const T h0 = L.h[0], h1 = L.h[1], h2 = L.h[2];
-      const T a0 = h1 * h2, a1 = h0 * h2, a2 = h0 * h1, det = h0 * h1 * h2;
+  // geo (FP64 trilinear levels): precomputed at setup, the geometry being a quarter of the FP64
+  // flops; otherwise evaluated on the fly.  (A separate kernel argument: a larger level
+  // descriptor changes the register allocation of the FP32 kernels.)
+  if (sizeof(T) == 8 && !CART && geo) {
+    // precomputed by k_col_geometry (col_geometry, same arithmetic): [cell][16][qz][iy][ix]
+    const T *gp = geo + (valid ? cell : 0) * (long long)(16 * NQ * NV * NV) + iy * NV + ix;
+    constexpr int ST = NQ * NV * NV;  // stride between the 16 fields
 #pragma unroll
-      for (int qz = 0; qz < NQ; ++qz) {
-        const T w = wxy * CT::W(qz);
-        G[qz][0] = w * a0 * a0 / det;
-        G[qz][1] = T(0);
-        G[qz][2] = T(0);
-        G[qz][3] = w * a1 * a1 / det;
-        G[qz][4] = T(0);
-        G[qz][5] = w * a2 * a2 / det;
-        Wd[qz] = w * det;
-        if (NEED_C) {
+    for (int qz = 0; qz < NQ; ++qz) {
+      const T *q = gp + qz * NV * NV;
+      if (DO_A) {
 #pragma unroll
-          for (int i = 0; i < 9; ++i) Cm[qz][i] = T(0);
-          Cm[qz][0] = w * a0;
-          Cm[qz][4] = w * a1;
-          Cm[qz][8] = w * a2;
+        for (int i = 0; i < 6; ++i) G[qz][i] = q[i * ST];
+        Wd[qz] = q[15 * ST];
+      }
+      if (NEED_C) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) Cm[qz][i] = q[(6 + i) * ST];
+      }
+    }
+  } else {
+    // on the fly (the same arithmetic as col_geometry, kept inline for the kernel's schedule)
+    {
+      const T wxy = CT::W(ix) * CT::W(iy);
+      if (CART) {
+        const T h0 = L.h[0], h1 = L.h[1], h2 = L.h[2];
+        const T a0 = h1 * h2, a1 = h0 * h2, a2 = h0 * h1, det = h0 * h1 * h2;
+  #pragma unroll
+        for (int qz = 0; qz < NQ; ++qz) {
+          const T w = wxy * CT::W(qz);
+          G[qz][0] = w * a0 * a0 / det;
+          G[qz][1] = T(0);
+          G[qz][2] = T(0);
+          G[qz][3] = w * a1 * a1 / det;
+          G[qz][4] = T(0);
+          G[qz][5] = w * a2 * a2 / det;
+          Wd[qz] = w * det;
+          if (NEED_C) {
+  #pragma unroll
+            for (int i = 0; i < 9; ++i) Cm[qz][i] = T(0);
+            Cm[qz][0] = w * a0;
+            Cm[qz][4] = w * a1;
+            Cm[qz][8] = w * a2;
+          }
         }
-      }
-    } else {
-      // vertices X[v][a], v = vx + 2 vy + 4 vz
-      T X[8][3];
-#pragma unroll
-      for (int v = 0; v < 8; ++v) {
-        const long long gv =
-            ((long long)(cz + ((v >> 2) & 1)) * (L.n[1] + 1) + (cy + ((v >> 1) & 1))) * (L.n[0] + 1) + (cx + (v & 1));
-#pragma unroll
-        for (int a = 0; a < 3; ++a) X[v][a] = L.vert[gv * 3 + a];
-      }
-      const T xi = CT::W(NQ + ix), eta = CT::W(NQ + iy);
-      // column 0 (d/dxi) at zeta = 0 and 1: bilinear in eta of the x-edge differences
-      // column 1 (d/deta) at zeta = 0 and 1: in xi of the y-edge differences
-      // column 2 (d/dzeta): bilinear in (xi, eta) of the z-edge differences (constant in zeta)
-      T c0[2][3], c1[2][3], c2[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-#pragma unroll
-        for (int z = 0; z < 2; ++z) {
-          const T e00 = X[4 * z + 1][a] - X[4 * z + 0][a], e10 = X[4 * z + 3][a] - X[4 * z + 2][a];
-          c0[z][a] = e00 + eta * (e10 - e00);
-          const T f00 = X[4 * z + 2][a] - X[4 * z + 0][a], f10 = X[4 * z + 3][a] - X[4 * z + 1][a];
-          c1[z][a] = f00 + xi * (f10 - f00);
+      } else {
+        // vertices X[v][a], v = vx + 2 vy + 4 vz
+        T X[8][3];
+  #pragma unroll
+        for (int v = 0; v < 8; ++v) {
+          const long long gv =
+              ((long long)(cz + ((v >> 2) & 1)) * (L.n[1] + 1) + (cy + ((v >> 1) & 1))) * (L.n[0] + 1) + (cx + (v & 1));
+  #pragma unroll
+          for (int a = 0; a < 3; ++a) X[v][a] = L.vert[gv * 3 + a];
         }
-        const T g00 = X[4][a] - X[0][a], g10 = X[5][a] - X[1][a], g01 = X[6][a] - X[2][a], g11 = X[7][a] - X[3][a];
-        const T gl = g00 + xi * (g10 - g00), gh = g01 + xi * (g11 - g01);
-        c2[a] = gl + eta * (gh - gl);
-      }
-#pragma unroll
-      for (int qz = 0; qz < NQ; ++qz) {
-        const T zeta = CT::W(NQ + qz);
-        T J[3][3];
-#pragma unroll
+        const T xi = CT::W(NQ + ix), eta = CT::W(NQ + iy);
+        // column 0 (d/dxi) at zeta = 0 and 1: bilinear in eta of the x-edge differences
+        // column 1 (d/deta) at zeta = 0 and 1: in xi of the y-edge differences
+        // column 2 (d/dzeta): bilinear in (xi, eta) of the z-edge differences (constant in zeta)
+        T c0[2][3], c1[2][3], c2[3];
+  #pragma unroll
         for (int a = 0; a < 3; ++a) {
-          J[a][0] = c0[0][a] + zeta * (c0[1][a] - c0[0][a]);
-          J[a][1] = c1[0][a] + zeta * (c1[1][a] - c1[0][a]);
-          J[a][2] = c2[a];
+  #pragma unroll
+          for (int z = 0; z < 2; ++z) {
+            const T e00 = X[4 * z + 1][a] - X[4 * z + 0][a], e10 = X[4 * z + 3][a] - X[4 * z + 2][a];
+            c0[z][a] = e00 + eta * (e10 - e00);
+            const T f00 = X[4 * z + 2][a] - X[4 * z + 0][a], f10 = X[4 * z + 3][a] - X[4 * z + 1][a];
+            c1[z][a] = f00 + xi * (f10 - f00);
+          }
+          const T g00 = X[4][a] - X[0][a], g10 = X[5][a] - X[1][a], g01 = X[6][a] - X[2][a], g11 = X[7][a] - X[3][a];
+          const T gl = g00 + xi * (g10 - g00), gh = g01 + xi * (g11 - g01);
+          c2[a] = gl + eta * (gh - gl);
         }
-        T adj[3][3];
-        adj[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-        adj[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
-        adj[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
-        adj[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-        adj[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
-        adj[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
-        adj[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-        adj[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
-        adj[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-        const T det = J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
-        const T w = wxy * CT::W(qz);
-        const T wd = w / det;
-        G[qz][0] = wd * (adj[0][0] * adj[0][0] + adj[0][1] * adj[0][1] + adj[0][2] * adj[0][2]);
-        G[qz][1] = wd * (adj[0][0] * adj[1][0] + adj[0][1] * adj[1][1] + adj[0][2] * adj[1][2]);
-        G[qz][2] = wd * (adj[0][0] * adj[2][0] + adj[0][1] * adj[2][1] + adj[0][2] * adj[2][2]);
-        G[qz][3] = wd * (adj[1][0] * adj[1][0] + adj[1][1] * adj[1][1] + adj[1][2] * adj[1][2]);
-        G[qz][4] = wd * (adj[1][0] * adj[2][0] + adj[1][1] * adj[2][1] + adj[1][2] * adj[2][2]);
-        G[qz][5] = wd * (adj[2][0] * adj[2][0] + adj[2][1] * adj[2][1] + adj[2][2] * adj[2][2]);
-        Wd[qz] = w * det;
-        if (NEED_C) {
-#pragma unroll
-          for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) Cm[qz][a * 3 + b] = w * adj[a][b];
+  #pragma unroll
+        for (int qz = 0; qz < NQ; ++qz) {
+          const T zeta = CT::W(NQ + qz);
+          T J[3][3];
+  #pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            J[a][0] = c0[0][a] + zeta * (c0[1][a] - c0[0][a]);
+            J[a][1] = c1[0][a] + zeta * (c1[1][a] - c1[0][a]);
+            J[a][2] = c2[a];
+          }
+          T adj[3][3];
+          adj[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+          adj[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+          adj[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+          adj[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+          adj[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+          adj[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+          adj[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+          adj[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+          adj[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+          const T det = J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
+          const T w = wxy * CT::W(qz);
+          const T wd = w / det;
+          G[qz][0] = wd * (adj[0][0] * adj[0][0] + adj[0][1] * adj[0][1] + adj[0][2] * adj[0][2]);
+          G[qz][1] = wd * (adj[0][0] * adj[1][0] + adj[0][1] * adj[1][1] + adj[0][2] * adj[1][2]);
+          G[qz][2] = wd * (adj[0][0] * adj[2][0] + adj[0][1] * adj[2][1] + adj[0][2] * adj[2][2]);
+          G[qz][3] = wd * (adj[1][0] * adj[1][0] + adj[1][1] * adj[1][1] + adj[1][2] * adj[1][2]);
+          G[qz][4] = wd * (adj[1][0] * adj[2][0] + adj[1][1] * adj[2][1] + adj[1][2] * adj[2][2]);
+          G[qz][5] = wd * (adj[2][0] * adj[2][0] + adj[2][1] * adj[2][1] + adj[2][2] * adj[2][2]);
+          Wd[qz] = w * det;
+          if (NEED_C) {
+  #pragma unroll
+            for (int a = 0; a < 3; ++a)
+  #pragma unroll
+              for (int b = 0; b < 3; ++b) Cm[qz][a * 3 + b] = w * adj[a][b];
+          }
         }
       }
     }
@@ -528,6 +655,37 @@ __global__ void __launch_bounds__(32 * WARPS)
         const long long gi = lattice_index<3, T>(L.Pn, (K - 1) * cx + ix, (K - 1) * cy + iy, (K - 1) * cz + iz);
         atomicAdd(&yp[gi], s);
       }
+    }
+  }
+}
+
+}  // namespace smf
+
+namespace smf {
+
+// Per-point geometry of every cell for the column kernel, written once at setup:
+// geo[cell][field][qz][iy][ix], fields G (6), Cm (9), Wd (1) as in col_geometry.
+template <int K, typename T>
+__global__ void k_col_geometry(const LevelDesc<T> L, T *__restrict__ geo) {
+  pdl_enter();
+  constexpr int NV = K + 1, NQ = K + 1, ST = NQ * NV * NV;
+  SMF_GRID_LOOP(t, L.n_cells * NV * NV) {
+    const long long cell = t / (NV * NV);
+    const int r = (int)(t - cell * NV * NV), iy = r / NV, ix = r - iy * NV;
+    const int cx = (int)(cell % L.n[0]);
+    const long long rr = cell / L.n[0];
+    const int cy = (int)(rr % L.n[1]), cz = (int)(rr / L.n[1]);
+    T G[NQ][6], Cm[NQ][9], Wd[NQ];
+    col_geometry<K, T, false, true>(L, ix, iy, cx, cy, cz, G, Cm, Wd);
+    T *base = geo + cell * (long long)(16 * ST) + iy * NV + ix;
+#pragma unroll
+    for (int qz = 0; qz < NQ; ++qz) {
+      T *q = base + qz * NV * NV;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) q[i * ST] = G[qz][i];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) q[(6 + i) * ST] = Cm[qz][i];
+      q[15 * ST] = Wd[qz];
     }
   }
 }

@@ -3,6 +3,7 @@
 #include <cstdlib>
 #include "apply.cuh"
 #include "apply_col.cuh"
+#include "vec.cuh"
 #include "host_tables.h"
 
 namespace smf {
@@ -30,30 +31,30 @@ static int launch_apply_dim(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode
 
 template <int K, typename T, int MODE, bool CART, int WARPS, bool FUSED>
 static int launch_col_w(const LevelDesc<T> &L, const T *u, const T *p, T *yu, T *yp, cudaStream_t s,
-                        const Fuse<T> &F) {
+                        const Fuse<T> &F, const T *geo) {
   using CS = ColShape<K>;
   const long long cpb = (long long)CS::CPW * (WARPS == 3 ? 1 : WARPS);  // WARPS 3: one cell group, 3 components
   const long long blocks = (L.n_cells + cpb - 1) / cpb;
   launch_kernel(stokes_cell_apply_col<K, T, MODE, CART, WARPS, FUSED>, dim3((unsigned)blocks), dim3(32 * WARPS), 0, s,
-                L, u, p, yu, yp, F);
+                L, u, p, yu, yp, F, geo);
   return 0;
 }
 
 template <int K, typename T, int MODE, bool CART, bool FUSED>
 static int launch_col(const LevelDesc<T> &L, const T *u, const T *p, T *yu, T *yp, cudaStream_t s, int shape,
-                      const Fuse<T> &F) {
+                      const Fuse<T> &F, const T *geo) {
   switch (shape) {
-    case 1: return launch_col_w<K, T, MODE, CART, 1, FUSED>(L, u, p, yu, yp, s, F);
-    case 3: return launch_col_w<K, T, MODE, CART, 3, FUSED>(L, u, p, yu, yp, s, F);
-    default: return launch_col_w<K, T, MODE, CART, 4, FUSED>(L, u, p, yu, yp, s, F);
+    case 1: return launch_col_w<K, T, MODE, CART, 1, FUSED>(L, u, p, yu, yp, s, F, geo);
+    case 3: return launch_col_w<K, T, MODE, CART, 3, FUSED>(L, u, p, yu, yp, s, F, geo);
+    default: return launch_col_w<K, T, MODE, CART, 4, FUSED>(L, u, p, yu, yp, s, F, geo);
   }
 }
 
 template <int K, typename T, int MODE, bool FUSED>
 static int launch_col_mode(const LevelDesc<T> &L, const T *u, const T *p, T *yu, T *yp, cudaStream_t s, int shape,
-                           const Fuse<T> &F) {
-  return L.cartesian ? launch_col<K, T, MODE, true, FUSED>(L, u, p, yu, yp, s, shape, F)
-                     : launch_col<K, T, MODE, false, FUSED>(L, u, p, yu, yp, s, shape, F);
+                           const Fuse<T> &F, const T *geo) {
+  return L.cartesian ? launch_col<K, T, MODE, true, FUSED>(L, u, p, yu, yp, s, shape, F, geo)
+                     : launch_col<K, T, MODE, false, FUSED>(L, u, p, yu, yp, s, shape, F, geo);
 }
 
 // shape: 3D launch shape chosen by the autotuner (1 / 4 warps per CTA column kernel, 3 = column
@@ -61,16 +62,16 @@ static int launch_col_mode(const LevelDesc<T> &L, const T *u, const T *p, T *yu,
 // 0 default = column kernel with 4 warps).
 template <int K, typename T>
 int launch_cell_apply_k(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, const T *u, const T *p, T *yu, T *yp,
-                        cudaStream_t s, int shape) {
+                        cudaStream_t s, int shape, const T *geo) {
   if (L.dim == 3 && !getenv_generic() && shape >= 0) {
     const Fuse<T> F{};
     switch (mode) {
-      case kApplyA: return launch_col_mode<K, T, kApplyA, false>(L, u, p, yu, yp, s, shape, F);
-      case kApplyBT: return launch_col_mode<K, T, kApplyBT, false>(L, u, p, yu, yp, s, shape, F);
-      case kApplyB: return launch_col_mode<K, T, kApplyB, false>(L, u, p, yu, yp, s, shape, F);
-      case kApplyA | kApplyBT: return launch_col_mode<K, T, kApplyA | kApplyBT, false>(L, u, p, yu, yp, s, shape, F);
+      case kApplyA: return launch_col_mode<K, T, kApplyA, false>(L, u, p, yu, yp, s, shape, F, geo);
+      case kApplyBT: return launch_col_mode<K, T, kApplyBT, false>(L, u, p, yu, yp, s, shape, F, geo);
+      case kApplyB: return launch_col_mode<K, T, kApplyB, false>(L, u, p, yu, yp, s, shape, F, geo);
+      case kApplyA | kApplyBT: return launch_col_mode<K, T, kApplyA | kApplyBT, false>(L, u, p, yu, yp, s, shape, F, geo);
       case kApplyA | kApplyBT | kApplyB:
-        return launch_col_mode<K, T, kApplyA | kApplyBT | kApplyB, false>(L, u, p, yu, yp, s, shape, F);
+        return launch_col_mode<K, T, kApplyA | kApplyBT | kApplyB, false>(L, u, p, yu, yp, s, shape, F, geo);
       default: break;
     }
   }
@@ -81,19 +82,26 @@ int launch_cell_apply_k(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, co
                      : launch_apply_dim<2, K, T, false>(L, tab, mode, u, p, yu, yp, s);
 }
 
+template <int K, typename T>
+int launch_col_geometry_k(const LevelDesc<T> &L, T *geo, cudaStream_t s) {
+  constexpr int NV = K + 1;
+  launch_kernel(k_col_geometry<K, T>, dim3(vec_blocks(L.n_cells * NV * NV)), dim3(kVecThreads), 0, s, L, geo);
+  return 0;
+}
+
 // Fused application (3D column kernel only; shape >= 0): returns -1 for a mode without a fused
 // instantiation so that the caller can reject it.
 template <int K, typename T>
 int launch_cell_apply_fused_k(const LevelDesc<T> &L, int mode, const T *u, const T *p, T *yu, T *yp, cudaStream_t s,
-                              int shape, const Fuse<T> &F) {
+                              int shape, const Fuse<T> &F, const T *geo) {
   if (L.dim != 3 || shape < 0) return -1;
   switch (mode) {
-    case kApplyA: return launch_col_mode<K, T, kApplyA, true>(L, u, p, yu, yp, s, shape, F);
-    case kApplyBT: return launch_col_mode<K, T, kApplyBT, true>(L, u, p, yu, yp, s, shape, F);
-    case kApplyB: return launch_col_mode<K, T, kApplyB, true>(L, u, p, yu, yp, s, shape, F);
-    case kApplyA | kApplyBT: return launch_col_mode<K, T, kApplyA | kApplyBT, true>(L, u, p, yu, yp, s, shape, F);
+    case kApplyA: return launch_col_mode<K, T, kApplyA, true>(L, u, p, yu, yp, s, shape, F, geo);
+    case kApplyBT: return launch_col_mode<K, T, kApplyBT, true>(L, u, p, yu, yp, s, shape, F, geo);
+    case kApplyB: return launch_col_mode<K, T, kApplyB, true>(L, u, p, yu, yp, s, shape, F, geo);
+    case kApplyA | kApplyBT: return launch_col_mode<K, T, kApplyA | kApplyBT, true>(L, u, p, yu, yp, s, shape, F, geo);
     case kApplyA | kApplyBT | kApplyB:
-      return launch_col_mode<K, T, kApplyA | kApplyBT | kApplyB, true>(L, u, p, yu, yp, s, shape, F);
+      return launch_col_mode<K, T, kApplyA | kApplyBT | kApplyB, true>(L, u, p, yu, yp, s, shape, F, geo);
     default: return -1;
   }
 }
@@ -139,15 +147,18 @@ int launch_cell_diag_k(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dS
   namespace smf {                                                                                              \
   template int launch_cell_apply_k<KK, float>(const LevelDesc<float> &, const Tab1D<float> *, int,             \
                                                const float *, const float *, float *, float *, cudaStream_t,   \
-                                               int);                                                           \
+                                               int, const float *);                                                           \
   template int launch_cell_apply_k<KK, double>(const LevelDesc<double> &, const Tab1D<double> *, int,          \
                                                 const double *, const double *, double *, double *,            \
-                                                cudaStream_t, int);                                             \
+                                                cudaStream_t, int, const double *);                                             \
   template int launch_cell_apply_fused_k<KK, float>(const LevelDesc<float> &, int, const float *, const float *, \
-                                                     float *, float *, cudaStream_t, int, const Fuse<float> &);   \
+                                                     float *, float *, cudaStream_t, int, const Fuse<float> &,       \
+                                                     const float *);   \
   template int launch_cell_apply_fused_k<KK, double>(const LevelDesc<double> &, int, const double *,             \
                                                       const double *, double *, double *, cudaStream_t, int,       \
-                                                      const Fuse<double> &);                                      \
+                                                      const Fuse<double> &, const double *);                                      \
+  template int launch_col_geometry_k<KK, float>(const LevelDesc<float> &, float *, cudaStream_t);             \
+  template int launch_col_geometry_k<KK, double>(const LevelDesc<double> &, double *, cudaStream_t);          \
   template int launch_cell_diag_k<KK, double>(const LevelDesc<double> &, const Tab1D<double> *, double *,      \
                                                double *, double *, cudaStream_t);                              \
   template int upload_col_tables<KK>(const Tab1D<double> &, cudaStream_t);                                     \

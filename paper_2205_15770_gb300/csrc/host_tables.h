@@ -14,18 +14,20 @@ double tridiag_max_eig(const std::vector<double> &a, const std::vector<double> &
 
 template <typename T>
 int launch_cell_apply(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, const T *u, const T *p, T *yu, T *yp,
-                      cudaStream_t s, int shape);
+                      cudaStream_t s, int shape, const T *geo = nullptr);
 template <typename T>
 int launch_cell_diag(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dSloc, T *dMp, cudaStream_t s);
 template <int K, typename T>
 int launch_cell_apply_k(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, const T *u, const T *p, T *yu, T *yp,
-                        cudaStream_t s, int shape);
+                        cudaStream_t s, int shape, const T *geo);
 template <typename T>
 int launch_cell_apply_fused(const LevelDesc<T> &L, int mode, const T *u, const T *p, T *yu, T *yp, cudaStream_t s,
-                            int shape, const Fuse<T> &F);
+                            int shape, const Fuse<T> &F, const T *geo);
 template <int K, typename T>
 int launch_cell_apply_fused_k(const LevelDesc<T> &L, int mode, const T *u, const T *p, T *yu, T *yp, cudaStream_t s,
-                              int shape, const Fuse<T> &F);
+                              int shape, const Fuse<T> &F, const T *geo);
+template <int K, typename T>
+int launch_col_geometry_k(const LevelDesc<T> &L, T *geo, cudaStream_t s);
 template <int K, typename T>
 int launch_cell_grad_k(const LevelDesc<T> &L, const Tab1D<T> *tab, const T *u, const T *lam, T *g, cudaStream_t s);
 template <int K>
