@@ -253,8 +253,10 @@ struct Runner {
   cudaStream_t s;
   std::vector<LevelRT<T>> &L;
   const Tab1D<T> *tab;
-  explicit Runner(stokes_ctx *c)
-      : C(c), s(c->s), L(levels<T>(c)), tab(tables<T>(c)) {}
+  explicit Runner(stokes_ctx *c) : C(c), s(c->s), L(levels<T>(c)), tab(tables<T>(c)) {}
+  // launches on the caller's stream (which may be the default stream 0)
+  struct OnStream {};
+  Runner(stokes_ctx *c, cudaStream_t stream, OnStream) : C(c), s(stream), L(levels<T>(c)), tab(tables<T>(c)) {}
 
   void note() {
     if (C->capturing)
@@ -295,8 +297,12 @@ struct Runner {
     note();
   }
   void vmult(int l, const T *x, T *y, bool identity) {
-    apply(l, kApplyA | kApplyBT | kApplyB, x, x + nu(l), y, y + nu(l));
-    if (identity) vec(k_identity_rows<T>, nu(l), L[l].d, x, y);
+    if (identity) {  // y = identity rows of x (0 elsewhere), then the cell kernel accumulates
+      vec(k_init_identity<T>, nu(l) + np(l), L[l].d, x, y);
+      apply_nz(l, kApplyA | kApplyBT | kApplyB, x, x + nu(l), y, y + nu(l));
+    } else {
+      apply(l, kApplyA | kApplyBT | kApplyB, x, x + nu(l), y, y + nu(l));
+    }
   }
   void sub(const T *a, const T *b, T *out, long long n) { vec(k_sub<T>, n, a, b, out, n); }
 
@@ -1825,12 +1831,20 @@ int stokes_vmult(stokes_ctx *C, int level, int precision, const void *x, void *y
     if (C) C->err = "invalid stokes_vmult arguments";
     return STOKES_EINVAL;
   }
-  StreamGuard sg(C, stream);
+  // The operator reads only x and the context's read-only level data, so it is launched directly
+  // on the caller's stream (no join with the context stream).
   if (precision == 64)
-    Runner<double>(C).vmult(level, (const double *)x, (double *)y, true);
+    Runner<double>(C, (cudaStream_t)stream, Runner<double>::OnStream{}).vmult(level, (const double *)x, (double *)y,
+                                                                           true);
   else
-    Runner<float>(C).vmult(level, (const float *)x, (float *)y, true);
-  return finish(C, STOKES_OK);
+    Runner<float>(C, (cudaStream_t)stream, Runner<float>::OnStream{}).vmult(level, (const float *)x, (float *)y, true);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cuda_fail(e, "stokes_vmult launch", __FILE__, __LINE__);
+    C->err = g_last_error;
+    return STOKES_ECUDA;
+  }
+  return STOKES_OK;
 }
 
 int stokes_apply_blocks(stokes_ctx *C, int level, int precision, int blocks, const void *u, const void *p, void *yu,

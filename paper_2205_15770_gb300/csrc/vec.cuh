@@ -269,17 +269,21 @@ __global__ void k_convert_zero(const Tin *__restrict__ a, Tout *__restrict__ out
   }
 }
 
-// y_i = x_i on constrained velocity DoFs (identity rows of K).
+// y = x on constrained velocity DoFs (identity rows of K), 0 on every other entry of [u | p]:
+// the start of y = K x before the cell kernel accumulates into the free rows.
 template <typename T>
-__global__ void k_identity_rows(const LevelDesc<T> L, const T *__restrict__ x, T *__restrict__ y) {
+__global__ void k_init_identity(const LevelDesc<T> L, const T *__restrict__ x, T *__restrict__ y) {
   pdl_enter();
-  SMF_GRID_LOOP(i, L.n_u) {
-    long long node = i % L.nv;
-    int gx = (int)(node % L.N[0]);
-    long long r = node / L.N[0];
-    int gy = (int)(r % L.N[1]);
-    int gz = (int)(r / L.N[1]);
-    if (vel_constrained(L.N, L.faces, L.dim, gx, gy, gz)) y[i] = x[i];
+  SMF_GRID_LOOP(i, L.n_u + L.n_p) {
+    T v = T(0);
+    if (i < L.n_u) {
+      const long long node = i % L.nv;
+      const int gx = (int)(node % L.N[0]);
+      const long long r = node / L.N[0];
+      const int gy = (int)(r % L.N[1]), gz = (int)(r / L.N[1]);
+      if (vel_constrained(L.N, L.faces, L.dim, gx, gy, gz)) v = x[i];
+    }
+    y[i] = v;
   }
 }
 
