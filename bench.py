@@ -73,6 +73,14 @@ def flops_per_cell_A(k, trilinear, dim=3):
     return dim * per_comp + geo
 
 
+def tuning_string(S):
+    """The setup's choices of a context as a STOKES_TUNING value (to profile the same configuration:
+    timings taken under a profiler choose differently)."""
+    j = lambda v: ",".join(str(int(x)) for x in v)
+    return (f"s32={j(S.launch_shapes(32))};s64={j(S.launch_shapes(64))};f32={j(S.fused_levels(32))};"
+            f"f64={j(S.fused_levels(64))}")
+
+
 def fp32_peak_tflops(sm_count, clock_mhz):
     """FP32 FMA peak: SMs x 128 lanes x 2 flops x clock."""
     return sm_count * 128 * 2 * clock_mhz * 1e6 / 1e12
@@ -384,6 +392,7 @@ def run_ours(args):
         "clocks": clk,
         "launch_shapes_fp32": S32[0].launch_shapes(32),
         "fused_smoothing_levels": {"fp32": S32[0].fused_levels(32), "fp64": S32[0].fused_levels(64)},
+        "tuning": tuning_string(S32[0]),
         "batched": batched,
         "adjoint": adjoint,
     }

@@ -941,12 +941,38 @@ static int finish(stokes_ctx *C, int st) {
   return STOKES_OK;
 }
 
+// The setup's timings replay CUDA graphs of the candidate work, so that they compare the GPU's
+// time for the work and not the host's launch rate (which a profiler attached to the process
+// changes).
+template <typename F>
+static int capture_graph(stokes_ctx *C, F &&work, cudaGraphExec_t *exec) {
+  SMF_CUDA_OK(cudaStreamBeginCapture(C->s, cudaStreamCaptureModeThreadLocal));
+  C->capturing = true;
+  C->cap_count = 0;
+  work();
+  C->capturing = false;
+  cudaGraph_t g;
+  SMF_CUDA_OK(cudaStreamEndCapture(C->s, &g));
+  const cudaError_t e = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  SMF_CUDA_OK(e);
+  return STOKES_OK;
+}
+static int time_graph(stokes_ctx *C, cudaGraphExec_t ex, cudaEvent_t e0, cudaEvent_t e1, float *ms) {
+  SMF_CUDA_OK(cudaEventRecord(e0, C->s));
+  SMF_CUDA_OK(cudaGraphLaunch(ex, C->s));
+  SMF_CUDA_OK(cudaEventRecord(e1, C->s));
+  SMF_CUDA_OK(cudaEventSynchronize(e1));
+  SMF_CUDA_OK(cudaEventElapsedTime(ms, e0, e1));
+  return STOKES_OK;
+}
+
 // Autotuner of the 3D cell-kernel launch shape, per level and precision: the velocity-block
-// apply is timed (CUDA events on the context stream) for the column kernel with 1 and 4
-// warps per CTA, the column kernel with the velocity components split over 3 warps, and the
-// point-per-thread kernel.  Candidates are interleaved over several
-// rounds and each keeps its best round, so clock ramps and one-off effects do not bias the
-// choice; the default shape (4 warps) is kept unless another is faster by more than 3 %.
+// apply is timed (graph replays, CUDA events on the context stream) for the column kernel with
+// 1 and 4 warps per CTA, the column kernel with the velocity components split over 3 warps, and
+// the point-per-thread kernel.  Candidates are interleaved over several rounds and each keeps
+// its best round, so clock ramps and one-off effects do not bias the choice; the default shape
+// (4 warps) is kept unless another is faster by more than 3 %.
 template <typename T>
 static int autotune_level(stokes_ctx *C, LevelRT<T> &R, const Tab1D<T> *tab) {
   if (R.d.dim != 3) return STOKES_OK;
@@ -956,39 +982,42 @@ static int autotune_level(stokes_ctx *C, LevelRT<T> &R, const Tab1D<T> *tab) {
   cudaEvent_t e0, e1;
   SMF_CUDA_OK(cudaEventCreate(&e0));
   SMF_CUDA_OK(cudaEventCreate(&e1));
+  cudaGraphExec_t ex[NC] = {};
   float best[NC] = {1e30f, 1e30f, 1e30f, 1e30f};
-  for (int w = 0; w < 3; ++w)
-    for (int c : cands) {
-      R.shape = c;
-      launch_cell_apply<T>(R.d, tab, kApplyA, R.x, nullptr, R.r, nullptr, C->s, R.shape, R.geo);
-    }
-  for (int round = 0; round < rounds; ++round)
-    for (int ci = 0; ci < NC; ++ci) {
-      R.shape = cands[ci];
-      cudaEventRecord(e0, C->s);
-      for (int r = 0; r < reps; ++r)
-        launch_cell_apply<T>(R.d, tab, kApplyA, R.x, nullptr, R.r, nullptr, C->s, R.shape, R.geo);
-      cudaEventRecord(e1, C->s);
-      SMF_CUDA_OK(cudaEventSynchronize(e1));
+  int st = STOKES_OK;
+  for (int ci = 0; ci < NC && st == STOKES_OK; ++ci) {
+    R.shape = cands[ci];
+    st = capture_graph(
+        C,
+        [&] {
+          for (int r = 0; r < reps; ++r)
+            launch_cell_apply<T>(R.d, tab, kApplyA, R.x, nullptr, R.r, nullptr, C->s, R.shape, R.geo);
+        },
+        &ex[ci]);
+  }
+  for (int round = -1; round < rounds && st == STOKES_OK; ++round)  // round -1: warm-up
+    for (int ci = 0; ci < NC && st == STOKES_OK; ++ci) {
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      best[ci] = std::min(best[ci], ms);
+      st = time_graph(C, ex[ci], e0, e1, &ms);
+      if (round >= 0) best[ci] = std::min(best[ci], ms);
       C->launches += reps;
     }
-  C->launches += 3 * NC;
+  for (auto e : ex)
+    if (e) cudaGraphExecDestroy(e);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != STOKES_OK) return st;
   int choice = 0;
   for (int ci = 1; ci < NC; ++ci)
     if (best[ci] < 0.97f * best[choice]) choice = ci;
   R.shape = cands[choice];
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   SMF_CUDA_OK(cudaMemsetAsync(R.r, 0, (R.d.n_u + R.d.n_p) * sizeof(T), C->s));
   return STOKES_OK;
 }
 
-// Fused or unfused smoothing per level: where the fused smoother is eligible, one smoothing step
-// of each kind is timed (CUDA events on the context stream, interleaved rounds, best round kept)
-// on the level's own buffers; the fused form is kept unless the unfused one is faster by more
+// Fused or unfused smoothing per level: where the fused smoother is eligible, smoothing steps of
+// each kind are timed (graph replays, CUDA events on the context stream, interleaved rounds, best
+// round kept) on the level's own buffers; the fused form is kept unless the unfused one is faster by more
 // than 3 %.  The fused form saves launches and vector passes but makes every cell-kernel gather
 // read several vectors, which costs more than it saves on the largest levels.
 template <typename T>
@@ -1000,23 +1029,69 @@ static int autotune_fusion(stokes_ctx *C, int l) {
   cudaEvent_t e0, e1;
   SMF_CUDA_OK(cudaEventCreate(&e0));
   SMF_CUDA_OK(cudaEventCreate(&e1));
+  cudaGraphExec_t ex[2] = {};
   float best[2] = {1e30f, 1e30f};
-  for (int round = -1; round < rounds; ++round)  // round -1: warm-up
-    for (int f = 0; f < 2; ++f) {
-      L.fuse = f == 1;
-      cudaEventRecord(e0, C->s);
-      for (int r = 0; r < reps; ++r) R.smooth(l, L.x, L.b, 1, false);
-      cudaEventRecord(e1, C->s);
-      SMF_CUDA_OK(cudaEventSynchronize(e1));
+  int st = STOKES_OK;
+  for (int f = 0; f < 2 && st == STOKES_OK; ++f) {
+    L.fuse = f == 1;
+    st = capture_graph(
+        C,
+        [&] {
+          for (int r = 0; r < reps; ++r) R.smooth(l, L.x, L.b, 1, false);
+        },
+        &ex[f]);
+  }
+  for (int round = -1; round < rounds && st == STOKES_OK; ++round)  // round -1: warm-up
+    for (int f = 0; f < 2 && st == STOKES_OK; ++f) {
       float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
+      st = time_graph(C, ex[f], e0, e1, &ms);
       if (round >= 0) best[f] = std::min(best[f], ms);
     }
-  L.fuse = !(best[0] < 0.97f * best[1]);
+  for (auto e : ex)
+    if (e) cudaGraphExecDestroy(e);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (st != STOKES_OK) return st;
+  L.fuse = !(best[0] < 0.97f * best[1]);
   SMF_CUDA_OK(cudaMemsetAsync(L.x, 0, (L.d.n_u + L.d.n_p) * sizeof(T), C->s));
   return zero_level_work(C, L);
+}
+
+// STOKES_TUNING="s32=a,b,..;s64=..;f32=..;f64=.." replaces the setup's timings: launch shapes
+// (1, 3, 4 or -1) and smoother forms (1 fused, 0 unfused) per level, coarsest first, for FP32 and
+// FP64.  Timings taken under a profiler differ from plain runs; a profile of the configuration
+// that a plain run chose passes that run's choices here (stokes_get_launch_shape and
+// stokes_get_smoother_fusion read them).
+static int parse_tuning(const char *spec, int nl, std::vector<int> tune[4]) {
+  const char *keys[4] = {"s32=", "s64=", "f32=", "f64="};
+  for (int t = 0; t < 4; ++t) {
+    const char *p = std::strstr(spec, keys[t]);
+    if (!p) {
+      set_error(std::string("STOKES_TUNING lacks ") + keys[t]);
+      return STOKES_EINVAL;
+    }
+    p += 4;
+    tune[t].clear();
+    while (true) {
+      char *end = nullptr;
+      const long v = std::strtol(p, &end, 10);
+      if (end == p) break;
+      const bool ok = t < 2 ? (v == 1 || v == 3 || v == 4 || v == -1) : (v == 0 || v == 1);
+      if (!ok) {
+        set_error(std::string("STOKES_TUNING: invalid value in ") + keys[t]);
+        return STOKES_EINVAL;
+      }
+      tune[t].push_back((int)v);
+      p = end;
+      if (*p != ',') break;
+      ++p;
+    }
+    if ((int)tune[t].size() != nl) {
+      set_error(std::string("STOKES_TUNING: ") + keys[t] + " needs one value per level");
+      return STOKES_EINVAL;
+    }
+  }
+  return STOKES_OK;
 }
 
 static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho, const double *mu_cell,
@@ -1208,10 +1283,22 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
     if ((st = build_xfer(C, C->L32[l].d, C->L32[l - 1].d, tt64, C->L32[l].xf))) return st;
   }
 
-  // launch-shape autotuning (STOKES_NO_AUTOTUNE=1 keeps the default shape)
+  // launch-shape autotuning (STOKES_NO_AUTOTUNE=1 keeps the default shape; STOKES_TUNING fixes
+  // shapes and smoother forms instead, see parse_tuning)
+  std::vector<int> tune[4];
+  const bool pinned = getenv("STOKES_TUNING") != nullptr;
+  if (pinned && (st = parse_tuning(getenv("STOKES_TUNING"), nl, tune))) return st;
+  if (pinned) {
+    for (int l = 0; l < nl; ++l) {
+      if (dim == 3) {
+        C->L32[l].shape = tune[0][l];
+        C->L64[l].shape = tune[1][l];
+      }
+    }
+  }
   {
     const char *na = getenv("STOKES_NO_AUTOTUNE");
-    if (!(na && na[0] == '1')) {
+    if (!(na && na[0] == '1') && !pinned) {
       for (int l = 0; l < nl; ++l) {
         if ((st = autotune_level<double>(C, C->L64[l], C->tab64))) return st;
         if ((st = autotune_level<float>(C, C->L32[l], C->tab32))) return st;
@@ -1268,11 +1355,17 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
   // fused or unfused smoothing per level (STOKES_NO_AUTOTUNE=1 keeps the fused form)
   {
     const char *na = getenv("STOKES_NO_AUTOTUNE");
-    if (!(na && na[0] == '1'))
+    if (pinned) {
+      for (int l = 0; l < nl; ++l) {
+        C->L32[l].fuse = tune[2][l] != 0;
+        C->L64[l].fuse = tune[3][l] != 0;
+      }
+    } else if (!(na && na[0] == '1')) {
       for (int l = 1; l < nl; ++l) {
         if ((st = autotune_fusion<float>(C, l))) return st;
         if ((st = autotune_fusion<double>(C, l))) return st;
       }
+    }
   }
   SMF_CUDA_OK(cudaStreamSynchronize(C->s));
   SMF_CUDA_OK(cudaGetLastError());

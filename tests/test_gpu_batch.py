@@ -98,3 +98,15 @@ def test_every_launch_shape_gives_the_same_operator():
         if ref is None:
             ref = y
         assert np.abs(y - ref).max() <= 1e-13 * np.abs(ref).max(), shape
+
+
+def test_tuning_string_pins_shapes_and_smoother_forms(monkeypatch):
+    from paper_2205_15770_gb300 import StokesError, StokesMG
+    monkeypatch.setenv("STOKES_TUNING", "s32=4,1,3;s64=-1,3,1;f32=0,0,1;f64=0,1,0")
+    S = StokesMG(dim=3, n=(8, 8, 8), n_levels=3, k=2, kA=1, kS=2, m=2)
+    assert S.launch_shapes(32) == [4, 1, 3] and S.launch_shapes(64) == [-1, 3, 1]
+    assert S.fused_levels(32) == [False, False, True]
+    assert S.fused_levels(64) == [False, True, False]
+    monkeypatch.setenv("STOKES_TUNING", "s32=4,4;s64=4,4,4;f32=0,1,1;f64=0,1,1")  # wrong length
+    with pytest.raises(StokesError):
+        StokesMG(dim=3, n=(8, 8, 8), n_levels=3, k=2, kA=1, kS=2, m=2)
