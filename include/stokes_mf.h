@@ -68,7 +68,10 @@ typedef struct {
   int kS;               /* Chebyshev degree of S^-1_hat */
   int m;                /* pre- and post-smoothing steps */
   int cycle;            /* 0 = V-cycle, 1 = W-cycle (Algorithm 1, gamma = 1 / 2) */
-  int schur_diag;       /* 0 = local diagonal (Eq. diag loc), 1 = pressure mass (Eq. diag p) */
+  int schur_diag;       /* D_S~ of the pressure Chebyshev (Algorithm 2): 0 = local diagonal (Eq. diag loc),
+                           1 = pressure mass (Eq. diag p), 2 = diag(B D_A^-1 B^T) (Eq. diag d),
+                           3 = exact diag(B A^-1_hat B^T) (small meshes only: setup fails with
+                           STOKES_EINVAL when it needs more than 4096 probes) */
   int vcycle_fp32;      /* 1: stokes_solve preconditions with the FP32 cycle, 0: FP64 */
   int gmres_restart;    /* FGMRES restart length */
   int eig_iters;        /* Lanczos steps for lambda_max estimates */

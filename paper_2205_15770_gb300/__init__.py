@@ -78,7 +78,7 @@ class StokesMG:
         self._lib.stokes_default_opts(C.byref(opts))
         opts.kA, opts.kS, opts.m = kA, kS, m
         opts.cycle = {"V": 0, "W": 1}[cycle]
-        opts.schur_diag = {"loc": 0, "p": 1}[schur_diag]
+        opts.schur_diag = {"loc": 0, "p": 1, "d": 2, "exact": 3}[schur_diag]
         opts.vcycle_fp32 = 1 if vcycle_fp32 else 0
         opts.gmres_restart = restart
         opts.eig_iters = eig_iters
@@ -384,7 +384,7 @@ class StokesBatch:
         self._lib.stokes_default_opts(C.byref(opts))
         opts.kA, opts.kS, opts.m = kA, kS, m
         opts.cycle = {"V": 0, "W": 1}[cycle]
-        opts.schur_diag = {"loc": 0, "p": 1}[schur_diag]
+        opts.schur_diag = {"loc": 0, "p": 1, "d": 2, "exact": 3}[schur_diag]
         opts.vcycle_fp32 = 1 if vcycle_fp32 else 0
         opts.gmres_restart = restart
         opts.eig_iters = eig_iters

@@ -690,6 +690,93 @@ static int sum64(stokes_ctx *C, const double *a, long long n, double *dev_out) {
 // velocity: M = A on level l; pressure: M = S~.  Start vector: SplitMix64(seed) (velocity,
 // constrained entries zeroed) or SplitMix64(seed + 1) with the kernel direction D^{1/2} 1
 // projected out under full Dirichlet data.
+// ---- Schur-complement diagonals "d" and "exact" (Algorithm 2, choice of D_S~) by probing -----
+// On the structured grid, velocity nodes whose indices differ by a multiple of 2k+1 along every
+// axis never share a pressure row of B, and pressure nodes (k-1)(k_A+3)+1 apart along every axis
+// are never coupled by S~ = B A^-1_hat B^T (its reach is B^T, k_A applications of A and B, about
+// k_A + 2 cells).  Probing with one vector per colour therefore yields one entry per row.
+__device__ __forceinline__ bool probe_colour(const int *g, int dim, int P, int cx, int cy, int cz) {
+  return g[0] % P == cx && g[1] % P == cy && (dim < 3 || g[2] % P == cz);
+}
+// v = D_A^-1/2 on the free DoFs of velocity component comp in the colour, 0 elsewhere.
+__global__ void k_probe_vel(const LevelDesc<double> L, int comp, int P, int cx, int cy, int cz,
+                            const double *__restrict__ DAinv, double *__restrict__ v) {
+  pdl_enter();
+  SMF_GRID_LOOP(i, L.n_u) {
+    const long long node = i % L.nv;
+    const int c = (int)(i / L.nv);
+    const int g[3] = {(int)(node % L.N[0]), (int)((node / L.N[0]) % L.N[1]), (int)(node / ((long long)L.N[0] * L.N[1]))};
+    const bool on = c == comp && probe_colour(g, L.dim, P, cx, cy, cz) &&
+                    !vel_constrained(L.N, L.faces, L.dim, g[0], g[1], g[2]);
+    v[i] = on ? sqrt(DAinv[i]) : 0.0;
+  }
+}
+__global__ void k_add_sq(const double *__restrict__ y, double *__restrict__ acc, long long n) {
+  pdl_enter();
+  SMF_GRID_LOOP(i, n) acc[i] += y[i] * y[i];
+}
+// q = 1 on the pressure nodes of the colour; with add_from: acc += w on those nodes.
+__global__ void k_probe_pre(const LevelDesc<double> L, int P, int cx, int cy, int cz, double *__restrict__ q,
+                            const double *__restrict__ add_from, double *__restrict__ acc) {
+  pdl_enter();
+  SMF_GRID_LOOP(i, L.n_p) {
+    const int g[3] = {(int)(i % L.Pn[0]), (int)((i / L.Pn[0]) % L.Pn[1]), (int)(i / ((long long)L.Pn[0] * L.Pn[1]))};
+    const bool on = probe_colour(g, L.dim, P, cx, cy, cz);
+    if (add_from) {
+      if (on) acc[i] += add_from[i];
+    } else {
+      q[i] = on ? 1.0 : 0.0;
+    }
+  }
+}
+
+// D_d[i] = sum_j B_ij^2 / D_A,jj: one B application per colour and velocity component on the
+// probe D_A^-1/2 restricted to the colour; its squared entries add up to D_d.
+static int schur_diag_d(stokes_ctx *C, int l, double *dS) {
+  Runner<double> R(C);
+  LevelRT<double> &LV = C->L64[l];
+  const LevelDesc<double> &d = LV.d;
+  const int P = 2 * d.k + 1, nz = d.dim == 3 ? P : 1;
+  double *v = C->lz0, *y = C->lz1;
+  SMF_CUDA_OK(cudaMemsetAsync(dS, 0, d.n_p * sizeof(double), C->s));
+  for (int comp = 0; comp < d.dim; ++comp)
+    for (int cz = 0; cz < nz; ++cz)
+      for (int cy = 0; cy < P; ++cy)
+        for (int cx = 0; cx < P; ++cx) {
+          R.vec(k_probe_vel, d.n_u, d, comp, P, cx, cy, cz, (const double *)LV.DAinv, v);
+          R.apply(l, kApplyB, v, nullptr, nullptr, y);
+          R.vec(k_add_sq, d.n_p, (const double *)y, dS, d.n_p);
+        }
+  SMF_CUDA_OK(cudaGetLastError());
+  return STOKES_OK;
+}
+
+// D_exact[i] = (B A^-1_hat B^T)_ii with A^-1_hat = sigma Cheb(A, D_A, k_A): one S~ application per
+// pressure colour.  Meant for small meshes: more than 4096 colours are rejected.
+static int schur_diag_exact(stokes_ctx *C, int l, double *dS) {
+  Runner<double> R(C);
+  const LevelDesc<double> &d = C->L64[l].d;
+  const int P = (d.k - 1) * (C->o.kA + 3) + 1;
+  const int px = std::min(P, d.Pn[0]), py = std::min(P, d.Pn[1]), pz = d.dim == 3 ? std::min(P, d.Pn[2]) : 1;
+  if ((long long)px * py * pz > 4096) {
+    set_error("schur_diag exact: " + std::to_string((long long)px * py * pz) +
+              " probes needed (more than 4096); the exact diagonal is for small meshes");
+    return STOKES_EINVAL;
+  }
+  double *q = C->lz0, *w = C->lz1;
+  SMF_CUDA_OK(cudaMemsetAsync(dS, 0, d.n_p * sizeof(double), C->s));
+  for (int cz = 0; cz < pz; ++cz)
+    for (int cy = 0; cy < py; ++cy)
+      for (int cx = 0; cx < px; ++cx) {
+        R.vec(k_probe_pre, d.n_p, d, P, cx, cy, cz, q, (const double *)nullptr, (double *)nullptr);
+        SMF_CUDA_OK(cudaMemsetAsync(w, 0, d.n_p * sizeof(double), C->s));
+        R.S_tilde(l, q, w);
+        R.vec(k_probe_pre, d.n_p, d, P, cx, cy, cz, (double *)nullptr, (const double *)w, dS);
+      }
+  SMF_CUDA_OK(cudaGetLastError());
+  return STOKES_OK;
+}
+
 static int lanczos(stokes_ctx *C, int l, bool velocity, double *est) {
   Runner<double> R(C);
   LevelRT<double> &LV = C->L64[l];
@@ -1114,8 +1201,8 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
   else
     stokes_default_opts(&C->o);
   if (C->o.kA < 0 || C->o.kA > 16 || C->o.kS < 0 || C->o.kS > 16 || C->o.m < 0 || C->o.gmres_restart < 1 ||
-      C->o.schur_diag < 0 || C->o.schur_diag > 1 || C->o.cycle < 0 || C->o.cycle > 1) {
-    set_error("invalid stokes_opts (kA, kS in [0,16], m >= 0, restart >= 1, schur_diag in {0,1}, cycle in {0,1})");
+      C->o.schur_diag < 0 || C->o.schur_diag > 3 || C->o.cycle < 0 || C->o.cycle > 1) {
+    set_error("invalid stokes_opts (kA, kS in [0,16], m >= 0, restart >= 1, schur_diag in {0,1,2,3}, cycle in {0,1})");
     return STOKES_EINVAL;
   }
   const unsigned full = dim == 3 ? 0x3Fu : 0xFu;
@@ -1334,12 +1421,22 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
     ++C->launches;
     k_expand_diag<double><<<vec_blocks(d.n_u), kVecThreads, 0, C->s>>>(d, dAs, C->DA[l]);
     k_reciprocal<double><<<vec_blocks(d.n_u), kVecThreads, 0, C->s>>>(C->DA[l], R.DAinv, d.n_u);
-    C->DS[l] = C->o.schur_diag == 0 ? dSloc : dMp;
-    k_reciprocal<double><<<vec_blocks(d.n_p), kVecThreads, 0, C->s>>>(C->DS[l], R.DSinv, d.n_p);
-    C->launches += 3;
+    C->launches += 2;
     double est;
     if ((st = lanczos(C, l, true, &est))) return st;
     C->betaA[l] = C->o.eig_safety * est;
+    switch (C->o.schur_diag) {
+      case 0: C->DS[l] = dSloc; break;
+      case 1: C->DS[l] = dMp; break;
+      default: {  // 2: d = diag(B D_A^-1 B^T), 3: exact = diag(B A^-1_hat B^T), both by probing
+        double *dS;
+        if ((st = dalloc(C, &dS, d.n_p))) return st;
+        if ((st = C->o.schur_diag == 2 ? schur_diag_d(C, l, dS) : schur_diag_exact(C, l, dS))) return st;
+        C->DS[l] = dS;
+      }
+    }
+    k_reciprocal<double><<<vec_blocks(d.n_p), kVecThreads, 0, C->s>>>(C->DS[l], R.DSinv, d.n_p);
+    ++C->launches;
     if ((st = lanczos(C, l, false, &est))) return st;
     C->betaS[l] = C->o.eig_safety * est;
     LevelRT<float> &F = C->L32[l];

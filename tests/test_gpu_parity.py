@@ -126,6 +126,48 @@ def test_pressure_mass_schur_diagonal():
     assert rel_err(_n(DS), mg.ops[-1]["Mp"].diagonal()) < 1e-12
 
 
+@pytest.mark.parametrize("name", ["2d_q3_pert", "3d_q2_pert", "3d_q3_cart", "3d_q2_channel"])
+def test_schur_diagonal_d(name):
+    # Eq. diag d: D = diag(B diag(A)^-1 B^T), probed through the matrix-free B on the GPU
+    case, H, mg, S = _pair(name, schur_diag="d", kA=1, kS=2)
+    for l in range(1, len(H.levels)):
+        sm = mg.smoothers[l]
+        DA, DS = S.diagonals(l)
+        assert rel_err(_n(DS), sm.DS) < 1e-12
+        assert abs(S.level_params(l)["beta_S"] - sm.beta_S) < 1e-9 * sm.beta_S
+    lev = H.levels[-1]
+    b = random_full(lev, 17, constrained_zero=True)
+    ref = mg.cycle(len(H.levels) - 1, np.zeros(lev.size), b)
+    assert rel_err(_n(S.vcycle(_t(b))), ref) < 1e-10
+
+
+@pytest.mark.parametrize("name", ["2d_q3_pert", "3d_q2_pert", "3d_q2_channel"])
+@pytest.mark.parametrize("kA", [1, 3])
+def test_schur_diagonal_exact(name, kA):
+    # the exact diagonal of S~ = B A^-1_hat B^T, probed through S~ on the GPU, against the oracle's
+    # dense A^-1_hat on the coarser level (the oracle's beta_A set to the GPU's Lanczos value)
+    from oracle.assemble import assemble
+    from oracle.smoother import LevelSmoother
+    case = CASES[name]
+    H = oracle_hierarchy(case)
+    S = gpu_solver(case, schur_diag="exact", kA=kA, kS=2)
+    lev = H.levels[1]
+    ops = assemble(lev, case.get("mu", 1.0), case.get("gamma_rho", 0.0))
+    prm = S.level_params(1)
+    sm = LevelSmoother(lev, ops, kA, 2, schur_diag="exact", mu=case.get("mu", 1.0),
+                       gamma_rho=case.get("gamma_rho", 0.0), beta_A=prm["beta_A"], beta_S=1.0)
+    DA, DS = S.diagonals(1)
+    assert rel_err(_n(DS), sm.DS) < 1e-12
+
+
+def test_schur_diagonal_exact_rejects_large_meshes():
+    from paper_2205_15770_gb300 import StokesError, StokesMG
+    with pytest.raises(StokesError) as e:
+        # k = 4, k_A = 3: probe period 19 pressure nodes, 37 nodes per axis on the 12^3 level
+        StokesMG(dim=3, n=(12, 12, 12), n_levels=2, k=4, schur_diag="exact", kA=3, kS=1)
+    assert "small meshes" in str(e.value)
+
+
 @pytest.mark.parametrize("name", ["2d_q2_cart", "2d_q3_pert", "3d_q2_pert", "3d_q4_pert", "3d_q2_channel"])
 def test_transfers(name):
     case, H, mg, S = _pair(name)
