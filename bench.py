@@ -586,6 +586,29 @@ def run_paper_sweep(args):
                         S.close()
 
 
+def run_schur_sweep(args):
+    """The paper's comparison of Schur-complement diagonals (Sec. 4.3, "Different diagonal
+    approximations"): 2D driven cavity, Q2-Q1 on 16^2 (2,467 DoFs, 4 levels), stationary FP64
+    W-cycle multigrid from x = 0; Jacobi (k_A = k_S = 0) and Chebyshev degree 3; smoothing steps
+    m in {1, 2, 4, 8, 16}; D_S~ in {loc, p, d, exact}: rate q = (r^j / r^{j-3})^(1/3)."""
+    import torch
+    from paper_2205_15770_gb300 import StokesMG
+    dim, n, levels = 2, 16, 4
+    for kdeg in (0, 3):
+        for diag in ("loc", "p", "d", "exact"):
+            for m in (1, 2, 4, 8, 16):
+                S = StokesMG(dim=dim, n=(n,) * dim, n_levels=levels, k=2, kA=kdeg, kS=kdeg, m=m, cycle="W",
+                             schur_diag=diag, vcycle_fp32=False)
+                uD = cavity_lid(S, dim, n)
+                b = S.lift_rhs(uD, torch.zeros_like(uD))
+                _, it, hist, q = S.mg_iterate(b, torch.zeros_like(b), max_iter=15, reduction=1e-10,
+                                              allow_divergence=True)
+                ok = bool(hist) and 0 < q < 1
+                print(json.dumps({"dofs": S.size(), "k": kdeg, "diag": diag, "m": m, "iterations": it,
+                                  "q": round(q, 4) if ok else None}), flush=True)
+                S.close()
+
+
 def run_channel(args):
     """Q_k-Q_{k-1} channel [0,4] x [0,1]^2 on 64^3 cells (aspect 4:1:1), parabolic inflow
     u = 16 y(1-y) z(1-z) on x = 0, no-slip walls, do-nothing outflow at x = 4, mu = 1e-3, 6 levels.
@@ -699,6 +722,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
+    ap.add_argument("--schur-sweep", action="store_true",
+                    help="2D cavity 16^2: rates q for the Schur diagonals loc/p/d/exact, k = 0 and 3, m = 1..16")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed steps by cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--channel", action="store_true",
@@ -722,6 +747,8 @@ def main():
         run_paper_sweep(args)
     elif args.smoother_sweep:
         run_smoother_sweep(args)
+    elif args.schur_sweep:
+        run_schur_sweep(args)
     elif args.kernel_only:
         run_kernel_only(args)
     elif args.impl == "reference":

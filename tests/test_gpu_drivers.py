@@ -74,6 +74,28 @@ def test_stationary_driver_matches_oracle():
     assert rel_err(x.cpu().numpy(), x_o) < 1e-8
 
 
+@pytest.mark.parametrize("diag", ["p", "d", "exact"])
+def test_stationary_driver_with_each_schur_diagonal(diag):
+    # the paper's diagonal comparison (2D, 16^2, Chebyshev degree 3, W-cycle): GPU residual
+    # history of the stationary driver against the oracle's
+    from oracle.assemble import load_vector_nodal
+    from oracle.mesh import Hierarchy
+    from oracle.mg import Multigrid
+    H = Hierarchy(2, 2, (16, 16), 4, W.lattice_vertices(2, (16, 16)))
+    mg = Multigrid(H, kA=3, kS=3, m=1, cycle="W", schur_diag=diag)
+    lev = H.levels[-1]
+    b = load_vector_nodal(lev, mg.ops[-1], W.fourier_forcing(2, 2, (16, 16), seed=0).reshape(-1))
+    _, res_o, q_o = mg.stationary(b)
+    from paper_2205_15770_gb300 import StokesMG
+    S = StokesMG(dim=2, n=(16, 16), n_levels=4, k=2, kA=3, kS=3, m=1, cycle="W", schur_diag=diag,
+                 vcycle_fp32=False)
+    _, it, hist, q = S.mg_iterate(_t(b), max_iter=15, reduction=1e-10)
+    assert it == len(res_o) - 1
+    # residuals near 1e-11 ||r_0|| carry the FP64 rounding of b - K x (~1e-16 |K||x|) in absolute terms
+    np.testing.assert_allclose(hist, res_o, rtol=1e-6, atol=1e-14 * res_o[0])
+    assert abs(q - q_o) < 1e-6
+
+
 def test_w_cycle_stationary_rates_close_to_v_cycle():
     # Sec. 4.3.4: the V-cycle gives almost the same rates as the W-cycle
     case = CASES["3d_q2_pert"]

@@ -94,3 +94,22 @@ def test_partial_dirichlet_has_no_pressure_kernel():
     x, its, _ = fgmres(lambda v: mg.K @ v, mg.precondition, b, rtol=1e-11)
     xd = spla.spsolve(mg.K.tocsc(), b)
     assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-8
+
+
+def test_schur_diagonal_choices_follow_the_papers_comparison():
+    # Sec. 4.3 (2D driven cavity, 2,467 DoFs): diag d gives nearly the rates of the exact diagonal,
+    # the local one falls behind, more smoothing steps help.  With k_A = 0, A^-1_hat = sigma
+    # diag(A)^-1, so the exact diagonal is sigma times diag d and the Chebyshev iteration (whose
+    # eigenvalue bound is rescaled by Lanczos) is the same: equal rates.
+    q = {}
+    for k in (0, 3):
+        for m in (1, 2):
+            for diag in ("loc", "p", "d", "exact"):
+                _, mg, _, b = _problem(2, 16, 4, kA=k, kS=k, m=m, cycle="W", schur_diag=diag)
+                q[(k, m, diag)] = mg.stationary(b)[2]
+    for m in (1, 2):
+        assert abs(q[(0, m, "d")] - q[(0, m, "exact")]) <= 1e-6 * q[(0, m, "exact")]
+        assert abs(q[(3, m, "d")] - q[(3, m, "exact")]) <= 0.2 * q[(3, m, "exact")]
+        assert q[(3, m, "loc")] > q[(3, m, "exact")]
+    for diag in ("loc", "p", "d", "exact"):
+        assert q[(3, 2, diag)] < q[(3, 1, diag)] < 1
