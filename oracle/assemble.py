@@ -5,7 +5,10 @@ Bilinear forms (Sec. 2, Eqs. a(u,v), b(v,q)):
     b(v,q) = -int q div v
 The sign of b follows the reading that makes K x = b the discretisation of
 -mu Lap u + grad p = f (the paper prints both signs; the velocity is unaffected,
-only p flips).  The linear system is K = [A B^T; B -C] with C = 0 (Eq. Kx=f).
+only p flips).  The linear system is K = [A B^T; B -C] (Eq. Kx=f).  The paper leaves
+the stabilisation C open (non-negative, usually 0, Sec. 1); read here as
+    c(p,q) = c_mass int p q + c_grad sum_tau h_tau^2 int_tau grad p . grad q,
+h_tau = |tau|^(1/d): a pressure-mass penalty plus a Brezzi-Pitkaranta pressure Laplacian.
 
 Dirichlet treatment: a constrained velocity DoF keeps its slot in the vector;
 its row and column of K are replaced by the identity (y_i = x_i).
@@ -32,7 +35,7 @@ class Tables:
         self.pre = Element1D(k - 1, nq)
         self.geo = Element1D(1, nq)
         self.phi, self.dphi, self.w = tensor_tables(self.vel, dim)
-        self.psi, _, _ = tensor_tables(self.pre, dim)
+        self.psi, self.dpsi, _ = tensor_tables(self.pre, dim)
         self.gphi, self.gdphi, _ = tensor_tables(self.geo, dim)
 
 
@@ -56,6 +59,8 @@ def element_matrices(level, tab, mu, gamma_rho, mu_cell=None, cells=None):
       Mv  (nc, nphi, nphi)        scalar velocity mass
       Mp  (nc, npsi, npsi)        pressure mass
       K0  (nc, nphi, nphi)        scalar stiffness grad.grad (no mu)
+      Kp  (nc, npsi, npsi)        pressure stiffness grad.grad
+      vol (nc,)                   cell volumes
     """
     Xv = level.cell_vertices()
     if cells is not None:
@@ -69,6 +74,8 @@ def element_matrices(level, tab, mu, gamma_rho, mu_cell=None, cells=None):
     Mv = np.einsum("cq,iq,jq->cij", wdet, tab.phi, tab.phi)
     Mp = np.einsum("cq,iq,jq->cij", wdet, tab.psi, tab.psi)
     B = -np.einsum("cq,iq,cjqa->ciaj", wdet, tab.psi, grad)
+    gradp = np.einsum("cqab,iqb->ciqa", JinvT, tab.dpsi)
+    Kp = np.einsum("cq,ciqa,cjqa->cij", wdet, gradp, gradp)
     if mu_cell is None:
         muv = np.full(len(Xv), float(mu))
     else:
@@ -76,7 +83,7 @@ def element_matrices(level, tab, mu, gamma_rho, mu_cell=None, cells=None):
         if cells is not None:
             muv = muv[cells]
     As = muv[:, None, None] * K0 + gamma_rho * Mv
-    return {"As": As, "B": B, "Mv": Mv, "Mp": Mp, "K0": K0}
+    return {"As": As, "B": B, "Mv": Mv, "Mp": Mp, "K0": K0, "Kp": Kp, "vol": wdet.sum(axis=1)}
 
 
 def _scatter(rows_loc, cols_loc, vals, shape):
@@ -86,7 +93,7 @@ def _scatter(rows_loc, cols_loc, vals, shape):
     return sp.coo_matrix((vals.reshape(-1), (r, c)), shape=shape).tocsr()
 
 
-def assemble(level, mu=1.0, gamma_rho=0.0, mu_cell=None, chunk=4096):
+def assemble(level, mu=1.0, gamma_rho=0.0, mu_cell=None, chunk=4096, c_mass=0.0, c_grad=0.0):
     """Assembled operators of one level.
 
     Returns dict of CSR matrices (all FP64):
@@ -96,7 +103,8 @@ def assemble(level, mu=1.0, gamma_rho=0.0, mu_cell=None, chunk=4096):
       B_full   n_p x n_u divergence block without constraints
       A        n_u x n_u velocity block, Dirichlet rows/columns -> identity
       B        n_p x n_u with constrained columns zeroed
-      K        [A B^T; B 0]
+      C        n_p x n_p stabilisation c_mass M_p + c_grad sum h^2 K_p (zero by default)
+      K        [A B^T; B -C]
       free     boolean mask of unconstrained entries of the full vector
     """
     tab = Tables(level.dim, level.k)
@@ -107,19 +115,24 @@ def assemble(level, mu=1.0, gamma_rho=0.0, mu_cell=None, chunk=4096):
     Mv = sp.csr_matrix((nv, nv))
     Mp = sp.csr_matrix((level.n_p, level.n_p))
     Bf = sp.csr_matrix((level.n_p, level.n_u))
+    Cs = sp.csr_matrix((level.n_p, level.n_p))
     for s in range(0, level.n_cells, chunk):
         cells = np.arange(s, min(s + chunk, level.n_cells))
         E = element_matrices(level, tab, mu, gamma_rho, mu_cell, cells)
         As = As + _scatter(vn[cells], vn[cells], E["As"], (nv, nv))
         Mv = Mv + _scatter(vn[cells], vn[cells], E["Mv"], (nv, nv))
         Mp = Mp + _scatter(pn[cells], pn[cells], E["Mp"], (level.n_p, level.n_p))
+        if c_mass or c_grad:
+            h2 = E["vol"] ** (2.0 / d)
+            Ce = c_mass * E["Mp"] + c_grad * h2[:, None, None] * E["Kp"]
+            Cs = Cs + _scatter(pn[cells], pn[cells], Ce, (level.n_p, level.n_p))
         nc = len(cells)
         cols = (vn[cells][:, None, :] + (np.arange(d) * nv)[None, :, None]).reshape(nc, -1)
         Bf = Bf + _scatter(pn[cells], cols, E["B"].reshape(nc, pn.shape[1], -1), (level.n_p, level.n_u))
-    return finish(level, As, Mv, Mp, Bf)
+    return finish(level, As, Mv, Mp, Bf, Cs, c_mass)
 
 
-def finish(level, As, Mv, Mp, Bf):
+def finish(level, As, Mv, Mp, Bf, C=None, c_mass=0.0):
     d = level.dim
     vmask = level.velocity_constrained()
     umask = np.tile(vmask, d)
@@ -127,10 +140,13 @@ def finish(level, As, Mv, Mp, Bf):
     A_full = sp.block_diag([As] * d, format="csr")
     A = (Zu @ A_full @ Zu + sp.diags(umask.astype(np.float64))).tocsr()
     B = (Bf @ Zu).tocsr()
-    K = sp.bmat([[A, B.T], [B, None]], format="csr")
+    C = sp.csr_matrix((level.n_p, level.n_p)) if C is None else C.tocsr()
+    K = sp.bmat([[A, B.T], [B, -C]], format="csr")
     free = ~level.constrained()
+    # constant pressures stay in the kernel of K under full Dirichlet data unless C has a mass part
+    pker = level.has_pressure_kernel() and c_mass == 0.0
     return {"As_full": As.tocsr(), "Mv_full": Mv.tocsr(), "Mp": Mp.tocsr(), "B_full": Bf.tocsr(),
-            "A": A, "B": B, "K": K, "free": free, "umask": umask}
+            "A": A, "B": B, "C": C, "K": K, "free": free, "umask": umask, "pker": pker}
 
 
 def load_vector_nodal(level, ops, f_nodal):

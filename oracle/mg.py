@@ -26,9 +26,9 @@ from .transfer import prolongation
 
 
 class CoarseSolver:
-    def __init__(self, level, K):
+    def __init__(self, level, K, pker=None):
         Kd = K.toarray()
-        self.bordered = level.has_pressure_kernel()
+        self.bordered = level.has_pressure_kernel() if pker is None else pker
         self.n = Kd.shape[0]
         if self.bordered:
             e = np.concatenate([np.zeros(level.n_u), np.ones(level.n_p)])
@@ -43,7 +43,7 @@ class CoarseSolver:
 
 class Multigrid:
     def __init__(self, hier, mu=1.0, gamma_rho=0.0, kA=3, kS=3, m=2, cycle="V", schur_diag="loc",
-                 mu_cells=None, eig_steps=40, eig_safety=1.1, seed=0x5EED):
+                 mu_cells=None, eig_steps=40, eig_safety=1.1, seed=0x5EED, c_mass=0.0, c_grad=0.0):
         """mu_cells: optional list (one array per level, coarse to fine) of per-cell viscosities."""
         self.hier = hier
         self.m = m
@@ -51,10 +51,10 @@ class Multigrid:
         self.ops, self.smoothers, self.P = [], [], []
         for l, lev in enumerate(hier.levels):
             mc = None if mu_cells is None else mu_cells[l]
-            ops = assemble(lev, mu, gamma_rho, mc)
+            ops = assemble(lev, mu, gamma_rho, mc, c_mass=c_mass, c_grad=c_grad)
             self.ops.append(ops)
             if l == 0:
-                self.coarse = CoarseSolver(lev, ops["K"])
+                self.coarse = CoarseSolver(lev, ops["K"], ops["pker"])
                 self.smoothers.append(None)
                 self.P.append(None)
             else:

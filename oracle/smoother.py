@@ -23,6 +23,7 @@ line, which does not match K_hat; the compact form is the one the analysis uses)
 from __future__ import annotations
 
 import numpy as np
+import scipy.sparse as sp
 from .assemble import Tables, element_matrices
 
 MASK64 = (1 << 64) - 1
@@ -135,6 +136,10 @@ class LevelSmoother:
         self.level, self.ops = level, ops
         self.kA, self.kS = kA, kS
         self.A, self.B = ops["A"], ops["B"]
+        self.C = ops.get("C")
+        if self.C is None:
+            self.C = sp.csr_matrix((level.n_p, level.n_p))
+        pker = ops.get("pker", level.has_pressure_kernel())
         self.BT = self.B.T.tocsr()
         self.n_u = level.n_u
         self.DA = self.A.diagonal().copy()
@@ -148,6 +153,8 @@ class LevelSmoother:
         self.beta_A = beta_A
         self.sigma = lemma1_scaling(kA)
         # --- pressure part -------------------------------------------------------------
+        # D_S~ approximates the diagonal of S~ = B A^-1_hat B^T + C (Sec. 1): each variant of the
+        # first term plus diag(C)
         if schur_diag == "loc":
             DS = local_schur_diag(level, mu, gamma_rho, mu_cell)
         elif schur_diag == "p":
@@ -160,12 +167,13 @@ class LevelSmoother:
             DS = np.einsum("ij,jk,ik->i", Bd, Ainv_hat, Bd)
         else:
             raise ValueError(schur_diag)
+        DS = DS + self.C.diagonal()
         self.DS = DS
         self.DSinv = 1.0 / DS
         if beta_S is None:
             v0 = splitmix64_uniform(seed + 1, level.n_p)
             sq = np.sqrt(self.DSinv)
-            if level.has_pressure_kernel():
+            if pker:
                 z = np.sqrt(DS)
                 v0 = v0 - (v0 @ z) / (z @ z) * z
             beta_S = eig_safety * lanczos_max(lambda v: sq * self.S_tilde(sq * v), v0, eig_steps)
@@ -177,7 +185,7 @@ class LevelSmoother:
         return self.sigma * chebyshev(lambda x: self.A @ x, self.DAinv, r, self.kA, self.beta_A)
 
     def S_tilde(self, q):
-        return self.B @ self.Ainv_hat(self.BT @ q)
+        return self.B @ self.Ainv_hat(self.BT @ q) + self.C @ q
 
     def Sinv_hat(self, r):
         return self.tau * chebyshev(self.S_tilde, self.DSinv, r, self.kS, self.beta_S)
@@ -194,7 +202,7 @@ class LevelSmoother:
         u, p = x[:nu], x[nu:]
         f, g = b[:nu], b[nu:]
         u_hat = u + self.Ainv_hat(f - self.A @ u - self.BT @ p)
-        dp = self.Sinv_hat(self.B @ u_hat - g)
+        dp = self.Sinv_hat(self.B @ u_hat - self.C @ p - g)
         u_new = u_hat - self.Ainv_hat(self.BT @ dp)
         return np.concatenate([u_new, p + dp])
 
