@@ -77,6 +77,11 @@ typedef struct {
   int eig_iters;        /* Lanczos steps for lambda_max estimates */
   double eig_safety;    /* beta = eig_safety * Lanczos estimate */
   unsigned long long seed; /* SplitMix64 seed of the Lanczos start vectors */
+  double c_mass;        /* stabilisation block C of K = [A B^T; B -C] (Sec. 1 leaves C open; zero by
+                           default): c(p,q) = c_mass int p q + c_grad sum_tau h_tau^2 int_tau
+                           grad p . grad q, h_tau = |tau|^(1/d); both >= 0.  With c_mass > 0 the
+                           constant pressure is no longer in the kernel of K (no zero-mean fixing) */
+  double c_grad;
 } stokes_opts;
 
 /* Fill *o with kA = kS = 3, m = 2, V-cycle, local Schur diagonal, FP32 cycle,
@@ -98,13 +103,15 @@ int stokes_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
 int stokes_sizes(const stokes_ctx *ctx, int level, long long *n_u, long long *n_p);
 
 /* y = K x on `level` (Sec. 3.1: Kx = sum_tau P_tau K_tau P_tau^T x by sum
- * factorisation).  x, y: device vectors of n_u + n_p entries; must not alias. */
+ * factorisation; K = [A B^T; B -C], C = 0 unless opts.c_mass / c_grad are set).  x, y: device
+ * vectors of n_u + n_p entries; must not alias.  Launched on `stream` itself. */
 int stokes_vmult(stokes_ctx *ctx, int level, int precision, const void *x, void *y, void *stream);
 
 /* Block applications on `level`: blocks is a bit set of 1 = A u, 2 = B^T p (both into
  * yu), 4 = B u (into yp); or exactly 8 = Z M_v u (velocity mass, constrained rows zero, every
  * entry of u read) or 16 = M_v Z u (its transpose: constrained entries of u read as 0, every
- * row written), Z = identity on free velocity DoFs, 0 on constrained ones.  Outputs are
+ * row written), Z = identity on free velocity DoFs, 0 on constrained ones.  Bit 64 adds -C p
+ * to yp (the stabilisation block; with bit 4, yp = B u - C p; not with 8 / 16).  Outputs are
  * overwritten; unused pointers may be NULL.  For blocks 1-7, rows of constrained velocity DoFs
  * of yu are zero (no identity term) and constrained entries of u are ignored. */
 int stokes_apply_blocks(stokes_ctx *ctx, int level, int precision, int blocks, const void *u,

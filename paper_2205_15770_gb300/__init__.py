@@ -50,7 +50,8 @@ class StokesMG:
 
     def __init__(self, dim, n, n_levels, k=2, mu=1.0, gamma_rho=0.0, vertices=None, lo=(0.0, 0.0, 0.0),
                  hi=(1.0, 1.0, 1.0), dirichlet_faces=None, mu_cell=None, kA=3, kS=3, m=2, cycle="V",
-                 schur_diag="loc", vcycle_fp32=True, restart=30, eig_iters=40, eig_safety=1.1, seed=0x5EED):
+                 schur_diag="loc", vcycle_fp32=True, restart=30, eig_iters=40, eig_safety=1.1, seed=0x5EED,
+                 c_mass=0.0, c_grad=0.0):
         self._lib = L.load()
         torch = _torch()
         self.dim, self.k, self.n_levels = dim, k, n_levels
@@ -84,6 +85,7 @@ class StokesMG:
         opts.eig_iters = eig_iters
         opts.eig_safety = eig_safety
         opts.seed = seed
+        opts.c_mass, opts.c_grad = float(c_mass), float(c_grad)
         ctx = C.c_void_p()
         st = self._lib.stokes_setup(C.byref(mesh), k, float(mu), float(gamma_rho), mu_ptr, C.byref(opts),
                                     self._stream(), C.byref(ctx))
@@ -150,14 +152,15 @@ class StokesMG:
         return y
 
     def apply_blocks(self, blocks, u=None, p=None, level=None, dtype=None):
-        """Returns (yu, yp) with yu = [A u] + [B^T p], yp = B u according to the block bit set."""
+        """Returns (yu, yp) with yu = [A u] + [B^T p], yp = [B u] - [C p] according to the block bit set
+        (1 A, 2 B^T, 4 B, 64 C; 8 / 16 mass)."""
         torch = _torch()
         lv = self._level(level)
         nu, npr = self.sizes(lv)
         ref = u if u is not None else p
         dt = ref.dtype
         yu = torch.empty(nu, dtype=dt, device=self.device) if blocks & (1 | 2 | 8 | 16) else None
-        yp = torch.empty(npr, dtype=dt, device=self.device) if blocks & 4 else None
+        yp = torch.empty(npr, dtype=dt, device=self.device) if blocks & (4 | 64) else None
         self._check(self._lib.stokes_apply_blocks(
             self._ctx, lv, self._prec(ref), blocks, _ptr(u, dt) if u is not None else None,
             _ptr(p, dt) if p is not None else None, _ptr(yu, dt) if yu is not None else None,
@@ -351,7 +354,7 @@ class StokesBatch:
     """
 
     def __init__(self, members, kA=3, kS=3, m=2, cycle="V", schur_diag="loc", vcycle_fp32=True, restart=30,
-                 eig_iters=40, eig_safety=1.1, seed=0x5EED):
+                 eig_iters=40, eig_safety=1.1, seed=0x5EED, c_mass=0.0, c_grad=0.0):
         self._lib = L.load()
         torch = _torch()
         nm = len(members)
@@ -390,6 +393,7 @@ class StokesBatch:
         opts.eig_iters = eig_iters
         opts.eig_safety = eig_safety
         opts.seed = seed
+        opts.c_mass, opts.c_grad = float(c_mass), float(c_grad)
         bt = C.c_void_p()
         st = self._lib.stokes_setup_batch(nm, meshes, ks, mus, gs, C.byref(opts), StokesMG._stream(), C.byref(bt))
         if st != 0:

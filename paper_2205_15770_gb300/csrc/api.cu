@@ -42,6 +42,15 @@ int launch_cell_apply(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, cons
   }
 }
 template <typename T>
+int launch_cell_C(const LevelDesc<T> &L, const Tab1D<T> *tab, T cm, T cg, const T *p, T *yp, T sign, T *diag,
+                  cudaStream_t s) {
+  switch (L.k) {
+    case 2: return launch_cell_C_k<2, T>(L, tab, cm, cg, p, yp, sign, diag, s);
+    case 3: return launch_cell_C_k<3, T>(L, tab, cm, cg, p, yp, sign, diag, s);
+    default: return launch_cell_C_k<4, T>(L, tab, cm, cg, p, yp, sign, diag, s);
+  }
+}
+template <typename T>
 int launch_col_geometry(const LevelDesc<T> &L, T *geo, cudaStream_t s) {
   switch (L.k) {
     case 2: return launch_col_geometry_k<2, T>(L, geo, s);
@@ -149,6 +158,7 @@ struct stokes_ctx {
   int dim = 0, k = 0, nl = 0;
   stokes_opts o{};
   double mu = 1, gamma_rho = 0;
+  double c_mass = 0, c_grad = 0;  // stabilisation block C (0: none)
   bool pker = false;
   std::vector<LevelRT<double>> L64;
   std::vector<LevelRT<float>> L32;
@@ -303,6 +313,14 @@ struct Runner {
     } else {
       apply(l, kApplyA | kApplyBT | kApplyB, x, x + nu(l), y, y + nu(l));
     }
+    applyC(l, x + nu(l), y + nu(l), T(-1));
+  }
+  // Stabilisation block (no launch when C = 0): yp += sign C p.
+  bool hasC() const { return C->c_mass != 0.0 || C->c_grad != 0.0; }
+  void applyC(int l, const T *p, T *yp, T sign) {
+    if (!hasC()) return;
+    launch_cell_C<T>(L[l].d, tab, (T)C->c_mass, (T)C->c_grad, p, yp, sign, (T *)nullptr, s);
+    note();
   }
   void sub(const T *a, const T *b, T *out, long long n) { vec(k_sub<T>, n, a, b, out, n); }
 
@@ -356,6 +374,7 @@ struct Runner {
     apply_nz(l, kApplyBT, nullptr, q, R.tu, nullptr);
     cheb(l, true, true, R.tu, nullptr, R.tu, nullptr, T(1), nullptr, T(1), R.au, nullptr);
     apply_nz(l, kApplyB, R.au, nullptr, nullptr, y);
+    applyC(l, q, y, T(1));  // S~ = B A^-1_hat B^T + C
   }
   // One inexact symmetric Uzawa step in compact form (Sec. 3.3.1, K_hat):
   //   u_hat = u + A^-1_hat (f - A u - B^T p); dp = S^-1_hat (B u_hat - g);
@@ -370,6 +389,7 @@ struct Runner {
     cheb(l, true, false, f, x_zero ? nullptr : R.tu, nullptr, x_zero ? nullptr : R.tu, T(1), u, T(1), R.uhat,
          nullptr);
     apply_nz(l, kApplyB, R.uhat, nullptr, nullptr, R.pt);
+    applyC(l, p, R.pt, T(-1));  // B u_hat - C p
     cheb(l, false, false, R.pt, g, R.pt, nullptr, T(1), nullptr, T(1), R.dp, p);
     apply_nz(l, kApplyBT, nullptr, R.dp, R.tu, nullptr);
     cheb(l, true, false, R.tu, nullptr, R.tu, nullptr, T(1), R.uhat, T(-1), u, nullptr);
@@ -413,7 +433,8 @@ struct Runner {
   // step, residual) or written by k_fused_finish.
   bool fused_ok(int l) const { return fused_eligible(l) && L[l].fuse; }
   bool fused_eligible(int l) const {
-    return C->fuse && C->o.kA == 1 && C->o.kS >= 1 && C->o.kS <= 4 && L[l].d.dim == 3 && L[l].shape >= 0;
+    return C->fuse && !hasC() && C->o.kA == 1 && C->o.kS >= 1 && C->o.kS <= 4 && L[l].d.dim == 3 &&
+           L[l].shape >= 0;
   }
   T *pairU(int l, int pr) { return pr == 0 ? L[l].tu : L[l].cx; }
   T *pairT(int l, int pr) { return pr == 0 ? L[l].ct : L[l].ct2; }
@@ -626,6 +647,7 @@ struct Runner {
         fused_residual_apply(l, x, pend);
       else
         apply_nz(l, kApplyA | kApplyBT | kApplyB, x, x + nu(l), R.kx, R.kx + nu(l));
+      applyC(l, x + nu(l), R.kx + nu(l), T(-1));
       vecp(k_residual<T, 1>, k_residual<T, VW>, {b, R.kx, R.r}, n, b, R.kx, R.r, n);
     }
     restrict_to(l, R.r, L[l - 1].b, L[l - 1].x);
@@ -1205,9 +1227,16 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
     set_error("invalid stokes_opts (kA, kS in [0,16], m >= 0, restart >= 1, schur_diag in {0,1,2,3}, cycle in {0,1})");
     return STOKES_EINVAL;
   }
+  if (!(C->o.c_mass >= 0) || !(C->o.c_grad >= 0) || !std::isfinite(C->o.c_mass) || !std::isfinite(C->o.c_grad)) {
+    set_error("invalid stokes_opts: c_mass and c_grad must be finite and >= 0");
+    return STOKES_EINVAL;
+  }
+  C->c_mass = C->o.c_mass;
+  C->c_grad = C->o.c_grad;
   const unsigned full = dim == 3 ? 0x3Fu : 0xFu;
   const unsigned faces = mesh->dirichlet_faces & full;
-  C->pker = faces == full;
+  // constant pressures span the kernel of K under full Dirichlet data, unless C has a mass part
+  C->pker = faces == full && C->c_mass == 0.0;
   const char *env = getenv("STOKES_NO_GRAPHS");
   C->use_graphs = !(env && env[0] == '1');
   const char *nofuse = getenv("STOKES_NO_FUSE");
@@ -1434,6 +1463,10 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
         if ((st = C->o.schur_diag == 2 ? schur_diag_d(C, l, dS) : schur_diag_exact(C, l, dS))) return st;
         C->DS[l] = dS;
       }
+    }
+    if (C->o.schur_diag != 3 && (C->c_mass != 0.0 || C->c_grad != 0.0)) {  // D_S~ += diag(C)
+      launch_cell_C<double>(d, C->tab64, C->c_mass, C->c_grad, nullptr, nullptr, 1.0, C->DS[l], C->s);
+      ++C->launches;
     }
     k_reciprocal<double><<<vec_blocks(d.n_p), kVecThreads, 0, C->s>>>(C->DS[l], R.DSinv, d.n_p);
     ++C->launches;
@@ -1951,6 +1984,8 @@ void stokes_default_opts(stokes_opts *o) {
   o->eig_iters = 40;
   o->eig_safety = 1.1;
   o->seed = 0x5EEDull;
+  o->c_mass = 0.0;
+  o->c_grad = 0.0;
 }
 
 int stokes_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho, const double *mu_cell,
@@ -2039,21 +2074,35 @@ int stokes_vmult(stokes_ctx *C, int level, int precision, const void *x, void *y
 
 int stokes_apply_blocks(stokes_ctx *C, int level, int precision, int blocks, const void *u, const void *p, void *yu,
                         void *yp, void *stream) {
-  const bool mass = blocks == kApplyMass || blocks == kApplyMassAll;
-  if (!check_level(C, level) || (precision != 32 && precision != 64) || blocks <= 0 || (blocks > 7 && !mass) ||
-      ((blocks & (1 | 8 | 16)) && (!u || !yu)) || ((blocks & 2) && (!p || !yu)) || ((blocks & 4) && (!u || !yp))) {
+  const bool withC = blocks & kApplyC;
+  const int base = blocks & ~kApplyC;
+  const bool mass = base == kApplyMass || base == kApplyMassAll;
+  if (!check_level(C, level) || (precision != 32 && precision != 64) || blocks <= 0 || (base > 7 && !mass) ||
+      (mass && withC) || ((base & (1 | 8 | 16)) && (!u || !yu)) || ((base & 2) && (!p || !yu)) ||
+      ((base & 4) && (!u || !yp)) || (withC && (!p || !yp))) {
     set_error("invalid stokes_apply_blocks arguments");
     if (C) C->err = "invalid stokes_apply_blocks arguments";
     return STOKES_EINVAL;
   }
   StreamGuard sg(C, stream);
-  const bool wu = blocks & (1 | 2 | 8 | 16), wp = blocks & 4;
-  if (precision == 64)
-    Runner<double>(C).apply(level, blocks, (const double *)u, (const double *)p, wu ? (double *)yu : nullptr,
-                            wp ? (double *)yp : nullptr);
-  else
-    Runner<float>(C).apply(level, blocks, (const float *)u, (const float *)p, wu ? (float *)yu : nullptr,
-                           wp ? (float *)yp : nullptr);
+  const bool wu = base & (1 | 2 | 8 | 16), wp = base & 4;
+  if (precision == 64) {
+    Runner<double> R(C);
+    if (base) R.apply(level, base, (const double *)u, (const double *)p, wu ? (double *)yu : nullptr,
+                      wp ? (double *)yp : nullptr);
+    if (withC) {
+      if (!wp) cudaMemsetAsync(yp, 0, R.np(level) * sizeof(double), C->s);
+      R.applyC(level, (const double *)p, (double *)yp, -1.0);
+    }
+  } else {
+    Runner<float> R(C);
+    if (base) R.apply(level, base, (const float *)u, (const float *)p, wu ? (float *)yu : nullptr,
+                      wp ? (float *)yp : nullptr);
+    if (withC) {
+      if (!wp) cudaMemsetAsync(yp, 0, R.np(level) * sizeof(float), C->s);
+      R.applyC(level, (const float *)p, (float *)yp, -1.0f);
+    }
+  }
   return finish(C, STOKES_OK);
 }
 

@@ -542,3 +542,125 @@ __global__ void __launch_bounds__(CellShape<DIM, K>::THREADS)
 }
 
 }  // namespace smf
+
+namespace smf {
+
+// Stabilisation block C (K = [A B^T; B -C]; the paper leaves C open, Sec. 1):
+//   c(p, q) = c_mass int p q + c_grad sum_tau h_tau^2 int_tau grad p . grad q,  h_tau = |tau|^(1/d).
+// One thread per cell: the pressure values and reference gradients at the (k+1)^d Gauss points
+// by tensor-product evaluation, the metric G = w adj adj^T / det of point_geometry, the
+// transposed evaluation and an atomic scatter.  Apply (diag == null): yp += sign * C p.
+// Diagonal (diag != null): diag += diag(C).
+template <int DIM, int K, typename T, bool CART>
+__global__ void stokes_cell_apply_C(const LevelDesc<T> L, const Tab1D<T> *__restrict__ tab, T c_mass, T c_grad,
+                                    const T *__restrict__ p, T *__restrict__ yp, T sign, T *__restrict__ diag) {
+  pdl_enter();
+  using CS = CellShape<DIM, K>;
+  constexpr int NQ = CS::NQ, NPR = CS::NPR, NPP = CS::NPP, NPT = CS::NP, NVX = CS::NVERT;
+  for (long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x; cell < L.n_cells;
+       cell += (long long)gridDim.x * blockDim.x) {
+    const int cx = (int)(cell % L.n[0]);
+    const long long r = cell / L.n[0];
+    const int cy = (int)(r % L.n[1]), cz = DIM == 3 ? (int)(r / L.n[1]) : 0;
+    T verts[NVX * DIM];
+    if (!CART) {
+      for (int v = 0; v < NVX; ++v) {
+        const long long gv = DIM == 3 ? ((long long)(cz + ((v >> 2) & 1)) * (L.n[1] + 1) + (cy + ((v >> 1) & 1))) *
+                                                (L.n[0] + 1) + (cx + (v & 1))
+                                      : (long long)(cy + ((v >> 1) & 1)) * (L.n[0] + 1) + (cx + (v & 1));
+        for (int a = 0; a < DIM; ++a) verts[v * DIM + a] = L.vert[gv * DIM + a];
+      }
+    }
+    auto node_index = [&](int n) {
+      const int nx = n % NPR, ny = (n / NPR) % NPR, nz = DIM == 3 ? n / (NPR * NPR) : 0;
+      return lattice_index<DIM, T>(L.Pn, (K - 1) * cx + nx, (K - 1) * cy + ny, (K - 1) * cz + nz);
+    };
+    T pn[NPP], acc[NPP];
+#pragma unroll
+    for (int n = 0; n < NPP; ++n) {
+      pn[n] = diag ? T(0) : p[node_index(n)];
+      acc[n] = T(0);
+    }
+    T vol = T(0);
+#pragma unroll 1
+    for (int q = 0; q < NPT; ++q) {
+      PointGeo<DIM, T> g;
+      point_geometry<DIM, K, T, CART>(L, tab->x, tab->w, verts, q % NQ, (q / NQ) % NQ, DIM == 3 ? q / (NQ * NQ) : 0, g);
+      vol += g.wdet;
+    }
+    const T h2 = DIM == 3 ? pow(vol, T(2) / T(3)) : vol;
+#pragma unroll 1
+    for (int q = 0; q < NPT; ++q) {
+      const int qd[3] = {q % NQ, (q / NQ) % NQ, DIM == 3 ? q / (NQ * NQ) : 0};
+      PointGeo<DIM, T> g;
+      point_geometry<DIM, K, T, CART>(L, tab->x, tab->w, verts, qd[0], qd[1], qd[2], g);
+      // basis values and reference gradients of the pressure nodes at this point
+      T val[NPP], grd[NPP][DIM];
+#pragma unroll
+      for (int n = 0; n < NPP; ++n) {
+        const int nd[3] = {n % NPR, (n / NPR) % NPR, DIM == 3 ? n / (NPR * NPR) : 0};
+        T pv[3], pd[3];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+          pv[a] = tab->Pv[qd[a] * NPR + nd[a]];
+          pd[a] = tab->Pd[qd[a] * NPR + nd[a]];
+        }
+        val[n] = pv[0] * pv[1] * (DIM == 3 ? pv[2] : T(1));
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+          T f = T(1);
+#pragma unroll
+          for (int b = 0; b < DIM; ++b) f *= (b == a ? pd[b] : pv[b]);
+          grd[n][a] = f;
+        }
+      }
+      const T cm = c_mass * g.wdet, cg = c_grad * h2;
+      if (diag) {
+#pragma unroll
+        for (int n = 0; n < NPP; ++n) {
+          T s = T(0);
+#pragma unroll
+          for (int a = 0; a < DIM; ++a)
+#pragma unroll
+            for (int b = 0; b < DIM; ++b) s += grd[n][a] * g.G[a * DIM + b] * grd[n][b];
+          acc[n] += cm * val[n] * val[n] + cg * s;
+        }
+      } else {
+        T pq = T(0), gr[DIM];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) gr[a] = T(0);
+#pragma unroll
+        for (int n = 0; n < NPP; ++n) {
+          pq += val[n] * pn[n];
+#pragma unroll
+          for (int a = 0; a < DIM; ++a) gr[a] += grd[n][a] * pn[n];
+        }
+        T flux[DIM];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+          T s = T(0);
+#pragma unroll
+          for (int b = 0; b < DIM; ++b) s += g.G[a * DIM + b] * gr[b];
+          flux[a] = cg * s;
+        }
+        const T mq = cm * pq;
+#pragma unroll
+        for (int n = 0; n < NPP; ++n) {
+          T s = val[n] * mq;
+#pragma unroll
+          for (int a = 0; a < DIM; ++a) s += grd[n][a] * flux[a];
+          acc[n] += s;
+        }
+      }
+    }
+#pragma unroll
+    for (int n = 0; n < NPP; ++n) {
+      if (diag)
+        atomicAdd(&diag[node_index(n)], acc[n]);
+      else
+        atomicAdd(&yp[node_index(n)], sign * acc[n]);
+    }
+  }
+}
+
+}  // namespace smf

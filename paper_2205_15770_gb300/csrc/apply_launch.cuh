@@ -82,6 +82,32 @@ int launch_cell_apply_k(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, co
                      : launch_apply_dim<2, K, T, false>(L, tab, mode, u, p, yu, yp, s);
 }
 
+template <int DIM, int K, typename T, bool CART>
+static void launch_C_dim(const LevelDesc<T> &L, const Tab1D<T> *tab, T cm, T cg, const T *p, T *yp, T sign, T *diag,
+                         cudaStream_t s) {
+  const long long nb = (L.n_cells + 127) / 128;
+  launch_kernel(stokes_cell_apply_C<DIM, K, T, CART>, dim3((unsigned)(nb < 152 * 16 ? nb : 152 * 16)), dim3(128), 0, s,
+                L, tab, cm, cg, p, yp, sign, diag);
+}
+
+// Stabilisation block C: yp += sign * C p (diag == null) or diag += diag(C).
+template <int K, typename T>
+int launch_cell_C_k(const LevelDesc<T> &L, const Tab1D<T> *tab, T cm, T cg, const T *p, T *yp, T sign, T *diag,
+                    cudaStream_t s) {
+  if (L.dim == 3) {
+    if (L.cartesian)
+      launch_C_dim<3, K, T, true>(L, tab, cm, cg, p, yp, sign, diag, s);
+    else
+      launch_C_dim<3, K, T, false>(L, tab, cm, cg, p, yp, sign, diag, s);
+  } else {
+    if (L.cartesian)
+      launch_C_dim<2, K, T, true>(L, tab, cm, cg, p, yp, sign, diag, s);
+    else
+      launch_C_dim<2, K, T, false>(L, tab, cm, cg, p, yp, sign, diag, s);
+  }
+  return 0;
+}
+
 template <int K, typename T>
 int launch_col_geometry_k(const LevelDesc<T> &L, T *geo, cudaStream_t s) {
   constexpr int NV = K + 1;
@@ -157,6 +183,10 @@ int launch_cell_diag_k(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dS
   template int launch_cell_apply_fused_k<KK, double>(const LevelDesc<double> &, int, const double *,             \
                                                       const double *, double *, double *, cudaStream_t, int,       \
                                                       const Fuse<double> &, const double *);                                      \
+  template int launch_cell_C_k<KK, float>(const LevelDesc<float> &, const Tab1D<float> *, float, float,        \
+                                           const float *, float *, float, float *, cudaStream_t);            \
+  template int launch_cell_C_k<KK, double>(const LevelDesc<double> &, const Tab1D<double> *, double, double,   \
+                                            const double *, double *, double, double *, cudaStream_t);       \
   template int launch_col_geometry_k<KK, float>(const LevelDesc<float> &, float *, cudaStream_t);             \
   template int launch_col_geometry_k<KK, double>(const LevelDesc<double> &, double *, cudaStream_t);          \
   template int launch_cell_diag_k<KK, double>(const LevelDesc<double> &, const Tab1D<double> *, double *,      \

@@ -19,6 +19,7 @@ enum ApplyMode : int {
   kApplyMass = 8,      // yu += Z M_v u (right-hand sides b = Z M_v f; every node of u is read)
   kApplyMassAll = 16,  // yu += M_v Z u (its transpose: free nodes of u read, every row written)
   kApplyUnmasked = 32, // with A / BT / B: read u at constrained nodes too (K_full u_D for lifting)
+  kApplyC = 64,        // yp -= C p (stabilisation block of K = [A B^T; B -C])
 };
 
 // 1D tables of one velocity degree k on the reference interval, (k+1) Gauss points.
@@ -29,6 +30,7 @@ struct Tab1D {
   T Sd[kMaxN1 * kMaxN1];   // Sd[q*(k+1)+m] = l_m'(x_q)      its derivative
   T D[kMaxN1 * kMaxN1];    // D[q*nq+m]     = g_m'(x_q)      collocation derivative (Lagrange through Gauss points)
   T Pv[kMaxN1 * kMaxDeg];  // Pv[q*k+m]     = pressure basis (degree k-1) at Gauss points
+  T Pd[kMaxN1 * kMaxDeg];  // Pd[q*k+m]     = its derivative
   T w[kMaxN1];             // Gauss weights on [0,1]
   T x[kMaxN1];             // Gauss points on [0,1]
   T nodes[kMaxN1];         // velocity Gauss-Lobatto nodes on [0,1]

@@ -91,7 +91,7 @@ void build_tables(int k, Tab1D<double> &t) {
   gauss_lobatto01(k, xv);
   gauss_lobatto01(k - 1, xp);
   for (int i = 0; i < kMaxN1 * kMaxN1; ++i) t.S[i] = t.Sd[i] = t.D[i] = 0.0;
-  for (int i = 0; i < kMaxN1 * kMaxDeg; ++i) t.Pv[i] = 0.0;
+  for (int i = 0; i < kMaxN1 * kMaxDeg; ++i) t.Pv[i] = t.Pd[i] = 0.0;
   for (int m = 0; m < kMaxN1; ++m) t.nodes[m] = m < nv ? xv[m] : 0.0;
   for (int q = 0; q < nq; ++q) {
     t.x[q] = xg[q];
@@ -101,7 +101,10 @@ void build_tables(int k, Tab1D<double> &t) {
       t.Sd[q * nv + m] = lagrange_deriv(xv, nv, m, xg[q]);
     }
     for (int m = 0; m < nq; ++m) t.D[q * nq + m] = lagrange_deriv(xg, nq, m, xg[q]);
-    for (int m = 0; m < np; ++m) t.Pv[q * np + m] = lagrange(xp, np, m, xg[q]);
+    for (int m = 0; m < np; ++m) {
+      t.Pv[q * np + m] = lagrange(xp, np, m, xg[q]);
+      t.Pd[q * np + m] = lagrange_deriv(xp, np, m, xg[q]);
+    }
   }
 }
 

@@ -27,6 +27,9 @@ template <int K, typename T>
 int launch_cell_apply_fused_k(const LevelDesc<T> &L, int mode, const T *u, const T *p, T *yu, T *yp, cudaStream_t s,
                               int shape, const Fuse<T> &F, const T *geo);
 template <int K, typename T>
+int launch_cell_C_k(const LevelDesc<T> &L, const Tab1D<T> *tab, T cm, T cg, const T *p, T *yp, T sign, T *diag,
+                    cudaStream_t s);
+template <int K, typename T>
 int launch_col_geometry_k(const LevelDesc<T> &L, T *geo, cudaStream_t s);
 template <int K, typename T>
 int launch_cell_grad_k(const LevelDesc<T> &L, const Tab1D<T> *tab, const T *u, const T *lam, T *g, cudaStream_t s);
