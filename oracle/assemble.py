@@ -2,6 +2,9 @@
 
 Bilinear forms (Sec. 2, Eqs. a(u,v), b(v,q)):
     a(u,v) = int mu grad u : grad v + gamma*rho u.v
+  or, in the symmetric-gradient form of Sec. 2 (sym=True),
+    a(u,v) = int mu eps(u) : eps(v) + gamma*rho u.v,   eps(u) = (grad u + grad u^T) / 2,
+  with mu and rho constant per cell (mu_cell, rho_cell; rho defaults to 1)
     b(v,q) = -int q div v
 The sign of b follows the reading that makes K x = b the discretisation of
 -mu Lap u + grad p = f (the paper prints both signs; the velocity is unaffected,
@@ -50,7 +53,7 @@ def geometry(tab, Xv):
     return J, detJ, JinvT
 
 
-def element_matrices(level, tab, mu, gamma_rho, mu_cell=None, cells=None):
+def element_matrices(level, tab, mu, gamma_rho, mu_cell=None, cells=None, rho_cell=None, sym=False):
     """Element matrices of a block of cells.
 
     Returns dict with
@@ -61,6 +64,9 @@ def element_matrices(level, tab, mu, gamma_rho, mu_cell=None, cells=None):
       K0  (nc, nphi, nphi)        scalar stiffness grad.grad (no mu)
       Kp  (nc, npsi, npsi)        pressure stiffness grad.grad
       vol (nc,)                   cell volumes
+      Af  (nc, d, nphi, d, nphi)  coupled velocity block of the symmetric form (sym=True):
+                                  Af[c,i,e,j] = mu_c (1/2 delta_ce int grad phi_i . grad phi_j
+                                  + 1/2 int d_e phi_i d_c phi_j) + delta_ce gamma rho_c int phi_i phi_j
     """
     Xv = level.cell_vertices()
     if cells is not None:
@@ -82,8 +88,20 @@ def element_matrices(level, tab, mu, gamma_rho, mu_cell=None, cells=None):
         muv = np.asarray(mu_cell, dtype=np.float64)
         if cells is not None:
             muv = muv[cells]
-    As = muv[:, None, None] * K0 + gamma_rho * Mv
-    return {"As": As, "B": B, "Mv": Mv, "Mp": Mp, "K0": K0, "Kp": Kp, "vol": wdet.sum(axis=1)}
+    rhov = np.ones(len(Xv)) if rho_cell is None else np.asarray(rho_cell, dtype=np.float64)
+    if rho_cell is not None and cells is not None:
+        rhov = rhov[cells]
+    grho = gamma_rho * rhov[:, None, None]
+    As = muv[:, None, None] * K0 + grho * Mv
+    out = {"As": As, "B": B, "Mv": Mv, "Mp": Mp, "K0": K0, "Kp": Kp, "vol": wdet.sum(axis=1)}
+    if sym:
+        d = level.dim
+        X = np.einsum("cq,ciqa,cjqb->cijab", wdet, grad, grad)   # int d_a phi_i d_b phi_j
+        eye = np.eye(d)
+        Af = 0.5 * np.einsum("ce,kij->kciej", eye, K0) + 0.5 * np.einsum("kijec->kciej", X)
+        Af = muv[:, None, None, None, None] * Af + np.einsum("ce,kij->kciej", eye, grho * Mv)
+        out["Af"] = Af
+    return out
 
 
 def _scatter(rows_loc, cols_loc, vals, shape):
@@ -93,7 +111,8 @@ def _scatter(rows_loc, cols_loc, vals, shape):
     return sp.coo_matrix((vals.reshape(-1), (r, c)), shape=shape).tocsr()
 
 
-def assemble(level, mu=1.0, gamma_rho=0.0, mu_cell=None, chunk=4096, c_mass=0.0, c_grad=0.0):
+def assemble(level, mu=1.0, gamma_rho=0.0, mu_cell=None, chunk=4096, c_mass=0.0, c_grad=0.0, rho_cell=None,
+             sym=False):
     """Assembled operators of one level.
 
     Returns dict of CSR matrices (all FP64):
@@ -116,9 +135,10 @@ def assemble(level, mu=1.0, gamma_rho=0.0, mu_cell=None, chunk=4096, c_mass=0.0,
     Mp = sp.csr_matrix((level.n_p, level.n_p))
     Bf = sp.csr_matrix((level.n_p, level.n_u))
     Cs = sp.csr_matrix((level.n_p, level.n_p))
+    Afull = sp.csr_matrix((level.n_u, level.n_u)) if sym else None
     for s in range(0, level.n_cells, chunk):
         cells = np.arange(s, min(s + chunk, level.n_cells))
-        E = element_matrices(level, tab, mu, gamma_rho, mu_cell, cells)
+        E = element_matrices(level, tab, mu, gamma_rho, mu_cell, cells, rho_cell, sym)
         As = As + _scatter(vn[cells], vn[cells], E["As"], (nv, nv))
         Mv = Mv + _scatter(vn[cells], vn[cells], E["Mv"], (nv, nv))
         Mp = Mp + _scatter(pn[cells], pn[cells], E["Mp"], (level.n_p, level.n_p))
@@ -128,16 +148,21 @@ def assemble(level, mu=1.0, gamma_rho=0.0, mu_cell=None, chunk=4096, c_mass=0.0,
             Cs = Cs + _scatter(pn[cells], pn[cells], Ce, (level.n_p, level.n_p))
         nc = len(cells)
         cols = (vn[cells][:, None, :] + (np.arange(d) * nv)[None, :, None]).reshape(nc, -1)
+        if sym:
+            Afull = Afull + _scatter(cols, cols, E["Af"].reshape(nc, cols.shape[1], cols.shape[1]),
+                                     (level.n_u, level.n_u))
         Bf = Bf + _scatter(pn[cells], cols, E["B"].reshape(nc, pn.shape[1], -1), (level.n_p, level.n_u))
-    return finish(level, As, Mv, Mp, Bf, Cs, c_mass)
+    return finish(level, As, Mv, Mp, Bf, Cs, c_mass, Afull)
 
 
-def finish(level, As, Mv, Mp, Bf, C=None, c_mass=0.0):
+def finish(level, As, Mv, Mp, Bf, C=None, c_mass=0.0, A_full=None):
     d = level.dim
     vmask = level.velocity_constrained()
     umask = np.tile(vmask, d)
     Zu = sp.diags((~umask).astype(np.float64))
-    A_full = sp.block_diag([As] * d, format="csr")
+    if A_full is None:
+        A_full = sp.block_diag([As] * d, format="csr")
+    A_full = A_full.tocsr()
     A = (Zu @ A_full @ Zu + sp.diags(umask.astype(np.float64))).tocsr()
     B = (Bf @ Zu).tocsr()
     C = sp.csr_matrix((level.n_p, level.n_p)) if C is None else C.tocsr()
@@ -145,7 +170,7 @@ def finish(level, As, Mv, Mp, Bf, C=None, c_mass=0.0):
     free = ~level.constrained()
     # constant pressures stay in the kernel of K under full Dirichlet data unless C has a mass part
     pker = level.has_pressure_kernel() and c_mass == 0.0
-    return {"As_full": As.tocsr(), "Mv_full": Mv.tocsr(), "Mp": Mp.tocsr(), "B_full": Bf.tocsr(),
+    return {"As_full": As.tocsr(), "A_full": A_full, "Mv_full": Mv.tocsr(), "Mp": Mp.tocsr(), "B_full": Bf.tocsr(),
             "A": A, "B": B, "C": C, "K": K, "free": free, "umask": umask, "pker": pker}
 
 
@@ -164,8 +189,7 @@ def lift(level, ops, uD):
     """Z K_full u_D: the operator applied to Dirichlet values without the constraint masking,
     with the rows of constrained DoFs zeroed (inhomogeneous data by lifting: solve
     K x0 = b - Z K_full u_D, then x = x0 + u_D)."""
-    d = level.dim
-    A_full = sp.block_diag([ops["As_full"]] * d, format="csr")
+    A_full = ops["A_full"]
     Bf = ops["B_full"]
     K_full = sp.bmat([[A_full, Bf.T], [Bf, None]], format="csr")
     y = K_full @ uD

@@ -43,15 +43,18 @@ class CoarseSolver:
 
 class Multigrid:
     def __init__(self, hier, mu=1.0, gamma_rho=0.0, kA=3, kS=3, m=2, cycle="V", schur_diag="loc",
-                 mu_cells=None, eig_steps=40, eig_safety=1.1, seed=0x5EED, c_mass=0.0, c_grad=0.0):
-        """mu_cells: optional list (one array per level, coarse to fine) of per-cell viscosities."""
+                 mu_cells=None, eig_steps=40, eig_safety=1.1, seed=0x5EED, c_mass=0.0, c_grad=0.0, rho_cells=None,
+                 sym=False):
+        """mu_cells / rho_cells: optional lists (one array per level, coarse to fine) of per-cell
+        viscosities / densities; sym: the symmetric-gradient form of a(u,v)."""
         self.hier = hier
         self.m = m
         self.gamma = {"V": 1, "W": 2}[cycle]
         self.ops, self.smoothers, self.P = [], [], []
         for l, lev in enumerate(hier.levels):
             mc = None if mu_cells is None else mu_cells[l]
-            ops = assemble(lev, mu, gamma_rho, mc, c_mass=c_mass, c_grad=c_grad)
+            rc = None if rho_cells is None else rho_cells[l]
+            ops = assemble(lev, mu, gamma_rho, mc, c_mass=c_mass, c_grad=c_grad, rho_cell=rc, sym=sym)
             self.ops.append(ops)
             if l == 0:
                 self.coarse = CoarseSolver(lev, ops["K"], ops["pker"])
@@ -59,7 +62,7 @@ class Multigrid:
                 self.P.append(None)
             else:
                 self.smoothers.append(LevelSmoother(lev, ops, kA, kS, schur_diag, mu, gamma_rho, mc,
-                                                    eig_steps, eig_safety, seed))
+                                                    eig_steps, eig_safety, seed, rho_cell=rc, sym=sym))
                 self.P.append(prolongation(hier.levels[l - 1], lev))
 
     @property

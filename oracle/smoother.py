@@ -106,11 +106,12 @@ def lanczos_max(apply_S, v0, steps):
     return float(np.linalg.eigvalsh(T)[-1])
 
 
-def local_schur_diag(level, mu, gamma_rho, mu_cell=None, chunk=4096):
+def local_schur_diag(level, mu, gamma_rho, mu_cell=None, chunk=4096, rho_cell=None, sym=False):
     """D_S_loc = sum_tau P_tau^T diag(B_tau diag(A_tau)^{-1} B_tau^T) P_tau  (Eq. diag loc).
 
-    A_tau is the cell's velocity block (same scalar block per component); B_tau
-    excludes constrained velocity DoFs (their columns of B are zero globally).
+    A_tau is the cell's velocity block (the same scalar block per component, or the coupled block
+    of the symmetric form); B_tau excludes constrained velocity DoFs (their columns of B are zero
+    globally).
     """
     tab = Tables(level.dim, level.k)
     vn = level.cell_velocity_nodes()
@@ -119,11 +120,15 @@ def local_schur_diag(level, mu, gamma_rho, mu_cell=None, chunk=4096):
     out = np.zeros(level.n_p)
     for s in range(0, level.n_cells, chunk):
         cells = np.arange(s, min(s + chunk, level.n_cells))
-        E = element_matrices(level, tab, mu, gamma_rho, mu_cell, cells)
-        diagA = np.einsum("cii->ci", E["As"])                  # (nc, nphi)
+        E = element_matrices(level, tab, mu, gamma_rho, mu_cell, cells, rho_cell, sym)
         free = (~vmask[vn[cells]]).astype(np.float64)           # (nc, nphi)
         B = E["B"]                                              # (nc, npsi, d, nphi)
-        loc = np.einsum("ciaj,cj->ci", B**2, free / diagA)
+        if sym:
+            diagA = np.einsum("kcici->kci", E["Af"])             # (nc, d, nphi)
+            loc = np.einsum("ciaj,caj->ci", B**2, free[:, None, :] / diagA)
+        else:
+            diagA = np.einsum("cii->ci", E["As"])              # (nc, nphi)
+            loc = np.einsum("ciaj,cj->ci", B**2, free / diagA)
         np.add.at(out, pn[cells], loc)
     return out
 
@@ -132,7 +137,7 @@ class LevelSmoother:
     """Algorithm 2 on one level plus the smoother and its building blocks."""
 
     def __init__(self, level, ops, kA, kS, schur_diag="loc", mu=1.0, gamma_rho=0.0, mu_cell=None,
-                 eig_steps=40, eig_safety=1.1, seed=0x5EED, beta_A=None, beta_S=None):
+                 eig_steps=40, eig_safety=1.1, seed=0x5EED, beta_A=None, beta_S=None, rho_cell=None, sym=False):
         self.level, self.ops = level, ops
         self.kA, self.kS = kA, kS
         self.A, self.B = ops["A"], ops["B"]
@@ -156,7 +161,7 @@ class LevelSmoother:
         # D_S~ approximates the diagonal of S~ = B A^-1_hat B^T + C (Sec. 1): each variant of the
         # first term plus diag(C)
         if schur_diag == "loc":
-            DS = local_schur_diag(level, mu, gamma_rho, mu_cell)
+            DS = local_schur_diag(level, mu, gamma_rho, mu_cell, rho_cell=rho_cell, sym=sym)
         elif schur_diag == "p":
             DS = ops["Mp"].diagonal().copy()
         elif schur_diag == "d":
