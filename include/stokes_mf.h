@@ -82,6 +82,11 @@ typedef struct {
                            grad p . grad q, h_tau = |tau|^(1/d); both >= 0.  With c_mass > 0 the
                            constant pressure is no longer in the kernel of K (no zero-mean fixing) */
   double c_grad;
+  int sym_grad;         /* 1: a(u,v) = int mu eps(u):eps(v) + gamma rho u.v, the symmetric-gradient form of
+                           Sec. 2 (eps(u) = (grad u + grad u^T)/2); 0: int mu grad u:grad v + gamma rho u.v */
+  const double *rho_cell; /* HOST, nullable: per-cell rho of the gamma rho u.v term on the finest level
+                           (n cells, x fastest; copied at setup; coarse levels take the mean of the
+                           2^d children); null: rho = 1.  Entries must be > 0 */
 } stokes_opts;
 
 /* Fill *o with kA = kS = 3, m = 2, V-cycle, local Schur diagonal, FP32 cycle,
@@ -177,7 +182,8 @@ int stokes_set_viscosity(stokes_ctx *ctx, const double *mu_cell, void *stream);
  * int_c grad lam_i . grad u_i dx, i.e. -lam^T (dK/dmu_c) u, for the solution u of K(mu) u = b
  * and the adjoint lam of K lam = dJ/du (K is symmetric).  u, lam: device double vectors of
  * n_u + n_p entries (velocity part used; constrained entries read as 0); dJ_dmu: device, n_cells
- * doubles (x fastest).  No counterpart in the paper (constant mu there). */
+ * doubles (x fastest).  No counterpart in the paper (constant mu there).  Laplacian form only:
+ * STOKES_EINVAL for a context of the symmetric-gradient form. */
 int stokes_cell_grad(stokes_ctx *ctx, const double *u, const double *lam, double *dJ_dmu, void *stream);
 
 /* Physical coordinates of the velocity nodes of `level` (the Gauss-Lobatto nodes of every cell

@@ -51,7 +51,7 @@ class StokesMG:
     def __init__(self, dim, n, n_levels, k=2, mu=1.0, gamma_rho=0.0, vertices=None, lo=(0.0, 0.0, 0.0),
                  hi=(1.0, 1.0, 1.0), dirichlet_faces=None, mu_cell=None, kA=3, kS=3, m=2, cycle="V",
                  schur_diag="loc", vcycle_fp32=True, restart=30, eig_iters=40, eig_safety=1.1, seed=0x5EED,
-                 c_mass=0.0, c_grad=0.0):
+                 c_mass=0.0, c_grad=0.0, sym_grad=False, rho_cell=None):
         self._lib = L.load()
         torch = _torch()
         self.dim, self.k, self.n_levels = dim, k, n_levels
@@ -86,6 +86,11 @@ class StokesMG:
         opts.eig_safety = eig_safety
         opts.seed = seed
         opts.c_mass, opts.c_grad = float(c_mass), float(c_grad)
+        opts.sym_grad = 1 if sym_grad else 0
+        if rho_cell is not None:
+            rc = np.ascontiguousarray(np.asarray(rho_cell, dtype=np.float64).reshape(-1))
+            self._keep.append(rc)
+            opts.rho_cell = rc.ctypes.data_as(C.POINTER(C.c_double))
         ctx = C.c_void_p()
         st = self._lib.stokes_setup(C.byref(mesh), k, float(mu), float(gamma_rho), mu_ptr, C.byref(opts),
                                     self._stream(), C.byref(ctx))

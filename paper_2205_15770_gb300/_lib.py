@@ -23,7 +23,7 @@ class StokesOpts(C.Structure):
     _fields_ = [("kA", C.c_int), ("kS", C.c_int), ("m", C.c_int), ("cycle", C.c_int), ("schur_diag", C.c_int),
                 ("vcycle_fp32", C.c_int), ("gmres_restart", C.c_int), ("eig_iters", C.c_int),
                 ("eig_safety", C.c_double), ("seed", C.c_ulonglong), ("c_mass", C.c_double),
-                ("c_grad", C.c_double)]
+                ("c_grad", C.c_double), ("sym_grad", C.c_int), ("rho_cell", C.POINTER(C.c_double))]
 
 
 # name -> (restype, argtypes)

@@ -34,11 +34,11 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
 
 template <typename T>
 int launch_cell_apply(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, const T *u, const T *p, T *yu, T *yp,
-                      cudaStream_t s, int shape, const T *geo) {
+                      cudaStream_t s, int shape, const T *geo, const T *rho) {
   switch (L.k) {
-    case 2: return launch_cell_apply_k<2, T>(L, tab, mode, u, p, yu, yp, s, shape, geo);
-    case 3: return launch_cell_apply_k<3, T>(L, tab, mode, u, p, yu, yp, s, shape, geo);
-    default: return launch_cell_apply_k<4, T>(L, tab, mode, u, p, yu, yp, s, shape, geo);
+    case 2: return launch_cell_apply_k<2, T>(L, tab, mode, u, p, yu, yp, s, shape, geo, rho);
+    case 3: return launch_cell_apply_k<3, T>(L, tab, mode, u, p, yu, yp, s, shape, geo, rho);
+    default: return launch_cell_apply_k<4, T>(L, tab, mode, u, p, yu, yp, s, shape, geo, rho);
   }
 }
 template <typename T>
@@ -69,11 +69,11 @@ int launch_cell_apply_fused(const LevelDesc<T> &L, int mode, const T *u, const T
 }
 template <>
 int launch_cell_diag<double>(const LevelDesc<double> &L, const Tab1D<double> *tab, double *a, double *b, double *c,
-                             cudaStream_t s) {
+                             cudaStream_t s, const double *rho, int sym) {
   switch (L.k) {
-    case 2: return launch_cell_diag_k<2, double>(L, tab, a, b, c, s);
-    case 3: return launch_cell_diag_k<3, double>(L, tab, a, b, c, s);
-    default: return launch_cell_diag_k<4, double>(L, tab, a, b, c, s);
+    case 2: return launch_cell_diag_k<2, double>(L, tab, a, b, c, s, rho, sym);
+    case 3: return launch_cell_diag_k<3, double>(L, tab, a, b, c, s, rho, sym);
+    default: return launch_cell_diag_k<4, double>(L, tab, a, b, c, s, rho, sym);
   }
 }
 
@@ -138,6 +138,7 @@ struct LevelRT {
   XferTabs<T> xf{};  // 1D transfer matrices between this level and the next coarser one
   bool fuse = true;  // fused smoothing on this level (set by the setup's timing, when eligible)
   const T *geo = nullptr;  // FP64 3D trilinear: precomputed per-point geometry of the column kernel
+  const T *rho = nullptr;  // per-cell density of the gamma rho mass term (null: rho = 1)
   T *DAinv = nullptr, *DSinv = nullptr;
   T *x = nullptr, *b = nullptr, *r = nullptr, *kx = nullptr;                   // full vectors
   T *tu = nullptr, *ru = nullptr, *uhat = nullptr, *cx = nullptr, *cd = nullptr, *ct = nullptr;  // velocity
@@ -159,6 +160,8 @@ struct stokes_ctx {
   stokes_opts o{};
   double mu = 1, gamma_rho = 0;
   double c_mass = 0, c_grad = 0;  // stabilisation block C (0: none)
+  bool sym = false;               // symmetric-gradient form of a(u,v)
+  std::vector<double> rho_host;   // caller's per-cell rho (finest level), kept for stokes_set_viscosity
   bool pker = false;
   std::vector<LevelRT<double>> L64;
   std::vector<LevelRT<float>> L32;
@@ -303,7 +306,7 @@ struct Runner {
   // Cycle form: the outputs are already zero (work buffers are zeroed by the kernel that
   // consumes them, so the captured cycle contains kernels only).
   void apply_nz(int l, int mode, const T *u, const T *p, T *yu, T *yp) {
-    launch_cell_apply<T>(L[l].d, tab, mode, u, p, yu, yp, s, L[l].shape, L[l].geo);
+    launch_cell_apply<T>(L[l].d, tab, form(mode), u, p, yu, yp, s, L[l].shape, L[l].geo, L[l].rho);
     note();
   }
   void vmult(int l, const T *x, T *y, bool identity) {
@@ -317,6 +320,8 @@ struct Runner {
   }
   // Stabilisation block (no launch when C = 0): yp += sign C p.
   bool hasC() const { return C->c_mass != 0.0 || C->c_grad != 0.0; }
+  // the velocity block's form: the symmetric-gradient bit joins every application of A
+  int form(int mode) const { return (C->sym && (mode & kApplyA)) ? (mode | kApplySym) : mode; }
   void applyC(int l, const T *p, T *yp, T sign) {
     if (!hasC()) return;
     launch_cell_C<T>(L[l].d, tab, (T)C->c_mass, (T)C->c_grad, p, yp, sign, (T *)nullptr, s);
@@ -433,7 +438,7 @@ struct Runner {
   // step, residual) or written by k_fused_finish.
   bool fused_ok(int l) const { return fused_eligible(l) && L[l].fuse; }
   bool fused_eligible(int l) const {
-    return C->fuse && !hasC() && C->o.kA == 1 && C->o.kS >= 1 && C->o.kS <= 4 && L[l].d.dim == 3 &&
+    return C->fuse && !hasC() && !C->sym && !L[l].rho && C->o.kA == 1 && C->o.kS >= 1 && C->o.kS <= 4 && L[l].d.dim == 3 &&
            L[l].shape >= 0;
   }
   T *pairU(int l, int pr) { return pr == 0 ? L[l].tu : L[l].cx; }
@@ -1100,7 +1105,8 @@ static int autotune_level(stokes_ctx *C, LevelRT<T> &R, const Tab1D<T> *tab) {
         C,
         [&] {
           for (int r = 0; r < reps; ++r)
-            launch_cell_apply<T>(R.d, tab, kApplyA, R.x, nullptr, R.r, nullptr, C->s, R.shape, R.geo);
+            launch_cell_apply<T>(R.d, tab, C->sym ? kApplyA | kApplySym : kApplyA, R.x, nullptr, R.r, nullptr, C->s,
+                                 R.shape, R.geo, R.rho);
         },
         &ex[ci]);
   }
@@ -1203,6 +1209,22 @@ static int parse_tuning(const char *spec, int nl, std::vector<int> tune[4]) {
   return STOKES_OK;
 }
 
+// Cell values of the next coarser level (n cells per direction): the mean of the 2^d children.
+static std::vector<double> coarsen_mean(const std::vector<double> &fm, const int n[3], int dim) {
+  std::vector<double> cm((size_t)n[0] * n[1] * n[2], 0.0);
+  const int fx = 2 * n[0], fy = 2 * n[1];
+  for (int cz = 0; cz < n[2]; ++cz)
+    for (int cy = 0; cy < n[1]; ++cy)
+      for (int cx = 0; cx < n[0]; ++cx) {
+        double sum = 0.0;
+        for (int dz = 0; dz < (dim == 3 ? 2 : 1); ++dz)
+          for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx) sum += fm[((size_t)(2 * cz + dz) * fy + (2 * cy + dy)) * fx + (2 * cx + dx)];
+        cm[((size_t)cz * n[1] + cy) * n[0] + cx] = sum / (dim == 3 ? 8.0 : 4.0);
+      }
+  return cm;
+}
+
 static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho, const double *mu_cell,
                     const stokes_opts *opts, stokes_ctx *C) {
   const int dim = mesh->dim, nl = mesh->n_levels;
@@ -1233,6 +1255,17 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
   }
   C->c_mass = C->o.c_mass;
   C->c_grad = C->o.c_grad;
+  C->sym = C->o.sym_grad != 0;
+  if (C->o.rho_cell) {
+    const long long nc = (long long)mesh->n[0] * mesh->n[1] * (dim == 3 ? mesh->n[2] : 1);
+    C->rho_host.assign(C->o.rho_cell, C->o.rho_cell + nc);
+    for (double v : C->rho_host)
+      if (!(v > 0) || !std::isfinite(v)) {
+        set_error("rho_cell entries must be positive");
+        return STOKES_EINVAL;
+      }
+    C->o.rho_cell = C->rho_host.data();
+  }
   const unsigned full = dim == 3 ? 0x3Fu : 0xFu;
   const unsigned faces = mesh->dirichlet_faces & full;
   // constant pressures span the kernel of K under full Dirichlet data, unless C has a mass part
@@ -1278,10 +1311,12 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
   const int nf[3] = {mesh->n[0], mesh->n[1], dim == 3 ? mesh->n[2] : 1};
   std::vector<double> mu_fine;
   if (mu_cell) mu_fine.assign(mu_cell, mu_cell + (long long)nf[0] * nf[1] * nf[2]);
-  std::vector<std::vector<double>> mu_levels(nl);
+  std::vector<std::vector<double>> mu_levels(nl), rho_levels(nl);
   for (int l = nl - 1; l >= 0; --l) {
     const int s = 1 << (nl - 1 - l);
     int n[3] = {nf[0] / s, nf[1] / s, dim == 3 ? nf[2] / s : 1};
+    if (!C->rho_host.empty())  // per-cell rho: coarse values are the mean of the 2^d children
+      rho_levels[l] = l == nl - 1 ? C->rho_host : coarsen_mean(rho_levels[l + 1], n, dim);
     if (mu_cell) {
       if (l < nl - 1) {  // mean of the 2^d children (fine level l+1 has 2n cells per direction)
         std::vector<double> &fm = mu_levels[l + 1];
@@ -1386,6 +1421,19 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
       d.mu_cell = dm;
       f.mu_cell = fm;
     }
+    if (!rho_levels[l].empty()) {
+      std::vector<double> &m = rho_levels[l];
+      std::vector<float> mf(m.begin(), m.end());
+      double *dr;
+      float *fr;
+      if ((st = dalloc(C, &dr, (long long)m.size()))) return st;
+      if ((st = dalloc(C, &fr, (long long)m.size()))) return st;
+      SMF_CUDA_OK(cudaMemcpyAsync(dr, m.data(), m.size() * sizeof(double), cudaMemcpyHostToDevice, C->s));
+      SMF_CUDA_OK(cudaMemcpyAsync(fr, mf.data(), mf.size() * sizeof(float), cudaMemcpyHostToDevice, C->s));
+      SMF_CUDA_OK(cudaStreamSynchronize(C->s));
+      C->L64[l].rho = dr;
+      C->L32[l].rho = fr;
+    }
     C->L64[l].d = d;
     C->L32[l].d = f;
     C->L64[l].geo = geo_l;
@@ -1442,13 +1490,13 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
     LevelRT<double> &R = C->L64[l];
     const LevelDesc<double> &d = R.d;
     double *dAs, *dSloc, *dMp;
-    if ((st = dalloc(C, &dAs, d.nv))) return st;
+    if ((st = dalloc(C, &dAs, C->sym ? d.n_u : d.nv))) return st;
     if ((st = dalloc(C, &dSloc, d.n_p))) return st;
     if ((st = dalloc(C, &dMp, d.n_p))) return st;
     if ((st = dalloc(C, &C->DA[l], d.n_u))) return st;
-    launch_cell_diag<double>(d, C->tab64, dAs, dSloc, dMp, C->s);
+    launch_cell_diag<double>(d, C->tab64, dAs, dSloc, dMp, C->s, R.rho, C->sym ? 1 : 0);
     ++C->launches;
-    k_expand_diag<double><<<vec_blocks(d.n_u), kVecThreads, 0, C->s>>>(d, dAs, C->DA[l]);
+    k_expand_diag<double><<<vec_blocks(d.n_u), kVecThreads, 0, C->s>>>(d, dAs, C->DA[l], C->sym ? 1 : 0);
     k_reciprocal<double><<<vec_blocks(d.n_u), kVecThreads, 0, C->s>>>(C->DA[l], R.DAinv, d.n_u);
     C->launches += 2;
     double est;
@@ -1986,6 +2034,8 @@ void stokes_default_opts(stokes_opts *o) {
   o->seed = 0x5EEDull;
   o->c_mass = 0.0;
   o->c_grad = 0.0;
+  o->sym_grad = 0;
+  o->rho_cell = nullptr;
 }
 
 int stokes_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho, const double *mu_cell,
@@ -2294,8 +2344,10 @@ int stokes_get_diagonals(stokes_ctx *C, int level, double *DA, double *DS, void 
 }
 
 int stokes_cell_grad(stokes_ctx *C, const double *u, const double *lam, double *dJ_dmu, void *stream) {
-  if (!C || !u || !lam || !dJ_dmu) {
-    set_error("invalid stokes_cell_grad arguments");
+  if (!C || !u || !lam || !dJ_dmu || C->sym) {
+    set_error(C && C->sym ? "stokes_cell_grad is the gradient of the Laplacian form; the context uses the "
+                            "symmetric-gradient form"
+                          : "invalid stokes_cell_grad arguments");
     if (C) C->err = g_last_error;
     return STOKES_EINVAL;
   }
@@ -2374,8 +2426,8 @@ int stokes_lift_rhs(stokes_ctx *C, const double *uD, double *b, void *stream) {
   const long long nu = L.d.n_u, n = nu + L.d.n_p;
   // kx = [A B^T; B 0] u_D with the Dirichlet values read (rows of constrained DoFs stay zero)
   R.zero(L.kx, n);
-  launch_cell_apply<double>(L.d, C->tab64, kApplyA | kApplyBT | kApplyB | kApplyUnmasked, uD, uD + nu, L.kx,
-                            L.kx + nu, C->s, -1);
+  launch_cell_apply<double>(L.d, C->tab64, Runner<double>(C).form(kApplyA | kApplyBT | kApplyB | kApplyUnmasked), uD,
+                            uD + nu, L.kx, L.kx + nu, C->s, -1, nullptr, L.rho);
   ++C->launches;
   R.vec(k_axpy<double>, n, b, -1.0, (const double *)L.kx, n);
   R.zero(L.kx, n);
@@ -2446,10 +2498,12 @@ int stokes_time_apply(stokes_ctx *C, int level, int precision, int blocks, int r
   for (int r = 0; r < reps; ++r) {
     if (precision == 64) {
       LevelRT<double> &R = C->L64[level];
-      launch_cell_apply<double>(R.d, C->tab64, blocks, R.x, R.x + R.d.n_u, R.r, R.r + R.d.n_u, C->s, R.shape, R.geo);
+      launch_cell_apply<double>(R.d, C->tab64, Runner<double>(C).form(blocks), R.x, R.x + R.d.n_u, R.r, R.r + R.d.n_u,
+                                C->s, R.shape, R.geo, R.rho);
     } else {
       LevelRT<float> &R = C->L32[level];
-      launch_cell_apply<float>(R.d, C->tab32, blocks, R.x, R.x + R.d.n_u, R.r, R.r + R.d.n_u, C->s, R.shape, R.geo);
+      launch_cell_apply<float>(R.d, C->tab32, Runner<float>(C).form(blocks), R.x, R.x + R.d.n_u, R.r, R.r + R.d.n_u,
+                               C->s, R.shape, R.geo, R.rho);
     }
     ++C->launches;
   }

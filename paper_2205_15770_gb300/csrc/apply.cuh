@@ -157,7 +157,7 @@ template <int DIM, int K, typename T, bool CART>
 __global__ void __launch_bounds__(CellShape<DIM, K>::THREADS)
     stokes_cell_apply(const LevelDesc<T> L, const Tab1D<T> *__restrict__ tab, const int mode,
                       const T *__restrict__ u, const T *__restrict__ p, T *__restrict__ yu,
-                      T *__restrict__ yp) {
+                      T *__restrict__ yp, const T *__restrict__ rho_cell) {
   pdl_enter();
   using CS = CellShape<DIM, K>;
   constexpr int NQ = CS::NQ, NV = CS::NV, NPR = CS::NPR, NP = CS::NP, NPP = CS::NPP;
@@ -200,6 +200,8 @@ __global__ void __launch_bounds__(CellShape<DIM, K>::THREADS)
   PointGeo<DIM, T> g;
   point_geometry<DIM, K, T, CART>(L, st->x, st->w, verts, qx, qy, qz, g);
   const T mu = L.mu_cell ? (valid ? L.mu_cell[cell] : T(0)) : L.mu;
+  // gamma rho of the cell (rho per cell when given, else 1)
+  const T grho = L.gamma_rho * (rho_cell ? (valid ? rho_cell[cell] : T(0)) : T(1));
 
   const bool needP = mode & kApplyBT;
   const bool massOp = mode & (kApplyMass | kApplyMassAll);
@@ -235,83 +237,132 @@ __global__ void __launch_bounds__(CellShape<DIM, K>::THREADS)
   const int gx = K * cx + ix, gy = K * cy + iy, gz = K * cz + iz;
   const long long vidx = lattice_index<DIM, T>(L.N, gx, gy, gz);
   const bool vfree = valid && !vel_constrained(L.N, L.faces, DIM, gx, gy, gz);
-  T qacc = T(0);
-#pragma unroll 1
-  for (int c = 0; c < DIM; ++c) {
-    T gr[3] = {T(0), T(0), T(0)};
-    T uq = T(0);
-    if (needU) {
-      // b = Z M_v f reads every node of f (boundary values couple into free rows); its transpose
-      // M_v Z reads the free nodes only and writes every row
-      bufA[t] = ((mode & (kApplyMass | kApplyUnmasked)) ? valid : vfree) ? u[c * L.nv + vidx] : T(0);
+  // forward sweeps of component c: value and reference gradient at this thread's Gauss point
+  auto forward = [&](int c, T &uq, T (&gr)[3]) {
+    // b = Z M_v f reads every node of f (boundary values couple into free rows); its transpose
+    // M_v Z reads the free nodes only and writes every row
+    bufA[t] = ((mode & (kApplyMass | kApplyUnmasked)) ? valid : vfree) ? u[c * L.nv + vidx] : T(0);
+    __syncthreads();
+    if (DIM == 3) {
+      bufB[t] = contract<0, NQ, NV, NV, NV, NV, false>(t, bufA, st->S);
       __syncthreads();
-      if (DIM == 3) {
-        bufB[t] = contract<0, NQ, NV, NV, NV, NV, false>(t, bufA, st->S);
-        __syncthreads();
-        bufA[t] = contract<1, NQ, NQ, NV, NV, NV, false>(t, bufB, st->S);
-        __syncthreads();
-        bufB[t] = contract<2, NQ, NQ, NQ, NV, NV, false>(t, bufA, st->S);
-        __syncthreads();
-        uq = bufB[t];
-        gr[0] = contract<0, NQ, NQ, NQ, NQ, NQ, false>(t, bufB, st->D);
-        gr[1] = contract<1, NQ, NQ, NQ, NQ, NQ, false>(t, bufB, st->D);
-        gr[2] = contract<2, NQ, NQ, NQ, NQ, NQ, false>(t, bufB, st->D);
-      } else {
-        bufB[t] = contract<0, NQ, NV, 1, NV, NV, false>(t, bufA, st->S);
-        __syncthreads();
-        bufA[t] = contract<1, NQ, NQ, 1, NV, NV, false>(t, bufB, st->S);
-        __syncthreads();
-        uq = bufA[t];
-        gr[0] = contract<0, NQ, NQ, 1, NQ, NQ, false>(t, bufA, st->D);
-        gr[1] = contract<1, NQ, NQ, 1, NQ, NQ, false>(t, bufA, st->D);
-      }
+      bufA[t] = contract<1, NQ, NQ, NV, NV, NV, false>(t, bufB, st->S);
+      __syncthreads();
+      bufB[t] = contract<2, NQ, NQ, NQ, NV, NV, false>(t, bufA, st->S);
+      __syncthreads();
+      uq = bufB[t];
+      gr[0] = contract<0, NQ, NQ, NQ, NQ, NQ, false>(t, bufB, st->D);
+      gr[1] = contract<1, NQ, NQ, NQ, NQ, NQ, false>(t, bufB, st->D);
+      gr[2] = contract<2, NQ, NQ, NQ, NQ, NQ, false>(t, bufB, st->D);
+    } else {
+      bufB[t] = contract<0, NQ, NV, 1, NV, NV, false>(t, bufA, st->S);
+      __syncthreads();
+      bufA[t] = contract<1, NQ, NQ, 1, NV, NV, false>(t, bufB, st->S);
+      __syncthreads();
+      uq = bufA[t];
+      gr[0] = contract<0, NQ, NQ, 1, NQ, NQ, false>(t, bufA, st->D);
+      gr[1] = contract<1, NQ, NQ, 1, NQ, NQ, false>(t, bufA, st->D);
     }
-    if (outP) {
+  };
+  // transposed sweeps of the reference fluxes f and the value term mv, scattered into component c
+  auto backward = [&](int c, const T (&f)[3], T mv) {
+    FX[t] = f[0];
+    FY[t] = f[1];
+    if (DIM == 3) FZ[t] = f[2];
+    __syncthreads();
+    T tq = mv + contract<0, NQ, NQ, (DIM == 3 ? NQ : 1), NQ, NQ, true>(t, FX, st->D) +
+           contract<1, NQ, NQ, (DIM == 3 ? NQ : 1), NQ, NQ, true>(t, FY, st->D);
+    if (DIM == 3) tq += contract<2, NQ, NQ, NQ, NQ, NQ, true>(t, FZ, st->D);
+    bufA[t] = tq;
+    __syncthreads();
+    T val;
+    if (DIM == 3) {
+      bufB[t] = contract<2, NQ, NQ, NV, NQ, NV, true>(t, bufA, st->S);
+      __syncthreads();
+      bufA[t] = contract<1, NQ, NV, NV, NQ, NV, true>(t, bufB, st->S);
+      __syncthreads();
+      val = contract<0, NV, NV, NV, NQ, NV, true>(t, bufA, st->S);
+    } else {
+      bufB[t] = contract<1, NQ, NV, 1, NQ, NV, true>(t, bufA, st->S);
+      __syncthreads();
+      val = contract<0, NV, NV, 1, NQ, NV, true>(t, bufB, st->S);
+    }
+    if ((mode & kApplyMassAll) ? valid : vfree) atomicAdd(&yu[c * L.nv + vidx], val);
+  };
+  T qacc = T(0);
+  if ((mode & kApplySym) && (mode & kApplyA)) {
+    // symmetric-gradient form (Sec. 2): the flux of test component c is mu eps(u)_{c.}, which
+    // needs the gradients of every component at the point.  Physical gradients from reference
+    // ones: grad_x u_c = adj^T grad u_c / det = (w adj)^T grad u_c / (w det).
+    T gq[3][3] = {}, uqa[3] = {};
 #pragma unroll
-      for (int b = 0; b < DIM; ++b) qacc -= g.C[b * DIM + c] * gr[b];
+    for (int c = 0; c < DIM; ++c) {
+      forward(c, uqa[c], gq[c]);
+      if (outP) {
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) qacc -= g.C[b * DIM + c] * gq[c][b];
+      }
+      __syncthreads();
     }
-    if (outU) {
+    T gp[3][3];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c)
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) {
+        T s = T(0);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) s += g.C[a * DIM + b] * gq[c][a];
+        gp[c][b] = s / g.wdet;
+      }
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
       T f[3] = {T(0), T(0), T(0)};
-      T mv = T(0);
-      if (mode & kApplyA) {
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) {
-          T s = T(0);
+      for (int a = 0; a < DIM; ++a) {
+        T s = T(0);
 #pragma unroll
-          for (int b = 0; b < DIM; ++b) s += g.G[a * DIM + b] * gr[b];
-          f[a] = mu * s;
-        }
-        mv = L.gamma_rho * g.wdet * uq;
+        for (int b = 0; b < DIM; ++b) s += g.C[a * DIM + b] * (T(0.5) * (gp[c][b] + gp[b][c]));
+        f[a] = mu * s;
       }
-      if (massOp) mv += g.wdet * uq;
       if (mode & kApplyBT) {
 #pragma unroll
         for (int b = 0; b < DIM; ++b) f[b] -= pq * g.C[b * DIM + c];
       }
-      FX[t] = f[0];
-      FY[t] = f[1];
-      if (DIM == 3) FZ[t] = f[2];
+      backward(c, f, grho * g.wdet * uqa[c]);
       __syncthreads();
-      T tq = mv + contract<0, NQ, NQ, (DIM == 3 ? NQ : 1), NQ, NQ, true>(t, FX, st->D) +
-             contract<1, NQ, NQ, (DIM == 3 ? NQ : 1), NQ, NQ, true>(t, FY, st->D);
-      if (DIM == 3) tq += contract<2, NQ, NQ, NQ, NQ, NQ, true>(t, FZ, st->D);
-      bufA[t] = tq;
-      __syncthreads();
-      T val;
-      if (DIM == 3) {
-        bufB[t] = contract<2, NQ, NQ, NV, NQ, NV, true>(t, bufA, st->S);
-        __syncthreads();
-        bufA[t] = contract<1, NQ, NV, NV, NQ, NV, true>(t, bufB, st->S);
-        __syncthreads();
-        val = contract<0, NV, NV, NV, NQ, NV, true>(t, bufA, st->S);
-      } else {
-        bufB[t] = contract<1, NQ, NV, 1, NQ, NV, true>(t, bufA, st->S);
-        __syncthreads();
-        val = contract<0, NV, NV, 1, NQ, NV, true>(t, bufB, st->S);
-      }
-      if ((mode & kApplyMassAll) ? valid : vfree) atomicAdd(&yu[c * L.nv + vidx], val);
     }
-    __syncthreads();
+  } else {
+#pragma unroll 1
+    for (int c = 0; c < DIM; ++c) {
+      T gr[3] = {T(0), T(0), T(0)};
+      T uq = T(0);
+      if (needU) forward(c, uq, gr);
+      if (outP) {
+#pragma unroll
+        for (int b = 0; b < DIM; ++b) qacc -= g.C[b * DIM + c] * gr[b];
+      }
+      if (outU) {
+        T f[3] = {T(0), T(0), T(0)};
+        T mv = T(0);
+        if (mode & kApplyA) {
+#pragma unroll
+          for (int a = 0; a < DIM; ++a) {
+            T s = T(0);
+#pragma unroll
+            for (int b = 0; b < DIM; ++b) s += g.G[a * DIM + b] * gr[b];
+            f[a] = mu * s;
+          }
+          mv = grho * g.wdet * uq;
+        }
+        if (massOp) mv += g.wdet * uq;
+        if (mode & kApplyBT) {
+#pragma unroll
+          for (int b = 0; b < DIM; ++b) f[b] -= pq * g.C[b * DIM + c];
+        }
+        backward(c, f, mv);
+      }
+      __syncthreads();
+    }
   }
 
   // ---- pressure test functions ----------------------------------------------------------
@@ -339,12 +390,13 @@ __global__ void __launch_bounds__(CellShape<DIM, K>::THREADS)
 }
 
 // Setup kernel, one cell per CTA, (k+1)^d threads:
-//   dAs[node]  += (A_tau)_jj        scalar velocity block diagonal (same for every component)
+//   dAs[node]  += (A_tau)_jj        scalar velocity block diagonal (same for every component);
+//                                   symmetric form (sym): dAs[c nv + node] per component c
 //   dSloc[i]   += sum_{c, j free} (B_tau)_{i,(c,j)}^2 / (A_tau)_jj   (Eq. diag loc)
 //   dMp[i]     += (M_p,tau)_ii      pressure mass diagonal (Eq. diag p)
 template <int DIM, int K, typename T, bool CART>
 __global__ void stokes_cell_diagonals(const LevelDesc<T> L, const Tab1D<T> *__restrict__ tab, T *dAs, T *dSloc,
-                                      T *dMp) {
+                                      T *dMp, const T *__restrict__ rho_cell, int sym) {
   using CS = CellShape<DIM, K>;
   constexpr int NQ = CS::NQ, NV = CS::NV, NPR = CS::NPR, NP = CS::NP, NPP = CS::NPP;
   __shared__ Tab1D<T> st;
@@ -393,7 +445,11 @@ __global__ void stokes_cell_diagonals(const LevelDesc<T> L, const Tab1D<T> *__re
     gr[2] = sx * sy * dz;
     val = sx * sy * sz;
   };
-  T ajj = T(0);
+  const T grho = L.gamma_rho * (rho_cell ? rho_cell[cell] : T(1));
+  // Laplacian form: the same diagonal for every component; symmetric form:
+  // mu (1/2 grad phi . grad phi + 1/2 (d_c phi)^2) + gamma rho phi^2 for component c, with
+  // d_c phi = (w adj^T grad phi)_c / (w det)
+  T ajjc[3] = {T(0), T(0), T(0)};
   for (int q = 0; q < NP; ++q) {
     T gr[3], val;
     grad_phi(q, gr, val);
@@ -402,12 +458,32 @@ __global__ void stokes_cell_diagonals(const LevelDesc<T> L, const Tab1D<T> *__re
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
       for (int b = 0; b < DIM; ++b) s += gr[a] * sG[q][a * DIM + b] * gr[b];
-    ajj += s + L.gamma_rho * sW[q] * val * val;
+    const T m = grho * sW[q] * val * val;
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      if (sym) {
+        T dc = T(0);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) dc += sC[q][a * DIM + c] * gr[a];
+        ajjc[c] += T(0.5) * s + T(0.5) * mu * dc * dc / sW[q] + m;
+      } else {
+        ajjc[c] += s + m;
+      }
+    }
   }
+  const T ajj = ajjc[0];
   sAjj[t] = ajj;
   const int gx = K * cx + jx, gy = K * cy + jy, gz = K * cz + jz;
   const bool jfree = !vel_constrained(L.N, L.faces, DIM, gx, gy, gz);
-  if (jfree) atomicAdd(&dAs[lattice_index<DIM, T>(L.N, gx, gy, gz)], ajj);
+  if (jfree) {
+    const long long node = lattice_index<DIM, T>(L.N, gx, gy, gz);
+    if (sym) {
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) atomicAdd(&dAs[c * L.nv + node], ajjc[c]);
+    } else {
+      atomicAdd(&dAs[node], ajj);
+    }
+  }
   // local Schur diagonal: columns (c, j = t) of B_tau
   if (jfree) {
     for (int c = 0; c < DIM; ++c) {
@@ -429,8 +505,9 @@ __global__ void stokes_cell_diagonals(const LevelDesc<T> L, const Tab1D<T> *__re
           bcol[i] -= psi * f;
         }
       }
+      const T ac = sym ? (c == 0 ? ajjc[0] : (c == 1 ? ajjc[1] : ajjc[2])) : ajj;
 #pragma unroll
-      for (int i = 0; i < NPP; ++i) atomicAdd(&sLoc[i], bcol[i] * bcol[i] / ajj);
+      for (int i = 0; i < NPP; ++i) atomicAdd(&sLoc[i], bcol[i] * bcol[i] / ac);
     }
   }
   __syncthreads();

@@ -20,12 +20,12 @@ static inline bool getenv_generic() {
 
 template <int DIM, int K, typename T, bool CART>
 static int launch_apply_dim(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, const T *u, const T *p, T *yu,
-                            T *yp, cudaStream_t s) {
+                            T *yp, cudaStream_t s, const T *rho) {
   using CS = CellShape<DIM, K>;
   const long long blocks = (L.n_cells + CS::CPB - 1) / CS::CPB;
   const size_t smem = sizeof(Tab1D<T>) + (size_t)CS::CPB * CS::PER_CELL * sizeof(T);
   launch_kernel(stokes_cell_apply<DIM, K, T, CART>, dim3((unsigned)blocks), dim3(CS::THREADS), smem, s, L, tab, mode, u,
-                p, yu, yp);
+                p, yu, yp, rho);
   return 0;
 }
 
@@ -62,8 +62,11 @@ static int launch_col_mode(const LevelDesc<T> &L, const T *u, const T *p, T *yu,
 // 0 default = column kernel with 4 warps).
 template <int K, typename T>
 int launch_cell_apply_k(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, const T *u, const T *p, T *yu, T *yp,
-                        cudaStream_t s, int shape, const T *geo) {
-  if (L.dim == 3 && !getenv_generic() && shape >= 0) {
+                        cudaStream_t s, int shape, const T *geo, const T *rho) {
+  // the column kernel serves the Laplacian form with a constant rho; the A block of the
+  // symmetric form or with a per-cell rho runs in the generic kernel
+  const bool generic_a = (mode & kApplyA) && ((mode & kApplySym) || rho);
+  if (L.dim == 3 && !getenv_generic() && shape >= 0 && !generic_a) {
     const Fuse<T> F{};
     switch (mode) {
       case kApplyA: return launch_col_mode<K, T, kApplyA, false>(L, u, p, yu, yp, s, shape, F, geo);
@@ -76,10 +79,10 @@ int launch_cell_apply_k(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, co
     }
   }
   if (L.dim == 3)
-    return L.cartesian ? launch_apply_dim<3, K, T, true>(L, tab, mode, u, p, yu, yp, s)
-                       : launch_apply_dim<3, K, T, false>(L, tab, mode, u, p, yu, yp, s);
-  return L.cartesian ? launch_apply_dim<2, K, T, true>(L, tab, mode, u, p, yu, yp, s)
-                     : launch_apply_dim<2, K, T, false>(L, tab, mode, u, p, yu, yp, s);
+    return L.cartesian ? launch_apply_dim<3, K, T, true>(L, tab, mode, u, p, yu, yp, s, rho)
+                       : launch_apply_dim<3, K, T, false>(L, tab, mode, u, p, yu, yp, s, rho);
+  return L.cartesian ? launch_apply_dim<2, K, T, true>(L, tab, mode, u, p, yu, yp, s, rho)
+                     : launch_apply_dim<2, K, T, false>(L, tab, mode, u, p, yu, yp, s, rho);
 }
 
 template <int DIM, int K, typename T, bool CART>
@@ -133,9 +136,10 @@ int launch_cell_apply_fused_k(const LevelDesc<T> &L, int mode, const T *u, const
 }
 
 template <int DIM, int K, typename T, bool CART>
-static int launch_diag_dim(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dSloc, T *dMp, cudaStream_t s) {
+static int launch_diag_dim(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dSloc, T *dMp, cudaStream_t s,
+                           const T *rho, int sym) {
   using CS = CellShape<DIM, K>;
-  stokes_cell_diagonals<DIM, K, T, CART><<<(unsigned)L.n_cells, CS::NP, 0, s>>>(L, tab, dAs, dSloc, dMp);
+  stokes_cell_diagonals<DIM, K, T, CART><<<(unsigned)L.n_cells, CS::NP, 0, s>>>(L, tab, dAs, dSloc, dMp, rho, sym);
   return 0;
 }
 
@@ -159,12 +163,13 @@ int launch_cell_grad_k(const LevelDesc<T> &L, const Tab1D<T> *tab, const T *u, c
 }
 
 template <int K, typename T>
-int launch_cell_diag_k(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dSloc, T *dMp, cudaStream_t s) {
+int launch_cell_diag_k(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dSloc, T *dMp, cudaStream_t s,
+                       const T *rho, int sym) {
   if (L.dim == 3)
-    return L.cartesian ? launch_diag_dim<3, K, T, true>(L, tab, dAs, dSloc, dMp, s)
-                       : launch_diag_dim<3, K, T, false>(L, tab, dAs, dSloc, dMp, s);
-  return L.cartesian ? launch_diag_dim<2, K, T, true>(L, tab, dAs, dSloc, dMp, s)
-                     : launch_diag_dim<2, K, T, false>(L, tab, dAs, dSloc, dMp, s);
+    return L.cartesian ? launch_diag_dim<3, K, T, true>(L, tab, dAs, dSloc, dMp, s, rho, sym)
+                       : launch_diag_dim<3, K, T, false>(L, tab, dAs, dSloc, dMp, s, rho, sym);
+  return L.cartesian ? launch_diag_dim<2, K, T, true>(L, tab, dAs, dSloc, dMp, s, rho, sym)
+                     : launch_diag_dim<2, K, T, false>(L, tab, dAs, dSloc, dMp, s, rho, sym);
 }
 
 }  // namespace smf
@@ -173,10 +178,10 @@ int launch_cell_diag_k(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dS
   namespace smf {                                                                                              \
   template int launch_cell_apply_k<KK, float>(const LevelDesc<float> &, const Tab1D<float> *, int,             \
                                                const float *, const float *, float *, float *, cudaStream_t,   \
-                                               int, const float *);                                                           \
+                                               int, const float *, const float *);                                                           \
   template int launch_cell_apply_k<KK, double>(const LevelDesc<double> &, const Tab1D<double> *, int,          \
                                                 const double *, const double *, double *, double *,            \
-                                                cudaStream_t, int, const double *);                                             \
+                                                cudaStream_t, int, const double *, const double *);                                             \
   template int launch_cell_apply_fused_k<KK, float>(const LevelDesc<float> &, int, const float *, const float *, \
                                                      float *, float *, cudaStream_t, int, const Fuse<float> &,       \
                                                      const float *);   \
@@ -190,7 +195,7 @@ int launch_cell_diag_k(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dS
   template int launch_col_geometry_k<KK, float>(const LevelDesc<float> &, float *, cudaStream_t);             \
   template int launch_col_geometry_k<KK, double>(const LevelDesc<double> &, double *, cudaStream_t);          \
   template int launch_cell_diag_k<KK, double>(const LevelDesc<double> &, const Tab1D<double> *, double *,      \
-                                               double *, double *, cudaStream_t);                              \
+                                               double *, double *, cudaStream_t, const double *, int);         \
   template int upload_col_tables<KK>(const Tab1D<double> &, cudaStream_t);                                     \
   template int launch_cell_grad_k<KK, double>(const LevelDesc<double> &, const Tab1D<double> *, const double *,  \
                                                const double *, double *, cudaStream_t);                        \

@@ -20,6 +20,7 @@ enum ApplyMode : int {
   kApplyMassAll = 16,  // yu += M_v Z u (its transpose: free nodes of u read, every row written)
   kApplyUnmasked = 32, // with A / BT / B: read u at constrained nodes too (K_full u_D for lifting)
   kApplyC = 64,        // yp -= C p (stabilisation block of K = [A B^T; B -C])
+  kApplySym = 128,     // with A: the symmetric-gradient form mu eps(u):eps(v) (generic kernel)
 };
 
 // 1D tables of one velocity degree k on the reference interval, (k+1) Gauss points.

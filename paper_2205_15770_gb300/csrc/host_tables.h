@@ -14,12 +14,13 @@ double tridiag_max_eig(const std::vector<double> &a, const std::vector<double> &
 
 template <typename T>
 int launch_cell_apply(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, const T *u, const T *p, T *yu, T *yp,
-                      cudaStream_t s, int shape, const T *geo = nullptr);
+                      cudaStream_t s, int shape, const T *geo = nullptr, const T *rho = nullptr);
 template <typename T>
-int launch_cell_diag(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dSloc, T *dMp, cudaStream_t s);
+int launch_cell_diag(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dSloc, T *dMp, cudaStream_t s,
+                     const T *rho, int sym);
 template <int K, typename T>
 int launch_cell_apply_k(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, const T *u, const T *p, T *yu, T *yp,
-                        cudaStream_t s, int shape, const T *geo);
+                        cudaStream_t s, int shape, const T *geo, const T *rho);
 template <typename T>
 int launch_cell_apply_fused(const LevelDesc<T> &L, int mode, const T *u, const T *p, T *yu, T *yp, cudaStream_t s,
                             int shape, const Fuse<T> &F, const T *geo);
@@ -36,5 +37,6 @@ int launch_cell_grad_k(const LevelDesc<T> &L, const Tab1D<T> *tab, const T *u, c
 template <int K>
 int upload_col_tables(const Tab1D<double> &t, cudaStream_t s);
 template <int K, typename T>
-int launch_cell_diag_k(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dSloc, T *dMp, cudaStream_t s);
+int launch_cell_diag_k(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dSloc, T *dMp, cudaStream_t s,
+                       const T *rho, int sym);
 }  // namespace smf

@@ -301,9 +301,10 @@ __global__ void k_zero_constrained(const LevelDesc<T> L, T *__restrict__ y) {
   }
 }
 
-// D_A over the full velocity vector from the scalar per-node diagonal; 1 on constrained DoFs.
+// D_A over the full velocity vector from the scalar per-node diagonal (per_comp: already one
+// value per velocity DoF, the symmetric form); 1 on constrained DoFs.
 template <typename T>
-__global__ void k_expand_diag(const LevelDesc<T> L, const T *__restrict__ dAs, T *__restrict__ DA) {
+__global__ void k_expand_diag(const LevelDesc<T> L, const T *__restrict__ dAs, T *__restrict__ DA, int per_comp) {
   pdl_enter();
   SMF_GRID_LOOP(i, L.n_u) {
     long long node = i % L.nv;
@@ -311,7 +312,7 @@ __global__ void k_expand_diag(const LevelDesc<T> L, const T *__restrict__ dAs, T
     long long r = node / L.N[0];
     int gy = (int)(r % L.N[1]);
     int gz = (int)(r / L.N[1]);
-    DA[i] = vel_constrained(L.N, L.faces, L.dim, gx, gy, gz) ? T(1) : dAs[node];
+    DA[i] = vel_constrained(L.N, L.faces, L.dim, gx, gy, gz) ? T(1) : dAs[per_comp ? i : node];
   }
 }
 
