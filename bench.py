@@ -609,6 +609,58 @@ def run_schur_sweep(args):
                 S.close()
 
 
+def run_variants(args):
+    """The next-steps rows on the 32^3 workload (same mesh, forcing and gamma = 1e2): FP32-MG FGMRES
+    solves to 1e-8 (ms per solve, iterations) and FP32 / FP64 vmult throughput for
+      laplacian:  the benchmark's form (reference line),
+      sym:        mu eps(u):eps(v) + gamma rho u.v with per-cell mu = exp(g1), rho = exp(g2 / 2)
+                  (g1, g2 seeded Gaussian fields, correlation length 0.2, sample std 1),
+      stabilised: C = 1e-2 M_p + 1e-1 sum_tau h_tau^2 K_p,tau."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2205_15770_gb300 import StokesMG
+    V = perturbed_vertices()
+    n = WL["n"][0]
+    mu = np.exp(W.gaussian_field_cells(n, seed=0)).reshape(-1)
+    rho = np.exp(0.5 * W.gaussian_field_cells(n, seed=1)).reshape(-1)
+    variants = {"laplacian": {}, "sym": dict(sym_grad=True, mu_cell=mu, rho_cell=rho),
+                "stabilised": dict(c_mass=1e-2, c_grad=1e-1)}
+    f = torch.as_tensor(forcing(), device="cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    for name, kw in variants.items():
+        S = StokesMG(dim=3, n=WL["n"], n_levels=WL["levels"], k=WL["k"], vertices=V, gamma_rho=1e2, kA=WL["kA"],
+                     kS=WL["kS"], m=WL["m"], **kw)
+        b = S.mass_rhs(f)
+        x = torch.zeros_like(b)
+        for _ in range(2):
+            S.solve(b, x.zero_(), rtol=WL["rtol"])
+        torch.cuda.synchronize()
+        e0, e1 = ev(), ev()
+        e0.record()
+        for _ in range(5):
+            _, its, rel = S.solve(b, x.zero_(), rtol=WL["rtol"])
+        e1.record()
+        e1.synchronize()
+        row = {"variant": name, "dofs": S.size(), "solve_ms": round(e0.elapsed_time(e1) / 5, 3), "iterations": its,
+               "final_rel_residual": rel, "fused_levels_fp32": S.fused_levels(32)}
+        for dt in (torch.float32, torch.float64):
+            xv = torch.randn(S.size(), dtype=dt, device="cuda")
+            yv = torch.empty_like(xv)
+            for _ in range(3):
+                S.vmult(xv, yv)
+            torch.cuda.synchronize()
+            reps = 20 if dt == torch.float32 else 5
+            e0.record()
+            for _ in range(reps):
+                S.vmult(xv, yv)
+            e1.record()
+            e1.synchronize()
+            row[f"vmult_{str(dt)[-7:]}_mdof_s"] = round(S.size() / (e0.elapsed_time(e1) / reps / 1e3) / 1e6, 1)
+        print(json.dumps(row), flush=True)
+        S.close()
+
+
 def run_channel(args):
     """Q_k-Q_{k-1} channel [0,4] x [0,1]^2 on 64^3 cells (aspect 4:1:1), parabolic inflow
     u = 16 y(1-y) z(1-z) on x = 0, no-slip walls, do-nothing outflow at x = 4, mu = 1e-3, 6 levels.
@@ -722,6 +774,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
+    ap.add_argument("--variants", action="store_true",
+                    help="32^3 workload in the symmetric-gradient form and with a stabilisation block: solve, vmult")
     ap.add_argument("--schur-sweep", action="store_true",
                     help="2D cavity 16^2: rates q for the Schur diagonals loc/p/d/exact, k = 0 and 3, m = 1..16")
     ap.add_argument("--profile-range", action="store_true",
@@ -749,6 +803,8 @@ def main():
         run_smoother_sweep(args)
     elif args.schur_sweep:
         run_schur_sweep(args)
+    elif args.variants:
+        run_variants(args)
     elif args.kernel_only:
         run_kernel_only(args)
     elif args.impl == "reference":

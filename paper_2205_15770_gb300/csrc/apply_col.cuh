@@ -618,9 +618,7 @@ __global__ void __launch_bounds__(32 * WARPS)
         T s = T(0);
 #pragma unroll
         for (int q = 0; q < NQ; ++q) s += CT::S(q * NV + iz) * s2[q];
-        const int gz = K * cz + iz;
-        if (valid && !vel_constrained(L.N, L.faces, 3, gx, gy, gz))
-          atomicAdd(&yu[c * L.nv + lattice_index<3, T>(L.N, gx, gy, gz)], s);
+        if (frs[iz]) atomicAdd(&yu[c * L.nv + col0 + iz * zstride], s);
       }
     }
   }
