@@ -80,7 +80,12 @@ typedef struct {
   double c_mass;        /* stabilisation block C of K = [A B^T; B -C] (Sec. 1 leaves C open; zero by
                            default): c(p,q) = c_mass int p q + c_grad sum_tau h_tau^2 int_tau
                            grad p . grad q, h_tau = |tau|^(1/d); both >= 0.  With c_mass > 0 the
-                           constant pressure is no longer in the kernel of K (no zero-mean fixing) */
+                           constant pressure is no longer in the kernel of K (no zero-mean fixing).
+                           Where the pressure space has at most 27 nodes per cell (k <= 3 in 3D, any k
+                           in 2D) setup stores C's packed symmetric element matrices on the device
+                           (k^d (k^d + 1) / 2 entries per cell: 36 for k = 2, 378 for k = 3 in
+                           3D; FP64 and FP32 copies); otherwise, and with the environment variable
+                           STOKES_C_MATRIX=none, C is evaluated on the fly */
   double c_grad;
   int sym_grad;         /* 1: a(u,v) = int mu eps(u):eps(v) + gamma rho u.v, the symmetric-gradient form of
                            Sec. 2 (eps(u) = (grad u + grad u^T)/2); 0: int mu grad u:grad v + gamma rho u.v */

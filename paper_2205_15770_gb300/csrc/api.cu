@@ -43,11 +43,19 @@ int launch_cell_apply(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, cons
 }
 template <typename T>
 int launch_cell_C(const LevelDesc<T> &L, const Tab1D<T> *tab, T cm, T cg, const T *p, T *yp, T sign, T *diag,
-                  cudaStream_t s) {
+                  const T *Ce, cudaStream_t s) {
   switch (L.k) {
-    case 2: return launch_cell_C_k<2, T>(L, tab, cm, cg, p, yp, sign, diag, s);
-    case 3: return launch_cell_C_k<3, T>(L, tab, cm, cg, p, yp, sign, diag, s);
-    default: return launch_cell_C_k<4, T>(L, tab, cm, cg, p, yp, sign, diag, s);
+    case 2: return launch_cell_C_k<2, T>(L, tab, cm, cg, p, yp, sign, diag, Ce, s);
+    case 3: return launch_cell_C_k<3, T>(L, tab, cm, cg, p, yp, sign, diag, Ce, s);
+    default: return launch_cell_C_k<4, T>(L, tab, cm, cg, p, yp, sign, diag, Ce, s);
+  }
+}
+int launch_cell_C_matrix(const LevelDesc<double> &L, const Tab1D<double> *tab, double cm, double cg, double *Ce,
+                         cudaStream_t s) {
+  switch (L.k) {
+    case 2: return launch_cell_C_matrix_k<2, double>(L, tab, cm, cg, Ce, s);
+    case 3: return launch_cell_C_matrix_k<3, double>(L, tab, cm, cg, Ce, s);
+    default: return launch_cell_C_matrix_k<4, double>(L, tab, cm, cg, Ce, s);
   }
 }
 template <typename T>
@@ -139,6 +147,7 @@ struct LevelRT {
   bool fuse = true;  // fused smoothing on this level (set by the setup's timing, when eligible)
   const T *geo = nullptr;  // FP64 3D trilinear: precomputed per-point geometry of the column kernel
   const T *rho = nullptr;  // per-cell density of the gamma rho mass term (null: rho = 1)
+  const T *Ce = nullptr;   // packed element matrices of the stabilisation block C (null: on the fly)
   T *DAinv = nullptr, *DSinv = nullptr;
   T *x = nullptr, *b = nullptr, *r = nullptr, *kx = nullptr;                   // full vectors
   T *tu = nullptr, *ru = nullptr, *uhat = nullptr, *cx = nullptr, *cd = nullptr, *ct = nullptr;  // velocity
@@ -324,7 +333,7 @@ struct Runner {
   int form(int mode) const { return (C->sym && (mode & kApplyA)) ? (mode | kApplySym) : mode; }
   void applyC(int l, const T *p, T *yp, T sign) {
     if (!hasC()) return;
-    launch_cell_C<T>(L[l].d, tab, (T)C->c_mass, (T)C->c_grad, p, yp, sign, (T *)nullptr, s);
+    launch_cell_C<T>(L[l].d, tab, (T)C->c_mass, (T)C->c_grad, p, yp, sign, (T *)nullptr, L[l].Ce, s);
     note();
   }
   void sub(const T *a, const T *b, T *out, long long n) { vec(k_sub<T>, n, a, b, out, n); }
@@ -1441,6 +1450,29 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
     if ((st = alloc_level_buffers(C, C->L32[l]))) return st;
   }
 
+  // element matrices of C where the pressure space is small (at most 27 nodes per cell: packed
+  // 378 entries per cell), built in FP64 and rounded for the FP32 levels; larger pressure spaces
+  // and STOKES_C_MATRIX=none keep C on the fly
+  {
+    const int npp = dim == 3 ? k * k * k : k * k;  // Q_{k-1}: k pressure nodes per direction
+    const char *cs = getenv("STOKES_C_MATRIX");
+    if ((C->c_mass != 0.0 || C->c_grad != 0.0) && npp <= kMaxCMatrixNodes && !(cs && std::strcmp(cs, "none") == 0)) {
+      for (int l = 0; l < nl; ++l) {
+        const LevelDesc<double> &d = C->L64[l].d;
+        const long long ne = d.n_cells * (long long)(npp * (npp + 1) / 2);
+        double *c64;
+        float *c32;
+        if ((st = dalloc(C, &c64, ne))) return st;
+        if ((st = dalloc(C, &c32, ne))) return st;
+        launch_cell_C_matrix(d, C->tab64, C->c_mass, C->c_grad, c64, C->s);
+        k_convert<double, float><<<vec_blocks(ne), kVecThreads, 0, C->s>>>(c64, c32, ne);
+        SMF_CUDA_OK(cudaGetLastError());
+        C->L64[l].Ce = c64;
+        C->L32[l].Ce = c32;
+      }
+    }
+  }
+
   // transfer matrices between consecutive levels
   for (int l = 1; l < nl; ++l) {
     if ((st = build_xfer(C, C->L64[l].d, C->L64[l - 1].d, tt64, C->L64[l].xf))) return st;
@@ -1513,7 +1545,7 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
       }
     }
     if (C->o.schur_diag != 3 && (C->c_mass != 0.0 || C->c_grad != 0.0)) {  // D_S~ += diag(C)
-      launch_cell_C<double>(d, C->tab64, C->c_mass, C->c_grad, nullptr, nullptr, 1.0, C->DS[l], C->s);
+      launch_cell_C<double>(d, C->tab64, C->c_mass, C->c_grad, nullptr, nullptr, 1.0, C->DS[l], nullptr, C->s);
       ++C->launches;
     }
     k_reciprocal<double><<<vec_blocks(d.n_p), kVecThreads, 0, C->s>>>(C->DS[l], R.DSinv, d.n_p);

@@ -87,26 +87,56 @@ int launch_cell_apply_k(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, co
 
 template <int DIM, int K, typename T, bool CART>
 static void launch_C_dim(const LevelDesc<T> &L, const Tab1D<T> *tab, T cm, T cg, const T *p, T *yp, T sign, T *diag,
-                         cudaStream_t s) {
+                         const T *Ce, cudaStream_t s) {
   const long long nb = (L.n_cells + 127) / 128;
-  launch_kernel(stokes_cell_apply_C<DIM, K, T, CART>, dim3((unsigned)(nb < 152 * 16 ? nb : 152 * 16)), dim3(128), 0, s,
-                L, tab, cm, cg, p, yp, sign, diag);
+  const dim3 grid((unsigned)(nb < 152 * 16 ? nb : 152 * 16));
+  if constexpr (CellShape<DIM, K>::NPP <= kMaxCMatrixNodes) {
+    if (Ce && !diag) {
+      launch_kernel(stokes_cell_apply_C_mat<DIM, K, T>, grid, dim3(128), 0, s, L, Ce, p, yp, sign);
+      return;
+    }
+  }
+  launch_kernel(stokes_cell_apply_C<DIM, K, T, CART>, grid, dim3(128), 0, s, L, tab, cm, cg, p, yp, sign, diag);
 }
 
-// Stabilisation block C: yp += sign * C p (diag == null) or diag += diag(C).
+// Stabilisation block C: yp += sign * C p (diag == null; from the element matrices Ce when not
+// null) or diag += diag(C).
 template <int K, typename T>
 int launch_cell_C_k(const LevelDesc<T> &L, const Tab1D<T> *tab, T cm, T cg, const T *p, T *yp, T sign, T *diag,
-                    cudaStream_t s) {
+                    const T *Ce, cudaStream_t s) {
   if (L.dim == 3) {
     if (L.cartesian)
-      launch_C_dim<3, K, T, true>(L, tab, cm, cg, p, yp, sign, diag, s);
+      launch_C_dim<3, K, T, true>(L, tab, cm, cg, p, yp, sign, diag, Ce, s);
     else
-      launch_C_dim<3, K, T, false>(L, tab, cm, cg, p, yp, sign, diag, s);
+      launch_C_dim<3, K, T, false>(L, tab, cm, cg, p, yp, sign, diag, Ce, s);
   } else {
     if (L.cartesian)
-      launch_C_dim<2, K, T, true>(L, tab, cm, cg, p, yp, sign, diag, s);
+      launch_C_dim<2, K, T, true>(L, tab, cm, cg, p, yp, sign, diag, Ce, s);
     else
-      launch_C_dim<2, K, T, false>(L, tab, cm, cg, p, yp, sign, diag, s);
+      launch_C_dim<2, K, T, false>(L, tab, cm, cg, p, yp, sign, diag, Ce, s);
+  }
+  return 0;
+}
+
+// Packed element matrices of C (stokes_cell_C_matrix): n_cells * NPP (NPP + 1) / 2 entries.
+template <int DIM, int K, typename T, bool CART>
+static void launch_C_matrix_dim(const LevelDesc<T> &L, const Tab1D<T> *tab, T cm, T cg, T *Ce, cudaStream_t s) {
+  if constexpr (CellShape<DIM, K>::NPP <= kMaxCMatrixNodes)
+    launch_kernel(stokes_cell_C_matrix<DIM, K, T, CART>,
+                  dim3(vec_blocks(L.n_cells * CellShape<DIM, K>::NPP)), dim3(kVecThreads), 0, s, L, tab, cm, cg, Ce);
+}
+template <int K, typename T>
+int launch_cell_C_matrix_k(const LevelDesc<T> &L, const Tab1D<T> *tab, T cm, T cg, T *Ce, cudaStream_t s) {
+  if (L.dim == 3) {
+    if (L.cartesian)
+      launch_C_matrix_dim<3, K, T, true>(L, tab, cm, cg, Ce, s);
+    else
+      launch_C_matrix_dim<3, K, T, false>(L, tab, cm, cg, Ce, s);
+  } else {
+    if (L.cartesian)
+      launch_C_matrix_dim<2, K, T, true>(L, tab, cm, cg, Ce, s);
+    else
+      launch_C_matrix_dim<2, K, T, false>(L, tab, cm, cg, Ce, s);
   }
   return 0;
 }
@@ -189,9 +219,13 @@ int launch_cell_diag_k(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dS
                                                       const double *, double *, double *, cudaStream_t, int,       \
                                                       const Fuse<double> &, const double *);                                      \
   template int launch_cell_C_k<KK, float>(const LevelDesc<float> &, const Tab1D<float> *, float, float,        \
-                                           const float *, float *, float, float *, cudaStream_t);            \
+                                           const float *, float *, float, float *, const float *,            \
+                                           cudaStream_t);                                                     \
   template int launch_cell_C_k<KK, double>(const LevelDesc<double> &, const Tab1D<double> *, double, double,   \
-                                            const double *, double *, double, double *, cudaStream_t);       \
+                                            const double *, double *, double, double *, const double *,      \
+                                            cudaStream_t);                                                    \
+  template int launch_cell_C_matrix_k<KK, double>(const LevelDesc<double> &, const Tab1D<double> *, double,     \
+                                                   double, double *, cudaStream_t);                           \
   template int launch_col_geometry_k<KK, float>(const LevelDesc<float> &, float *, cudaStream_t);             \
   template int launch_col_geometry_k<KK, double>(const LevelDesc<double> &, double *, cudaStream_t);          \
   template int launch_cell_diag_k<KK, double>(const LevelDesc<double> &, const Tab1D<double> *, double *,      \

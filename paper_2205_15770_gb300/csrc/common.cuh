@@ -10,6 +10,7 @@ namespace smf {
 
 constexpr int kMaxDeg = 4;            // highest velocity degree k supported
 constexpr int kMaxN1 = kMaxDeg + 1;   // nodes / Gauss points per direction
+constexpr int kMaxCMatrixNodes = 27;  // stored element matrices of C up to this many pressure nodes per cell
 
 // Operator block selection for the cell kernel (bit set).
 enum ApplyMode : int {

@@ -29,7 +29,9 @@ int launch_cell_apply_fused_k(const LevelDesc<T> &L, int mode, const T *u, const
                               int shape, const Fuse<T> &F, const T *geo);
 template <int K, typename T>
 int launch_cell_C_k(const LevelDesc<T> &L, const Tab1D<T> *tab, T cm, T cg, const T *p, T *yp, T sign, T *diag,
-                    cudaStream_t s);
+                    const T *Ce, cudaStream_t s);
+template <int K, typename T>
+int launch_cell_C_matrix_k(const LevelDesc<T> &L, const Tab1D<T> *tab, T cm, T cg, T *Ce, cudaStream_t s);
 template <int K, typename T>
 int launch_col_geometry_k(const LevelDesc<T> &L, T *geo, cudaStream_t s);
 template <int K, typename T>

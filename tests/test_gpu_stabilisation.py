@@ -30,8 +30,13 @@ def _mg(case, **kw):
 
 @pytest.mark.parametrize("name", ["2d_q2_ragged", "2d_q3_pert", "3d_q2_pert", "3d_q3_cart", "3d_q4_pert"])
 @pytest.mark.parametrize("stab", [dict(c_mass=0.3), dict(c_grad=2.0), STAB])
-def test_operator_with_stabilisation(name, stab):
+@pytest.mark.parametrize("storage", ["matrix", "none"])
+def test_operator_with_stabilisation(name, stab, storage, monkeypatch):
+    """C from the stored packed element matrices (pressure spaces up to 27 nodes per cell) and
+    evaluated on the fly (STOKES_C_MATRIX=none; always for Q3 pressure in 3D)."""
     from oracle.assemble import assemble
+    if storage == "none":
+        monkeypatch.setenv("STOKES_C_MATRIX", "none")
     case = CASES[name]
     lev = oracle_hierarchy(case).levels[-1]
     ops = assemble(lev, case.get("mu", 1.0), case.get("gamma_rho", 0.0), **stab)
