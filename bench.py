@@ -73,6 +73,20 @@ def flops_per_cell_A(k, trilinear, dim=3):
     return dim * per_comp + geo
 
 
+def flops_per_cell_full(k, dim=3):
+    """Algorithmic flops of one cell of the full operator K x (A u + B^T p, B u) when the per-point
+    geometry is a stored input (the FP64 column kernel reads it): the velocity block without the
+    geometry term of flops_per_cell_A, the pressure interpolation k^d -> (k+1)^d and its transpose
+    (3 sweeps each way), and per point and velocity component the B^T term p C_c (3 multiply-adds)
+    and the B term C_c . grad u_c (3 multiply-adds)."""
+    n1, npr = k + 1, k
+    sweeps = npr ** 3 * n1 + npr ** 2 * n1 ** 2 + npr * n1 ** 3
+    return flops_per_cell_A(k, False, dim) + 2 * 2 * sweeps + 2 * 2 * 3 * dim * n1 ** dim
+
+
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal at the 2070 MHz boost clock
+
+
 def tuning_string(S):
     """The setup's choices of a context as a STOKES_TUNING value (to profile the same configuration:
     timings taken under a profiler choose differently)."""
@@ -340,6 +354,10 @@ def run_ours(args):
     peak = fp32_peak_tflops(props.multi_processor_count, max_mhz)
     traffic = traffic_record(kernel_source_sha())
     avg64 = S.time_apply(1, precision=64, reps=10)
+    S.time_apply(7, precision=64, reps=3)
+    avg64_full = S.time_apply(7, precision=64, reps=20)
+    fl64 = flops_per_cell_full(WL["k"]) * n_cells
+    peak64 = FP64_NOMINAL_TFLOPS * max_mhz / 2070.0
 
     # --- batched multi-mesh solves (16 unit-cube meshes of uneven size, seeded) -----------------
     batched = run_batched(args) if not args.no_extras else None
@@ -378,12 +396,19 @@ def run_ours(args):
         "iterations_fp64_mg": it64, "fp32_vs_fp64_mg_solution_rel_diff": diff,
         "vmult_mdof_s": {k2: round(v, 1) for k2, v in vm.items()},
         "setup_s_per_context": round(setup_s, 3),
-        "roofline": {"bound": "alu", "kernel": "stokes_cell_apply<3,2,float,trilinear> (A block)",
+        "roofline": {"bound": "alu", "kernel": "stokes_cell_apply_col<2,float,A,trilinear> (A block, column kernel)",
                      "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
                      "frac": round(achieved / peak, 4), "traffic": traffic,
                      "avg_launch_us": round(avg_ms * 1e3, 2), "flops_per_launch": fl,
                      "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
                      "fp64_avg_launch_us": round(avg64 * 1e3, 2),
+                     "fp64_operator": {
+                         "bound": "alu",
+                         "kernel": "stokes_cell_apply_col<2,double,A+B^T+B,trilinear> (FGMRES operator, stored geometry)",
+                         "achieved": round(fl64 / (avg64_full / 1e3) / 1e12, 4), "peak": round(peak64, 3),
+                         "unit": "TFLOP/s", "frac": round(fl64 / (avg64_full / 1e3) / 1e12 / peak64, 4),
+                         "avg_launch_us": round(avg64_full * 1e3, 2), "flops_per_launch": fl64,
+                         "peak_source": f"nominal FP64 {FP64_NOMINAL_TFLOPS} TFLOP/s scaled to {max_mhz:.0f} MHz"},
                      "hbm_peak_gbs": (peaks or {}).get("hbm_gbs", FALLBACK_HBM_GBS),
                      "hbm_peak_source": peaks_src},
         "e2e": {"value": round(e2e_val, 3), "unit": "MDoF/s", "h2d_bytes_per_step": solves * N * 8,

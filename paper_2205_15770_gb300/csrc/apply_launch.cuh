@@ -3,6 +3,7 @@
 #include <cstdlib>
 #include "apply.cuh"
 #include "apply_col.cuh"
+#include "apply_c.cuh"
 #include "vec.cuh"
 #include "host_tables.h"
 
