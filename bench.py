@@ -710,13 +710,18 @@ def run_channel(args):
     from paper_2205_15770_gb300 import StokesMG
     peaks, src = measured_peaks()
     hbm = (peaks or {}).get("hbm_gbs", FALLBACK_HBM_GBS)
+    props = torch.cuda.get_device_properties(0)
+    p32 = fp32_peak_tflops(props.multi_processor_count, 2070.0)
     out = {"workload": "channel [0,4]x[0,1]^2, 64^3 hexes, mu 1e-3, inflow 16y(1-y)z(1-z), do-nothing outflow",
-           "hbm_peak_gbs": hbm, "hbm_peak_source": src, "k": {}}
-    for k in (2, 3, 4):
-        S = StokesMG(dim=3, n=(64, 64, 64), n_levels=6, k=k, mu=1e-3, hi=(4.0, 1.0, 1.0), dirichlet_faces=0x3D,
+           "hbm_peak_gbs": hbm, "hbm_peak_source": src, "fp32_peak_tflops": round(p32, 2),
+           "fp64_peak_tflops": FP64_NOMINAL_TFLOPS, "k": {}}
+    # k = 2, 3, 4 on 64^3 cells, and the Q2 size sweep's 128^3 point (53.1M DoFs, 7 levels)
+    for n, k in ((64, 2), (64, 3), (64, 4), (128, 2)):
+        nl = 6 if n == 64 else 7
+        S = StokesMG(dim=3, n=(n, n, n), n_levels=nl, k=k, mu=1e-3, hi=(4.0, 1.0, 1.0), dirichlet_faces=0x3D,
                      kA=WL["kA"], kS=WL["kS"], m=WL["m"])
         N = S.size()
-        row = {"dofs": N}
+        row = {"dofs": N, "cells": n ** 3}
         for prec, dt in ((32, torch.float32), (64, torch.float64)):
             x = torch.randn(N, dtype=dt, device="cuda")
             y = torch.empty_like(x)
@@ -733,9 +738,12 @@ def run_channel(args):
             ms = e0.elapsed_time(e1) / reps
             kern = S.time_apply(7, precision=prec, reps=reps)
             bytes_alg = 2 * N * (4 if prec == 32 else 8)
+            tflops = flops_per_cell_full(k) * n ** 3 / (kern / 1e3) / 1e12
             row[f"fp{prec}"] = {"vmult_ms": round(ms, 3), "mdof_s": round(N / (ms / 1e3) / 1e6, 1),
                                 "kernel_ms": round(kern, 3),
-                                "hbm_frac_of_kernel": round(bytes_alg / (kern / 1e3) / 1e9 / hbm, 4)}
+                                "hbm_frac_of_kernel": round(bytes_alg / (kern / 1e3) / 1e9 / hbm, 4),
+                                "tflops": round(tflops, 3),
+                                "alu_frac": round(tflops / (p32 if prec == 32 else FP64_NOMINAL_TFLOPS), 4)}
         if k == 3:
             nodes = S.velocity_nodes()
             nu, _ = S.sizes()
@@ -758,7 +766,10 @@ def run_channel(args):
             row["solve"] = {"ms": round(ms, 2), "iterations": its, "rel_residual": rel,
                             "mdof_s": round(N / (ms / 1e3) / 1e6, 2),
                             "max_u": float((xs[:nv] + uD[:nv]).max())}
-        out["k"][k] = row
+        if n == 64:
+            out["k"][k] = row
+        else:
+            out["q2_128cubed"] = row
         S.close()
         del S
         torch.cuda.empty_cache()
