@@ -83,6 +83,24 @@ def test_fused_cycle_matches_oracle(name, cycle):
 
 
 @pytest.mark.parametrize("name", ["3d_q2_pert", "3d_q2_channel"])
+def test_fused_cycle_with_the_benchmark_smoother(name):
+    """(k_A, k_S, m) = (1, 1, 2) with the Schur-complement diagonal d, the benchmark's smoother."""
+    case = CASES[name]
+    kw = dict(kA=1, kS=1, m=2, schur_diag="d")
+    H, mg = _oracle_mg(case, **kw)
+    lev = H.levels[-1]
+    S = gpu_solver(case, **kw)
+    b = random_full(lev, 18, constrained_zero=True)
+    x0 = random_full(lev, 19, constrained_zero=True)
+    for start in (np.zeros(lev.size), x0):
+        ref = mg.cycle(len(H.levels) - 1, start.copy(), b)
+        xg = S.vcycle(_t(b), _t(start))
+        assert rel_err(_n(xg), ref) < 1e-10
+        x32 = S.vcycle(_t(b, torch.float32), _t(start, torch.float32))
+        assert rel_err(_n(x32), ref) < 1e-3
+
+
+@pytest.mark.parametrize("name", ["3d_q2_pert", "3d_q2_channel"])
 def test_fused_and_unfused_paths_agree(monkeypatch, name):
     case = CASES[name]
     lev = oracle_hierarchy(case).levels[-1]
