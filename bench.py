@@ -176,9 +176,16 @@ def run_oracle_subprocess(steps=1, warmup=0):
 
 # ---------------------------------------------------------------------------------------------
 class ClockSampler:
+    """nvidia-smi clock / throttle sampling every 200 ms.  Started before the warm-up steps (so the
+    sampler's own start-up is not inside the timed region); mark() and stop() bracket the timed
+    region, and only the samples stamped inside it (widened by one period) are reported."""
+
     def __init__(self, gpu_index):
+        import datetime
+        self._dt = datetime
         self.path = tempfile.mktemp(suffix=".csv")
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        self.t0 = self.t1 = None
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
@@ -189,9 +196,14 @@ class ClockSampler:
         except Exception:
             self.p = None
 
+    def mark(self):
+        self.t0 = self._dt.datetime.now()
+
     def stop(self):
+        self.t1 = self._dt.datetime.now()
         if self.p is None:
             return None
+        time.sleep(0.25)  # let the sample that covers the end of the region land
         self.p.terminate()
         try:
             self.p.wait(timeout=5)
@@ -200,16 +212,23 @@ class ClockSampler:
         self.f.close()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        lo = (self.t0 or self.t1) - self._dt.timedelta(seconds=0.2)
+        hi = self.t1 + self._dt.timedelta(seconds=0.2)
+        rows = []
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
+                ts = self._dt.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+                rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
+        inside = [r for r in rows if lo <= r[0] <= hi] or rows[-2:]
+        for _, a, b, flags in inside:
+            sm.append(a)
+            mx.append(b)
+            for nm, v in zip(names, flags):
                 if v.lower() == "active":
                     reasons.add(nm)
         os.unlink(self.path)
@@ -229,14 +248,14 @@ def measured_peaks():
     return None, "fallback"
 
 
-def traffic_record(kernel_src_sha):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, or None
-    when the kernel source changed since the counters were taken."""
+def traffic_record(key, kernel_src_sha):
+    """DRAM bytes per launch of the kernel `key` ("fp32_a_block", "fp64_operator") from the
+    committed ncu summary, or None when the kernel source changed since the counters were taken."""
     p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
     if not os.path.exists(p):
         return None
     try:
-        rec = json.load(open(p))
+        rec = json.load(open(p)).get(key, {})
     except Exception:
         return None
     if rec.get("kernel_source_sha256") != kernel_src_sha:
@@ -291,16 +310,18 @@ def run_ours(args):
             its.append(it)
         return its
 
+    clocks = ClockSampler(local)
     for _ in range(args.warmup):
         step(S32, X)
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
+    clocks.mark()
     if args.profile_range:
         torch.cuda.profiler.start()
     l0 = sum(S.launch_count for S in S32)
     total_ms = 0.0
+    step_ms = []
     iters = None
     for _ in range(args.steps):
         flush.zero_()  # L2 flush (256 MB write) between timed steps, outside the events
@@ -309,7 +330,8 @@ def run_ours(args):
         iters = step(S32, X)
         e1.record()
         e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
+        step_ms.append(e0.elapsed_time(e1))
+        total_ms += step_ms[-1]
     torch.cuda.synchronize()
     launches = sum(S.launch_count for S in S32) - l0
     if args.profile_range:
@@ -358,7 +380,8 @@ def run_ours(args):
         e1.synchronize()
         vm[f"fp{prec}"] = N / (e0.elapsed_time(e1) / reps / 1e3) / 1e6
 
-    # --- roofline of the dominant kernel (velocity-block cell apply, FP32, finest level) --------
+    # --- rooflines: the FP64 full operator of the FGMRES loop (the largest launch-list share) and
+    # the FP32 A-block apply the V-cycle repeats, both on the finest level ----------------------
     S = S32[1]
     S.time_apply(1, precision=32, reps=20)
     avg_ms = S.time_apply(1, precision=32, reps=200)
@@ -368,7 +391,9 @@ def run_ours(args):
     props = torch.cuda.get_device_properties(local)
     max_mhz = clk["sm_max_mhz"] if clk else 2070.0
     peak = fp32_peak_tflops(props.multi_processor_count, max_mhz)
-    traffic = traffic_record(kernel_source_sha())
+    sha = kernel_source_sha()
+    traffic = traffic_record("fp32_a_block", sha)
+    traffic64 = traffic_record("fp64_operator", sha)
     avg64 = S.time_apply(1, precision=64, reps=10)
     S.time_apply(7, precision=64, reps=3)
     avg64_full = S.time_apply(7, precision=64, reps=20)
@@ -398,6 +423,10 @@ def run_ours(args):
     e2e_val = replica_throughput(e2e_s * 1e3, world, solves, N)
 
     peaks, peaks_src = measured_peaks()
+    hbm_peak = (peaks or {}).get("hbm_gbs", FALLBACK_HBM_GBS)
+    # FP64 operator bytes: x read, y written, and the stored per-point geometry (16 values per
+    # Gauss point) read once
+    bytes64 = 2 * N * 8 + n_cells * 16 * (WL["k"] + 1) ** 3 * 8
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "MDoF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True, "scaling": "weak",
@@ -405,6 +434,7 @@ def run_ours(args):
         "config": {"workload": WORKLOAD_NAME, "dofs_per_solve": N, "solves_per_step": solves,
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "flushed by a 256 MB write before every timed step"},
+        "step_ms": [round(t, 3) for t in step_ms],
         "iterations_fp32_mg": iters, "final_rel_residual": rels,
         "solve_ms": {"fp32_mg_per_solve": round(ms_per_step / solves, 3), "fp64_mg_per_solve": round(ms64 / solves, 3)},
         "solve_s_per_mdof": {"fp32_mg": ms_per_step / solves / 1e3 / (N / 1e6),
@@ -412,21 +442,22 @@ def run_ours(args):
         "iterations_fp64_mg": it64, "fp32_vs_fp64_mg_solution_rel_diff": diff,
         "vmult_mdof_s": {k2: round(v, 1) for k2, v in vm.items()},
         "setup_s_per_context": round(setup_s, 3),
-        "roofline": {"bound": "alu", "kernel": "stokes_cell_apply_col<2,float,A,trilinear> (A block, column kernel)",
-                     "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-                     "frac": round(achieved / peak, 4), "traffic": traffic,
-                     "avg_launch_us": round(avg_ms * 1e3, 2), "flops_per_launch": fl,
-                     "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz",
-                     "fp64_avg_launch_us": round(avg64 * 1e3, 2),
-                     "fp64_operator": {
-                         "bound": "alu",
-                         "kernel": "stokes_cell_apply_col<2,double,A+B^T+B,trilinear> (FGMRES operator, stored geometry)",
-                         "achieved": round(fl64 / (avg64_full / 1e3) / 1e12, 4), "peak": round(peak64, 3),
-                         "unit": "TFLOP/s", "frac": round(fl64 / (avg64_full / 1e3) / 1e12 / peak64, 4),
-                         "avg_launch_us": round(avg64_full * 1e3, 2), "flops_per_launch": fl64,
-                         "peak_source": f"nominal FP64 {FP64_NOMINAL_TFLOPS} TFLOP/s scaled to {max_mhz:.0f} MHz"},
-                     "hbm_peak_gbs": (peaks or {}).get("hbm_gbs", FALLBACK_HBM_GBS),
-                     "hbm_peak_source": peaks_src},
+        "roofline": {"bound": "alu",
+                     "kernel": "stokes_cell_apply_col<2,double,A+B^T+B,trilinear> (FGMRES operator, stored geometry)",
+                     "achieved": round(fl64 / (avg64_full / 1e3) / 1e12, 4), "peak": round(peak64, 3),
+                     "unit": "TFLOP/s", "frac": round(fl64 / (avg64_full / 1e3) / 1e12 / peak64, 4),
+                     "traffic": traffic64, "avg_launch_us": round(avg64_full * 1e3, 2), "flops_per_launch": fl64,
+                     "algorithmic_bytes_per_launch": bytes64,
+                     "peak_source": f"nominal FP64 {FP64_NOMINAL_TFLOPS} TFLOP/s (GB300) scaled to {max_mhz:.0f} MHz",
+                     "hbm_frac": round(bytes64 / (avg64_full / 1e3) / 1e9 / hbm_peak, 4),
+                     "fp32_a_block": {
+                         "bound": "alu", "kernel": "stokes_cell_apply_col<2,float,A,trilinear> (A block, V-cycle)",
+                         "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "avg_launch_us": round(avg_ms * 1e3, 2), "flops_per_launch": fl,
+                         "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz"},
+                     "fp64_a_block_avg_launch_us": round(avg64 * 1e3, 2),
+                     "hbm_peak_gbs": hbm_peak, "hbm_peak_source": peaks_src},
         "e2e": {"value": round(e2e_val, 3), "unit": "MDoF/s", "h2d_bytes_per_step": solves * N * 8,
                 "d2h_bytes_per_step": solves * N * 8},
         "gpu_launches": int(launches),
@@ -514,7 +545,8 @@ def run_adjoint():
     mu = np.exp(W.gaussian_field_cells(n, seed=0)).reshape(-1)
     mu_obs = np.exp(W.gaussian_field_cells(n, seed=1)).reshape(-1)
     f = torch.as_tensor(W.fourier_forcing(3, 2, (n,) * 3, seed=0).reshape(-1), device="cuda")
-    S = StokesMG(dim=3, n=(n,) * 3, n_levels=5, k=2, vcycle_fp32=False)
+    S = StokesMG(dim=3, n=(n,) * 3, n_levels=5, k=2, vcycle_fp32=False, kA=WL["kA"], kS=WL["kS"], m=WL["m"],
+                 schur_diag=WL["schur_diag"])
     u_obs = stokes_solve_fn(S, torch.as_tensor(mu_obs, device="cuda"), f, 1e-10).detach()
     nu = S.sizes()[0]
     S.set_viscosity(mu)
@@ -780,20 +812,23 @@ def run_channel(args):
 
 
 def run_kernel_only(args):
-    """Set up one FP32 context of the workload (gamma = 1e2) and launch the dominant kernel (A-block
-    cell apply, FP32, finest level) a few times inside a cudaProfilerStart/Stop range; for ncu."""
+    """Set up one context of the workload (gamma = 1e2) and launch one cell kernel of the finest
+    level a few times inside a cudaProfilerStart/Stop range, for ncu: the FP32 A-block apply
+    (--kernel-precision 32) or the FP64 full operator of the FGMRES loop (64)."""
     import torch
     from paper_2205_15770_gb300 import StokesMG
     torch.cuda.set_device(0)
     S = StokesMG(dim=3, n=WL["n"], n_levels=WL["levels"], k=WL["k"], vertices=perturbed_vertices(), gamma_rho=1e2,
                  kA=WL["kA"], kS=WL["kS"], m=WL["m"], schur_diag=WL["schur_diag"])
-    S.time_apply(1, precision=32, reps=3)
+    prec = args.kernel_precision
+    mode = 1 if prec == 32 else 7
+    S.time_apply(mode, precision=prec, reps=3)
     torch.cuda.synchronize()
     torch.cuda.profiler.start()
-    ms = S.time_apply(1, precision=32, reps=3)
+    ms = S.time_apply(mode, precision=prec, reps=3)
     torch.cuda.profiler.stop()
-    print(json.dumps({"kernel": "stokes_cell_apply A-block fp32", "avg_launch_us": ms * 1e3,
-                      "cells": WL["n"][0] * WL["n"][1] * WL["n"][2]}))
+    print(json.dumps({"kernel": "stokes_cell_apply_col " + ("A block fp32" if prec == 32 else "full operator fp64"),
+                      "avg_launch_us": ms * 1e3, "cells": WL["n"][0] * WL["n"][1] * WL["n"][2]}))
     S.close()
 
 
@@ -839,6 +874,8 @@ def main():
                     help="the paper's (k_A, k_S, m) rate study on the lid-driven cavities (stationary FP64 MG)")
     ap.add_argument("--smoother-sweep", action="store_true",
                     help="time-to-1e-8 of the workload for a list of (k_A, k_S, m); prints one JSON line each")
+    ap.add_argument("--kernel-precision", type=int, choices=(32, 64), default=32,
+                    help="with --kernel-only: the FP32 A block (32) or the FP64 full operator (64)")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only launch the dominant kernel inside a profiler range (for ncu --set full)")
     ap.add_argument("--_oracle-sample", nargs=2, type=int, default=None, dest="oracle_sample")
