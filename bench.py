@@ -183,7 +183,8 @@ class ClockSampler:
     def __init__(self, gpu_index):
         import datetime
         self._dt = datetime
-        self.path = tempfile.mktemp(suffix=".csv")
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
         self.t0 = self.t1 = None
         q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -202,6 +203,11 @@ class ClockSampler:
     def stop(self):
         self.t1 = self._dt.datetime.now()
         if self.p is None:
+            try:
+                self.f.close()
+                os.unlink(self.path)
+            except Exception:
+                pass
             return None
         time.sleep(0.25)  # let the sample that covers the end of the region land
         self.p.terminate()
@@ -210,32 +216,43 @@ class ClockSampler:
         except Exception:
             self.p.kill()
         self.f.close()
-        sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        lo = (self.t0 or self.t1) - self._dt.timedelta(seconds=0.2)
-        hi = self.t1 + self._dt.timedelta(seconds=0.2)
-        rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 10:
-                continue
-            try:
-                ts = self._dt.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
-                rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
-            except ValueError:
-                continue
-        inside = [r for r in rows if lo <= r[0] <= hi] or rows[-2:]
-        for _, a, b, flags in inside:
-            sm.append(a)
-            mx.append(b)
-            for nm, v in zip(names, flags):
-                if v.lower() == "active":
-                    reasons.add(nm)
+        with open(self.path) as fh:
+            out = parse_clock_samples(fh.read().splitlines(), self.t0 or self.t1, self.t1)
         os.unlink(self.path)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return out
+
+
+def parse_clock_samples(lines, t0, t1):
+    """Clock summary of the nvidia-smi CSV lines (timestamp, index, clocks.sm, clocks.max.sm,
+    power.draw, reasons.active, hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown,
+    sw_power_cap) stamped within [t0 - 0.2 s, t1 + 0.2 s] (the last two samples when none is):
+    median SM clock, max clock, the throttle reasons seen active, the number of samples."""
+    import datetime
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    lo = t0 - datetime.timedelta(seconds=0.2)
+    hi = t1 + datetime.timedelta(seconds=0.2)
+    rows = []
+    for line in lines:
+        parts = [p.strip() for p in line.split(",")]
+        if len(parts) < 10:
+            continue
+        try:
+            ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f")
+            rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
+        except ValueError:
+            continue
+    inside = [r for r in rows if lo <= r[0] <= hi] or rows[-2:]
+    sm, mx, reasons = [], [], set()
+    for _, a, b, flags in inside:
+        sm.append(a)
+        mx.append(b)
+        for nm, v in zip(names, flags):
+            if v.lower() == "active":
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+            "samples": len(sm)}
 
 
 def measured_peaks():

@@ -71,3 +71,24 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
         steps, warmup = 1, 0
     bench.run_reference(A())
     assert called == []
+
+
+def test_clock_samples_inside_the_timed_region():
+    """Only samples stamped within the timed region (widened by one 200 ms period) count; a
+    throttle reason seen there is reported, one outside it is not."""
+    import datetime
+    import bench
+    t0 = datetime.datetime(2026, 1, 1, 12, 0, 0)
+    t1 = t0 + datetime.timedelta(seconds=1)
+
+    def line(dt, mhz, thermal):
+        ts = (t0 + datetime.timedelta(seconds=dt)).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return f"{ts}, 0, {mhz}, 2070, 800.0, 0x0, Not Active, Not Active, {thermal}, Not Active"
+
+    lines = [line(-2.0, 1500, "Active"), line(0.1, 2070, "Not Active"), line(0.5, 2050, "Not Active"),
+             line(1.1, 2060, "Not Active"), line(3.0, 1400, "Active"), "garbage"]
+    out = bench.parse_clock_samples(lines, t0, t1)
+    assert out == {"sm_mhz": 2060.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 3}
+    lines.insert(2, line(0.3, 2000, "Active"))
+    assert bench.parse_clock_samples(lines, t0, t1)["reasons"] == ["sw_thermal_slowdown"]
+    assert bench.parse_clock_samples([], t0, t1) is None
