@@ -752,6 +752,43 @@ def run_variants(args):
         S.close()
 
 
+def run_mesh_sweep(args):
+    """Mesh independence of the benchmark's solver: the same perturbed unit-cube workload (0.1 h
+    perturbation of each mesh, seed 0, Q2-Q1, coarsest mesh 2^3) on n = 8..128 cells per direction,
+    FP32-MG FGMRES to 1e-8 for gamma = 0 and 1e2: iterations and solve time per n."""
+    import torch
+    import workloads as W
+    from paper_2205_15770_gb300 import StokesMG
+    for n in (8, 16, 32, 64, 128):
+        nl = n.bit_length() - 1  # n = 2^(nl) -> levels down to 2^3
+        V = W.perturbed_vertices(3, (n, n, n), seed=WL["seed"], amplitude=WL["amplitude"])
+        f = torch.as_tensor(W.fourier_forcing(3, WL["k"], (n, n, n), seed=WL["seed"]).reshape(-1), device="cuda")
+        row = {"n": n, "levels": nl, "iterations": [], "solve_ms": []}
+        for g in (0.0, 1e2):
+            S = StokesMG(dim=3, n=(n, n, n), n_levels=nl, k=WL["k"], vertices=V, gamma_rho=g, kA=WL["kA"],
+                         kS=WL["kS"], m=WL["m"], schur_diag=WL["schur_diag"], restart=WL["restart"])
+            row["dofs"] = S.size()
+            b = S.mass_rhs(f)
+            x = torch.zeros_like(b)
+            S.solve(b, x, rtol=WL["rtol"])
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 3
+            e0.record()
+            for _ in range(reps):
+                x.zero_()
+                _, its, rel = S.solve(b, x, rtol=WL["rtol"])
+            e1.record()
+            e1.synchronize()
+            row["iterations"].append(its)
+            row["solve_ms"].append(round(e0.elapsed_time(e1) / reps, 3))
+            S.close()
+            del S
+            torch.cuda.empty_cache()
+        row["mdof_s"] = round(row["dofs"] / (min(row["solve_ms"]) / 1e3) / 1e6, 2)
+        print(json.dumps(row), flush=True)
+
+
 def run_channel(args):
     """Q_k-Q_{k-1} channel [0,4] x [0,1]^2 on 64^3 cells (aspect 4:1:1), parabolic inflow
     u = 16 y(1-y) z(1-z) on x = 0, no-slip walls, do-nothing outflow at x = 4, mu = 1e-3, 6 levels.
@@ -879,6 +916,8 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and adjoint measurements")
+    ap.add_argument("--mesh-sweep", action="store_true",
+                    help="the workload on 8^3..128^3 cells: FGMRES iterations and solve time per mesh size")
     ap.add_argument("--variants", action="store_true",
                     help="32^3 workload in the symmetric-gradient form and with a stabilisation block: solve, vmult")
     ap.add_argument("--schur-sweep", action="store_true",
@@ -912,6 +951,8 @@ def main():
         run_schur_sweep(args)
     elif args.variants:
         run_variants(args)
+    elif args.mesh_sweep:
+        run_mesh_sweep(args)
     elif args.kernel_only:
         run_kernel_only(args)
     elif args.impl == "reference":
