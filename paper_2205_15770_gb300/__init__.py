@@ -17,7 +17,7 @@ import numpy as np
 
 from . import _lib as L
 
-__all__ = ["StokesMG", "StokesBatch", "StokesError", "ALL_FACES", "stokes_solve_fn"]
+__all__ = ["StokesMG", "StokesBatch", "StokesError", "ALL_FACES", "stokes_solve_fn", "fma_peak"]
 
 ALL_FACES = {2: 0xF, 3: 0x3F}
 BLOCK_A, BLOCK_BT, BLOCK_B = 1, 2, 4
@@ -43,6 +43,17 @@ def _ptr(t, dtype):
     if not t.is_contiguous():
         raise ValueError("tensor must be contiguous")
     return C.c_void_p(t.data_ptr())
+
+
+def fma_peak(precision=32):
+    """Measured FMA throughput of the current device in TFLOP/s (stokes_fma_peak)."""
+    torch = _torch()
+    lib = L.load()
+    out = C.c_double()
+    st = lib.stokes_fma_peak(int(precision), C.byref(out), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != 0:
+        raise StokesError(st, lib.stokes_global_last_error().decode())
+    return out.value
 
 
 class StokesMG:

@@ -54,6 +54,7 @@ SIGNATURES = {
     "stokes_mg_iterate": (C.c_int, [P, P, P, C.c_int, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_double),
                                     C.POINTER(C.c_double), P]),
     "stokes_time_apply": (C.c_int, [P, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), P]),
+    "stokes_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double), P]),
     "stokes_get_launch_shape": (C.c_int, [P, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "stokes_get_smoother_fusion": (C.c_int, [P, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "stokes_setup_batch": (C.c_int, [C.c_int, C.POINTER(StokesMesh), C.POINTER(C.c_int), C.POINTER(C.c_double),

@@ -160,6 +160,27 @@ struct GraphSlot {
   long long kernels = 0;
 };
 
+// FMA throughput probe: 8 independent multiply-add chains per thread (x <- x m + c, contracting
+// towards c / (1 - m)), `iters` x 16 rounds; the result is stored only if it equals -1, which the
+// compiler cannot rule out, so no chain is removed.
+template <typename T>
+__global__ void k_fma_peak(T *out, int iters, T seed) {
+  T a[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) a[j] = seed + T(threadIdx.x + j) * T(1e-7);
+  const T m = T(0.999999), c = T(1e-7);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) a[j] = fma(a[j], m, c);
+  }
+  T sum = T(0);
+#pragma unroll
+  for (int j = 0; j < 8; ++j) sum += a[j];
+  if (sum == T(-1)) out[(long long)blockIdx.x * blockDim.x + threadIdx.x] = sum;
+}
+
 }  // namespace smf
 
 using namespace smf;
@@ -2513,6 +2534,44 @@ int stokes_mg_iterate(stokes_ctx *C, const double *b, double *x, int max_iter, d
     for (size_t i = 0; i < res.size(); ++i) res_history[i] = res[i];
   if (rate) *rate = it >= 3 ? std::pow(res[it] / res[it - 3], 1.0 / 3.0) : std::nan("");
   return finish(C, res.back() <= reduction * res[0] ? STOKES_OK : STOKES_ENOTCONV);
+}
+
+int stokes_fma_peak(int precision, double *tflops, void *stream) {
+  if ((precision != 32 && precision != 64) || !tflops) {
+    set_error("invalid stokes_fma_peak arguments");
+    return STOKES_EINVAL;
+  }
+  int dev = 0, sms = 0;
+  SMF_CUDA_OK(cudaGetDevice(&dev));
+  SMF_CUDA_OK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int threads = 256, blocks = sms * 8;
+  const int iters = precision == 32 ? 4000 : 100;  // about 5-10 ms per launch on GB300
+  void *out = nullptr;
+  SMF_CUDA_OK(cudaMalloc(&out, (size_t)blocks * threads * 8));
+  cudaEvent_t e0, e1;
+  SMF_CUDA_OK(cudaEventCreate(&e0));
+  SMF_CUDA_OK(cudaEventCreate(&e1));
+  auto launch = [&]() {
+    if (precision == 32)
+      k_fma_peak<float><<<blocks, threads, 0, s>>>((float *)out, iters, 1.0f);
+    else
+      k_fma_peak<double><<<blocks, threads, 0, s>>>((double *)out, iters, 1.0);
+  };
+  launch();  // warm-up
+  const int reps = 5;
+  SMF_CUDA_OK(cudaEventRecord(e0, s));
+  for (int r = 0; r < reps; ++r) launch();
+  SMF_CUDA_OK(cudaEventRecord(e1, s));
+  SMF_CUDA_OK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  SMF_CUDA_OK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  const double fmas = (double)blocks * threads * iters * 16.0 * 8.0 * reps;
+  *tflops = 2.0 * fmas / (ms * 1e-3) / 1e12;
+  return STOKES_OK;
 }
 
 int stokes_time_apply(stokes_ctx *C, int level, int precision, int blocks, int reps, double *avg_ms, void *stream) {
