@@ -1431,7 +1431,11 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
         const char *gs = getenv("STOKES_GEO");
         const bool g64 = !(gs && std::strcmp(gs, "none") == 0);
         const long long per = 16LL * (k + 1) * (k + 1) * (k + 1), cells = d.n_cells;
-        if (g64 && cells * per * (long long)sizeof(double) <= (4LL << 30)) {
+        // stored when it takes at most a quarter of the device memory still free (7.2 GB for a
+        // trilinear 128^3 level; HBM-resident rather than recomputed in FP64)
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
+        if (g64 && cells * per * (long long)sizeof(double) <= (long long)(free_b / 4)) {
           if ((st = dalloc(C, &geo_l, cells * per))) return st;
           launch_col_geometry<double>(d, geo_l, C->s);
           SMF_CUDA_OK(cudaGetLastError());
