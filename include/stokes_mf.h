@@ -261,7 +261,10 @@ void stokes_destroy_batch(stokes_batch *batch);
 /* Launch shape of the 3D cell kernel that setup's autotuner chose for `level` and `precision`:
  * 1 or 4 = column kernel with that many warps per CTA, 3 = column kernel with the three velocity
  * components on the three warps of a CTA (shorter per-warp chain for small levels), -1 =
- * point-per-thread kernel, 0 = not tuned (2D, or STOKES_NO_AUTOTUNE=1).  The environment variable
+ * point-per-thread kernel, 5 = cell-component kernel (one thread per cell and velocity component,
+ * the component's whole tensor in registers; 3D Cartesian levels with k = 2, 3 and FP32 trilinear
+ * levels with k = 2, the Laplacian form with a constant rho; other applications on such a level run
+ * in the 4-warp column kernel), 0 = not tuned (2D, or STOKES_NO_AUTOTUNE=1).  The environment variable
  * STOKES_TUNING="s32=..;s64=..;f32=..;f64=.." (comma lists, one value per level, coarsest first)
  * replaces the setup's timings of shapes and smoother forms, e.g. to profile the configuration a
  * plain run chose (a profiler changes the timings); malformed values make setup fail with

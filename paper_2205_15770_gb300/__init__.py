@@ -335,7 +335,7 @@ class StokesMG:
 
     def launch_shapes(self, precision=32):
         """Autotuned 3D cell-kernel launch shape per level (1 / 4 warps per CTA, 3 = components split over
-        3 warps, -1 = point kernel)."""
+        3 warps, -1 = point kernel, 5 = cell-component kernel)."""
         out = []
         for l in range(self.n_levels):
             v = C.c_int()
@@ -354,7 +354,7 @@ class StokesMG:
 
     def set_launch_shape(self, level, shape, precision=32):
         """Override the autotuned launch shape (1 or 4 warps per CTA column kernel, 3 component split,
-        -1 point kernel)."""
+        -1 point kernel, 5 cell-component kernel)."""
         self._check(self._lib.stokes_set_launch_shape(self._ctx, level, precision, shape))
 
     @property

@@ -19,7 +19,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libstokes_mf.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
-SOURCES = ["api.cu", "kernels_misc.cu", "apply_k2.cu", "apply_k3.cu", "apply_k4.cu", "host_tables.cpp"]
+SOURCES = ["api.cu", "kernels_misc.cu", "apply_k2.cu", "apply_k3.cu", "apply_k4.cu", "apply_cc_k2.cu", "apply_cc_k3.cu",
+           "host_tables.cpp"]
 
 
 def nvcc_path():

@@ -35,6 +35,16 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
 template <typename T>
 int launch_cell_apply(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, const T *u, const T *p, T *yu, T *yp,
                       cudaStream_t s, int shape, const T *geo, const T *rho) {
+  if (shape == 5) {
+    // cell-component kernel (Laplacian form, constant rho); the column kernel serves the rest
+    const bool generic_a = (mode & kApplyA) && ((mode & kApplySym) || rho);
+    if (!generic_a) {
+      const int r = L.k == 2 ? launch_cell_apply_cc_k<2, T>(L, mode, u, p, yu, yp, s)
+                             : (L.k == 3 ? launch_cell_apply_cc_k<3, T>(L, mode, u, p, yu, yp, s) : -1);
+      if (r == 0) return 0;
+    }
+    shape = 4;
+  }
   switch (L.k) {
     case 2: return launch_cell_apply_k<2, T>(L, tab, mode, u, p, yu, yp, s, shape, geo, rho);
     case 3: return launch_cell_apply_k<3, T>(L, tab, mode, u, p, yu, yp, s, shape, geo, rho);
@@ -143,6 +153,7 @@ template <typename T>
 struct LevelRT {
   LevelDesc<T> d{};
   int shape = 0;  // 3D cell-kernel launch shape chosen by the autotuner (see launch_cell_apply_k)
+  int fshape = 4;  // column-kernel shape of the fused smoother's launches (1, 3 or 4)
   XferTabs<T> xf{};  // 1D transfer matrices between this level and the next coarser one
   bool fuse = true;  // fused smoothing on this level (set by the setup's timing, when eligible)
   const T *geo = nullptr;  // FP64 3D trilinear: precomputed per-point geometry of the column kernel
@@ -479,7 +490,8 @@ struct Runner {
     return b[j];
   }
   void fapply(int l, int mode, const T *u, const T *p, T *yu, T *yp, const Fuse<T> &F) {
-    launch_cell_apply_fused<T>(L[l].d, mode, u, p, yu, yp, s, L[l].shape, F, L[l].geo);
+    const int sh = L[l].shape == 5 ? L[l].fshape : L[l].shape;
+    launch_cell_apply_fused<T>(L[l].d, mode, u, p, yu, yp, s, sh, F, L[l].geo);
     note();
   }
   // Velocity Chebyshev with k_A = 1 from zero on r: x_1 = c0 D^-1 r, t = A x_1,
@@ -1113,21 +1125,24 @@ static int time_graph(stokes_ctx *C, cudaGraphExec_t ex, cudaEvent_t e0, cudaEve
 
 // Autotuner of the 3D cell-kernel launch shape, per level and precision: the velocity-block
 // apply is timed (graph replays, CUDA events on the context stream) for the column kernel with
-// 1 and 4 warps per CTA, the column kernel with the velocity components split over 3 warps, and
-// the point-per-thread kernel.  Candidates are interleaved over several rounds and each keeps
-// its best round, so clock ramps and one-off effects do not bias the choice; the default shape
-// (4 warps) is kept unless another is faster by more than 3 %.
+// 1 and 4 warps per CTA, the column kernel with the velocity components split over 3 warps, the
+// point-per-thread kernel and, where it serves the level, the cell-component kernel (shape 5).
+// Candidates are interleaved over several rounds and each keeps its best round, so clock ramps
+// and one-off effects do not bias the choice; the default shape (4 warps) is kept unless another
+// is faster by more than 3 %.  The fastest column shape is also kept apart (fshape): the fused
+// smoother's launches run in the column kernel.
 template <typename T>
 static int autotune_level(stokes_ctx *C, LevelRT<T> &R, const Tab1D<T> *tab) {
   if (R.d.dim != 3) return STOKES_OK;
-  constexpr int NC = 4;
-  const int cands[NC] = {4, 1, 3, -1};
+  const bool cc = cc_level_supported(R.d.dim, R.d.k, R.d.cartesian, sizeof(T)) && !C->sym && !R.rho;
+  const int NC = cc ? 5 : 4;
+  const int cands[5] = {4, 1, 3, -1, 5};
   const int reps = sizeof(T) == 8 ? 3 : 20, rounds = 3;
   cudaEvent_t e0, e1;
   SMF_CUDA_OK(cudaEventCreate(&e0));
   SMF_CUDA_OK(cudaEventCreate(&e1));
-  cudaGraphExec_t ex[NC] = {};
-  float best[NC] = {1e30f, 1e30f, 1e30f, 1e30f};
+  cudaGraphExec_t ex[5] = {};
+  float best[5] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
   int st = STOKES_OK;
   for (int ci = 0; ci < NC && st == STOKES_OK; ++ci) {
     R.shape = cands[ci];
@@ -1156,6 +1171,10 @@ static int autotune_level(stokes_ctx *C, LevelRT<T> &R, const Tab1D<T> *tab) {
   for (int ci = 1; ci < NC; ++ci)
     if (best[ci] < 0.97f * best[choice]) choice = ci;
   R.shape = cands[choice];
+  int fc = 0;  // column shapes only: 4, 1, 3
+  for (int ci = 1; ci < 3; ++ci)
+    if (best[ci] < 0.97f * best[fc]) fc = ci;
+  R.fshape = cands[fc];
   SMF_CUDA_OK(cudaMemsetAsync(R.r, 0, (R.d.n_u + R.d.n_p) * sizeof(T), C->s));
   return STOKES_OK;
 }
@@ -1203,7 +1222,7 @@ static int autotune_fusion(stokes_ctx *C, int l) {
 }
 
 // STOKES_TUNING="s32=a,b,..;s64=..;f32=..;f64=.." replaces the setup's timings: launch shapes
-// (1, 3, 4 or -1) and smoother forms (1 fused, 0 unfused) per level, coarsest first, for FP32 and
+// (1, 3, 4, -1 or 5) and smoother forms (1 fused, 0 unfused) per level, coarsest first, for FP32 and
 // FP64.  Timings taken under a profiler differ from plain runs; a profile of the configuration
 // that a plain run chose passes that run's choices here (stokes_get_launch_shape and
 // stokes_get_smoother_fusion read them).
@@ -1221,7 +1240,7 @@ static int parse_tuning(const char *spec, int nl, std::vector<int> tune[4]) {
       char *end = nullptr;
       const long v = std::strtol(p, &end, 10);
       if (end == p) break;
-      const bool ok = t < 2 ? (v == 1 || v == 3 || v == 4 || v == -1) : (v == 0 || v == 1);
+      const bool ok = t < 2 ? (v == 1 || v == 3 || v == 4 || v == -1 || v == 5) : (v == 0 || v == 1);
       if (!ok) {
         set_error(std::string("STOKES_TUNING: invalid value in ") + keys[t]);
         return STOKES_EINVAL;
@@ -1329,6 +1348,8 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
     const int e = k == 2 ? upload_col_tables<2>(t64, C->s) : (k == 3 ? upload_col_tables<3>(t64, C->s)
                                                                      : upload_col_tables<4>(t64, C->s));
     if (e) SMF_CUDA_OK((cudaError_t)e);
+    const int e2 = k == 2 ? upload_cc_tables<2>(t64, C->s) : (k == 3 ? upload_cc_tables<3>(t64, C->s) : 0);
+    if (e2) SMF_CUDA_OK((cudaError_t)e2);
   }
 
   // level hierarchy (host copies of geometry and viscosity, coarse from fine)
@@ -2735,8 +2756,8 @@ int stokes_get_smoother_fusion(stokes_ctx *C, int level, int precision, int *fus
 
 int stokes_set_launch_shape(stokes_ctx *C, int level, int precision, int shape) {
   if (!C || level < 0 || level >= C->nl || (precision != 32 && precision != 64) ||
-      !(shape == 1 || shape == 3 || shape == 4 || shape == -1)) {
-    set_error("invalid stokes_set_launch_shape arguments (shape in {1,3,4,-1})");
+      !(shape == 1 || shape == 3 || shape == 4 || shape == -1 || shape == 5)) {
+    set_error("invalid stokes_set_launch_shape arguments (shape in {1,3,4,-1,5})");
     if (C) C->err = g_last_error;
     return STOKES_EINVAL;
   }

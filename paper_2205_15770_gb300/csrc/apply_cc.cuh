@@ -1,0 +1,645 @@
+// 3D cell kernel, "cell-component" layout (launch shape 5): one thread per (cell, velocity
+// component).  Same operator as stokes_cell_apply_col and stokes_cell_apply (paper Sec. 3.1:
+// K x = sum_tau P_tau K_tau P_tau^T x with the element action by sum factorisation; Sec. 2
+// bilinear forms a(u,v) = mu grad u : grad v + gamma rho u.v and b(v,q) = -q div v), mapped so
+// that a thread holds the whole (k+1)^3 tensor of its velocity component in registers: every 1D
+// contraction is a register loop against uniform tables and no value crosses lanes (the column
+// kernel moves x / y contractions through warp shuffles, which bound its issue rate).
+//   * 10 cells per warp, lane = c * 10 + s (velocity component c, cell s of the warp's group);
+//     lanes 30 and 31 idle.
+//   * Trilinear cells (FP32, k = 2): the three threads of a cell evaluate the cell-map geometry
+//     of one plane of Gauss points each (qz = c) and share it through shared memory
+//     (G = mu w adj(J) adj(J)^T / det J, gamma rho w det J, and the columns of w adj(J)), so each
+//     point's geometry is computed once per cell; the point operation reads it back as float4.
+//   * Cartesian cells (FP32 and FP64, k = 2, 3): the element matrices are Kronecker products of
+//     the 1D stiffness, mass and mixed matrices (exact for the (k+1)-point Gauss rule used
+//     everywhere else), so the A block is 7 sweeps of 1D matrices over the nodal values and
+//     B, B^T are 3 sweeps each; no quadrature-point arrays, no shared memory.
+//   * Scatter by atomicAdd at the gather's indices; constrained DoFs read as 0 and not written.
+#pragma once
+#include "apply.cuh"
+#include "host_tables.h"
+#include "vec.cuh"
+
+namespace smf {
+
+constexpr int kCcCells = 10;  // cells per warp of the cell-component kernel
+
+// 1D tables of this translation unit's degree for the cell-component kernel.
+template <typename T>
+struct CCTab {
+  T S[kMaxN1 * kMaxN1];    // S[q*NV+m]  = l_m(x_q)   velocity basis at the Gauss points
+  T D[kMaxN1 * kMaxN1];    // D[q*NQ+m]  = g_m'(x_q)  collocation derivative at the Gauss points
+  T P[kMaxN1 * kMaxDeg];   // P[q*NPR+a] = psi_a(x_q) pressure basis at the Gauss points
+  T W[kMaxN1];             // Gauss weights on [0,1]
+  T X[kMaxN1];             // Gauss points on [0,1]
+  T Kh[kMaxN1 * kMaxN1];   // Kh[i*NV+j] = int_0^1 l_i' l_j'
+  T Mh[kMaxN1 * kMaxN1];   // Mh[i*NV+j] = int_0^1 l_i l_j
+  T Gh[kMaxDeg * kMaxN1];  // Gh[a*NV+j] = int_0^1 psi_a l_j'
+  T Nh[kMaxDeg * kMaxN1];  // Nh[a*NV+j] = int_0^1 psi_a l_j
+};
+static __constant__ CCTab<float> c_ccf;
+static __constant__ CCTab<double> c_ccd;
+template <typename T>
+__device__ __forceinline__ const CCTab<T> &cct();
+template <>
+__device__ __forceinline__ const CCTab<float> &cct<float>() {
+  return c_ccf;
+}
+template <>
+__device__ __forceinline__ const CCTab<double> &cct<double>() {
+  return c_ccd;
+}
+
+template <int K>
+cudaError_t cc_prefer_shared();
+
+// Fills this translation unit's tables from the FP64 1D tables (the integrals by the same
+// (k+1)-point Gauss rule, exact for these polynomial degrees).
+template <int K>
+int upload_cc_tables(const Tab1D<double> &t, cudaStream_t s) {
+  constexpr int NQ = K + 1, NV = K + 1, NPR = K;
+  CCTab<double> h{};
+  for (int q = 0; q < NQ; ++q) {
+    for (int m = 0; m < NV; ++m) h.S[q * NV + m] = t.S[q * NV + m];
+    for (int m = 0; m < NQ; ++m) h.D[q * NQ + m] = t.D[q * NQ + m];
+    for (int a = 0; a < NPR; ++a) h.P[q * NPR + a] = t.Pv[q * NPR + a];
+    h.W[q] = t.w[q];
+    h.X[q] = t.x[q];
+  }
+  for (int i = 0; i < NV; ++i)
+    for (int j = 0; j < NV; ++j) {
+      double kk = 0, mm = 0;
+      for (int q = 0; q < NQ; ++q) {
+        kk += t.w[q] * t.Sd[q * NV + i] * t.Sd[q * NV + j];
+        mm += t.w[q] * t.S[q * NV + i] * t.S[q * NV + j];
+      }
+      h.Kh[i * NV + j] = kk;
+      h.Mh[i * NV + j] = mm;
+    }
+  for (int a = 0; a < NPR; ++a)
+    for (int j = 0; j < NV; ++j) {
+      double gg = 0, nn = 0;
+      for (int q = 0; q < NQ; ++q) {
+        gg += t.w[q] * t.Pv[q * NPR + a] * t.Sd[q * NV + j];
+        nn += t.w[q] * t.Pv[q * NPR + a] * t.S[q * NV + j];
+      }
+      h.Gh[a * NV + j] = gg;
+      h.Nh[a * NV + j] = nn;
+    }
+  CCTab<float> f{};
+  {
+    const double *src = reinterpret_cast<const double *>(&h);
+    float *dst = reinterpret_cast<float *>(&f);
+    for (size_t i = 0; i < sizeof(h) / sizeof(double); ++i) dst[i] = (float)src[i];
+  }
+  cudaError_t e = cc_prefer_shared<K>();
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_ccd, &h, sizeof(h), 0, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyToSymbolAsync(c_ccf, &f, sizeof(f), 0, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return e == cudaSuccess ? 0 : (int)e;
+}
+
+// 1D contractions of a register tensor a[z][y][x] along x (0), y (1) or z (2):
+//   out[.. i ..] = sum_j M(i, j) in[.. j ..]
+template <int NI, int NO, int E1, int E2, typename T, typename F>
+__device__ __forceinline__ void cc_sweep0(const T (&in)[E2][E1][NI], T (&out)[E2][E1][NO], F M) {
+#pragma unroll
+  for (int z = 0; z < E2; ++z)
+#pragma unroll
+    for (int y = 0; y < E1; ++y)
+#pragma unroll
+      for (int i = 0; i < NO; ++i) {
+        T s = M(i, 0) * in[z][y][0];
+#pragma unroll
+        for (int j = 1; j < NI; ++j) s += M(i, j) * in[z][y][j];
+        out[z][y][i] = s;
+      }
+}
+template <int NI, int NO, int E0, int E2, typename T, typename F>
+__device__ __forceinline__ void cc_sweep1(const T (&in)[E2][NI][E0], T (&out)[E2][NO][E0], F M) {
+#pragma unroll
+  for (int z = 0; z < E2; ++z)
+#pragma unroll
+    for (int x = 0; x < E0; ++x)
+#pragma unroll
+      for (int i = 0; i < NO; ++i) {
+        T s = M(i, 0) * in[z][0][x];
+#pragma unroll
+        for (int j = 1; j < NI; ++j) s += M(i, j) * in[z][j][x];
+        out[z][i][x] = s;
+      }
+}
+template <int NI, int NO, int E0, int E1, typename T, typename F>
+__device__ __forceinline__ void cc_sweep2(const T (&in)[NI][E1][E0], T (&out)[NO][E1][E0], F M) {
+#pragma unroll
+  for (int y = 0; y < E1; ++y)
+#pragma unroll
+    for (int x = 0; x < E0; ++x)
+#pragma unroll
+      for (int i = 0; i < NO; ++i) {
+        T s = M(i, 0) * in[0][y][x];
+#pragma unroll
+        for (int j = 1; j < NI; ++j) s += M(i, j) * in[j][y][x];
+        out[i][y][x] = s;
+      }
+}
+
+// Shared-memory geometry record of one Gauss point of one cell (trilinear, FP32): NF float4,
+// [0] = (G00, G01, G02, G11), [1] = (G12, G22, gamma rho w det, 0) with G = mu w adj adj^T / det,
+// [2 + j] = column j of w adj(J) (present when a B block is applied).
+template <int MODE>
+struct CcGeo {
+  static constexpr int NF = (MODE & (kApplyB | kApplyBT)) ? 5 : 2;
+};
+
+#ifndef SMF_CC_SLICE_UNROLL
+#define SMF_CC_SLICE_UNROLL 1
+#endif
+#ifndef SMF_CC_TARGET_WARPS
+#define SMF_CC_TARGET_WARPS 16
+#endif
+template <int K, typename T, int MODE, bool CART>
+struct CcLaunch {
+  static constexpr int NQ = K + 1;
+  static constexpr int WARPS = (!CART && (MODE & (kApplyB | kApplyBT))) ? 2 : 4;
+  static constexpr size_t SMEM =
+      CART ? 0 : (size_t)WARPS * NQ * NQ * NQ * CcGeo<MODE>::NF * kCcCells * sizeof(float4);
+  // resident warps per SM the register allocation is held to (FP32; FP64 keeps its registers)
+  static constexpr int MINB = (sizeof(T) == 4 && K == 2) ? (SMF_CC_TARGET_WARPS + WARPS - 1) / WARPS : 1;
+};
+
+template <int K, typename T, int MODE, bool CART>
+__global__ void __launch_bounds__(32 * CcLaunch<K, T, MODE, CART>::WARPS, CcLaunch<K, T, MODE, CART>::MINB)
+    stokes_cell_apply_cc(const LevelDesc<T> L, const T *__restrict__ u, const T *__restrict__ p,
+                         T *__restrict__ yu, T *__restrict__ yp) {
+  pdl_enter();
+  constexpr int NV = K + 1, NQ = K + 1, NPR = K, CPW = kCcCells;
+  constexpr int WARPS = CcLaunch<K, T, MODE, CART>::WARPS;
+  constexpr bool DO_A = MODE & kApplyA, DO_BT = MODE & kApplyBT, DO_B = MODE & kApplyB;
+  constexpr bool NEED_U = DO_A || DO_B;
+  static_assert(CART || (K == 2 && sizeof(T) == 4), "trilinear cell-component kernel: FP32, k = 2");
+  const CCTab<T> &tb = cct<T>();
+
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool pad = lane >= 3 * CPW;
+  const int c = pad ? 0 : lane / CPW;
+  const int s = pad ? 0 : lane - c * CPW;
+  const long long cell_raw = ((long long)blockIdx.x * WARPS + warp) * CPW + s;
+  const bool valid = !pad && cell_raw < L.n_cells;
+  const long long cell = valid ? cell_raw : 0;
+  const int cx = (int)(cell % L.n[0]);
+  const long long rr = cell / L.n[0];
+  const int cy = (int)(rr % L.n[1]), cz = (int)(rr / L.n[1]);
+  const int gx0 = K * cx, gy0 = K * cy, gz0 = K * cz;
+
+  // free (unconstrained) velocity nodes per direction; invalid lanes have none
+  bool fx[NV], fy[NV], fz[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    fx[i] = valid && !((L.faces & 1u) && gx0 + i == 0) && !((L.faces & 2u) && gx0 + i == L.N[0] - 1);
+    fy[i] = !((L.faces & 4u) && gy0 + i == 0) && !((L.faces & 8u) && gy0 + i == L.N[1] - 1);
+    fz[i] = !((L.faces & 16u) && gz0 + i == 0) && !((L.faces & 32u) && gz0 + i == L.N[2] - 1);
+  }
+  const long long N0 = L.N[0], N01 = (long long)L.N[0] * L.N[1];
+  const long long vbase = c * L.nv + ((long long)gz0 * L.N[1] + gy0) * N0 + gx0;
+  // A warp whose cells all lie inside (every node free; idle lanes do not count) gathers and
+  // scatters without per-node predicates.
+  bool interior = true;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) interior = interior && fx[i] && fy[i] && fz[i];
+  const bool fast = __all_sync(0xffffffffu, interior || pad);
+
+  // ---- gathers --------------------------------------------------------------------------------
+  T uv[NV][NV][NV];
+  const T *ub = u + vbase;
+  if (NEED_U && !CART) {
+    if (fast) {
+#pragma unroll
+      for (int iz = 0; iz < NV; ++iz)
+#pragma unroll
+        for (int iy = 0; iy < NV; ++iy)
+#pragma unroll
+          for (int ix = 0; ix < NV; ++ix) uv[iz][iy][ix] = ub[iz * N01 + iy * N0 + ix];
+    } else {
+#pragma unroll
+      for (int iz = 0; iz < NV; ++iz)
+#pragma unroll
+        for (int iy = 0; iy < NV; ++iy)
+#pragma unroll
+          for (int ix = 0; ix < NV; ++ix)
+            uv[iz][iy][ix] = (fx[ix] && fy[iy] && fz[iz]) ? ub[iz * N01 + iy * N0 + ix] : T(0);
+    }
+  }
+  T pv[NPR][NPR][NPR];
+  const long long P0 = L.Pn[0], P01 = (long long)L.Pn[0] * L.Pn[1];
+  const long long pbase = ((long long)((K - 1) * cz) * L.Pn[1] + (K - 1) * cy) * P0 + (K - 1) * cx;
+  if (DO_BT && !CART) {
+#pragma unroll
+    for (int a3 = 0; a3 < NPR; ++a3)
+#pragma unroll
+      for (int a2 = 0; a2 < NPR; ++a2)
+#pragma unroll
+        for (int a1 = 0; a1 < NPR; ++a1) pv[a3][a2][a1] = valid ? p[pbase + a3 * P01 + a2 * P0 + a1] : T(0);
+  }
+  const T mu = L.mu_cell ? L.mu_cell[cell] : L.mu;
+
+  T yv[NV][NV][NV];   // velocity test-function sums (nodal) of this component
+  T qn[NPR][NPR][NPR];  // pressure test-function sums of this component's B u_c
+  if constexpr (CART) {
+    // Kronecker form, one x-slice (all (z, y) nodes at x-node i) at a time so that only the
+    // output tensor, a slice and its transforms are live:
+    //   A u_c = ax Kh x Mh x Mh + ay Mh x Kh x Mh + az Mh x Mh x Kh + be Mh x Mh x Mh  (x, y, z)
+    //   B u_c = (Bx x By x Bz) u_c,  B^T p = (Bx x By x Bz)^T p
+    // with ax = mu h_y h_z / h_x (and cyclic), be = gamma rho h_x h_y h_z; the 1D factors of B are
+    // Gh along the component's own direction and Nh along the others, scaled by -prod_{d != c} h_d.
+    const T h0 = L.h[0], h1 = L.h[1], h2 = L.h[2];
+    const T bsc = -(c == 0 ? h1 * h2 : (c == 1 ? h0 * h2 : h0 * h1));
+    T Bx[NPR][NV], By[NPR][NV], Bz[NPR][NV];  // lane-dependent (component c); Bz carries bsc
+    if (DO_B || DO_BT) {
+#pragma unroll
+      for (int a = 0; a < NPR; ++a)
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+          const T g = tb.Gh[a * NV + j], n = tb.Nh[a * NV + j];
+          Bx[a][j] = c == 0 ? g : n;
+          By[a][j] = c == 1 ? g : n;
+          Bz[a][j] = bsc * (c == 2 ? g : n);
+        }
+    }
+    const T ax = mu * h1 * h2 / h0, ay = mu * h0 * h2 / h1, az = mu * h0 * h1 / h2;
+    const T be = L.gamma_rho * h0 * h1 * h2;
+    if (DO_A || DO_BT) {
+#pragma unroll
+      for (int z = 0; z < NV; ++z)
+#pragma unroll
+        for (int y = 0; y < NV; ++y)
+#pragma unroll
+          for (int x = 0; x < NV; ++x) yv[z][y][x] = T(0);
+    }
+    if (DO_B) {
+#pragma unroll
+      for (int a3 = 0; a3 < NPR; ++a3)
+#pragma unroll
+        for (int a2 = 0; a2 < NPR; ++a2)
+#pragma unroll
+          for (int a1 = 0; a1 < NPR; ++a1) qn[a3][a2][a1] = T(0);
+    }
+    if (NEED_U) {
+      // FP64 and k = 3: the slice loop stays rolled (registers for the output tensor first)
+      constexpr int SLICE_UNROLL = (K == 2 && sizeof(T) == 4) ? NV : SMF_CC_SLICE_UNROLL;
+      unsigned fxm = 0;
+#pragma unroll
+      for (int i = 0; i < NV; ++i) fxm |= fx[i] ? (1u << i) : 0u;
+#pragma unroll SLICE_UNROLL
+      for (int i = 0; i < NV; ++i) {
+        T sl[NV][NV];  // [z][y] at x-node i
+        const bool fxi = (fxm >> i) & 1u;
+#pragma unroll
+        for (int z = 0; z < NV; ++z)
+#pragma unroll
+          for (int y = 0; y < NV; ++y)
+            sl[z][y] = (fast || (fxi && fy[y] && fz[z])) ? ub[z * N01 + y * N0 + i] : T(0);
+        if (DO_B) {
+          T t1[NV][NPR];
+#pragma unroll
+          for (int z = 0; z < NV; ++z)
+#pragma unroll
+            for (int b = 0; b < NPR; ++b) {
+              T acc = By[b][0] * sl[z][0];
+#pragma unroll
+              for (int y = 1; y < NV; ++y) acc += By[b][y] * sl[z][y];
+              t1[z][b] = acc;
+            }
+#pragma unroll
+          for (int a3 = 0; a3 < NPR; ++a3)
+#pragma unroll
+            for (int b = 0; b < NPR; ++b) {
+              T q = Bz[a3][0] * t1[0][b];
+#pragma unroll
+              for (int z = 1; z < NV; ++z) q += Bz[a3][z] * t1[z][b];
+#pragma unroll
+              for (int a = 0; a < NPR; ++a) qn[a3][b][a] += Bx[a][i] * q;
+            }
+        }
+        if (DO_A) {
+          T a1[NV][NV], a2[NV][NV];  // [z][y']: Mh and Kh along y
+#pragma unroll
+          for (int z = 0; z < NV; ++z)
+#pragma unroll
+            for (int yo = 0; yo < NV; ++yo) {
+              T m = tb.Mh[yo * NV] * sl[z][0], k = tb.Kh[yo * NV] * sl[z][0];
+#pragma unroll
+              for (int y = 1; y < NV; ++y) {
+                m += tb.Mh[yo * NV + y] * sl[z][y];
+                k += tb.Kh[yo * NV + y] * sl[z][y];
+              }
+              a1[z][yo] = m;
+              a2[z][yo] = k;
+            }
+#pragma unroll
+          for (int zo = 0; zo < NV; ++zo)
+#pragma unroll
+            for (int y = 0; y < NV; ++y) {
+              T v = tb.Mh[zo * NV] * a1[0][y], t2 = tb.Mh[zo * NV] * a2[0][y], t3 = tb.Kh[zo * NV] * a1[0][y];
+#pragma unroll
+              for (int z = 1; z < NV; ++z) {
+                v += tb.Mh[zo * NV + z] * a1[z][y];
+                t2 += tb.Mh[zo * NV + z] * a2[z][y];
+                t3 += tb.Kh[zo * NV + z] * a1[z][y];
+              }
+              const T w = ay * t2 + az * t3 + be * v;
+              const T av = ax * v;
+#pragma unroll
+              for (int j = 0; j < NV; ++j) yv[zo][y][j] += tb.Kh[j * NV + i] * av + tb.Mh[j * NV + i] * w;
+            }
+        }
+      }
+    }
+    if (DO_BT) {  // yv += (Bx x By x Bz)^T p, one pressure x-slice at a time
+#pragma unroll
+      for (int a = 0; a < NPR; ++a) {
+        T ps[NPR][NPR];  // [c3][b] at pressure x-node a
+#pragma unroll
+        for (int c3 = 0; c3 < NPR; ++c3)
+#pragma unroll
+          for (int b = 0; b < NPR; ++b) ps[c3][b] = valid ? p[pbase + c3 * P01 + b * P0 + a] : T(0);
+        T t[NPR][NV];  // [c3][y]
+#pragma unroll
+        for (int c3 = 0; c3 < NPR; ++c3)
+#pragma unroll
+          for (int y = 0; y < NV; ++y) {
+            T acc = By[0][y] * ps[c3][0];
+#pragma unroll
+            for (int b = 1; b < NPR; ++b) acc += By[b][y] * ps[c3][b];
+            t[c3][y] = acc;
+          }
+#pragma unroll
+        for (int z = 0; z < NV; ++z)
+#pragma unroll
+          for (int y = 0; y < NV; ++y) {
+            T r = Bz[0][z] * t[0][y];
+#pragma unroll
+            for (int c3 = 1; c3 < NPR; ++c3) r += Bz[c3][z] * t[c3][y];
+#pragma unroll
+            for (int j = 0; j < NV; ++j) yv[z][y][j] += Bx[a][j] * r;
+          }
+      }
+    }
+  } else {
+    // ---- trilinear geometry: plane qz = c of this cell, shared through shared memory ----------
+    constexpr int NF = CcGeo<MODE>::NF;
+    extern __shared__ float4 cc_geo_smem[];
+    float4 *gs = cc_geo_smem + (size_t)warp * (NQ * NQ * NQ * NF * CPW);
+    {
+      T X[8][3];
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        const long long gv =
+            ((long long)(cz + ((v >> 2) & 1)) * (L.n[1] + 1) + (cy + ((v >> 1) & 1))) * (L.n[0] + 1) + (cx + (v & 1));
+#pragma unroll
+        for (int a = 0; a < 3; ++a) X[v][a] = L.vert[gv * 3 + a];
+      }
+      // edge vectors: ex[y][z] along x, ey[x][z] along y, ez[x][y] along z (vertex v = x + 2y + 4z)
+      const T zeta = tb.X[c], wz = tb.W[c];
+      T ce[2][3], cf[2][3], ez[2][2][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+#pragma unroll
+        for (int y = 0; y < 2; ++y) {
+          const T e0 = X[1 + 2 * y][a] - X[2 * y][a], e1 = X[5 + 2 * y][a] - X[4 + 2 * y][a];
+          ce[y][a] = e0 + zeta * (e1 - e0);
+        }
+#pragma unroll
+        for (int x = 0; x < 2; ++x) {
+          const T f0 = X[x + 2][a] - X[x][a], f1 = X[x + 6][a] - X[x + 4][a];
+          cf[x][a] = f0 + zeta * (f1 - f0);
+        }
+#pragma unroll
+        for (int x = 0; x < 2; ++x)
+#pragma unroll
+          for (int y = 0; y < 2; ++y) ez[x][y][a] = X[x + 2 * y + 4][a] - X[x + 2 * y][a];
+      }
+      const T grho = L.gamma_rho;
+#pragma unroll
+      for (int qy = 0; qy < NQ; ++qy) {
+        const T eta = tb.X[qy];
+        T c0[3], gl[2][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          c0[a] = ce[0][a] + eta * (ce[1][a] - ce[0][a]);
+#pragma unroll
+          for (int x = 0; x < 2; ++x) gl[x][a] = ez[x][0][a] + eta * (ez[x][1][a] - ez[x][0][a]);
+        }
+#pragma unroll
+        for (int qx = 0; qx < NQ; ++qx) {
+          const T xi = tb.X[qx];
+          T c1[3], c2[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            c1[a] = cf[0][a] + xi * (cf[1][a] - cf[0][a]);
+            c2[a] = gl[0][a] + xi * (gl[1][a] - gl[0][a]);
+          }
+          // rows of adj(J) for J = [c0 c1 c2]: c1 x c2, c2 x c0, c0 x c1
+          T r[3][3];
+          r[0][0] = c1[1] * c2[2] - c1[2] * c2[1];
+          r[0][1] = c1[2] * c2[0] - c1[0] * c2[2];
+          r[0][2] = c1[0] * c2[1] - c1[1] * c2[0];
+          r[1][0] = c2[1] * c0[2] - c2[2] * c0[1];
+          r[1][1] = c2[2] * c0[0] - c2[0] * c0[2];
+          r[1][2] = c2[0] * c0[1] - c2[1] * c0[0];
+          r[2][0] = c0[1] * c1[2] - c0[2] * c1[1];
+          r[2][1] = c0[2] * c1[0] - c0[0] * c1[2];
+          r[2][2] = c0[0] * c1[1] - c0[1] * c1[0];
+          const T det = c0[0] * r[0][0] + c0[1] * r[0][1] + c0[2] * r[0][2];
+          const T w = tb.W[qx] * tb.W[qy] * wz;
+          const T wd = __fdividef(mu * w, det);
+          auto dot = [&](int i, int j) { return r[i][0] * r[j][0] + r[i][1] * r[j][1] + r[i][2] * r[j][2]; };
+          const int pt = (c * NQ + qy) * NQ + qx;
+          if (!pad) {
+            float4 *g = gs + (size_t)pt * NF * CPW + s;
+            g[0] = make_float4(wd * dot(0, 0), wd * dot(0, 1), wd * dot(0, 2), wd * dot(1, 1));
+            g[CPW] = make_float4(wd * dot(1, 2), wd * dot(2, 2), grho * w * det, 0.f);
+            if (NF > 2) {
+#pragma unroll
+              for (int j = 0; j < 3; ++j) g[(2 + j) * CPW] = make_float4(w * r[0][j], w * r[1][j], w * r[2][j], 0.f);
+            }
+          }
+        }
+      }
+    }
+    __syncwarp();
+
+    // ---- this component at the Gauss points --------------------------------------------------
+    auto Sf = [&](int i, int j) { return tb.S[i * NV + j]; };
+    auto St = [&](int i, int j) { return tb.S[j * NV + i]; };
+    auto Pf = [&](int i, int j) { return tb.P[i * NPR + j]; };
+    auto Pt = [&](int i, int j) { return tb.P[j * NPR + i]; };
+    T uq[NQ][NQ][NQ];
+    if (NEED_U) {
+      T t1[NV][NV][NQ], t2[NV][NQ][NQ];
+      cc_sweep0<NV, NQ, NV, NV>(uv, t1, Sf);
+      cc_sweep1<NV, NQ, NQ, NV>(t1, t2, Sf);
+      cc_sweep2<NV, NQ, NQ, NQ>(t2, uq, Sf);
+    }
+    T pq[NQ][NQ][NQ];
+    if (DO_BT) {
+      T t1[NPR][NPR][NQ], t2[NPR][NQ][NQ];
+      cc_sweep0<NPR, NQ, NPR, NPR>(pv, t1, Pf);
+      cc_sweep1<NPR, NQ, NQ, NPR>(t1, t2, Pf);
+      cc_sweep2<NPR, NQ, NQ, NQ>(t2, pq, Pf);
+    }
+    T tq[NQ][NQ][NQ], qacc[NQ][NQ][NQ];
+#pragma unroll
+    for (int qz = 0; qz < NQ; ++qz)
+#pragma unroll
+      for (int qy = 0; qy < NQ; ++qy)
+#pragma unroll
+        for (int qx = 0; qx < NQ; ++qx) tq[qz][qy][qx] = T(0);
+#pragma unroll
+    for (int qz = 0; qz < NQ; ++qz)
+#pragma unroll
+      for (int qy = 0; qy < NQ; ++qy)
+#pragma unroll
+        for (int qx = 0; qx < NQ; ++qx) {
+          const int pt = (qz * NQ + qy) * NQ + qx;
+          const float4 *g = gs + (size_t)pt * NF * CPW + s;
+          T gx = T(0), gy = T(0), gz = T(0);
+          if (NEED_U) {
+#pragma unroll
+            for (int m = 0; m < NQ; ++m) {
+              gx += tb.D[qx * NQ + m] * uq[qz][qy][m];
+              gy += tb.D[qy * NQ + m] * uq[qz][m][qx];
+              gz += tb.D[qz * NQ + m] * uq[m][qy][qx];
+            }
+          }
+          T f0 = T(0), f1 = T(0), f2 = T(0);
+          if (DO_A) {
+            const float4 g0 = g[0], g1 = g[CPW];
+            f0 = g0.x * gx + g0.y * gy + g0.z * gz;
+            f1 = g0.y * gx + g0.w * gy + g1.x * gz;
+            f2 = g0.z * gx + g1.x * gy + g1.y * gz;
+            tq[qz][qy][qx] += g1.z * uq[qz][qy][qx];
+          }
+          if (DO_B || DO_BT) {
+            const float4 cc = g[(2 + c) * CPW];
+            if (DO_BT) {
+              f0 -= pq[qz][qy][qx] * cc.x;
+              f1 -= pq[qz][qy][qx] * cc.y;
+              f2 -= pq[qz][qy][qx] * cc.z;
+            }
+            if (DO_B) qacc[qz][qy][qx] = -(cc.x * gx + cc.y * gy + cc.z * gz);
+          }
+          if (DO_A || DO_BT) {
+#pragma unroll
+            for (int m = 0; m < NQ; ++m) {
+              tq[qz][qy][m] += tb.D[qx * NQ + m] * f0;
+              tq[qz][m][qx] += tb.D[qy * NQ + m] * f1;
+              tq[m][qy][qx] += tb.D[qz * NQ + m] * f2;
+            }
+          }
+        }
+    if (DO_A || DO_BT) {
+      T t1[NV][NQ][NQ], t2[NV][NV][NQ];
+      cc_sweep2<NQ, NV, NQ, NQ>(tq, t1, St);
+      cc_sweep1<NQ, NV, NQ, NV>(t1, t2, St);
+      cc_sweep0<NQ, NV, NV, NV>(t2, yv, St);
+    }
+    if (DO_B) {
+      T t1[NPR][NQ][NQ], t2[NPR][NPR][NQ];
+      cc_sweep2<NQ, NPR, NQ, NQ>(qacc, t1, Pt);
+      cc_sweep1<NQ, NPR, NQ, NPR>(t1, t2, Pt);
+      cc_sweep0<NQ, NPR, NPR, NPR>(t2, qn, Pt);
+    }
+  }
+
+  // ---- scatter ---------------------------------------------------------------------------------
+  if (DO_A || DO_BT) {
+    T *yb = yu + vbase;
+    if (fast) {
+      if (!pad) {
+#pragma unroll
+        for (int iz = 0; iz < NV; ++iz)
+#pragma unroll
+          for (int iy = 0; iy < NV; ++iy)
+#pragma unroll
+            for (int ix = 0; ix < NV; ++ix) atomicAdd(&yb[iz * N01 + iy * N0 + ix], yv[iz][iy][ix]);
+      }
+    } else {
+#pragma unroll
+      for (int iz = 0; iz < NV; ++iz)
+#pragma unroll
+        for (int iy = 0; iy < NV; ++iy)
+#pragma unroll
+          for (int ix = 0; ix < NV; ++ix)
+            if (fx[ix] && fy[iy] && fz[iz]) atomicAdd(&yb[iz * N01 + iy * N0 + ix], yv[iz][iy][ix]);
+    }
+  }
+  if (DO_B && valid) {
+#pragma unroll
+    for (int a3 = 0; a3 < NPR; ++a3)
+#pragma unroll
+      for (int a2 = 0; a2 < NPR; ++a2)
+#pragma unroll
+        for (int a1 = 0; a1 < NPR; ++a1) atomicAdd(&yp[pbase + a3 * P01 + a2 * P0 + a1], qn[a3][a2][a1]);
+  }
+}
+
+// The trilinear kernels keep their geometry in shared memory: ask for the largest shared-memory
+// carveout so that occupancy is set by registers, not by the default L1 / shared split.
+template <int K>
+cudaError_t cc_prefer_shared() {
+  if constexpr (K == 2) {
+    const int pc = (int)cudaSharedmemCarveoutMaxShared;
+    cudaError_t e = cudaFuncSetAttribute(stokes_cell_apply_cc<2, float, kApplyA, false>,
+                                         cudaFuncAttributePreferredSharedMemoryCarveout, pc);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(stokes_cell_apply_cc<2, float, kApplyBT, false>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, pc);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(stokes_cell_apply_cc<2, float, kApplyB, false>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, pc);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(stokes_cell_apply_cc<2, float, kApplyA | kApplyBT, false>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, pc);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(stokes_cell_apply_cc<2, float, kApplyA | kApplyBT | kApplyB, false>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, pc);
+    return e;
+  }
+  return cudaSuccess;
+}
+
+template <int K, typename T, int MODE, bool CART>
+static void launch_cc_mode(const LevelDesc<T> &L, const T *u, const T *p, T *yu, T *yp, cudaStream_t s) {
+  using CL = CcLaunch<K, T, MODE, CART>;
+  const long long cpb = (long long)kCcCells * CL::WARPS;
+  const long long blocks = (L.n_cells + cpb - 1) / cpb;
+  launch_kernel(stokes_cell_apply_cc<K, T, MODE, CART>, dim3((unsigned)blocks), dim3(32 * CL::WARPS), CL::SMEM, s, L,
+                u, p, yu, yp);
+}
+
+// Launches shape 5 for the modes the kernel has (A, B^T, B, A + B^T, full); -1 otherwise.
+template <int K, typename T>
+int launch_cell_apply_cc_k(const LevelDesc<T> &L, int mode, const T *u, const T *p, T *yu, T *yp, cudaStream_t s) {
+  if (!cc_level_supported(L.dim, L.k, L.cartesian, sizeof(T)) || L.k != K) return -1;
+  constexpr bool TRI = K == 2 && sizeof(T) == 4;
+#define SMF_CC_CASE(M)                                                       \
+  case M:                                                                    \
+    if (L.cartesian)                                                         \
+      launch_cc_mode<K, T, M, true>(L, u, p, yu, yp, s);                     \
+    else if constexpr (TRI)                                                  \
+      launch_cc_mode<K, T, M, false>(L, u, p, yu, yp, s);                    \
+    return 0;
+  switch (mode) {
+    SMF_CC_CASE(kApplyA)
+    SMF_CC_CASE(kApplyBT)
+    SMF_CC_CASE(kApplyB)
+    SMF_CC_CASE(kApplyA | kApplyBT)
+    SMF_CC_CASE(kApplyA | kApplyBT | kApplyB)
+    default: return -1;
+  }
+#undef SMF_CC_CASE
+}
+
+}  // namespace smf

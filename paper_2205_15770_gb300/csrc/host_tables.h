@@ -38,6 +38,18 @@ template <int K, typename T>
 int launch_cell_grad_k(const LevelDesc<T> &L, const Tab1D<T> *tab, const T *u, const T *lam, T *g, cudaStream_t s);
 template <int K>
 int upload_col_tables(const Tab1D<double> &t, cudaStream_t s);
+// Cell-component kernel (launch shape 5, apply_cc.cuh): 3D Cartesian levels with k = 2, 3 (FP32
+// and FP64) and trilinear levels with k = 2 (FP32).  launch_cell_apply_cc_k returns -1 for a level
+// or mode it does not serve.
+inline bool cc_level_supported(int dim, int k, int cartesian, size_t elt) {
+  if (dim != 3) return false;
+  if (cartesian) return k == 2 || k == 3;
+  return k == 2 && elt == 4;
+}
+template <int K, typename T>
+int launch_cell_apply_cc_k(const LevelDesc<T> &L, int mode, const T *u, const T *p, T *yu, T *yp, cudaStream_t s);
+template <int K>
+int upload_cc_tables(const Tab1D<double> &t, cudaStream_t s);
 template <int K, typename T>
 int launch_cell_diag_k(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dSloc, T *dMp, cudaStream_t s,
                        const T *rho, int sym);

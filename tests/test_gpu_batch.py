@@ -63,7 +63,7 @@ def test_autotuned_launch_shapes_are_valid():
     S = StokesMG(dim=3, n=(16, 16, 16), n_levels=4, k=2)
     for prec in (32, 64):
         shapes = S.launch_shapes(prec)
-        assert len(shapes) == 4 and all(s in (1, 3, 4, -1) for s in shapes), shapes
+        assert len(shapes) == 4 and all(s in (1, 3, 4, -1, 5) for s in shapes), shapes
 
 
 @pytest.mark.parametrize("k", [2, 3, 4])
@@ -77,7 +77,7 @@ def test_every_launch_shape_gives_the_same_blocks(k, blocks):
     u = torch.as_tensor(W.random_vector(nu, 11), device="cuda")
     p = torch.as_tensor(W.random_vector(npr, 12), device="cuda")
     ref = None
-    for shape in (4, 1, 3, -1):
+    for shape in (4, 1, 3, -1, 5):
         S.set_launch_shape(0, shape, precision=64)
         yu, yp = S.apply_blocks(blocks, u=u, p=p)
         y = torch.cat([t for t in (yu, yp) if t is not None]).cpu().numpy()
@@ -92,7 +92,7 @@ def test_every_launch_shape_gives_the_same_operator():
     S = StokesMG(dim=3, n=(8, 8, 8), n_levels=2, k=2, vertices=V, gamma_rho=3.0)
     x = torch.as_tensor(W.random_vector(S.size(), 9), device="cuda")
     ref = None
-    for shape in (4, 1, 3, -1):
+    for shape in (4, 1, 3, -1, 5):
         S.set_launch_shape(1, shape, precision=64)
         y = S.vmult(x).cpu().numpy()
         if ref is None:
