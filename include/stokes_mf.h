@@ -173,6 +173,16 @@ int mg_vcycle(stokes_ctx *ctx, int precision, const void *b, void *x, void *stre
 int stokes_solve(stokes_ctx *ctx, const double *b, double *x, double rtol, int maxit, int *iters,
                  double *final_rel_res, void *stream);
 
+/* Where stokes_solve and stokes_solve_batch run the inner FGMRES iterations: 1 = on the device
+ * (the Hessenberg update, Givens rotations and the stopping test run in a kernel; the iterations
+ * of one restart cycle are one CUDA-graph launch with a conditional while node, and the host
+ * synchronises once per restart cycle), 0 = host-driven (one synchronisation per iteration;
+ * STOKES_HOST_KRYLOV=1, STOKES_NO_GRAPHS=1, or conditional graph nodes refused by the runtime),
+ * -1 = not decided yet (no solve so far).  No counterpart in the paper (the outer Krylov loop is
+ * a layer on top of its Algorithm 1). */
+int stokes_krylov_mode(const stokes_ctx *ctx);
+int stokes_batch_krylov_mode(const stokes_batch *batch);
+
 /* stokes_solve with HOST vectors: copies b in, solves from x = 0, copies x out. */
 int stokes_solve_host(stokes_ctx *ctx, const double *b_host, double *x_host, double rtol, int maxit,
                       int *iters, double *final_rel_res, void *stream);

@@ -361,6 +361,12 @@ class StokesMG:
     def launch_count(self):
         return int(self._lib.stokes_launch_count(self._ctx))
 
+    @property
+    def krylov_mode(self):
+        """1: inner FGMRES iterations on the device (one graph launch per restart cycle), 0: host-driven,
+        -1: no solve yet (stokes_krylov_mode)."""
+        return int(self._lib.stokes_krylov_mode(self._ctx))
+
 
 class StokesBatch:
     """Independent meshes solved together (stokes_setup_batch / stokes_solve_batch).
@@ -440,6 +446,12 @@ class StokesBatch:
         self._check(self._lib.stokes_solve_batch(self._bt, bp, xp, float(rtol), int(maxit), its, rel,
                                                  StokesMG._stream()))
         return xs, list(its), list(rel)
+
+    @property
+    def krylov_mode(self):
+        """1: every member's inner FGMRES iterations on the device in one graph launch per restart cycle,
+        0: host-driven lockstep, -1: no solve yet (stokes_batch_krylov_mode)."""
+        return int(self._lib.stokes_batch_krylov_mode(self._bt))
 
     def close(self):
         if getattr(self, "_bt", None):

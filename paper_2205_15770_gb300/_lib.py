@@ -66,6 +66,8 @@ SIGNATURES = {
     "stokes_destroy_batch": (None, [P]),
     "stokes_set_launch_shape": (C.c_int, [P, C.c_int, C.c_int, C.c_int]),
     "stokes_launch_count": (C.c_longlong, [P]),
+    "stokes_krylov_mode": (C.c_int, [P]),
+    "stokes_batch_krylov_mode": (C.c_int, [P]),
     "stokes_last_error": (C.c_char_p, [P]),
     "stokes_global_last_error": (C.c_char_p, []),
     "stokes_destroy": (None, [P]),

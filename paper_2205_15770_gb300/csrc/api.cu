@@ -17,13 +17,28 @@
 namespace smf {
 
 static thread_local std::string g_last_error;
-bool pdl_on() {
+// Programmatic dependent launch: 1 (default) for launches outside stream capture (direct calls
+// such as stokes_vmult, where the next kernel's launch overlaps the current one), 0 inside
+// captured graphs (measured faster for the solver's long chains of small kernels), 2 everywhere
+// (STOKES_PDL=all), 0 everywhere (STOKES_NO_PDL=1).
+static int pdl_mode() {
   static int v = -1;
   if (v < 0) {
     const char *e = getenv("STOKES_NO_PDL");
-    v = (e && e[0] == '1') ? 0 : 1;
+    const char *a = getenv("STOKES_PDL");
+    v = (e && e[0] == '1') ? 0 : ((a && std::strcmp(a, "all") == 0) ? 2 : 1);
   }
-  return v == 1;
+  return v;
+}
+bool pdl_on(cudaStream_t s) {
+  const int m = pdl_mode();
+  if (m != 1) return m == 2;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return cs == cudaStreamCaptureStatusNone;
 }
 void set_error(const std::string &m) { g_last_error = m; }
 int cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
@@ -225,6 +240,14 @@ struct stokes_ctx {
   bool use_graphs = true;
   bool fuse = true;  // fused smoothing where eligible (STOKES_NO_FUSE=1: the unfused path)
   GraphSlot g32[2], g64[2];  // [x_zero]
+  // FGMRES with the Arnoldi state on the device: one graph (conditional while node over the inner
+  // iterations of a restart cycle) replayed per cycle; kry_mode -1 not built yet, 0 host-driven
+  // loop (STOKES_HOST_KRYLOV=1, or conditional graph nodes unavailable), 1 device loop
+  KrylovDev kd{};
+  double *zcur = nullptr;
+  cudaGraphExec_t kry = nullptr;
+  long long kry_body = 0;
+  int kry_mode = -1;
   cudaStream_t s = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   // setup inputs, kept for stokes_set_viscosity
@@ -1560,6 +1583,20 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
   double **lz[] = {&C->lz0, &C->lz1, &C->lz2, &C->lz3, &C->sq};
   for (auto p : lz)
     if ((st = dalloc(C, p, N))) return st;
+  {
+    const int m = C->restart;
+    KrylovDev &K = C->kd;
+    K.m = m;
+    if ((st = dalloc(C, &K.H, (long long)(m + 1) * m))) return st;
+    if ((st = dalloc(C, &K.cs, m))) return st;
+    if ((st = dalloc(C, &K.sn, m))) return st;
+    if ((st = dalloc(C, &K.g, m + 1))) return st;
+    if ((st = dalloc(C, &K.y, m))) return st;
+    if ((st = dalloc(C, &K.thresh, 1))) return st;
+    if ((st = dalloc(C, &K.ctl, 4))) return st;
+    K.hcol = C->hdev;
+    if ((st = dalloc(C, &C->zcur, N))) return st;
+  }
 
   // smoother setup per level (Algorithm 2), FP64
   C->sigma = lemma1_scaling(C->o.kA);
@@ -1638,6 +1675,98 @@ static bool check_level(stokes_ctx *C, int level) {
 }
 
 // FP64 flexible GMRES (restarted), right-preconditioned by one multigrid cycle per iteration.
+// Destroys every captured graph of the context (cycles and the device Krylov loop).
+static void drop_graphs(stokes_ctx *C) {
+  for (int i = 0; i < 2; ++i) {
+    if (C->g32[i].exec) cudaGraphExecDestroy(C->g32[i].exec);
+    if (C->g64[i].exec) cudaGraphExecDestroy(C->g64[i].exec);
+    C->g32[i].exec = nullptr;
+    C->g64[i].exec = nullptr;
+  }
+  if (C->kry) cudaGraphExecDestroy(C->kry);
+  C->kry = nullptr;
+  if (C->kry_mode == 1) C->kry_mode = -1;
+}
+
+// The inner FGMRES iteration on the device (one Arnoldi step, Sec. 4 outer loop around the
+// multigrid preconditioner of Algorithm 1): z_j = MG(0, v_j) into zcur and Z_j, w = K z_j (FP64),
+// CGS2 against v_0..v_j, v_{j+1} = w / ||w||, then the Givens update that sets `cond`.
+static void krylov_body(stokes_ctx *C, cudaGraphConditionalHandle cond, bool set_cond) {
+  Runner<double> R64(C);
+  Runner<float> R32(C);
+  const int top = C->nl - 1;
+  const long long N = C->L64[top].d.n_u + C->L64[top].d.n_p;
+  const int nb = vec_blocks(N), m = C->restart;
+  const int *ctl = C->kd.ctl;
+  if (C->o.vcycle_fp32) {
+    LevelRT<float> &T32 = C->L32[top];
+    R32.vec(k_slot_convert<float>, N, (const double *)C->V, N, ctl, T32.b, T32.x, N);
+    R32.cycle(top, T32.x, T32.b, true);
+    R32.vec(k_convert_to_slot<float>, N, (const float *)T32.x, C->zcur, C->Z, N, ctl, N);
+  } else {
+    LevelRT<double> &T64 = C->L64[top];
+    R64.vec(k_slot_convert<double>, N, (const double *)C->V, N, ctl, T64.b, T64.x, N);
+    R64.cycle(top, T64.x, T64.b, true);
+    R64.vec(k_convert_to_slot<double>, N, (const double *)T64.x, C->zcur, C->Z, N, ctl, N);
+  }
+  R64.vmult(top, C->zcur, C->w, true);
+  for (int pass = 0; pass < 2; ++pass) {
+    k_mdot_partial_cnt<<<kRedBlocks, kVecThreads, 0, C->s>>>(C->V, N, ctl, 1, C->w, N, C->partial);
+    k_final_reduce_cnt<<<m, kVecThreads, 0, C->s>>>(C->partial, kRedBlocks, ctl, 1, C->hdev + pass * (m + 2));
+    k_maxpy_cnt<<<nb, kVecThreads, 0, C->s>>>(C->V, N, ctl, 1, C->hdev + pass * (m + 2), C->w, N, -1.0);
+  }
+  k_mdot_partial<<<kRedBlocks, kVecThreads, 0, C->s>>>(C->w, N, 1, C->w, N, C->partial);
+  k_final_reduce<<<1, kVecThreads, 0, C->s>>>(C->partial, kRedBlocks, 1, C->hdev + 2 * (m + 2));
+  k_scale_to_slot<<<nb, kVecThreads, 0, C->s>>>(C->w, C->hdev + 2 * (m + 2), C->V, N, ctl, N);
+  k_fgmres_givens<<<1, 32, 0, C->s>>>(C->kd, cond, set_cond ? 1 : 0);
+  C->cap_count += 10;
+}
+
+// Builds the device Krylov graph: a conditional while node whose body is krylov_body.  Returns
+// false (and leaves kry_mode at 0, the host-driven loop) when the runtime refuses conditional
+// nodes; errors of that attempt are cleared.
+static bool krylov_build(stokes_ctx *C) {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+  cudaGraphConditionalHandle cond{};
+  if (ok) ok = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  cudaGraphNodeParams cp = {};
+  cudaGraphNode_t wnode = nullptr;
+  if (ok) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    ok = cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
+  }
+  if (ok) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    ok = cudaStreamBeginCaptureToGraph(C->s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+         cudaSuccess;
+    if (ok) {
+      C->capturing = true;
+      C->cap_count = 0;
+      krylov_body(C, cond, true);
+      C->capturing = false;
+      cudaGraph_t out = body;
+      ok = cudaStreamEndCapture(C->s, &out) == cudaSuccess;
+    }
+  }
+  if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    if (ex) cudaGraphExecDestroy(ex);
+    cudaGetLastError();
+    C->kry_mode = 0;
+    return false;
+  }
+  C->kry = ex;
+  C->kry_body = C->cap_count;
+  C->kry_mode = 1;
+  return true;
+}
+
 static int fgmres(stokes_ctx *C, const double *b, double *x, double rtol, int maxit, int *iters, double *final_rel) {
   Runner<double> R64(C);
   Runner<float> R32(C);
@@ -1662,6 +1791,13 @@ static int fgmres(stokes_ctx *C, const double *b, double *x, double rtol, int ma
   double xn2;
   if ((st = dot64(C, x, x, N, &xn2))) return st;
   bool x_is_zero = xn2 == 0.0;
+  if (C->kry_mode < 0) {
+    const char *hk = getenv("STOKES_HOST_KRYLOV");
+    if ((hk && hk[0] == '1') || !C->use_graphs)
+      C->kry_mode = 0;
+    else
+      krylov_build(C);
+  }
   while (true) {
     if (x_is_zero) {  // r = b - K 0
       SMF_CUDA_OK(cudaMemcpyAsync(C->V, b, N * sizeof(double), cudaMemcpyDeviceToDevice, C->s));
@@ -1688,6 +1824,23 @@ static int fgmres(stokes_ctx *C, const double *b, double *x, double rtol, int ma
     }
     k_scale<double><<<nb, kVecThreads, 0, C->s>>>(C->V, 1.0 / beta, C->V, N);
     ++C->launches;
+    if (C->kry_mode == 1) {
+      // inner iterations on the device: one graph launch per restart cycle, then y = R^-1 g and
+      // x += Z y; the host reads the iteration count once per cycle
+      int hctl[4] = {0, it, 0, maxit};
+      const double g0 = beta, th = rtol * bnorm;
+      SMF_CUDA_OK(cudaMemcpyAsync(C->kd.ctl, hctl, sizeof(hctl), cudaMemcpyHostToDevice, C->s));
+      SMF_CUDA_OK(cudaMemcpyAsync(C->kd.g, &g0, sizeof(double), cudaMemcpyHostToDevice, C->s));
+      SMF_CUDA_OK(cudaMemcpyAsync(C->kd.thresh, &th, sizeof(double), cudaMemcpyHostToDevice, C->s));
+      SMF_CUDA_OK(cudaGraphLaunch(C->kry, C->s));
+      k_fgmres_trisolve<<<1, 32, 0, C->s>>>(C->kd);
+      k_maxpy_cnt<<<nb, kVecThreads, 0, C->s>>>(C->Z, N, C->kd.ctl, 0, C->kd.y, x, N, 1.0);
+      SMF_CUDA_OK(cudaMemcpyAsync(hctl, C->kd.ctl, sizeof(hctl), cudaMemcpyDeviceToHost, C->s));
+      SMF_CUDA_OK(cudaStreamSynchronize(C->s));
+      C->launches += C->kry_body * (long long)(hctl[1] - it) + 2;
+      it = hctl[1];
+      continue;
+    }
     std::fill(H.begin(), H.end(), 0.0);
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
@@ -1795,6 +1948,11 @@ struct stokes_batch {
   long long graph_kernels = 0;
   std::vector<double *> pinned;
   std::string err;
+  // Arnoldi loops of all members on the device: one graph per batch (while node over the
+  // iterations, an if node per member); kmode -1 not built, 0 host-driven lockstep, 1 device
+  cudaGraphExec_t kgraph = nullptr;
+  std::vector<long long> kbody;
+  int kmode = -1;
 };
 
 namespace smf {
@@ -1832,9 +1990,95 @@ static void dot64_async(stokes_ctx *C, const double *a, const double *b, long lo
   C->launches += 2;
 }
 
+// The device Arnoldi graph of a batch: a while node (runs while any member does) whose body is
+// k_batch_select, one conditional if node per member holding that member's krylov_body, and
+// k_batch_any after all of them.  Members' bodies are independent branches of the body graph.
+static bool batch_kbuild(stokes_batch *Bt) {
+  const int nm = (int)Bt->ctx.size();
+  Bt->kmode = 0;
+  if (nm > kBatchMax) return false;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  BatchCond bc;
+  bc.n = nm;
+  bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+  if (ok) ok = cudaGraphConditionalHandleCreate(&bc.loop, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  cudaGraphNodeParams wp = {};
+  cudaGraphNode_t wn = nullptr;
+  if (ok) {
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = bc.loop;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    ok = cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, &wp) == cudaSuccess;
+  }
+  cudaGraph_t body = ok ? wp.conditional.phGraph_out[0] : nullptr;
+  for (int i = 0; i < nm && ok; ++i) {
+    ok = cudaGraphConditionalHandleCreate(&bc.member[i], body, 0, 0) == cudaSuccess;
+    bc.ctl[i] = Bt->ctx[i]->kd.ctl;
+  }
+  cudaGraphNode_t seln = nullptr, anyn = nullptr;
+  std::vector<cudaGraphNode_t> ifn(nm, nullptr);
+  void *args[1] = {&bc};
+  if (ok) {
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)k_batch_select;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(kBatchMax);
+    kp.kernelParams = args;
+    ok = cudaGraphAddKernelNode(&seln, body, nullptr, 0, &kp) == cudaSuccess;
+  }
+  Bt->kbody.assign(nm, 0);
+  for (int i = 0; i < nm && ok; ++i) {
+    stokes_ctx *C = Bt->ctx[i];
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = bc.member[i];
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    ok = cudaGraphAddNode(&ifn[i], body, &seln, nullptr, 1, &ip) == cudaSuccess;
+    if (!ok) break;
+    cudaGraph_t ib = ip.conditional.phGraph_out[0];
+    ok = cudaStreamBeginCaptureToGraph(C->s, ib, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (!ok) break;
+    C->capturing = true;
+    C->cap_count = 0;
+    krylov_body(C, cudaGraphConditionalHandle{}, false);
+    C->capturing = false;
+    cudaGraph_t out = ib;
+    ok = cudaStreamEndCapture(C->s, &out) == cudaSuccess;
+    Bt->kbody[i] = C->cap_count;
+  }
+  if (ok) {
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)k_batch_any;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(32);
+    kp.kernelParams = args;
+    ok = cudaGraphAddKernelNode(&anyn, body, ifn.data(), nm, &kp) == cudaSuccess;
+  }
+  if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    if (ex) cudaGraphExecDestroy(ex);
+    cudaGetLastError();
+    return false;
+  }
+  Bt->kgraph = ex;
+  Bt->kmode = 1;
+  return true;
+}
+
 static int batch_solve(stokes_batch *Bt, const double *const *b, double *const *x, double rtol, int maxit, int *iters,
                        double *final_rel) {
   const int nm = (int)Bt->ctx.size();
+  if (Bt->kmode < 0) {
+    const char *hk = getenv("STOKES_HOST_KRYLOV");
+    if ((hk && hk[0] == '1') || !Bt->ctx[0]->use_graphs)
+      Bt->kmode = 0;
+    else
+      batch_kbuild(Bt);
+  }
   std::vector<BatchState> S(nm);
   for (int i = 0; i < nm; ++i) {
     BatchState &st = S[i];
@@ -1917,6 +2161,46 @@ static int batch_solve(stokes_batch *Bt, const double *const *b, double *const *
     int nactive = 0;
     for (auto &st : S) nactive += st.done ? 0 : 1;
     if (nactive == 0) break;
+    if (Bt->kmode == 1) {
+      // (b') every active member's inner iterations in one graph launch; stopped members idle
+      for (auto &st : S) {
+        stokes_ctx *C = st.C;
+        int hctl[4] = {0, st.it, st.done ? 5 : 0, maxit};
+        SMF_CUDA_OK(cudaMemcpyAsync(C->kd.ctl, hctl, sizeof(hctl), cudaMemcpyHostToDevice, C->s));
+        if (!st.done) {
+          const double g0 = st.g[0], th = rtol * st.bnorm;
+          SMF_CUDA_OK(cudaMemcpyAsync(C->kd.g, &g0, sizeof(double), cudaMemcpyHostToDevice, C->s));
+          SMF_CUDA_OK(cudaMemcpyAsync(C->kd.thresh, &th, sizeof(double), cudaMemcpyHostToDevice, C->s));
+        }
+      }
+      for (int i = 0; i < nm; ++i) {
+        SMF_CUDA_OK(cudaEventRecord(Bt->join[i], Bt->ctx[i]->s));
+        SMF_CUDA_OK(cudaStreamWaitEvent(Bt->s, Bt->join[i], 0));
+      }
+      SMF_CUDA_OK(cudaGraphLaunch(Bt->kgraph, Bt->s));
+      SMF_CUDA_OK(cudaEventRecord(Bt->fork, Bt->s));
+      for (auto &st : S) {
+        stokes_ctx *C = st.C;
+        SMF_CUDA_OK(cudaStreamWaitEvent(C->s, Bt->fork, 0));
+        if (st.done) continue;
+        const int top = C->nl - 1;
+        const long long N = C->L64[top].d.n_u + C->L64[top].d.n_p;
+        k_fgmres_trisolve<<<1, 32, 0, C->s>>>(C->kd);
+        k_maxpy_cnt<<<vec_blocks(N), kVecThreads, 0, C->s>>>(C->Z, N, C->kd.ctl, 0, C->kd.y, st.x, N, 1.0);
+        SMF_CUDA_OK(cudaMemcpyAsync(st.hhost, C->kd.ctl, 4 * sizeof(int), cudaMemcpyDeviceToHost, C->s));
+      }
+      for (int i = 0; i < nm; ++i) {
+        BatchState &st = S[i];
+        if (st.done) continue;
+        SMF_CUDA_OK(cudaStreamSynchronize(st.C->s));
+        int hctl[4];
+        std::memcpy(hctl, st.hhost, sizeof(hctl));
+        st.C->launches += Bt->kbody[i] * (long long)(hctl[1] - st.it) + 2;
+        st.it = hctl[1];
+        st.need_start = true;
+      }
+      continue;
+    }
     // (b) one Arnoldi step for every active mesh; the FP32 cycles of all meshes in one graph
     for (auto &st : S) {
       if (st.done) continue;
@@ -2721,6 +3005,7 @@ void stokes_destroy_batch(stokes_batch *Bt) {
   if (!Bt) return;
   if (Bt->s) cudaStreamSynchronize(Bt->s);
   if (Bt->graph) cudaGraphExecDestroy(Bt->graph);
+  if (Bt->kgraph) cudaGraphExecDestroy(Bt->kgraph);
   for (auto *C : Bt->ctx) stokes_destroy(C);
   for (auto *h : Bt->pinned)
     if (h) cudaFreeHost(h);
@@ -2774,16 +3059,13 @@ int stokes_set_launch_shape(stokes_ctx *C, int level, int precision, int shape) 
     return st;
   }
   // captured cycles baked the previous shape in: drop them so the next call recaptures
-  for (int i = 0; i < 2; ++i) {
-    if (C->g32[i].exec) cudaGraphExecDestroy(C->g32[i].exec);
-    if (C->g64[i].exec) cudaGraphExecDestroy(C->g64[i].exec);
-    C->g32[i].exec = nullptr;
-    C->g64[i].exec = nullptr;
-  }
+  drop_graphs(C);
   return STOKES_OK;
 }
 
 long long stokes_launch_count(const stokes_ctx *C) { return C ? C->launches : 0; }
+int stokes_krylov_mode(const stokes_ctx *C) { return C ? C->kry_mode : -1; }
+int stokes_batch_krylov_mode(const stokes_batch *Bt) { return Bt ? Bt->kmode : -1; }
 
 const char *stokes_last_error(const stokes_ctx *C) { return C ? C->err.c_str() : g_last_error.c_str(); }
 const char *stokes_global_last_error(void) { return g_last_error.c_str(); }
@@ -2791,10 +3073,7 @@ const char *stokes_global_last_error(void) { return g_last_error.c_str(); }
 void stokes_destroy(stokes_ctx *C) {
   if (!C) return;
   if (C->s) cudaStreamSynchronize(C->s);
-  for (int i = 0; i < 2; ++i) {
-    if (C->g32[i].exec) cudaGraphExecDestroy(C->g32[i].exec);
-    if (C->g64[i].exec) cudaGraphExecDestroy(C->g64[i].exec);
-  }
+  drop_graphs(C);
   for (void *p : C->allocs) cudaFree(p);
   if (C->ev_in) cudaEventDestroy(C->ev_in);
   if (C->ev_out) cudaEventDestroy(C->ev_out);

@@ -112,9 +112,10 @@ __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
-// Host side: launch with the programmatic-stream-serialization attribute (PDL) unless
-// STOKES_NO_PDL=1.  Every kernel of the library begins with pdl_enter().
-bool pdl_on();
+// Host side: launch with the programmatic-stream-serialization attribute (PDL) where pdl_on(s)
+// says so (by default outside stream capture only).  Every kernel of the library begins with
+// pdl_enter().
+bool pdl_on(cudaStream_t s);
 template <typename... KArgs, typename... Args>
 inline void launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                           Args... args) {
@@ -124,7 +125,7 @@ inline void launch_kernel(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t 
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
-  if (pdl_on()) {
+  if (pdl_on(s)) {
     at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     at[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;

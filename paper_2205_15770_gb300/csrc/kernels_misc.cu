@@ -151,3 +151,117 @@ __global__ void k_extract_inverse(const double *__restrict__ M, int nb, int n0, 
 }
 
 }  // namespace smf
+
+namespace smf {
+
+__global__ void k_mdot_partial_cnt(const double *__restrict__ V, long long ldv, const int *__restrict__ ctl, int add,
+                                   const double *__restrict__ w, long long n, double *__restrict__ partial) {
+  pdl_enter();
+  __shared__ double sh[32];
+  const int nvec = ctl[0] + add;
+  for (int j = 0; j < nvec; ++j) {
+    const double *v = V + (long long)j * ldv;
+    double s = 0.0;
+    SMF_GRID_LOOP(i, n) s += v[i] * w[i];
+    s = block_reduce_sum<double>(s, sh);
+    if (threadIdx.x == 0) partial[(long long)j * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+__global__ void k_final_reduce_cnt(const double *__restrict__ partial, int nparts, const int *__restrict__ ctl, int add,
+                                   double *__restrict__ out) {
+  pdl_enter();
+  __shared__ double sh[32];
+  const int j = blockIdx.x;
+  if (j >= ctl[0] + add) return;  // uniform per block
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nparts; b += blockDim.x) s += partial[(long long)j * nparts + b];
+  s = block_reduce_sum<double>(s, sh);
+  if (threadIdx.x == 0) out[j] = s;
+}
+
+__global__ void k_maxpy_cnt(const double *__restrict__ V, long long ldv, const int *__restrict__ ctl, int add,
+                            const double *__restrict__ h, double *__restrict__ w, long long n, double sign) {
+  pdl_enter();
+  const int nvec = ctl[0] + add;
+  SMF_GRID_LOOP(i, n) {
+    double s = 0.0;
+    for (int j = 0; j < nvec; ++j) s += h[j] * V[(long long)j * ldv + i];
+    w[i] += sign * s;
+  }
+}
+
+__global__ void k_scale_to_slot(const double *__restrict__ w, const double *__restrict__ nrm2, double *__restrict__ V,
+                                long long ldv, const int *__restrict__ ctl, long long n) {
+  pdl_enter();
+  const double s = 1.0 / sqrt(nrm2[0]);
+  double *out = V + (long long)(ctl[0] + 1) * ldv;
+  SMF_GRID_LOOP(i, n) out[i] = s * w[i];
+}
+
+__global__ void k_fgmres_givens(KrylovDev K, cudaGraphConditionalHandle cond, int set_cond) {
+  pdl_enter();
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const int m = K.m, j = K.ctl[0];
+  double *H = K.H;
+  for (int i = 0; i <= j; ++i) H[i * m + j] = K.hcol[i] + K.hcol[(m + 2) + i];
+  H[(j + 1) * m + j] = sqrt(K.hcol[2 * (m + 2)]);
+  for (int i = 0; i < j; ++i) {
+    const double a = H[i * m + j], b = H[(i + 1) * m + j];
+    H[i * m + j] = K.cs[i] * a + K.sn[i] * b;
+    H[(i + 1) * m + j] = -K.sn[i] * a + K.cs[i] * b;
+  }
+  const double den = hypot(H[j * m + j], H[(j + 1) * m + j]);
+  K.cs[j] = H[j * m + j] / den;
+  K.sn[j] = H[(j + 1) * m + j] / den;
+  H[j * m + j] = den;
+  H[(j + 1) * m + j] = 0.0;
+  const double gj = K.g[j];
+  K.g[j + 1] = -K.sn[j] * gj;
+  K.g[j] = K.cs[j] * gj;
+  const int it = K.ctl[1] + 1;
+  K.ctl[1] = it;
+  K.ctl[0] = j + 1;
+  int stop = 0;
+  if (!isfinite(K.g[j + 1]))
+    stop = 3;
+  else if (fabs(K.g[j + 1]) <= K.thresh[0])
+    stop = 1;
+  else if (it >= K.ctl[3])
+    stop = 2;
+  else if (j + 1 >= m)
+    stop = 4;
+  K.ctl[2] = stop;
+  if (set_cond) cudaGraphSetConditional(cond, stop == 0 ? 1u : 0u);
+}
+
+__global__ void k_fgmres_trisolve(KrylovDev K) {
+  pdl_enter();
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  const int m = K.m, jd = K.ctl[0];
+  for (int i = jd - 1; i >= 0; --i) {
+    double s = K.g[i];
+    for (int c = i + 1; c < jd; ++c) s -= K.H[i * m + c] * K.y[c];
+    K.y[i] = s / K.H[i * m + i];
+  }
+}
+
+}  // namespace smf
+
+namespace smf {
+
+__global__ void k_batch_select(const BatchCond B) {
+  pdl_enter();
+  const int i = threadIdx.x;
+  if (blockIdx.x == 0 && i < B.n) cudaGraphSetConditional(B.member[i], B.ctl[i][2] == 0 ? 1u : 0u);
+}
+
+__global__ void k_batch_any(const BatchCond B) {
+  pdl_enter();
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  int any = 0;
+  for (int i = 0; i < B.n; ++i) any |= B.ctl[i][2] == 0;
+  cudaGraphSetConditional(B.loop, any ? 1u : 0u);
+}
+
+}  // namespace smf

@@ -374,3 +374,75 @@ __global__ void k_scale_by_inv_sqrt(const double *__restrict__ w, const double *
                                     double *__restrict__ out, long long n);
 
 }  // namespace smf
+
+namespace smf {
+
+// ---- FGMRES with the Arnoldi state on the device ----------------------------------------------
+// The inner iterations of one restart cycle run as a CUDA graph with a conditional while node:
+// every kernel reads the iteration index j from device memory (ctl[0]), and k_fgmres_givens
+// decides on the device whether the loop continues.  ctl = {j, it, stop, maxit}; stop: 0 running,
+// 1 converged (|g_{j+1}| <= thresh), 2 maxit, 3 non-finite, 4 restart length reached.
+struct KrylovDev {
+  double *H = nullptr;     // (m+1) x m Hessenberg, row-major H[i * m + j] (rotated in place)
+  double *cs = nullptr, *sn = nullptr;  // Givens rotations (m)
+  double *g = nullptr;     // rotated right-hand side (m + 1)
+  double *y = nullptr;     // triangular-solve result (m)
+  double *hcol = nullptr;  // CGS2 coefficients of the two passes ([0, m+2), [m+2, 2m+4)) and ||w||^2
+  double *thresh = nullptr;  // rtol * ||b||
+  int *ctl = nullptr;
+  int m = 0;
+};
+// partial[jj * gridDim.x + b] = block b's part of V_jj . w for jj < ctl[0] + add
+__global__ void k_mdot_partial_cnt(const double *__restrict__ V, long long ldv, const int *__restrict__ ctl, int add,
+                                   const double *__restrict__ w, long long n, double *__restrict__ partial);
+// out[jj] = sum_b partial[jj * nparts + b], one block per jj; blocks jj >= ctl[0] + add return
+__global__ void k_final_reduce_cnt(const double *__restrict__ partial, int nparts, const int *__restrict__ ctl, int add,
+                                   double *__restrict__ out);
+// w += sign * sum_{jj < ctl[0] + add} h[jj] V_jj
+__global__ void k_maxpy_cnt(const double *__restrict__ V, long long ldv, const int *__restrict__ ctl, int add,
+                            const double *__restrict__ h, double *__restrict__ w, long long n, double sign);
+// V_{ctl[0] + 1} = w / sqrt(*nrm2)
+__global__ void k_scale_to_slot(const double *__restrict__ w, const double *__restrict__ nrm2, double *__restrict__ V,
+                                long long ldv, const int *__restrict__ ctl, long long n);
+// one Arnoldi column: Hessenberg entries, earlier rotations, new rotation, residual estimate,
+// stop decision; sets the while-node condition
+__global__ void k_fgmres_givens(KrylovDev K, cudaGraphConditionalHandle cond, int set_cond);
+// Batched Arnoldi loop: member i runs its iteration while its ctl[i][2] == 0 (conditional if
+// nodes, one per member, inside one while node that runs while any member does).
+constexpr int kBatchMax = 64;
+struct BatchCond {
+  int n = 0;
+  cudaGraphConditionalHandle loop{};
+  cudaGraphConditionalHandle member[kBatchMax] = {};
+  const int *ctl[kBatchMax] = {};
+};
+__global__ void k_batch_select(const BatchCond B);  // member conditions from their stop flags
+__global__ void k_batch_any(const BatchCond B);     // loop condition: any member still running
+// y = R^{-1} g on the first ctl[0] columns (R the rotated Hessenberg, upper triangular)
+__global__ void k_fgmres_trisolve(KrylovDev K);
+
+// out = (Tout) V_{ctl[0]}, zero (may be null) zeroed: the preconditioner's right-hand side
+template <typename Tout>
+__global__ void k_slot_convert(const double *__restrict__ V, long long ldv, const int *__restrict__ ctl,
+                               Tout *__restrict__ out, Tout *__restrict__ zero, long long n) {
+  pdl_enter();
+  const double *a = V + (long long)ctl[0] * ldv;
+  SMF_GRID_LOOP(i, n) {
+    out[i] = (Tout)a[i];
+    if (zero) zero[i] = Tout(0);
+  }
+}
+// z = (double) a and Z_{ctl[0]} = z: the preconditioned vector for the operator and the update
+template <typename Tin>
+__global__ void k_convert_to_slot(const Tin *__restrict__ a, double *__restrict__ z, double *__restrict__ Z,
+                                  long long ldz, const int *__restrict__ ctl, long long n) {
+  pdl_enter();
+  double *zj = Z + (long long)ctl[0] * ldz;
+  SMF_GRID_LOOP(i, n) {
+    const double v = (double)a[i];
+    z[i] = v;
+    zj[i] = v;
+  }
+}
+
+}  // namespace smf

@@ -45,6 +45,35 @@ def test_batch_matches_single_solves_and_oracle_residuals():
         assert np.abs(xs1.cpu().numpy() - x).max() <= 1e-8 * np.abs(x).max(), i
 
 
+@pytest.mark.parametrize("host", [False, True])
+def test_batch_device_krylov_loop_matches_host_loop(monkeypatch, host):
+    """The batch's inner FGMRES iterations on the device (one graph launch per restart cycle, a
+    conditional node per member) and host-driven: same iteration counts as single-mesh solves,
+    with members of different lengths (a restart of 3 forces several cycles)."""
+    from paper_2205_15770_gb300 import StokesBatch, StokesMG
+    if host:
+        monkeypatch.setenv("STOKES_HOST_KRYLOV", "1")
+    else:
+        monkeypatch.delenv("STOKES_HOST_KRYLOV", raising=False)
+    members = [dict(dim=3, n=(4, 4, 4), n_levels=2, gamma_rho=0.0),
+               dict(dim=3, n=(8, 8, 8), n_levels=3, gamma_rho=1e3),
+               dict(dim=3, n=(6, 6, 6), n_levels=2, gamma_rho=10.0)]
+    Bt = StokesBatch(members, kA=1, kS=1, m=2, schur_diag="d", restart=3)
+    bs = [mv.mass_rhs(torch.as_tensor(W.fourier_forcing(3, 2, mb["n"], seed=20 + i).reshape(-1), device="cuda"))
+          for i, (mb, mv) in enumerate(zip(members, Bt.members))]
+    xs, its, rels = Bt.solve(bs, rtol=1e-10)
+    assert Bt.krylov_mode == (0 if host else 1)
+    for i, mb in enumerate(members):
+        assert rels[i] <= 1e-10
+        S = StokesMG(dim=3, n=mb["n"], n_levels=mb["n_levels"], gamma_rho=mb["gamma_rho"], kA=1, kS=1, m=2,
+                     schur_diag="d", restart=3)
+        xs1, its1, _ = S.solve(bs[i], rtol=1e-10)
+        assert its[i] == its1, (i, its, its1)
+        assert np.abs(xs1.cpu().numpy() - xs[i].cpu().numpy()).max() <= 1e-8 * xs1.abs().max().item()
+        S.close()
+    Bt.close()
+
+
 def test_batch_zero_rhs_member():
     from paper_2205_15770_gb300 import StokesBatch
     members = [dict(dim=3, n=(4, 4, 4), n_levels=2), dict(dim=3, n=(4, 4, 4), n_levels=2, gamma_rho=5.0)]

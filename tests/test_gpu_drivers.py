@@ -132,3 +132,34 @@ def test_velocity_node_coordinates(name):
         w = np.array([np.prod([xi[a] if (v >> a) & 1 else 1 - xi[a] for a in range(d)]) for v in range(2 ** d)])
         ref[vn[:, j]] = np.einsum("v,cva->ca", w, Xv)
     assert np.abs(xyz - ref).max() < 1e-13
+
+
+@pytest.mark.parametrize("fp32", [True, False])
+def test_device_krylov_loop_matches_host_loop(monkeypatch, fp32):
+    """FGMRES with the Arnoldi state and the stopping test on the device (one graph launch per
+    restart cycle) against the host-driven loop: same iteration counts, solutions within 1e-10,
+    both at the requested FP64 residual under the oracle's assembled K."""
+    import workloads as W
+    from oracle.assemble import load_vector_nodal
+    from oracle.mg import Multigrid
+    from parity_cases import CASES, gpu_solver, oracle_hierarchy
+    case = CASES["3d_q2_pert"]
+    H = oracle_hierarchy(case)
+    mg = Multigrid(H, gamma_rho=case["gamma_rho"], kA=1, kS=1, m=2, schur_diag="d")
+    lev = H.levels[-1]
+    b = load_vector_nodal(lev, mg.ops[-1], W.fourier_forcing(3, 2, case["n"], seed=8).reshape(-1))
+    out = {}
+    for host in (False, True):
+        if host:
+            monkeypatch.setenv("STOKES_HOST_KRYLOV", "1")
+        else:
+            monkeypatch.delenv("STOKES_HOST_KRYLOV", raising=False)
+        S = gpu_solver(case, kA=1, kS=1, m=2, schur_diag="d", vcycle_fp32=fp32, restart=4)
+        x, its, rel = S.solve(torch.as_tensor(b, device="cuda"), rtol=1e-10)
+        assert S.krylov_mode == (0 if host else 1)
+        xs = x.cpu().numpy()
+        assert np.linalg.norm(b - mg.K @ xs) <= 1.01e-10 * np.linalg.norm(b)
+        out[host] = (xs, its)
+        S.close()
+    assert out[False][1] == out[True][1]
+    assert np.abs(out[False][0] - out[True][0]).max() <= 1e-10 * np.abs(out[True][0]).max()
