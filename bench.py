@@ -73,50 +73,12 @@ def dofs(n, k=2, dim=3):
     return nu + npr
 
 
-def flops_per_cell_A(k, trilinear, dim=3):
-    """Algorithmic flops of one cell of the velocity-block apply (A u) by sum factorisation.
-
-    Per component: forward interpolation d sweeps and collocation gradient d sweeps, backward
-    the transposes (4 d (k+1)^d (k+1) multiply-adds), the point operation (d^2 multiply-adds
-    plus 5 flops per point).  Trilinear geometry (3D, as the column kernel evaluates it): per
-    (x, y) node column 78 flops to set up the edge vectors of the Jacobian, per point 83 flops
-    (two Jacobian columns linear in zeta, adjugate, determinant, w/det, G = w adj adj^T / det,
-    w det).  Cartesian cells: geometry is a constant.
-    """
-    n1 = k + 1
-    npt = n1 ** dim
-    per_comp = 2 * (4 * dim * npt * n1 + dim * dim * npt) + 5 * npt
-    geo = 0
-    if trilinear:
-        geo = n1 ** (dim - 1) * 78 + npt * 83
-    return dim * per_comp + geo
-
-
-def flops_per_cell_full(k, dim=3):
-    """Algorithmic flops of one cell of the full operator K x (A u + B^T p, B u) when the per-point
-    geometry is a stored input (the FP64 column kernel reads it): the velocity block without the
-    geometry term of flops_per_cell_A, the pressure interpolation k^d -> (k+1)^d and its transpose
-    (3 sweeps each way), and per point and velocity component the B^T term p C_c (3 multiply-adds)
-    and the B term C_c . grad u_c (3 multiply-adds)."""
-    n1, npr = k + 1, k
-    sweeps = npr ** 3 * n1 + npr ** 2 * n1 ** 2 + npr * n1 ** 3
-    return flops_per_cell_A(k, False, dim) + 2 * 2 * sweeps + 2 * 2 * 3 * dim * n1 ** dim
-
-
-FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (vector and tensor), nominal at the 2070 MHz boost clock
-
-
 def tuning_string(S):
     """The setup's choices of a context as a STOKES_TUNING value (to profile the same configuration:
     timings taken under a profiler choose differently)."""
     j = lambda v: ",".join(str(int(x)) for x in v)
     return (f"s32={j(S.launch_shapes(32))};s64={j(S.launch_shapes(64))};f32={j(S.fused_levels(32))};"
             f"f64={j(S.fused_levels(64))}")
-
-
-def fp32_peak_tflops(sm_count, clock_mhz):
-    """FP32 FMA peak: SMs x 128 lanes x 2 flops x clock."""
-    return sm_count * 128 * 2 * clock_mhz * 1e6 / 1e12
 
 
 # ---------------------------------------------------------------------------------------------
@@ -130,48 +92,138 @@ def forcing():
     return W.fourier_forcing(WL["dim"], WL["k"], WL["n"], seed=WL["seed"]).reshape(-1)
 
 
+ORACLE_GAMMA = 1e2  # the middle gamma of the workload: the CPU sample solves this one
+
+
 def oracle_sample(steps=1, warmup=0):
-    """CPU oracle on a bounded sample of the workload: the 16^3 level of the same perturbed
-    hierarchy (every second vertex of the 32^3 mesh; 112,724 DoFs, 4 levels), the same three
-    gamma values, FP64 multigrid + FGMRES to 1e-8.  Returns seconds per step (3 solves)."""
-    import numpy as np
+    """CPU oracle on the workload itself: the 32^3 perturbed hierarchy (859,812 DoFs, 5 levels),
+    gamma = 1e2, the same smoother and Schur diagonal, FP64 multigrid + FGMRES(30) to 1e-8 from
+    x = 0.  Setup (assembly, Lanczos, Schur diagonal, coarse LU) is untimed; each step is one
+    solve.  Returns seconds per step."""
     from oracle.assemble import load_vector_nodal
     from oracle.krylov import fgmres
     from oracle.mesh import Hierarchy
     from oracle.mg import Multigrid
-    import workloads as W
-    V = perturbed_vertices()[::2, ::2, ::2]
-    n = tuple(c // 2 for c in WL["n"])
-    H = Hierarchy(3, 2, n, WL["levels"] - 1, V)
+    t0 = time.perf_counter()
+    H = Hierarchy(3, 2, WL["n"], WL["levels"], perturbed_vertices())
     lev = H.levels[-1]
-    f = W.fourier_forcing(3, 2, n, seed=WL["seed"]).reshape(-1)
-    mgs, bs = [], []
-    for g in WL["gammas"]:
-        mg = Multigrid(H, gamma_rho=g, kA=WL["kA"], kS=WL["kS"], m=WL["m"], schur_diag=WL["schur_diag"])
-        mgs.append(mg)
-        bs.append(load_vector_nodal(lev, mg.ops[-1], f))
-    times, iters = [], []
+    mg = Multigrid(H, gamma_rho=ORACLE_GAMMA, kA=WL["kA"], kS=WL["kS"], m=WL["m"], schur_diag=WL["schur_diag"])
+    b = load_vector_nodal(lev, mg.ops[-1], forcing())
+    setup_s = time.perf_counter() - t0
+    times, iters = [], None
     for s in range(warmup + steps):
         t0 = time.perf_counter()
-        its = []
-        for mg, b in zip(mgs, bs):
-            _, it, _ = fgmres(lambda v, mg=mg: mg.K @ v, mg.precondition, b, rtol=WL["rtol"], restart=WL["restart"])
-            its.append(it)
+        _, it, _ = fgmres(lambda v: mg.K @ v, mg.precondition, b, rtol=WL["rtol"], restart=WL["restart"])
         dt = time.perf_counter() - t0
         if s >= warmup:
             times.append(dt)
-            iters = its
-    return {"seconds_per_step": sum(times) / len(times), "dofs": lev.size, "solves_per_step": len(WL["gammas"]),
-            "iterations": iters, "steps": steps}
+            iters = it
+    return {"seconds_per_step": sum(times) / len(times), "dofs": lev.size, "solves_per_step": 1,
+            "iterations": iters, "steps": steps, "setup_s": round(setup_s, 2)}
 
 
-def run_oracle_subprocess(steps=1, warmup=0):
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+def host_cpu_info():
+    """Logical CPUs of this host and its CPU model (from /proc/cpuinfo where present)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+                if key == "cpu part" and model is None:
+                    model = "cpu part " + line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return {"nproc": os.cpu_count(), "model": model, "machine": platform.machine()}
+
+
+def _oracle_env(threads):
+    t = str(threads)
+    return dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t)
+
+
+def run_oracle_subprocess(steps=1, warmup=0, threads=1):
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--_oracle-sample", str(steps), str(warmup)],
-                       capture_output=True, text=True, env=env, timeout=3600)
+                       capture_output=True, text=True, env=_oracle_env(threads), timeout=3600)
     if r.returncode != 0:
         raise RuntimeError("oracle sample failed:\n" + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_table_rows():
+    """The CPU-baseline plan's measurements of the oracle (one process, the thread count set by the
+    caller's environment): CSR SpMV MDoF/s on the 2D 16^2 cavity mesh, the 32^3 workload mesh and
+    the channel [0,4]x[0,1]^2 (Q2, 32^3 cells: the per-DoF rate of the 64^3 channel, whose CSR
+    assembly would take minutes), and time-to-solution of the 2D 16^2 problem (FGMRES + one V(3,3)
+    cycle, rtol 1e-10) and of the 32^3 workload for each gamma (rtol 1e-8)."""
+    import numpy as np
+    from oracle.assemble import assemble, load_vector_nodal
+    from oracle.krylov import fgmres
+    from oracle.mesh import Hierarchy, Level
+    from oracle.mg import Multigrid
+    import workloads as W
+    rows = []
+
+    def spmv_rate(K, reps):
+        x = np.random.default_rng(0).uniform(-1, 1, K.shape[0])
+        K @ x
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            K @ x
+        dt = (time.perf_counter() - t0) / reps
+        return K.shape[0] / dt / 1e6
+
+    lev2 = Level(2, 2, (16, 16), W.lattice_vertices(2, (16, 16)))
+    rows.append({"row": "spmv", "config": "2D Q2-Q1 16^2", "dofs": lev2.size,
+                 "mdof_s": spmv_rate(assemble(lev2)["K"], 2000)})
+    lev3 = Level(3, 2, WL["n"], perturbed_vertices())
+    rows.append({"row": "spmv", "config": "3D Q2-Q1 32^3 perturbed", "dofs": lev3.size,
+                 "mdof_s": spmv_rate(assemble(lev3, 1.0, 1e2)["K"], 20)})
+    levc = Level(3, 2, (32, 32, 32), W.lattice_vertices(3, (32, 32, 32), hi=(4.0, 1.0, 1.0)), 0x3F & ~0x2)
+    rows.append({"row": "spmv", "config": "3D Q2-Q1 channel 32^3 cells", "dofs": levc.size,
+                 "mdof_s": spmv_rate(assemble(levc, 1e-3)["K"], 20)})
+    # 2D 16^2, FGMRES + V(3,3) to 1e-10 (manufactured forcing of the 2D case)
+    H2 = Hierarchy(2, 2, (16, 16), 4, W.lattice_vertices(2, (16, 16)))
+    mg2 = Multigrid(H2, kA=3, kS=3, m=2)
+    l2 = H2.levels[-1]
+    ax = W.velocity_lattice(2, 2, (16, 16))
+    Y, X = np.meshgrid(ax[1], ax[0], indexing="ij")
+    f1, f2 = W.mms2d_forcing(X, Y)
+    b2 = load_vector_nodal(l2, mg2.ops[-1], np.stack([f1, f2]).reshape(-1))
+    t0 = time.perf_counter()
+    reps = 20
+    for _ in range(reps):
+        _, it2, _ = fgmres(lambda v: mg2.K @ v, mg2.precondition, b2, rtol=1e-10)
+    rows.append({"row": "solve", "config": "2D Q2-Q1 16^2, FGMRES + V(3,3), rtol 1e-10", "dofs": l2.size,
+                 "seconds": (time.perf_counter() - t0) / reps, "iterations": it2})
+    H3 = Hierarchy(3, 2, WL["n"], WL["levels"], perturbed_vertices())
+    l3 = H3.levels[-1]
+    for g in WL["gammas"]:
+        mg3 = Multigrid(H3, gamma_rho=g, kA=WL["kA"], kS=WL["kS"], m=WL["m"], schur_diag=WL["schur_diag"])
+        b3 = load_vector_nodal(l3, mg3.ops[-1], forcing())
+        t0 = time.perf_counter()
+        _, it3, _ = fgmres(lambda v: mg3.K @ v, mg3.precondition, b3, rtol=WL["rtol"], restart=WL["restart"])
+        rows.append({"row": "solve", "config": f"3D Q2-Q1 32^3 perturbed, gamma {g:g}, FP64-MG FGMRES, rtol 1e-8",
+                     "dofs": l3.size, "seconds": time.perf_counter() - t0, "iterations": it3})
+    return rows
+
+
+def run_cpu_table(args):
+    """The oracle's CPU-baseline table on this host, with 1 thread and with every logical CPU."""
+    info = host_cpu_info()
+    print(json.dumps({"host": info}), flush=True)
+    for threads in (1, info["nproc"] or 1):
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--_cpu-table-rows"], capture_output=True,
+                           text=True, env=_oracle_env(threads), timeout=3600)
+        if r.returncode != 0:
+            print(json.dumps({"threads": threads, "error": r.stderr[-1500:]}), flush=True)
+            continue
+        for row in json.loads(r.stdout.strip().splitlines()[-1]):
+            row["threads"] = threads
+            print(json.dumps(row), flush=True)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -282,9 +334,79 @@ def traffic_record(key, kernel_src_sha):
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("apply.cuh", "apply_col.cuh", "common.cuh"):
+    for f in ("apply.cuh", "apply_col.cuh", "apply_cc.cuh", "common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2205_15770_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
+
+
+# Flops per cell of the full operator K x by sum factorisation and algorithmic bytes per DoF, the
+# scope table's measurement model (FMA = 2 flops; forward + backward 24 (k+1)^4 per scalar field,
+# the pressure sweeps and point terms; trilinear cells add the geometry from the 8 vertices).
+FLOPS_PER_CELL_8D = {("trilinear", 2): 12768, ("affine", 2): 6963, ("affine", 3): 21808, ("affine", 4): 53005}
+BYTES_PER_DOF_8D = {(32, "trilinear"): 8.5, (32, "affine"): 8.0, (64, "trilinear"): 17.0, (64, "affine"): 16.0}
+NOMINAL_BF16_DENSE_TFLOPS = 2250.0  # GB300 dense bf16 tensor rate (nominal)
+LANES_PER_SM = {32: 128, 64: 2}     # FP32 / FP64 FMA lanes per SM (FP64 = 1/64 of FP32)
+KERNEL_NAMES = {
+    "fp32_operator": "full operator K x, FP32, finest level (V-cycle residual and vmult)",
+    "fp64_operator": "full operator K x, FP64, finest level (FGMRES operator; stored per-point geometry)",
+    "fp32_a_block": "A block, FP32, finest level (the V-cycle's most frequent application)",
+}
+
+
+def alu_peak_tflops(prec, sm_count, mhz):
+    """FMA peak from the unit counts and the clock: SMs x lanes x 2 flops x clock."""
+    return sm_count * LANES_PER_SM[prec] * 2 * mhz * 1e6 / 1e12
+
+
+def roofline_entry(key, prec, blocks, avg_ms, n_cells, n_dofs, sm_count, mhz, fma_tflops, peaks, sha, shape):
+    geom = "trilinear"
+    e = {"kernel": KERNEL_NAMES[key], "launch_shape": shape, "avg_launch_us": round(avg_ms * 1e3, 2)}
+    peak = alu_peak_tflops(prec, sm_count, mhz)
+    bf16 = (peaks or {}).get("bf16_tflops")
+    nominal = alu_peak_tflops(prec, 152, 2070.0)
+    if blocks == 7:
+        fl = FLOPS_PER_CELL_8D[(geom, WL["k"])] * n_cells
+        by = BYTES_PER_DOF_8D[(prec, geom)] * n_dofs
+        ach = fl / (avg_ms / 1e3) / 1e12
+        e.update({"bound": "alu", "achieved": round(ach, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+                  "frac": round(ach / peak, 4), "flops_per_launch": fl, "algorithmic_bytes_per_launch": by,
+                  "peak_source": f"derived: {sm_count} SMs x {LANES_PER_SM[prec]} FP{prec} lanes x 2 x {mhz:.0f} MHz",
+                  "frac_of_measured_fma": round(ach / fma_tflops, 4),
+                  "measured_fma_tflops": round(fma_tflops, 3)})
+        if bf16:
+            dv = bf16 * nominal / NOMINAL_BF16_DENSE_TFLOPS
+            e["peak_from_measured_bf16"] = round(dv, 4)
+            e["frac_of_peak_from_measured_bf16"] = round(ach / dv, 4)
+        hbm = (peaks or {}).get("hbm_gbs", FALLBACK_HBM_GBS)
+        e["hbm_frac_algorithmic"] = round(by / (avg_ms / 1e3) / 1e9 / hbm, 4)
+    tr = traffic_record(key, sha)
+    e["traffic"] = tr
+    if tr and blocks == 7:
+        e["traffic_over_algorithmic_bytes"] = round(tr / e["algorithmic_bytes_per_launch"], 2)
+    share = launch_share(key)
+    if share is not None:
+        e["launch_list_share"] = share
+    return e
+
+
+def roofline_object(rl, peaks, peaks_src):
+    """The kernel with the largest share of the committed launch list leads; the others follow."""
+    order = sorted(rl, key=lambda k: -(rl[k].get("launch_list_share") or 0.0))
+    lead = next(k for k in order if "frac" in rl[k])
+    out = dict(rl[lead])
+    out["key"] = lead
+    out["others"] = {k: rl[k] for k in order if k != lead}
+    out["hbm_peak_gbs"] = (peaks or {}).get("hbm_gbs", FALLBACK_HBM_GBS)
+    out["hbm_peak_source"] = peaks_src
+    return out
+
+
+def launch_share(key):
+    p = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    try:
+        return json.load(open(p)).get(key, {}).get("launch_share")
+    except Exception:
+        return None
 
 
 # ---------------------------------------------------------------------------------------------
@@ -397,28 +519,26 @@ def run_ours(args):
         e1.synchronize()
         vm[f"fp{prec}"] = N / (e0.elapsed_time(e1) / reps / 1e3) / 1e6
 
-    # --- rooflines: the FP64 full operator of the FGMRES loop (the largest launch-list share) and
-    # the FP32 A-block apply the V-cycle repeats, both on the finest level ----------------------
+    # --- rooflines on the finest level, in the terms of the scope table's measurement row:
+    # flops per cell of the full operator K x (sum factorisation, FMA = 2 flops; trilinear Q2:
+    # 12,768) and algorithmic bytes per DoF (x read + y written: FP32 8.5, FP64 17 with the
+    # vertices); ALU peaks from the unit counts and the clock, beside the FP32 / FP64 rates derived
+    # from the measured bf16 peak by the nominal ratio and the library's FMA probe --------------
     S = S32[1]
-    S.time_apply(1, precision=32, reps=20)
-    avg_ms = S.time_apply(1, precision=32, reps=200)
     n_cells = WL["n"][0] * WL["n"][1] * WL["n"][2]
-    fl = flops_per_cell_A(WL["k"], True) * n_cells
-    achieved = fl / (avg_ms / 1e3) / 1e12
     props = torch.cuda.get_device_properties(local)
     max_mhz = clk["sm_max_mhz"] if clk else 2070.0
-    peak = fp32_peak_tflops(props.multi_processor_count, max_mhz)
-    sha = kernel_source_sha()
-    traffic = traffic_record("fp32_a_block", sha)
-    traffic64 = traffic_record("fp64_operator", sha)
-    avg64 = S.time_apply(1, precision=64, reps=10)
-    S.time_apply(7, precision=64, reps=3)
-    avg64_full = S.time_apply(7, precision=64, reps=20)
-    fl64 = flops_per_cell_full(WL["k"]) * n_cells
-    peak64 = FP64_NOMINAL_TFLOPS * max_mhz / 2070.0
-    # the FMA rates this GPU sustains (microbenchmark in the library), beside the derived peaks
     from paper_2205_15770_gb300 import fma_peak
-    fma32, fma64 = fma_peak(32), fma_peak(64)
+    fma = {32: fma_peak(32), 64: fma_peak(64)}
+    peaks, peaks_src = measured_peaks()
+    sha = kernel_source_sha()
+    rl = {}
+    for key, prec, blocks, reps in (("fp32_operator", 32, 7, 200), ("fp64_operator", 64, 7, 20),
+                                    ("fp32_a_block", 32, 1, 200)):
+        S.time_apply(blocks, precision=prec, reps=max(3, reps // 10))
+        avg = S.time_apply(blocks, precision=prec, reps=reps)
+        rl[key] = roofline_entry(key, prec, blocks, avg, n_cells, N, props.multi_processor_count, max_mhz, fma[prec],
+                                 peaks, sha, S.launch_shapes(prec)[-1])
 
     # --- batched multi-mesh solves (16 unit-cube meshes of uneven size, seeded) -----------------
     batched = run_batched(args) if not args.no_extras else None
@@ -442,11 +562,6 @@ def run_ours(args):
     e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world, device="cuda")
     e2e_val = replica_throughput(e2e_s * 1e3, world, solves, N)
 
-    peaks, peaks_src = measured_peaks()
-    hbm_peak = (peaks or {}).get("hbm_gbs", FALLBACK_HBM_GBS)
-    # FP64 operator bytes: x read, y written, and the stored per-point geometry (16 values per
-    # Gauss point) read once
-    bytes64 = 2 * N * 8 + n_cells * 16 * (WL["k"] + 1) ** 3 * 8
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "MDoF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3), "higher_is_better": True, "scaling": "weak",
@@ -462,26 +577,7 @@ def run_ours(args):
         "iterations_fp64_mg": it64, "fp32_vs_fp64_mg_solution_rel_diff": diff,
         "vmult_mdof_s": {k2: round(v, 1) for k2, v in vm.items()},
         "setup_s_per_context": round(setup_s, 3),
-        "roofline": {"bound": "alu",
-                     "kernel": "stokes_cell_apply_col<2,double,A+B^T+B,trilinear> (FGMRES operator, stored geometry)",
-                     "achieved": round(fl64 / (avg64_full / 1e3) / 1e12, 4), "peak": round(peak64, 3),
-                     "unit": "TFLOP/s", "frac": round(fl64 / (avg64_full / 1e3) / 1e12 / peak64, 4),
-                     "traffic": traffic64, "avg_launch_us": round(avg64_full * 1e3, 2), "flops_per_launch": fl64,
-                     "algorithmic_bytes_per_launch": bytes64,
-                     "peak_source": f"nominal FP64 {FP64_NOMINAL_TFLOPS} TFLOP/s (GB300) scaled to {max_mhz:.0f} MHz",
-                     "hbm_frac": round(bytes64 / (avg64_full / 1e3) / 1e9 / hbm_peak, 4),
-                     "measured_fma_tflops": {"fp32": round(fma32, 2), "fp64": round(fma64, 3),
-                                             "source": "stokes_fma_peak (8 FMA chains per thread, 8 CTAs per SM)"},
-                     "frac_of_measured_fma": round(fl64 / (avg64_full / 1e3) / 1e12 / fma64, 4),
-                     "fp32_a_block": {
-                         "bound": "alu", "kernel": "stokes_cell_apply_col<2,float,A,trilinear> (A block, V-cycle)",
-                         "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-                         "frac": round(achieved / peak, 4), "frac_of_measured_fma": round(achieved / fma32, 4),
-                         "traffic": traffic,
-                         "avg_launch_us": round(avg_ms * 1e3, 2), "flops_per_launch": fl,
-                         "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x 2 x {max_mhz:.0f} MHz"},
-                     "fp64_a_block_avg_launch_us": round(avg64 * 1e3, 2),
-                     "hbm_peak_gbs": hbm_peak, "hbm_peak_source": peaks_src},
+        "roofline": roofline_object(rl, peaks, peaks_src),
         "e2e": {"value": round(e2e_val, 3), "unit": "MDoF/s", "h2d_bytes_per_step": solves * N * 8,
                 "d2h_bytes_per_step": solves * N * 8},
         "gpu_launches": int(launches),
@@ -494,13 +590,13 @@ def run_ours(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
-            o = run_oracle_subprocess(3, 0)
-            out["cpu_baseline"] = {"value": round(o["solves_per_step"] * o["dofs"] / o["seconds_per_step"] / 1e6, 4),
+            o = run_oracle_subprocess(1, 0, threads=1)
+            out["cpu_baseline"] = {"value": round(o["dofs"] / o["seconds_per_step"] / 1e6, 4),
                                    "unit": "MDoF/s", "cores": 1, "kind": "oracle",
-                                   "sample": ("3 steps of 3 FP64-MG FGMRES solves to 1e-8 (gamma 0, 1e2, 1e4) on the "
-                                              "16^3 level of the same perturbed hierarchy (112,724 DoFs, 4 levels), "
-                                              "same smoother and Schur diagonal, numpy/scipy, 1 thread; setup untimed"),
-                                   "iterations": o["iterations"]}
+                                   "sample": ("one FP64-MG FGMRES(30) solve to 1e-8 of the same 32^3 workload "
+                                              f"(859,812 DoFs, 5 levels) at gamma {ORACLE_GAMMA:g}, same smoother "
+                                              "and Schur diagonal, numpy/scipy, 1 thread; setup untimed"),
+                                   "iterations": o["iterations"], "same_config": True, "host": host_cpu_info()}
         except Exception as e:  # report, do not hide
             out["cpu_baseline"] = {"value": None, "error": str(e)[-300:]}
     if rank == 0:
@@ -685,26 +781,34 @@ def run_paper_sweep(args):
 
 
 def run_schur_sweep(args):
-    """The paper's comparison of Schur-complement diagonals (Sec. 4.3, "Different diagonal
-    approximations"): 2D driven cavity, Q2-Q1 on 16^2 (2,467 DoFs, 4 levels), stationary FP64
-    W-cycle multigrid from x = 0; Jacobi (k_A = k_S = 0) and Chebyshev degree 3; smoothing steps
-    m in {1, 2, 4, 8, 16}; D_S~ in {loc, p, d, exact}: rate q = (r^j / r^{j-3})^(1/3)."""
+    """The paper's comparison of Schur-complement diagonals on its two 2D problems: the laser beam
+    (Sec. 4.2: unit square, mu = 0.0022, u_D = 0, Gaussian force c1 exp(-c2 |x - x0|^2) in y at
+    x0 = (0.75, 0.75)) and the driven cavity (Sec. 4.3.2), both Q2-Q1 on 16^2 (2,467 DoFs, 4 levels),
+    stationary FP64 W-cycle multigrid from x = 0; Jacobi (k_A = k_S = 0) and Chebyshev degree 3;
+    smoothing steps m in {1, 2, 4, 8, 16}; D_S~ in {loc, p, d, exact}: rate q = (r^j / r^{j-3})^(1/3)."""
     import torch
+    import workloads as W
     from paper_2205_15770_gb300 import StokesMG
     dim, n, levels = 2, 16, 4
-    for kdeg in (0, 3):
-        for diag in ("loc", "p", "d", "exact"):
-            for m in (1, 2, 4, 8, 16):
-                S = StokesMG(dim=dim, n=(n,) * dim, n_levels=levels, k=2, kA=kdeg, kS=kdeg, m=m, cycle="W",
-                             schur_diag=diag, vcycle_fp32=False)
-                uD = cavity_lid(S, dim, n)
-                b = S.lift_rhs(uD, torch.zeros_like(uD))
-                _, it, hist, q = S.mg_iterate(b, torch.zeros_like(b), max_iter=15, reduction=1e-10,
-                                              allow_divergence=True)
-                ok = bool(hist) and 0 < q < 1
-                print(json.dumps({"dofs": S.size(), "k": kdeg, "diag": diag, "m": m, "iterations": it,
-                                  "q": round(q, 4) if ok else None}), flush=True)
-                S.close()
+    for problem in ("laser", "cavity"):
+        for kdeg in (0, 3):
+            for diag in ("loc", "p", "d", "exact"):
+                for m in (1, 2, 4, 8, 16):
+                    mu = 0.0022 if problem == "laser" else 1.0
+                    S = StokesMG(dim=dim, n=(n,) * dim, n_levels=levels, k=2, mu=mu, kA=kdeg, kS=kdeg, m=m,
+                                 cycle="W", schur_diag=diag, vcycle_fp32=False)
+                    if problem == "laser":
+                        f = torch.as_tensor(W.laser_beam_forcing((n, n)).reshape(-1), device="cuda")
+                        b = S.mass_rhs(f)
+                    else:
+                        uD = cavity_lid(S, dim, n)
+                        b = S.lift_rhs(uD, torch.zeros_like(uD))
+                    _, it, hist, q = S.mg_iterate(b, torch.zeros_like(b), max_iter=15, reduction=1e-10,
+                                                  allow_divergence=True)
+                    ok = bool(hist) and 0 < q < 1
+                    print(json.dumps({"problem": problem, "dofs": S.size(), "k": kdeg, "diag": diag, "m": m,
+                                      "iterations": it, "q": round(q, 4) if ok else None}), flush=True)
+                    S.close()
 
 
 def run_variants(args):
@@ -807,10 +911,12 @@ def run_channel(args):
     peaks, src = measured_peaks()
     hbm = (peaks or {}).get("hbm_gbs", FALLBACK_HBM_GBS)
     props = torch.cuda.get_device_properties(0)
-    p32 = fp32_peak_tflops(props.multi_processor_count, 2070.0)
+    pk = {prec: alu_peak_tflops(prec, props.multi_processor_count, 2070.0) for prec in (32, 64)}
     out = {"workload": "channel [0,4]x[0,1]^2, 64^3 hexes, mu 1e-3, inflow 16y(1-y)z(1-z), do-nothing outflow",
-           "hbm_peak_gbs": hbm, "hbm_peak_source": src, "fp32_peak_tflops": round(p32, 2),
-           "fp64_peak_tflops": FP64_NOMINAL_TFLOPS, "k": {}}
+           "hbm_peak_gbs": hbm, "hbm_peak_source": src, "fp32_peak_tflops": round(pk[32], 2),
+           "fp64_peak_tflops": round(pk[64], 3),
+           "flops_model": "full operator K x per affine cell: k=2 6,963, k=3 21,808, k=4 53,005 flops",
+           "k": {}}
     # k = 2, 3, 4 on 64^3 cells, and the Q2 size sweep's 128^3 point (53.1M DoFs, 7 levels)
     for n, k in ((64, 2), (64, 3), (64, 4), (128, 2)):
         nl = 6 if n == 64 else 7
@@ -833,13 +939,12 @@ def run_channel(args):
             e1.synchronize()
             ms = e0.elapsed_time(e1) / reps
             kern = S.time_apply(7, precision=prec, reps=reps)
-            bytes_alg = 2 * N * (4 if prec == 32 else 8)
-            tflops = flops_per_cell_full(k) * n ** 3 / (kern / 1e3) / 1e12
+            bytes_alg = BYTES_PER_DOF_8D[(prec, "affine")] * N
+            tflops = FLOPS_PER_CELL_8D[("affine", k)] * n ** 3 / (kern / 1e3) / 1e12
             row[f"fp{prec}"] = {"vmult_ms": round(ms, 3), "mdof_s": round(N / (ms / 1e3) / 1e6, 1),
-                                "kernel_ms": round(kern, 3),
+                                "kernel_ms": round(kern, 3), "launch_shape": S.launch_shapes(prec)[-1],
                                 "hbm_frac_of_kernel": round(bytes_alg / (kern / 1e3) / 1e9 / hbm, 4),
-                                "tflops": round(tflops, 3),
-                                "alu_frac": round(tflops / (p32 if prec == 32 else FP64_NOMINAL_TFLOPS), 4)}
+                                "tflops": round(tflops, 3), "alu_frac": round(tflops / pk[prec], 4)}
         if k == 3:
             nodes = S.velocity_nodes()
             nu, _ = S.sizes()
@@ -882,33 +987,41 @@ def run_kernel_only(args):
     S = StokesMG(dim=3, n=WL["n"], n_levels=WL["levels"], k=WL["k"], vertices=perturbed_vertices(), gamma_rho=1e2,
                  kA=WL["kA"], kS=WL["kS"], m=WL["m"], schur_diag=WL["schur_diag"])
     prec = args.kernel_precision
-    mode = 1 if prec == 32 else 7
+    mode = args.kernel_mode if args.kernel_mode else (1 if prec == 32 else 7)
+    # the finest level's launch shape is pinned (a profiler changes the setup's timings): the
+    # cell-component kernel in FP32, the 4-warp column kernel with stored geometry in FP64
+    shape = args.kernel_shape if args.kernel_shape else (5 if prec == 32 else 4)
+    S.set_launch_shape(WL["levels"] - 1, shape, precision=prec)
     S.time_apply(mode, precision=prec, reps=3)
     torch.cuda.synchronize()
     torch.cuda.profiler.start()
     ms = S.time_apply(mode, precision=prec, reps=3)
     torch.cuda.profiler.stop()
-    print(json.dumps({"kernel": "stokes_cell_apply_col " + ("A block fp32" if prec == 32 else "full operator fp64"),
+    print(json.dumps({"kernel": f"cell kernel, blocks {mode}, FP{prec}, launch shape {S.launch_shapes(prec)[-1]}",
                       "avg_launch_us": ms * 1e3, "cells": WL["n"][0] * WL["n"][1] * WL["n"][2]}))
     S.close()
 
 
 def run_reference(args):
+    """The oracle as the reference arm: each step one FP64-MG FGMRES solve of the 32^3 workload at
+    gamma = 1e2 (the CPU program is bounded to one untimed warm-up solve at most)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    o = run_oracle_subprocess(args.steps, args.warmup)
-    value = o["solves_per_step"] * o["dofs"] / o["seconds_per_step"] / 1e6
+    warm = min(args.warmup, 1)
+    o = run_oracle_subprocess(args.steps, warm, threads=1)
+    value = o["dofs"] / o["seconds_per_step"] / 1e6
+    sample = (f"each step: one FP64-MG FGMRES(30) solve to 1e-8 of the 32^3 workload at gamma {ORACLE_GAMMA:g} "
+              "(859,812 DoFs, 5 levels), numpy/scipy, 1 thread; setup untimed")
     out = {
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "MDoF/s",
-        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": warm,
         "ms_per_step": round(o["seconds_per_step"] * 1e3, 1), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "dofs_per_solve": o["dofs"], "solves_per_step": o["solves_per_step"],
+        "config": {"workload": WORKLOAD_NAME, "dofs_per_solve": o["dofs"], "solves_per_step": 1,
                    "parallelism": "single"},
-        "cpu_baseline": {"value": round(value, 4), "unit": "MDoF/s", "cores": 1, "kind": "oracle",
-                         "sample": ("each step: 3 FP64-MG FGMRES solves to 1e-8 (gamma 0, 1e2, 1e4) on the 16^3 "
-                                    "level of the same perturbed hierarchy (112,724 DoFs), numpy/scipy, 1 thread")},
+        "cpu_baseline": {"value": round(value, 4), "unit": "MDoF/s", "cores": 1, "kind": "oracle", "sample": sample,
+                         "host": host_cpu_info()},
         "e2e": {"value": round(value, 4), "unit": "MDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "iterations": o["iterations"],
     }
@@ -928,7 +1041,7 @@ def main():
     ap.add_argument("--variants", action="store_true",
                     help="32^3 workload in the symmetric-gradient form and with a stabilisation block: solve, vmult")
     ap.add_argument("--schur-sweep", action="store_true",
-                    help="2D cavity 16^2: rates q for the Schur diagonals loc/p/d/exact, k = 0 and 3, m = 1..16")
+                    help="2D laser beam and cavity 16^2: rates q for the Schur diagonals loc/p/d/exact, k = 0, 3, m = 1..16")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed steps by cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--channel", action="store_true",
@@ -939,12 +1052,25 @@ def main():
                     help="time-to-1e-8 of the workload for a list of (k_A, k_S, m); prints one JSON line each")
     ap.add_argument("--kernel-precision", type=int, choices=(32, 64), default=32,
                     help="with --kernel-only: the FP32 A block (32) or the FP64 full operator (64)")
+    ap.add_argument("--kernel-mode", type=int, default=0,
+                    help="with --kernel-only: the block bit set (1 A, 2 B^T, 4 B, 7 full; default 1 / 7 by precision)")
+    ap.add_argument("--kernel-shape", type=int, default=0,
+                    help="with --kernel-only: the finest level's launch shape (default 5 in FP32, 4 in FP64)")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only launch the dominant kernel inside a profiler range (for ncu --set full)")
+    ap.add_argument("--cpu-table", action="store_true",
+                    help="the oracle's CPU-baseline table on this host (SpMV rates, solve times; 1 and all threads)")
     ap.add_argument("--_oracle-sample", nargs=2, type=int, default=None, dest="oracle_sample")
+    ap.add_argument("--_cpu-table-rows", action="store_true", dest="cpu_table_rows")
     args = ap.parse_args()
     if args.oracle_sample is not None:
         print(json.dumps(oracle_sample(*args.oracle_sample)))
+        return
+    if args.cpu_table_rows:
+        print(json.dumps(cpu_table_rows()))
+        return
+    if args.cpu_table:
+        run_cpu_table(args)
         return
     if args.warmup < 3 and args.impl == "ours":
         ap.error("--warmup must be >= 3")

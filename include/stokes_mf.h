@@ -148,7 +148,9 @@ int stokes_smooth(stokes_ctx *ctx, int level, int precision, int steps, const vo
  * contents (the used part is cleared at the start of each call): calls that overlap on the GPU --
  * different streams, contexts or host threads -- race on it.  The array's device address is looked
  * up once per device (in stokes_setup, or by the first call on a device that had no setup); make
- * that first call before any stream capture. */
+ * that first call before any stream capture.  Call it with the context's device current (the one
+ * current at stokes_setup): the array has one instance per device, and another device's instance
+ * is rejected with STOKES_EINVAL. */
 int stokes_smooth_noalloc(stokes_ctx *ctx, int level, int precision, int steps, const void *b,
                           void *x, void *stream);
 

@@ -434,8 +434,10 @@ class StokesBatch:
         if st != 0:
             raise StokesError(st, self._lib.stokes_batch_last_error(self._bt).decode())
 
-    def solve(self, bs, xs=None, rtol=1e-8, maxit=200):
-        """Solve all members; bs, xs: lists of float64 CUDA tensors.  Returns (xs, iterations, rel residuals)."""
+    def solve(self, bs, xs=None, rtol=1e-8, maxit=200, check=True):
+        """Solve all members; bs, xs: lists of float64 CUDA tensors.  Returns (xs, iterations, rel residuals);
+        with check=False a failing member raises nothing and the status (the first non-OK member's,
+        0 if none) is returned as a fourth value."""
         torch = _torch()
         xs = [torch.zeros_like(b) for b in bs] if xs is None else xs
         nm = self.n_meshes
@@ -443,9 +445,15 @@ class StokesBatch:
         xp = (C.c_void_p * nm)(*[_ptr(x, torch.float64).value for x in xs])
         its = (C.c_int * nm)()
         rel = (C.c_double * nm)()
-        self._check(self._lib.stokes_solve_batch(self._bt, bp, xp, float(rtol), int(maxit), its, rel,
-                                                 StokesMG._stream()))
+        st = self._lib.stokes_solve_batch(self._bt, bp, xp, float(rtol), int(maxit), its, rel, StokesMG._stream())
+        if not check:
+            return xs, list(its), list(rel), st
+        self._check(st)
         return xs, list(its), list(rel)
+
+    @property
+    def last_error(self):
+        return self._lib.stokes_batch_last_error(self._bt).decode()
 
     @property
     def krylov_mode(self):

@@ -213,6 +213,7 @@ using namespace smf;
 
 struct stokes_ctx {
   int dim = 0, k = 0, nl = 0;
+  int device = -1;  // the CUDA device that was current at setup (every buffer lives there)
   stokes_opts o{};
   double mu = 1, gamma_rho = 0;
   double c_mass = 0, c_grad = 0;  // stabilisation block C (0: none)
@@ -1475,11 +1476,13 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
         const char *gs = getenv("STOKES_GEO");
         const bool g64 = !(gs && std::strcmp(gs, "none") == 0);
         const long long per = 16LL * (k + 1) * (k + 1) * (k + 1), cells = d.n_cells;
-        // stored when it takes at most a quarter of the device memory still free (7.2 GB for a
-        // trilinear 128^3 level; HBM-resident rather than recomputed in FP64)
+        // stored when it takes at most 1/16 of the device's memory (17.8 GB on a GB300; 7.2 GB for
+        // a trilinear 128^3 level), a fixed budget so that the choice does not depend on what other
+        // processes hold; skipped only when it would take more than half of the memory still free
         size_t free_b = 0, total_b = 0;
-        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
-        if (g64 && cells * per * (long long)sizeof(double) <= (long long)(free_b / 4)) {
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = total_b = 0;
+        const long long gbytes = cells * per * (long long)sizeof(double);
+        if (g64 && gbytes <= (long long)(total_b / 16) && gbytes <= (long long)(free_b / 2)) {
           if ((st = dalloc(C, &geo_l, cells * per))) return st;
           launch_col_geometry<double>(d, geo_l, C->s);
           SMF_CUDA_OK(cudaGetLastError());
@@ -2439,6 +2442,10 @@ int stokes_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho, co
   }
   cudaStream_t user = (cudaStream_t)stream;
   cudaStreamSynchronize(user);
+  if (cudaGetDevice(&C->device) != cudaSuccess) {
+    cudaGetLastError();
+    C->device = -1;
+  }
   int st = do_setup(mesh, k, mu, gamma_rho, mu_cell, opts, C);
   if (st == STOKES_OK) {
     cudaError_t e = cudaGetLastError();
@@ -2563,6 +2570,15 @@ int stokes_smooth_noalloc(stokes_ctx *C, int level, int precision, int steps, co
     set_error("stokes_smooth_noalloc: level " + std::to_string(level) + " needs " + std::to_string(need) +
               " bytes of smoother scratch, more than the " + std::to_string(kNoAllocScratchBytes) +
               " bytes of the static scratch array; use stokes_smooth");
+    C->err = g_last_error;
+    return STOKES_EINVAL;
+  }
+  // the static array has one instance per device: use the context's, which needs its device current
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != C->device) {
+    cudaGetLastError();
+    set_error("stokes_smooth_noalloc: make the context's device (" + std::to_string(C->device) +
+              ") current before the call");
     C->err = g_last_error;
     return STOKES_EINVAL;
   }

@@ -97,18 +97,29 @@ def test_stationary_driver_with_each_schur_diagonal(diag):
 
 
 def test_w_cycle_stationary_rates_close_to_v_cycle():
-    # Sec. 4.3.4: the V-cycle gives almost the same rates as the W-cycle
+    """Sec. 4.3.4: the V-cycle gives almost the same rate as the W-cycle.  The rates themselves are
+    pinned to the oracle's stationary iteration (same mesh, data and smoother): for (k_A, k_S, m) =
+    (1, 1, 2) with the local Schur diagonal in 3D both are q = 0.598, in line with the paper's 3D
+    finding that this setting converges at q ~ 0.6 (Sec. 4.5; the GPU sweep of the 3D cavity gives
+    0.60 as well), so the bound is q < 0.65 rather than a bound taken from 2D settings."""
+    from oracle.assemble import load_vector_nodal
+    from oracle.mg import Multigrid
     case = CASES["3d_q2_pert"]
     H = oracle_hierarchy(case)
     lev = H.levels[-1]
+    fn = W.fourier_forcing(3, 2, case["n"], seed=3).reshape(-1)
     qs = {}
     for cyc in ("V", "W"):
         S = gpu_solver(case, kA=1, kS=1, m=2, cycle=cyc)
-        f = torch.as_tensor(W.fourier_forcing(3, 2, case["n"], seed=3).reshape(-1), device="cuda")
-        b = S.mass_rhs(f)
+        b = S.mass_rhs(torch.as_tensor(fn, device="cuda"))
         _, it, hist, q = S.mg_iterate(b, max_iter=15, reduction=1e-10)
         qs[cyc] = q
         assert hist[-1] <= 1e-7 * hist[0]  # at most 15 cycles, as in the paper's protocol
+        mg = Multigrid(H, gamma_rho=case["gamma_rho"], kA=1, kS=1, m=2, cycle=cyc)
+        _, res, q_or = mg.stationary(load_vector_nodal(lev, mg.ops[-1], fn))
+        assert abs(q - q_or) < 1e-6, (cyc, q, q_or)
+        S.close()
+    assert qs["V"] < 0.65, qs
     assert abs(qs["W"] - qs["V"]) <= 0.05, qs
 
 
@@ -163,3 +174,31 @@ def test_device_krylov_loop_matches_host_loop(monkeypatch, fp32):
         S.close()
     assert out[False][1] == out[True][1]
     assert np.abs(out[False][0] - out[True][0]).max() <= 1e-10 * np.abs(out[True][0]).max()
+
+
+@pytest.mark.parametrize("diag,kdeg,m", [("loc", 0, 4), ("p", 3, 1), ("d", 3, 2), ("exact", 3, 1)])
+def test_laser_beam_stationary_driver_matches_oracle(diag, kdeg, m):
+    """The laser-beam problem of Sec. 4.2 (unit square, Q2-Q1 on 16^2 = 2467 DoFs, mu = 0.0022,
+    u_D = 0, Gaussian force at (0.75, 0.75)): the GPU stationary FP64 W-cycle iteration against the
+    oracle's for each Schur diagonal, residual histories within 1e-6 and the rate q within 1e-6."""
+    from oracle.assemble import load_vector_nodal
+    from oracle.mesh import Hierarchy
+    from oracle.mg import Multigrid
+    from paper_2205_15770_gb300 import StokesMG
+    mu = 0.0022
+    H = Hierarchy(2, 2, (16, 16), 4, W.lattice_vertices(2, (16, 16)))
+    mg = Multigrid(H, mu=mu, kA=kdeg, kS=kdeg, m=m, cycle="W", schur_diag=diag)
+    lev = H.levels[-1]
+    assert lev.size == 2467
+    fn = W.laser_beam_forcing((16, 16)).reshape(-1)
+    b = load_vector_nodal(lev, mg.ops[-1], fn)
+    _, res_o, q_o = mg.stationary(b)
+    S = StokesMG(dim=2, n=(16, 16), n_levels=4, k=2, mu=mu, kA=kdeg, kS=kdeg, m=m, cycle="W", schur_diag=diag,
+                 vcycle_fp32=False)
+    bg = S.mass_rhs(_t(fn))
+    assert rel_err(bg.cpu().numpy(), b) < 1e-12
+    _, it, hist, q = S.mg_iterate(bg, max_iter=15, reduction=1e-10, allow_divergence=True)
+    assert it == len(res_o) - 1
+    np.testing.assert_allclose(hist, res_o, rtol=1e-6, atol=1e-14 * res_o[0])
+    assert abs(q - q_o) < 1e-6
+    S.close()

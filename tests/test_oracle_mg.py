@@ -113,3 +113,78 @@ def test_schur_diagonal_choices_follow_the_papers_comparison():
         assert q[(3, m, "loc")] > q[(3, m, "exact")]
     for diag in ("loc", "p", "d", "exact"):
         assert q[(3, 2, diag)] < q[(3, 1, diag)] < 1
+
+
+# ---- exact pin of Algorithm 1: the cycle's error propagation operator ----------------------------
+def _dense_smoother_propagation(sm, K):
+    """S = I - M_s K for one compact-form Uzawa step (Sec. 3.3.1, K_hat), written from the dense
+    A^-1_hat and S^-1_hat: for a residual (r_u, r_p),
+        dp = S^-1_hat (B A^-1_hat r_u - r_p),  du = A^-1_hat (r_u - B^T dp)."""
+    Ai, Si = sm.dense_Ainv_hat(), sm.dense_Sinv_hat()
+    B = sm.B.toarray()
+    Cm = sm.C.toarray()
+    nu, npr = Ai.shape[0], Si.shape[0]
+    # dp = Si (B Ai r_u - r_p - C p)  -- with C = 0 here the pressure residual is g - B u
+    M = np.zeros((nu + npr, nu + npr))
+    M[nu:, :nu] = Si @ B @ Ai
+    M[nu:, nu:] = -Si
+    M[:nu, :nu] = Ai - Ai @ B.T @ M[nu:, :nu]
+    M[:nu, nu:] = -Ai @ B.T @ M[nu:, nu:]
+    assert np.abs(Cm).max() == 0.0
+    return np.eye(nu + npr) - M @ K.toarray()
+
+
+def _bordered_pinv(lev, K):
+    """The coarse direct solve as a matrix: top-left block of inv([K e; e^T 0]), e = (0, 1_p) when
+    the constant pressure spans the kernel, else inv(K) (numpy, independent of the oracle's LU)."""
+    Kd = K.toarray()
+    if not lev.has_pressure_kernel():
+        return np.linalg.inv(Kd)
+    e = np.concatenate([np.zeros(lev.n_u), np.ones(lev.n_p)])
+    Kb = np.block([[Kd, e[:, None]], [e[None, :], np.zeros((1, 1))]])
+    return np.linalg.inv(Kb)[: lev.size, : lev.size]
+
+
+def _cycle_propagation(mg, l, gamma):
+    """E_l = S_l^m (I - P_l (I - E_{l-1}^gamma) K_{l-1}^+ P_l^T K_l) S_l^m, E_0 = 0 (exact coarse
+    solve): the error propagation of Algorithm 1 (pre-smoothing, residual, restriction, gamma
+    recursive calls from zero, prolongation and correction, post-smoothing)."""
+    if l == 0:
+        return np.zeros((mg.hier.levels[0].size,) * 2)
+    K = mg.ops[l]["K"]
+    S = np.linalg.matrix_power(_dense_smoother_propagation(mg.smoothers[l], K), mg.m)
+    P = mg.P[l].toarray()
+    Ec = _cycle_propagation(mg, l - 1, gamma)
+    lc = mg.hier.levels[l - 1]
+    inner = (np.eye(lc.size) - np.linalg.matrix_power(Ec, gamma)) @ _bordered_pinv(lc, mg.ops[l - 1]["K"])
+    return S @ (np.eye(K.shape[0]) - P @ inner @ P.T @ K.toarray()) @ S
+
+
+@pytest.mark.parametrize("dim,n,levels,cycle,diag", [(2, 4, 2, "V", "loc"), (3, 4, 2, "V", "d"),
+                                                     (2, 8, 3, "V", "d"), (2, 8, 3, "W", "loc")])
+def test_cycle_error_propagation_is_algorithm_1(dim, n, levels, cycle, diag):
+    """One oracle cycle maps the error x - x* to E (x - x*), E formed densely from the smoother,
+    transfer and coarse-solve matrices in the order of Algorithm 1, to 1e-12.  A dropped or
+    reordered step (smoothing on one side only, a missing restriction or correction, the wrong
+    number of recursive calls) changes E."""
+    H, mg, lev, _ = _problem(dim, n, levels, perturb=True, gamma_rho=3.0, kA=2, kS=1, m=2, cycle=cycle,
+                             schur_diag=diag)
+    rng = np.random.default_rng(7)
+    free = ~lev.constrained()
+    x_true = rng.standard_normal(lev.size) * free
+    b = mg.K @ x_true
+    x0 = rng.standard_normal(lev.size) * free
+    x1 = mg.cycle(levels - 1, x0, b)
+    E = _cycle_propagation(mg, levels - 1, mg.gamma)
+    pred = E @ (x0 - x_true)
+    err = np.abs((x1 - x_true) - pred).max() / np.abs(pred).max()
+    assert err < 1e-12, err
+    # the pin is sharp: the cycle without its post-smoothing, or with the other number of recursive
+    # calls, is far from E
+    K = mg.ops[-1]["K"]
+    S = np.linalg.matrix_power(_dense_smoother_propagation(mg.smoothers[-1], K), mg.m)
+    E_nopost = np.linalg.solve(S, E)
+    assert np.abs(E_nopost @ (x0 - x_true) - pred).max() / np.abs(pred).max() > 1e-3
+    if levels == 3:
+        E_other = _cycle_propagation(mg, levels - 1, 3 - mg.gamma)
+        assert np.abs(E_other @ (x0 - x_true) - pred).max() / np.abs(pred).max() > 1e-3

@@ -22,11 +22,16 @@ def _t(a, dtype):
 
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 2e-5)])
 @pytest.mark.parametrize("kA,kS", [(3, 3), (1, 2)])  # (1, 2): the fused smoother
-def test_noalloc_smoothing_matches_stokes_smooth_on_two_calls(dtype, tol, kA, kS):
+def test_noalloc_smoothing_matches_stokes_smooth_on_two_calls(monkeypatch, dtype, tol, kA, kS):
     case = CASES["3d_q2_pert"]
     H = oracle_hierarchy(case)
+    if kA == 1:
+        # no setup timing: the fused form is kept wherever eligible, so the fused path is the one run
+        monkeypatch.setenv("STOKES_NO_AUTOTUNE", "1")
     S = gpu_solver(case, kA=kA, kS=kS)
     level = len(H.levels) - 1
+    prec = 64 if dtype == torch.float64 else 32
+    assert S.fused_levels(prec)[level] == (kA == 1)
     lev = H.levels[level]
     b = _t(random_full(lev, 21, constrained_zero=True), dtype)
     x0 = _t(random_full(lev, 22, constrained_zero=True), dtype)

@@ -21,6 +21,7 @@ __all__ = [
     "perturbed_vertices",
     "fourier_forcing",
     "mms2d_forcing",
+    "laser_beam_forcing",
     "velocity_lattice",
     "gaussian_field_cells",
     "random_vector",
@@ -122,6 +123,18 @@ def mms2d_forcing(x, y, mu=1.0):
     dpdx = -pi * sx * cy
     dpdy = -pi * cx * sy
     return -mu * lap_u1 + dpdx, -mu * lap_u2 + dpdy
+
+
+def laser_beam_forcing(n, k=2, x0=(0.75, 0.75), c1=1e-3, c2=100.0):
+    """The laser-beam test of the paper (Sec. 4.2.1) on the unit square, Q_k velocity nodes of an
+    n[0] x n[1] Cartesian mesh: f = (0, c1 exp(-c2 |x - x0|^2)) with x0 = (0.75, 0.75),
+    c1 = 1e-3, c2 = 100 (the paper's mu = 0.0022 and homogeneous Dirichlet data are set by the
+    caller).  Shape (2, N_y, N_x).  Equispaced lattice points are the velocity nodes for k = 2."""
+    ax = velocity_lattice(2, k, n)
+    Y, X = np.meshgrid(ax[1], ax[0], indexing="ij")
+    f = np.zeros((2,) + X.shape)
+    f[1] = c1 * np.exp(-c2 * ((X - x0[0]) ** 2 + (Y - x0[1]) ** 2))
+    return f
 
 
 def gaussian_field_cells(n, seed, corr_length=0.2, std=1.0):
