@@ -540,6 +540,9 @@ def run_ours(args):
         rl[key] = roofline_entry(key, prec, blocks, avg, n_cells, N, props.multi_processor_count, max_mhz, fma[prec],
                                  peaks, sha, S.launch_shapes(prec)[-1])
 
+    # --- deterministic mode: colour-class cooperative cell kernels, plain read-modify-write scatter
+    deterministic = run_deterministic(S32[1], B[1], common) if not args.no_extras else None
+
     # --- batched multi-mesh solves (16 unit-cube meshes of uneven size, seeded) -----------------
     batched = run_batched(args) if not args.no_extras else None
     # --- adjoint (32^3 Cartesian, mu = exp(g)): forward + adjoint solve + viscosity gradient ----
@@ -587,6 +590,7 @@ def run_ours(args):
         "tuning": tuning_string(S32[0]),
         "batched": batched,
         "adjoint": adjoint,
+        "deterministic": deterministic,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
@@ -605,6 +609,52 @@ def run_ours(args):
         S.close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_deterministic(S_atomic, b, common):
+    """The workload's gamma = 1e2 solve and vmults in deterministic mode against the default (atomic)
+    context: time per FP32-MG solve, FP32 / FP64 vmult, and whether two solves repeat bitwise."""
+    import torch
+    from paper_2205_15770_gb300 import StokesMG
+    kw = dict(common)
+    S = StokesMG(gamma_rho=1e2, vcycle_fp32=True, deterministic=True, **kw)
+
+    def t_solve(Sx, reps=3):
+        x = torch.zeros_like(b)
+        Sx.solve(b, x, rtol=WL["rtol"])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            x.zero_()
+            _, it, _ = Sx.solve(b, x, rtol=WL["rtol"])
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps, it, x.clone()
+
+    def t_vmult(Sx, dt, reps):
+        xv = torch.randn(b.numel(), dtype=dt, device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+        yv = torch.empty_like(xv)
+        Sx.vmult(xv, yv)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            Sx.vmult(xv, yv)
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps * 1e3
+
+    ms_det, it_det, x1 = t_solve(S)
+    _, _, x2 = t_solve(S, reps=1)
+    ms_atomic, it_atomic, _ = t_solve(S_atomic)
+    out = {"solve_ms": round(ms_det, 3), "iterations": it_det, "atomic_solve_ms": round(ms_atomic, 3),
+           "atomic_iterations": it_atomic, "solves_repeat_bitwise": bool(torch.equal(x1, x2))}
+    for prec, dt, reps in ((32, torch.float32, 50), (64, torch.float64, 10)):
+        out[f"vmult_fp{prec}_us"] = round(t_vmult(S, dt, reps), 2)
+        out[f"atomic_vmult_fp{prec}_us"] = round(t_vmult(S_atomic, dt, reps), 2)
+    S.close()
+    return out
 
 
 def run_batched(args):

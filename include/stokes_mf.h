@@ -92,10 +92,21 @@ typedef struct {
   const double *rho_cell; /* HOST, nullable: per-cell rho of the gamma rho u.v term on the finest level
                            (n cells, x fastest; copied at setup; coarse levels take the mean of the
                            2^d children); null: rho = 1.  Entries must be > 0 */
+  int deterministic;    /* 1: bitwise-reproducible operator applications.  Every cell-kernel launch of
+                           the solver runs as one cooperative launch that walks the 8 classes of cells
+                           with equal index parities (no two cells of a class share a node; the paper's
+                           K x = sum_tau P_tau K_tau P_tau^T x summed class by class) with a grid barrier
+                           between classes, and scatters by plain read-modify-write instead of atomic
+                           adds; the smoother is the unfused one.  3D, k = 2 (any mesh) or k = 3
+                           (Cartesian), Laplacian form, constant rho, C = 0 (else STOKES_EINVAL) */
+  unsigned int wait_cycles; /* deterministic mode: clock64() cycles a CTA waits at a grid barrier before
+                           it gives up, flags the error and returns (0: 2^31, about 1 s); calls then
+                           return STOKES_ETIMEOUT */
 } stokes_opts;
 
 /* Fill *o with kA = kS = 3, m = 2, V-cycle, local Schur diagonal, FP32 cycle,
- * restart 30, 40 Lanczos steps, safety 1.1, seed 0x5EED. */
+ * restart 30, 40 Lanczos steps, safety 1.1, seed 0x5EED, no stabilisation, the Laplacian form,
+ * atomic (not deterministic) scatter. */
 void stokes_default_opts(stokes_opts *o);
 
 /* Build the level hierarchy, geometry, 1D tables, Jacobi/Schur diagonals, the
@@ -183,6 +194,11 @@ int stokes_solve(stokes_ctx *ctx, const double *b, double *x, double rtol, int m
  * -1 = not decided yet (no solve so far).  No counterpart in the paper (the outer Krylov loop is
  * a layer on top of its Algorithm 1). */
 int stokes_krylov_mode(const stokes_ctx *ctx);
+
+/* Deterministic mode (opts.deterministic): replace the grid-barrier wait budget of opts.wait_cycles
+ * (clock64() cycles; 0 = 2^31).  Synchronises the context stream; STOKES_EINVAL for a context not in
+ * deterministic mode.  No counterpart in the paper. */
+int stokes_set_wait_cycles(stokes_ctx *ctx, unsigned int cycles);
 int stokes_batch_krylov_mode(const stokes_batch *batch);
 
 /* stokes_solve with HOST vectors: copies b in, solves from x = 0, copies x out. */

@@ -62,7 +62,7 @@ class StokesMG:
     def __init__(self, dim, n, n_levels, k=2, mu=1.0, gamma_rho=0.0, vertices=None, lo=(0.0, 0.0, 0.0),
                  hi=(1.0, 1.0, 1.0), dirichlet_faces=None, mu_cell=None, kA=3, kS=3, m=2, cycle="V",
                  schur_diag="loc", vcycle_fp32=True, restart=30, eig_iters=40, eig_safety=1.1, seed=0x5EED,
-                 c_mass=0.0, c_grad=0.0, sym_grad=False, rho_cell=None):
+                 c_mass=0.0, c_grad=0.0, sym_grad=False, rho_cell=None, deterministic=False, wait_cycles=0):
         self._lib = L.load()
         torch = _torch()
         self.dim, self.k, self.n_levels = dim, k, n_levels
@@ -98,6 +98,8 @@ class StokesMG:
         opts.seed = seed
         opts.c_mass, opts.c_grad = float(c_mass), float(c_grad)
         opts.sym_grad = 1 if sym_grad else 0
+        opts.deterministic = 1 if deterministic else 0
+        opts.wait_cycles = int(wait_cycles)
         if rho_cell is not None:
             rc = np.ascontiguousarray(np.asarray(rho_cell, dtype=np.float64).reshape(-1))
             self._keep.append(rc)
@@ -366,6 +368,10 @@ class StokesMG:
         """1: inner FGMRES iterations on the device (one graph launch per restart cycle), 0: host-driven,
         -1: no solve yet (stokes_krylov_mode)."""
         return int(self._lib.stokes_krylov_mode(self._ctx))
+
+    def set_wait_cycles(self, cycles):
+        """Deterministic mode: the grid-barrier wait budget in clock cycles (0: the default)."""
+        self._check(self._lib.stokes_set_wait_cycles(self._ctx, int(cycles)))
 
 
 class StokesBatch:

@@ -23,7 +23,8 @@ class StokesOpts(C.Structure):
     _fields_ = [("kA", C.c_int), ("kS", C.c_int), ("m", C.c_int), ("cycle", C.c_int), ("schur_diag", C.c_int),
                 ("vcycle_fp32", C.c_int), ("gmres_restart", C.c_int), ("eig_iters", C.c_int),
                 ("eig_safety", C.c_double), ("seed", C.c_ulonglong), ("c_mass", C.c_double),
-                ("c_grad", C.c_double), ("sym_grad", C.c_int), ("rho_cell", C.POINTER(C.c_double))]
+                ("c_grad", C.c_double), ("sym_grad", C.c_int), ("rho_cell", C.POINTER(C.c_double)),
+                ("deterministic", C.c_int), ("wait_cycles", C.c_uint)]
 
 
 # name -> (restype, argtypes)
@@ -67,6 +68,7 @@ SIGNATURES = {
     "stokes_set_launch_shape": (C.c_int, [P, C.c_int, C.c_int, C.c_int]),
     "stokes_launch_count": (C.c_longlong, [P]),
     "stokes_krylov_mode": (C.c_int, [P]),
+    "stokes_set_wait_cycles": (C.c_int, [P, C.c_uint]),
     "stokes_batch_krylov_mode": (C.c_int, [P]),
     "stokes_last_error": (C.c_char_p, [P]),
     "stokes_global_last_error": (C.c_char_p, []),

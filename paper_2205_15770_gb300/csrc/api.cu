@@ -49,14 +49,17 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
 
 template <typename T>
 int launch_cell_apply(const LevelDesc<T> &L, const Tab1D<T> *tab, int mode, const T *u, const T *p, T *yu, T *yp,
-                      cudaStream_t s, int shape, const T *geo, const T *rho) {
-  if (shape == 5) {
-    // cell-component kernel (Laplacian form, constant rho); the column kernel serves the rest
+                      cudaStream_t s, int shape, const T *geo, const T *rho, const GridBarrier *det) {
+  if (shape == 5 || det) {
+    // cell-component kernel (Laplacian form, constant rho); the column kernel serves the rest.
+    // det: its deterministic cooperative form (setup admits deterministic mode only where it serves
+    // every application of the solve)
     const bool generic_a = (mode & kApplyA) && ((mode & kApplySym) || rho);
     if (!generic_a) {
-      const int r = L.k == 2 ? launch_cell_apply_cc_k<2, T>(L, mode, u, p, yu, yp, s)
-                             : (L.k == 3 ? launch_cell_apply_cc_k<3, T>(L, mode, u, p, yu, yp, s) : -1);
+      const int r = L.k == 2 ? launch_cell_apply_cc_k<2, T>(L, mode, u, p, yu, yp, geo, det, s)
+                             : (L.k == 3 ? launch_cell_apply_cc_k<3, T>(L, mode, u, p, yu, yp, geo, det, s) : -1);
       if (r == 0) return 0;
+      if (r > 0) return cuda_fail((cudaError_t)r, "deterministic cell-kernel launch", __FILE__, __LINE__);
     }
     shape = 4;
   }
@@ -246,6 +249,10 @@ struct stokes_ctx {
   // loop (STOKES_HOST_KRYLOV=1, or conditional graph nodes unavailable), 1 device loop
   KrylovDev kd{};
   double *zcur = nullptr;
+  // deterministic mode (opts.deterministic): every 3D cell-kernel application runs in the
+  // cooperative colour-class form; gb: its grid-barrier state (arrivals, round, error, budget)
+  bool det = false;
+  GridBarrier gb{};
   cudaGraphExec_t kry = nullptr;
   long long kry_body = 0;
   int kry_mode = -1;
@@ -371,7 +378,8 @@ struct Runner {
   // Cycle form: the outputs are already zero (work buffers are zeroed by the kernel that
   // consumes them, so the captured cycle contains kernels only).
   void apply_nz(int l, int mode, const T *u, const T *p, T *yu, T *yp) {
-    launch_cell_apply<T>(L[l].d, tab, form(mode), u, p, yu, yp, s, L[l].shape, L[l].geo, L[l].rho);
+    launch_cell_apply<T>(L[l].d, tab, form(mode), u, p, yu, yp, s, L[l].shape, L[l].geo, L[l].rho,
+                         C->det ? &C->gb : nullptr);
     note();
   }
   void vmult(int l, const T *x, T *y, bool identity) {
@@ -503,8 +511,8 @@ struct Runner {
   // step, residual) or written by k_fused_finish.
   bool fused_ok(int l) const { return fused_eligible(l) && L[l].fuse; }
   bool fused_eligible(int l) const {
-    return C->fuse && !hasC() && !C->sym && !L[l].rho && C->o.kA == 1 && C->o.kS >= 1 && C->o.kS <= 4 && L[l].d.dim == 3 &&
-           L[l].shape >= 0;
+    return C->fuse && !C->det && !hasC() && !C->sym && !L[l].rho && C->o.kA == 1 && C->o.kS >= 1 && C->o.kS <= 4 &&
+           L[l].d.dim == 3 && L[l].shape >= 0;
   }
   T *pairU(int l, int pr) { return pr == 0 ? L[l].tu : L[l].cx; }
   T *pairT(int l, int pr) { return pr == 0 ? L[l].ct : L[l].ct2; }
@@ -1107,6 +1115,7 @@ struct StreamGuard {
   }
 };
 
+static int det_check(stokes_ctx *C, cudaStream_t s);
 static int finish(stokes_ctx *C, int st) {
   if (st != STOKES_OK) {
     C->err = g_last_error;
@@ -1118,7 +1127,8 @@ static int finish(stokes_ctx *C, int st) {
     C->err = g_last_error;
     return STOKES_ECUDA;
   }
-  return STOKES_OK;
+  if ((st = det_check(C, C->s)) != STOKES_OK) C->err = g_last_error;
+  return st;
 }
 
 // The setup's timings replay CUDA graphs of the candidate work, so that they compare the GPU's
@@ -1158,7 +1168,8 @@ static int time_graph(stokes_ctx *C, cudaGraphExec_t ex, cudaEvent_t e0, cudaEve
 template <typename T>
 static int autotune_level(stokes_ctx *C, LevelRT<T> &R, const Tab1D<T> *tab) {
   if (R.d.dim != 3) return STOKES_OK;
-  const bool cc = cc_level_supported(R.d.dim, R.d.k, R.d.cartesian, sizeof(T)) && !C->sym && !R.rho;
+  const bool cc = cc_level_supported(R.d.dim, R.d.k, R.d.cartesian, sizeof(T)) && !C->sym && !R.rho &&
+                  (R.d.cartesian || sizeof(T) == 4 || R.geo);
   const int NC = cc ? 5 : 4;
   const int cands[5] = {4, 1, 3, -1, 5};
   const int reps = sizeof(T) == 8 ? 3 : 20, rounds = 3;
@@ -1329,6 +1340,13 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
   C->c_mass = C->o.c_mass;
   C->c_grad = C->o.c_grad;
   C->sym = C->o.sym_grad != 0;
+  C->det = C->o.deterministic != 0;
+  if (C->det && (dim != 3 || (k != 2 && k != 3) || (k == 3 && mesh->vertices) || C->sym || C->o.rho_cell ||
+                 C->c_mass != 0.0 || C->c_grad != 0.0)) {
+    set_error("deterministic mode needs 3D, k = 2 (any mesh) or k = 3 (Cartesian), the Laplacian form with a "
+              "constant rho and C = 0");
+    return STOKES_EINVAL;
+  }
   if (C->o.rho_cell) {
     const long long nc = (long long)mesh->n[0] * mesh->n[1] * (dim == 3 ? mesh->n[2] : 1);
     C->rho_host.assign(C->o.rho_cell, C->o.rho_cell + nc);
@@ -1551,10 +1569,28 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
     if ((st = build_xfer(C, C->L32[l].d, C->L32[l - 1].d, tt64, C->L32[l].xf))) return st;
   }
 
+  // deterministic mode: grid-barrier state, the cell-component kernel on every level
+  if (C->det) {
+    for (int l = 0; l < nl; ++l)
+      if (!C->L64[l].d.cartesian && !C->L64[l].geo) {
+        set_error("deterministic mode: level " + std::to_string(l) +
+                  " is too large to keep its FP64 per-point geometry stored (1/16 of the device memory)");
+        return STOKES_EINVAL;
+      }
+    if ((st = dalloc(C, &C->gb.state, 4))) return st;
+    // setup runs with the default budget; opts.wait_cycles applies from the end of setup on
+    const unsigned hs[4] = {0u, 0u, 0u, 0u};
+    SMF_CUDA_OK(cudaMemcpyAsync(C->gb.state, hs, sizeof(hs), cudaMemcpyHostToDevice, C->s));
+    for (int l = 0; l < nl; ++l) {
+      C->L32[l].shape = C->L64[l].shape = 5;
+      C->L32[l].fuse = C->L64[l].fuse = false;
+    }
+  }
+
   // launch-shape autotuning (STOKES_NO_AUTOTUNE=1 keeps the default shape; STOKES_TUNING fixes
   // shapes and smoother forms instead, see parse_tuning)
   std::vector<int> tune[4];
-  const bool pinned = getenv("STOKES_TUNING") != nullptr;
+  const bool pinned = getenv("STOKES_TUNING") != nullptr && !C->det;
   if (pinned && (st = parse_tuning(getenv("STOKES_TUNING"), nl, tune))) return st;
   if (pinned) {
     for (int l = 0; l < nl; ++l) {
@@ -1566,7 +1602,7 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
   }
   {
     const char *na = getenv("STOKES_NO_AUTOTUNE");
-    if (!(na && na[0] == '1') && !pinned) {
+    if (!(na && na[0] == '1') && !pinned && !C->det) {
       for (int l = 0; l < nl; ++l) {
         if ((st = autotune_level<double>(C, C->L64[l], C->tab64))) return st;
         if ((st = autotune_level<float>(C, C->L32[l], C->tab32))) return st;
@@ -1656,7 +1692,7 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
         C->L32[l].fuse = tune[2][l] != 0;
         C->L64[l].fuse = tune[3][l] != 0;
       }
-    } else if (!(na && na[0] == '1')) {
+    } else if (!(na && na[0] == '1') && !C->det) {
       for (int l = 1; l < nl; ++l) {
         if ((st = autotune_fusion<float>(C, l))) return st;
         if ((st = autotune_fusion<double>(C, l))) return st;
@@ -1665,6 +1701,11 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
   }
   SMF_CUDA_OK(cudaStreamSynchronize(C->s));
   SMF_CUDA_OK(cudaGetLastError());
+  if (C->det) {
+    if ((st = det_check(C, C->s))) return st;
+    SMF_CUDA_OK(cudaMemcpyAsync(C->gb.state + 3, &C->o.wait_cycles, sizeof(unsigned), cudaMemcpyHostToDevice, C->s));
+    SMF_CUDA_OK(cudaStreamSynchronize(C->s));
+  }
   return STOKES_OK;
 }
 
@@ -1678,6 +1719,28 @@ static bool check_level(stokes_ctx *C, int level) {
 }
 
 // FP64 flexible GMRES (restarted), right-preconditioned by one multigrid cycle per iteration.
+// Deterministic mode: clear the grid-barrier state (arrivals, round, error flag) on stream s before
+// a call's launches; after them, synchronise and report a wait that ran out as STOKES_ETIMEOUT.
+static int det_begin(stokes_ctx *C, cudaStream_t s) {
+  if (C->det) SMF_CUDA_OK(cudaMemsetAsync(C->gb.state, 0, 3 * sizeof(unsigned), s));
+  return STOKES_OK;
+}
+static int det_check(stokes_ctx *C, cudaStream_t s) {
+  if (!C->det) return STOKES_OK;
+  unsigned err = 0;
+  SMF_CUDA_OK(cudaMemcpyAsync(&err, C->gb.state + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  SMF_CUDA_OK(cudaStreamSynchronize(s));
+  if (err) {
+    // reported once: the state is cleared for the calls that follow
+    SMF_CUDA_OK(cudaMemsetAsync(C->gb.state, 0, 3 * sizeof(unsigned), s));
+    SMF_CUDA_OK(cudaStreamSynchronize(s));
+    set_error("a grid-barrier wait of the deterministic cell kernel ran out of its budget (opts.wait_cycles); "
+              "results of this call are invalid");
+    return STOKES_ETIMEOUT;
+  }
+  return STOKES_OK;
+}
+
 // Destroys every captured graph of the context (cycles and the device Krylov loop).
 static void drop_graphs(stokes_ctx *C) {
   for (int i = 0; i < 2; ++i) {
@@ -1811,6 +1874,7 @@ static int fgmres(stokes_ctx *C, const double *b, double *x, double rtol, int ma
     }
     double beta2;
     if ((st = dot64(C, C->V, C->V, N, &beta2))) return st;
+    if ((st = det_check(C, C->s))) return st;
     const double beta = std::sqrt(beta2);
     if (beta0 < 0) beta0 = beta;
     rel = beta / bnorm;
@@ -2401,6 +2465,8 @@ void stokes_default_opts(stokes_opts *o) {
   o->c_grad = 0.0;
   o->sym_grad = 0;
   o->rho_cell = nullptr;
+  o->deterministic = 0;
+  o->wait_cycles = 0;
 }
 
 int stokes_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho, const double *mu_cell,
@@ -2477,6 +2543,10 @@ int stokes_vmult(stokes_ctx *C, int level, int precision, const void *x, void *y
   }
   // The operator reads only x and the context's read-only level data, so it is launched directly
   // on the caller's stream (no join with the context stream).
+  if (det_begin(C, (cudaStream_t)stream) != STOKES_OK) {
+    C->err = g_last_error;
+    return STOKES_ECUDA;
+  }
   if (precision == 64)
     Runner<double>(C, (cudaStream_t)stream, Runner<double>::OnStream{}).vmult(level, (const double *)x, (double *)y,
                                                                            true);
@@ -2488,7 +2558,9 @@ int stokes_vmult(stokes_ctx *C, int level, int precision, const void *x, void *y
     C->err = g_last_error;
     return STOKES_ECUDA;
   }
-  return STOKES_OK;
+  const int dst = det_check(C, (cudaStream_t)stream);
+  if (dst != STOKES_OK) C->err = g_last_error;
+  return dst;
 }
 
 int stokes_apply_blocks(stokes_ctx *C, int level, int precision, int blocks, const void *u, const void *p, void *yu,
@@ -2504,6 +2576,7 @@ int stokes_apply_blocks(stokes_ctx *C, int level, int precision, int blocks, con
     return STOKES_EINVAL;
   }
   StreamGuard sg(C, stream);
+  det_begin(C, C->s);
   const bool wu = base & (1 | 2 | 8 | 16), wp = base & 4;
   if (precision == 64) {
     Runner<double> R(C);
@@ -2551,6 +2624,7 @@ int stokes_smooth(stokes_ctx *C, int level, int precision, int steps, const void
     return STOKES_EINVAL;
   }
   StreamGuard sg(C, stream);
+  det_begin(C, C->s);
   if (precision == 64)
     Runner<double>(C).smooth(level, (double *)x, (const double *)b, steps, false);
   else
@@ -2645,6 +2719,7 @@ int mg_vcycle(stokes_ctx *C, int precision, const void *b, void *x, void *stream
     return STOKES_EINVAL;
   }
   StreamGuard sg(C, stream);
+  det_begin(C, C->s);
   const int top = C->nl - 1;
   int st;
   if (precision == 64) {
@@ -2673,6 +2748,7 @@ int stokes_solve(stokes_ctx *C, const double *b, double *x, double rtol, int max
     return STOKES_EINVAL;
   }
   StreamGuard sg(C, stream);
+  det_begin(C, C->s);
   int st = fgmres(C, b, x, rtol, maxit, iters, final_rel_res);
   return finish(C, st);
 }
@@ -2820,6 +2896,7 @@ int stokes_mg_iterate(stokes_ctx *C, const double *b, double *x, int max_iter, d
     return STOKES_EINVAL;
   }
   StreamGuard sg(C, stream);
+  det_begin(C, C->s);
   Runner<double> R(C);
   const int top = C->nl - 1;
   LevelRT<double> &L = C->L64[top];
@@ -2907,6 +2984,7 @@ int stokes_time_apply(stokes_ctx *C, int level, int precision, int blocks, int r
     return STOKES_EINVAL;
   }
   StreamGuard sg(C, stream);
+  det_begin(C, C->s);
   cudaEvent_t e0, e1;
   SMF_CUDA_OK(cudaEventCreate(&e0));
   SMF_CUDA_OK(cudaEventCreate(&e1));
@@ -2915,11 +2993,11 @@ int stokes_time_apply(stokes_ctx *C, int level, int precision, int blocks, int r
     if (precision == 64) {
       LevelRT<double> &R = C->L64[level];
       launch_cell_apply<double>(R.d, C->tab64, Runner<double>(C).form(blocks), R.x, R.x + R.d.n_u, R.r, R.r + R.d.n_u,
-                                C->s, R.shape, R.geo, R.rho);
+                                C->s, R.shape, R.geo, R.rho, C->det ? &C->gb : nullptr);
     } else {
       LevelRT<float> &R = C->L32[level];
       launch_cell_apply<float>(R.d, C->tab32, Runner<float>(C).form(blocks), R.x, R.x + R.d.n_u, R.r, R.r + R.d.n_u,
-                               C->s, R.shape, R.geo, R.rho);
+                               C->s, R.shape, R.geo, R.rho, C->det ? &C->gb : nullptr);
     }
     ++C->launches;
   }
@@ -2940,6 +3018,11 @@ int stokes_setup_batch(int n_meshes, const stokes_mesh *meshes, const int *k, co
     return STOKES_EINVAL;
   }
   *out = nullptr;
+  if (opts && opts->deterministic) {
+    set_error("stokes_setup_batch: deterministic mode is for single contexts (its cooperative launches "
+              "assume the whole GPU)");
+    return STOKES_EINVAL;
+  }
   stokes_batch *Bt = new (std::nothrow) stokes_batch();
   if (!Bt) {
     set_error("host allocation failed");
@@ -3081,6 +3164,17 @@ int stokes_set_launch_shape(stokes_ctx *C, int level, int precision, int shape) 
 
 long long stokes_launch_count(const stokes_ctx *C) { return C ? C->launches : 0; }
 int stokes_krylov_mode(const stokes_ctx *C) { return C ? C->kry_mode : -1; }
+int stokes_set_wait_cycles(stokes_ctx *C, unsigned int cycles) {
+  if (!C || !C->det) {
+    set_error("stokes_set_wait_cycles: the context is not in deterministic mode");
+    if (C) C->err = g_last_error;
+    return STOKES_EINVAL;
+  }
+  C->o.wait_cycles = cycles;
+  SMF_CUDA_OK(cudaMemcpyAsync(C->gb.state + 3, &cycles, sizeof(unsigned), cudaMemcpyHostToDevice, C->s));
+  SMF_CUDA_OK(cudaStreamSynchronize(C->s));
+  return STOKES_OK;
+}
 int stokes_batch_krylov_mode(const stokes_batch *Bt) { return Bt ? Bt->kmode : -1; }
 
 const char *stokes_last_error(const stokes_ctx *C) { return C ? C->err.c_str() : g_last_error.c_str(); }

@@ -394,23 +394,41 @@ __global__ void __launch_bounds__(CellShape<DIM, K>::THREADS)
 //                                   symmetric form (sym): dAs[c nv + node] per component c
 //   dSloc[i]   += sum_{c, j free} (B_tau)_{i,(c,j)}^2 / (A_tau)_jj   (Eq. diag loc)
 //   dMp[i]     += (M_p,tau)_ii      pressure mass diagonal (Eq. diag p)
+// colour >= 0 (3D): one launch per class of cells with the same index parities (bit a = parity
+// along axis a), the blocks taking that class's cells; no two cells of a class share a node, so a
+// node's entries are added in class order and the diagonals are bitwise reproducible (the local
+// Schur sum inside a cell is then also added in a fixed order where it fits in shared memory).
 template <int DIM, int K, typename T, bool CART>
 __global__ void stokes_cell_diagonals(const LevelDesc<T> L, const Tab1D<T> *__restrict__ tab, T *dAs, T *dSloc,
-                                      T *dMp, const T *__restrict__ rho_cell, int sym) {
+                                      T *dMp, const T *__restrict__ rho_cell, int sym, int colour) {
   using CS = CellShape<DIM, K>;
   constexpr int NQ = CS::NQ, NV = CS::NV, NPR = CS::NPR, NP = CS::NP, NPP = CS::NPP;
+  constexpr bool ORDERED = NP * NPP <= 2048;
   __shared__ Tab1D<T> st;
   __shared__ T sG[NP][DIM * DIM];
   __shared__ T sC[NP][DIM * DIM];
   __shared__ T sW[NP];
   __shared__ T sAjj[NP];
   __shared__ T sLoc[NPP];
+  __shared__ T sPart[ORDERED ? NP : 1][ORDERED ? NPP : 1];
   __shared__ T verts[CS::NVERT * DIM];
-  const long long cell = blockIdx.x;
   const int t = threadIdx.x;
-  const int cx = (int)(cell % L.n[0]);
-  const int cy = (int)((cell / L.n[0]) % L.n[1]);
-  const int cz = (int)(cell / ((long long)L.n[0] * L.n[1]));
+  int cx, cy, cz;
+  long long cell;
+  if (colour < 0) {
+    cell = blockIdx.x;
+    cx = (int)(cell % L.n[0]);
+    cy = (int)((cell / L.n[0]) % L.n[1]);
+    cz = (int)(cell / ((long long)L.n[0] * L.n[1]));
+  } else {
+    const int px = colour & 1, py = (colour >> 1) & 1, pz = (colour >> 2) & 1;
+    const long long ex = (L.n[0] - px + 1) / 2, ey = (L.n[1] - py + 1) / 2;
+    const long long k = blockIdx.x;
+    cx = 2 * (int)(k % ex) + px;
+    cy = 2 * (int)((k / ex) % ey) + py;
+    cz = 2 * (int)(k / (ex * ey)) + pz;
+    cell = ((long long)cz * L.n[1] + cy) * L.n[0] + cx;
+  }
   load_tables(tab, reinterpret_cast<T *>(&st));
   if (!CART && t < CS::NVERT * DIM) {
     const int v = t / DIM, a = t % DIM;
@@ -485,6 +503,10 @@ __global__ void stokes_cell_diagonals(const LevelDesc<T> L, const Tab1D<T> *__re
     }
   }
   // local Schur diagonal: columns (c, j = t) of B_tau
+  if (ORDERED) {
+#pragma unroll
+    for (int i = 0; i < NPP; ++i) sPart[ORDERED ? t : 0][ORDERED ? i : 0] = T(0);
+  }
   if (jfree) {
     for (int c = 0; c < DIM; ++c) {
       T bcol[NPP];
@@ -506,9 +528,20 @@ __global__ void stokes_cell_diagonals(const LevelDesc<T> L, const Tab1D<T> *__re
         }
       }
       const T ac = sym ? (c == 0 ? ajjc[0] : (c == 1 ? ajjc[1] : ajjc[2])) : ajj;
+      if (ORDERED) {
 #pragma unroll
-      for (int i = 0; i < NPP; ++i) atomicAdd(&sLoc[i], bcol[i] * bcol[i] / ac);
+        for (int i = 0; i < NPP; ++i) sPart[ORDERED ? t : 0][ORDERED ? i : 0] += bcol[i] * bcol[i] / ac;
+      } else {
+#pragma unroll
+        for (int i = 0; i < NPP; ++i) atomicAdd(&sLoc[i], bcol[i] * bcol[i] / ac);
+      }
     }
+  }
+  __syncthreads();
+  if (ORDERED && t < NPP) {
+    T sum = T(0);
+    for (int j = 0; j < NP; ++j) sum += sPart[ORDERED ? j : 0][ORDERED ? t : 0];
+    sLoc[t] = sum;
   }
   __syncthreads();
   if (t < NPP) {

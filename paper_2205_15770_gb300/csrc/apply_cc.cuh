@@ -17,6 +17,8 @@
 //     B, B^T are 3 sweeps each; no quadrature-point arrays, no shared memory.
 //   * Scatter by atomicAdd at the gather's indices; constrained DoFs read as 0 and not written.
 #pragma once
+#include <algorithm>
+
 #include "apply.cuh"
 #include "host_tables.h"
 #include "vec.cuh"
@@ -162,35 +164,68 @@ struct CcGeo {
 template <int K, typename T, int MODE, bool CART>
 struct CcLaunch {
   static constexpr int NQ = K + 1;
-  static constexpr int WARPS = (!CART && (MODE & (kApplyB | kApplyBT))) ? 2 : 4;
-  static constexpr size_t SMEM =
-      CART ? 0 : (size_t)WARPS * NQ * NQ * NQ * CcGeo<MODE>::NF * kCcCells * sizeof(float4);
+  // trilinear cells: FP32 shares the geometry through shared memory, FP64 reads the per-point
+  // geometry stored at setup (the column kernel's layout)
+  static constexpr bool SMEM_GEO = !CART && sizeof(T) == 4;
+  static constexpr int WARPS = (SMEM_GEO && (MODE & (kApplyB | kApplyBT))) ? 2 : 4;
+  static constexpr size_t GEO_BYTES =
+      SMEM_GEO ? (size_t)WARPS * NQ * NQ * NQ * CcGeo<MODE>::NF * kCcCells * sizeof(float4) : 0;
+  // deterministic launches: the three component threads' pressure sums of a cell meet here
+  static constexpr size_t RED_BYTES = (MODE & kApplyB) ? (size_t)WARPS * kCcCells * 3 * K * K * K * sizeof(T) : 0;
+  static constexpr size_t SMEM = GEO_BYTES;
+  static constexpr size_t SMEM_DET = GEO_BYTES + RED_BYTES;
   // resident warps per SM the register allocation is held to (FP32; FP64 keeps its registers)
   static constexpr int MINB = (sizeof(T) == 4 && K == 2) ? (SMF_CC_TARGET_WARPS + WARPS - 1) / WARPS : 1;
 };
 
-template <int K, typename T, int MODE, bool CART>
-__global__ void __launch_bounds__(32 * CcLaunch<K, T, MODE, CART>::WARPS, CcLaunch<K, T, MODE, CART>::MINB)
-    stokes_cell_apply_cc(const LevelDesc<T> L, const T *__restrict__ u, const T *__restrict__ p,
-                         T *__restrict__ yu, T *__restrict__ yp) {
-  pdl_enter();
+// Cells of colour class `colour` (bit a = parity of the cell index along axis a): no two of them
+// share a velocity or pressure node.
+__host__ __device__ inline long long colour_extent(const int n[3], int colour, int a) {
+  const int par = (colour >> a) & 1;
+  return (n[a] - par + 1) / 2;
+}
+
+// One warp's group of cells.  colour < 0: cells group * 10 .. + 9 in lexicographic order, scatter
+// by atomicAdd.  colour >= 0 (DET): the group-th 10 cells of that colour class, scatter by plain
+// read-modify-write through L2 (no other thread touches the node in this class), the three
+// component threads' pressure sums added in a fixed order: bitwise reproducible results.
+template <int K, typename T, int MODE, bool CART, bool DET>
+__device__ __forceinline__ void cc_group(const LevelDesc<T> &L, const T *__restrict__ u, const T *__restrict__ p,
+                                         T *__restrict__ yu, T *__restrict__ yp, const T *__restrict__ geo,
+                                         long long group, int colour) {
   constexpr int NV = K + 1, NQ = K + 1, NPR = K, CPW = kCcCells;
-  constexpr int WARPS = CcLaunch<K, T, MODE, CART>::WARPS;
   constexpr bool DO_A = MODE & kApplyA, DO_BT = MODE & kApplyBT, DO_B = MODE & kApplyB;
   constexpr bool NEED_U = DO_A || DO_B;
-  static_assert(CART || (K == 2 && sizeof(T) == 4), "trilinear cell-component kernel: FP32, k = 2");
+  using CL = CcLaunch<K, T, MODE, CART>;
+  static_assert(CART || K == 2, "trilinear cell-component kernel: k = 2");
   const CCTab<T> &tb = cct<T>();
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool pad = lane >= 3 * CPW;
   const int c = pad ? 0 : lane / CPW;
   const int s = pad ? 0 : lane - c * CPW;
-  const long long cell_raw = ((long long)blockIdx.x * WARPS + warp) * CPW + s;
-  const bool valid = !pad && cell_raw < L.n_cells;
-  const long long cell = valid ? cell_raw : 0;
-  const int cx = (int)(cell % L.n[0]);
-  const long long rr = cell / L.n[0];
-  const int cy = (int)(rr % L.n[1]), cz = (int)(rr / L.n[1]);
+  bool valid;
+  int cx = 0, cy = 0, cz = 0;
+  if (!DET) {
+    const long long cell_raw = group * CPW + s;
+    valid = !pad && cell_raw < L.n_cells;
+    const long long cl = valid ? cell_raw : 0;
+    cx = (int)(cl % L.n[0]);
+    const long long rr = cl / L.n[0];
+    cy = (int)(rr % L.n[1]);
+    cz = (int)(rr / L.n[1]);
+  } else {
+    const long long ex = colour_extent(L.n, colour, 0), ey = colour_extent(L.n, colour, 1);
+    const long long ez = colour_extent(L.n, colour, 2);
+    const long long k = group * CPW + s;
+    valid = !pad && k < ex * ey * ez;
+    if (valid) {
+      cx = 2 * (int)(k % ex) + (colour & 1);
+      cy = 2 * (int)((k / ex) % ey) + ((colour >> 1) & 1);
+      cz = 2 * (int)(k / (ex * ey)) + ((colour >> 2) & 1);
+    }
+  }
+  const long long cell = ((long long)cz * L.n[1] + cy) * L.n[0] + cx;
   const int gx0 = K * cx, gy0 = K * cy, gz0 = K * cz;
 
   // free (unconstrained) velocity nodes per direction; invalid lanes have none
@@ -391,7 +426,7 @@ __global__ void __launch_bounds__(32 * CcLaunch<K, T, MODE, CART>::WARPS, CcLaun
     constexpr int NF = CcGeo<MODE>::NF;
     extern __shared__ float4 cc_geo_smem[];
     float4 *gs = cc_geo_smem + (size_t)warp * (NQ * NQ * NQ * NF * CPW);
-    {
+    if constexpr (CL::SMEM_GEO) {
       T X[8][3];
 #pragma unroll
       for (int v = 0; v < 8; ++v) {
@@ -467,8 +502,13 @@ __global__ void __launch_bounds__(32 * CcLaunch<K, T, MODE, CART>::WARPS, CcLaun
           }
         }
       }
+      __syncwarp();
     }
-    __syncwarp();
+    // FP64: the per-point factors stored at setup, [cell][field][qz][qy][qx]: G (6, times mu
+    // here), w adj (9, row-major), w det (1, times gamma rho here)
+    constexpr int GST = NQ * NQ * NQ;
+    const T *gc = CL::SMEM_GEO ? nullptr : geo + cell * (long long)(16 * GST);
+    const T grho_g = L.gamma_rho;
 
     // ---- this component at the Gauss points --------------------------------------------------
     auto Sf = [&](int i, int j) { return tb.S[i * NV + j]; };
@@ -504,6 +544,26 @@ __global__ void __launch_bounds__(32 * CcLaunch<K, T, MODE, CART>::WARPS, CcLaun
         for (int qx = 0; qx < NQ; ++qx) {
           const int pt = (qz * NQ + qy) * NQ + qx;
           const float4 *g = gs + (size_t)pt * NF * CPW + s;
+          // G00 G01 G02 G11 G12 G22 (mu included), gamma rho w det, column c of w adj
+          auto geo_G = [&](T(&gg)[7]) {
+            if constexpr (CL::SMEM_GEO) {
+              const float4 g0 = g[0], g1 = g[CPW];
+              gg[0] = g0.x; gg[1] = g0.y; gg[2] = g0.z; gg[3] = g0.w; gg[4] = g1.x; gg[5] = g1.y; gg[6] = g1.z;
+            } else {
+#pragma unroll
+              for (int i = 0; i < 6; ++i) gg[i] = mu * gc[i * GST + pt];
+              gg[6] = grho_g * gc[15 * GST + pt];
+            }
+          };
+          auto geo_C = [&](T(&cc)[3]) {
+            if constexpr (CL::SMEM_GEO) {
+              const float4 v = g[(2 + c) * CPW];
+              cc[0] = v.x; cc[1] = v.y; cc[2] = v.z;
+            } else {
+#pragma unroll
+              for (int a = 0; a < 3; ++a) cc[a] = gc[(6 + 3 * a + c) * GST + pt];
+            }
+          };
           T gx = T(0), gy = T(0), gz = T(0);
           if (NEED_U) {
 #pragma unroll
@@ -515,20 +575,22 @@ __global__ void __launch_bounds__(32 * CcLaunch<K, T, MODE, CART>::WARPS, CcLaun
           }
           T f0 = T(0), f1 = T(0), f2 = T(0);
           if (DO_A) {
-            const float4 g0 = g[0], g1 = g[CPW];
-            f0 = g0.x * gx + g0.y * gy + g0.z * gz;
-            f1 = g0.y * gx + g0.w * gy + g1.x * gz;
-            f2 = g0.z * gx + g1.x * gy + g1.y * gz;
-            tq[qz][qy][qx] += g1.z * uq[qz][qy][qx];
+            T G[7];
+            geo_G(G);
+            f0 = G[0] * gx + G[1] * gy + G[2] * gz;
+            f1 = G[1] * gx + G[3] * gy + G[4] * gz;
+            f2 = G[2] * gx + G[4] * gy + G[5] * gz;
+            tq[qz][qy][qx] += G[6] * uq[qz][qy][qx];
           }
           if (DO_B || DO_BT) {
-            const float4 cc = g[(2 + c) * CPW];
+            T cc[3];
+            geo_C(cc);
             if (DO_BT) {
-              f0 -= pq[qz][qy][qx] * cc.x;
-              f1 -= pq[qz][qy][qx] * cc.y;
-              f2 -= pq[qz][qy][qx] * cc.z;
+              f0 -= pq[qz][qy][qx] * cc[0];
+              f1 -= pq[qz][qy][qx] * cc[1];
+              f2 -= pq[qz][qy][qx] * cc[2];
             }
-            if (DO_B) qacc[qz][qy][qx] = -(cc.x * gx + cc.y * gy + cc.z * gz);
+            if (DO_B) qacc[qz][qy][qx] = -(cc[0] * gx + cc[1] * gy + cc[2] * gz);
           }
           if (DO_A || DO_BT) {
 #pragma unroll
@@ -556,7 +618,18 @@ __global__ void __launch_bounds__(32 * CcLaunch<K, T, MODE, CART>::WARPS, CcLaun
   // ---- scatter ---------------------------------------------------------------------------------
   if (DO_A || DO_BT) {
     T *yb = yu + vbase;
-    if (fast) {
+    if (DET) {
+#pragma unroll
+      for (int iz = 0; iz < NV; ++iz)
+#pragma unroll
+        for (int iy = 0; iy < NV; ++iy)
+#pragma unroll
+          for (int ix = 0; ix < NV; ++ix)
+            if (fx[ix] && fy[iy] && fz[iz]) {
+              T *a = &yb[iz * N01 + iy * N0 + ix];
+              __stcg(a, __ldcg(a) + yv[iz][iy][ix]);
+            }
+    } else if (fast) {
       if (!pad) {
 #pragma unroll
         for (int iz = 0; iz < NV; ++iz)
@@ -575,62 +648,174 @@ __global__ void __launch_bounds__(32 * CcLaunch<K, T, MODE, CART>::WARPS, CcLaun
             if (fx[ix] && fy[iy] && fz[iz]) atomicAdd(&yb[iz * N01 + iy * N0 + ix], yv[iz][iy][ix]);
     }
   }
-  if (DO_B && valid) {
+  if (DO_B) {
+    constexpr int NP3 = NPR * NPR * NPR;
+    if (DET) {
+      // the cell's three component sums meet in shared memory; component 0 adds them in order
+      extern __shared__ float4 cc_geo_smem[];
+      T *red = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(cc_geo_smem) + CL::GEO_BYTES) +
+               (size_t)warp * CPW * 3 * NP3;
+      if (!pad) {
 #pragma unroll
-    for (int a3 = 0; a3 < NPR; ++a3)
+        for (int a3 = 0; a3 < NPR; ++a3)
 #pragma unroll
-      for (int a2 = 0; a2 < NPR; ++a2)
+          for (int a2 = 0; a2 < NPR; ++a2)
 #pragma unroll
-        for (int a1 = 0; a1 < NPR; ++a1) atomicAdd(&yp[pbase + a3 * P01 + a2 * P0 + a1], qn[a3][a2][a1]);
+            for (int a1 = 0; a1 < NPR; ++a1) red[(s * 3 + c) * NP3 + (a3 * NPR + a2) * NPR + a1] = qn[a3][a2][a1];
+      }
+      __syncwarp();
+      if (valid && c == 0) {
+#pragma unroll
+        for (int a3 = 0; a3 < NPR; ++a3)
+#pragma unroll
+          for (int a2 = 0; a2 < NPR; ++a2)
+#pragma unroll
+            for (int a1 = 0; a1 < NPR; ++a1) {
+              const int e = (a3 * NPR + a2) * NPR + a1;
+              const T v = (red[(s * 3 + 0) * NP3 + e] + red[(s * 3 + 1) * NP3 + e]) + red[(s * 3 + 2) * NP3 + e];
+              T *a = &yp[pbase + a3 * P01 + a2 * P0 + a1];
+              __stcg(a, __ldcg(a) + v);
+            }
+      }
+    } else if (valid) {
+#pragma unroll
+      for (int a3 = 0; a3 < NPR; ++a3)
+#pragma unroll
+        for (int a2 = 0; a2 < NPR; ++a2)
+#pragma unroll
+          for (int a1 = 0; a1 < NPR; ++a1) atomicAdd(&yp[pbase + a3 * P01 + a2 * P0 + a1], qn[a3][a2][a1]);
+    }
+  }
+  __syncwarp();  // the warp's shared memory is reused by its next group
+}
+
+template <int K, typename T, int MODE, bool CART>
+__global__ void __launch_bounds__(32 * CcLaunch<K, T, MODE, CART>::WARPS, CcLaunch<K, T, MODE, CART>::MINB)
+    stokes_cell_apply_cc(const LevelDesc<T> L, const T *__restrict__ u, const T *__restrict__ p,
+                         T *__restrict__ yu, T *__restrict__ yp, const T *__restrict__ geo) {
+  pdl_enter();
+  cc_group<K, T, MODE, CART, false>(L, u, p, yu, yp, geo,
+                                    (long long)blockIdx.x * CcLaunch<K, T, MODE, CART>::WARPS + (threadIdx.x >> 5), -1);
+}
+
+// Deterministic form: one cooperative launch walks the 8 colour classes of cells in order, each
+// class by all CTAs (a warp per group of 10 cells), with a grid barrier between classes.  The
+// barrier waits are bounded (GridBarrier::budget); a wait that runs out sets the error flag and
+// every CTA returns.
+template <int K, typename T, int MODE, bool CART>
+__global__ void __launch_bounds__(32 * CcLaunch<K, T, MODE, CART>::WARPS, CcLaunch<K, T, MODE, CART>::MINB)
+    stokes_cell_apply_cc_det(const LevelDesc<T> L, const T *__restrict__ u, const T *__restrict__ p,
+                             T *__restrict__ yu, T *__restrict__ yp, const T *__restrict__ geo, const GridBarrier gb) {
+  pdl_enter();
+  constexpr int WARPS = CcLaunch<K, T, MODE, CART>::WARPS;
+  const long long wstride = (long long)gridDim.x * WARPS;
+  for (int colour = 0; colour < 8; ++colour) {
+    const long long cells = colour_extent(L.n, colour, 0) * colour_extent(L.n, colour, 1) *
+                            colour_extent(L.n, colour, 2);
+    const long long groups = (cells + kCcCells - 1) / kCcCells;
+    for (long long g = (long long)blockIdx.x * WARPS + (threadIdx.x >> 5); g < groups; g += wstride)
+      cc_group<K, T, MODE, CART, true>(L, u, p, yu, yp, geo, g, colour);
+    if (colour < 7 && !grid_barrier(gb)) return;
   }
 }
 
 // The trilinear kernels keep their geometry in shared memory: ask for the largest shared-memory
 // carveout so that occupancy is set by registers, not by the default L1 / shared split.
+template <int K, typename T, int MODE>
+static cudaError_t cc_carveout_mode() {
+  const int pc = (int)cudaSharedmemCarveoutMaxShared;
+  cudaError_t e = cudaFuncSetAttribute(stokes_cell_apply_cc<K, T, MODE, false>,
+                                       cudaFuncAttributePreferredSharedMemoryCarveout, pc);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(stokes_cell_apply_cc_det<K, T, MODE, false>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, pc);
+  return e;
+}
 template <int K>
 cudaError_t cc_prefer_shared() {
   if constexpr (K == 2) {
-    const int pc = (int)cudaSharedmemCarveoutMaxShared;
-    cudaError_t e = cudaFuncSetAttribute(stokes_cell_apply_cc<2, float, kApplyA, false>,
-                                         cudaFuncAttributePreferredSharedMemoryCarveout, pc);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(stokes_cell_apply_cc<2, float, kApplyBT, false>,
-                               cudaFuncAttributePreferredSharedMemoryCarveout, pc);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(stokes_cell_apply_cc<2, float, kApplyB, false>,
-                               cudaFuncAttributePreferredSharedMemoryCarveout, pc);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(stokes_cell_apply_cc<2, float, kApplyA | kApplyBT, false>,
-                               cudaFuncAttributePreferredSharedMemoryCarveout, pc);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(stokes_cell_apply_cc<2, float, kApplyA | kApplyBT | kApplyB, false>,
-                               cudaFuncAttributePreferredSharedMemoryCarveout, pc);
+    cudaError_t e = cc_carveout_mode<2, float, kApplyA>();
+    if (e == cudaSuccess) e = cc_carveout_mode<2, float, kApplyBT>();
+    if (e == cudaSuccess) e = cc_carveout_mode<2, float, kApplyB>();
+    if (e == cudaSuccess) e = cc_carveout_mode<2, float, kApplyA | kApplyBT>();
+    if (e == cudaSuccess) e = cc_carveout_mode<2, float, kApplyA | kApplyBT | kApplyB>();
     return e;
   }
   return cudaSuccess;
 }
 
 template <int K, typename T, int MODE, bool CART>
-static void launch_cc_mode(const LevelDesc<T> &L, const T *u, const T *p, T *yu, T *yp, cudaStream_t s) {
+static void launch_cc_mode(const LevelDesc<T> &L, const T *u, const T *p, T *yu, T *yp, const T *geo,
+                           cudaStream_t s) {
   using CL = CcLaunch<K, T, MODE, CART>;
   const long long cpb = (long long)kCcCells * CL::WARPS;
   const long long blocks = (L.n_cells + cpb - 1) / cpb;
   launch_kernel(stokes_cell_apply_cc<K, T, MODE, CART>, dim3((unsigned)blocks), dim3(32 * CL::WARPS), CL::SMEM, s, L,
-                u, p, yu, yp);
+                u, p, yu, yp, geo);
+}
+
+// Cooperative launch of the deterministic form: at most as many CTAs as can be resident at once
+// (the occupancy of this instantiation times the SM count), so that every CTA reaches every
+// barrier; never more than the largest colour class needs.
+template <int K, typename T, int MODE, bool CART>
+static int launch_cc_det_mode(const LevelDesc<T> &L, const T *u, const T *p, T *yu, T *yp, const T *geo,
+                              const GridBarrier &gb, cudaStream_t s) {
+  using CL = CcLaunch<K, T, MODE, CART>;
+  static int resident = -1;
+  if (resident < 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stokes_cell_apply_cc_det<K, T, MODE, CART>,
+                                                      32 * CL::WARPS, CL::SMEM_DET) != cudaSuccess)
+      return (int)cudaGetLastError();
+    resident = per_sm * sms;
+  }
+  if (resident <= 0) return (int)cudaErrorCooperativeLaunchTooLarge;
+  long long biggest = 0;
+  for (int colour = 0; colour < 8; ++colour)
+    biggest = std::max(biggest, colour_extent(L.n, colour, 0) * colour_extent(L.n, colour, 1) *
+                                    colour_extent(L.n, colour, 2));
+  const long long cpb = (long long)kCcCells * CL::WARPS;
+  const long long need = std::max(1ll, (biggest + cpb - 1) / cpb);
+  const unsigned grid = (unsigned)std::min<long long>(need, resident);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(32 * CL::WARPS);
+  cfg.dynamicSmemBytes = CL::SMEM_DET;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return (int)cudaLaunchKernelEx(&cfg, stokes_cell_apply_cc_det<K, T, MODE, CART>, L, u, p, yu, yp, geo, gb);
+}
+
+// Whether this kernel serves the level: 3D; Cartesian k = 2, 3; trilinear k = 2 in FP32, and in
+// FP64 where the per-point geometry is stored (geo).
+template <typename T>
+inline bool cc_serves(const LevelDesc<T> &L, const T *geo) {
+  if (!cc_level_supported(L.dim, L.k, L.cartesian, sizeof(T))) return false;
+  return L.cartesian || sizeof(T) == 4 || geo != nullptr;
 }
 
 // Launches shape 5 for the modes the kernel has (A, B^T, B, A + B^T, full); -1 otherwise.
+// det: the deterministic cooperative form with the grid barrier *det (returns a cudaError_t code
+// > 0 when that launch fails).
 template <int K, typename T>
-int launch_cell_apply_cc_k(const LevelDesc<T> &L, int mode, const T *u, const T *p, T *yu, T *yp, cudaStream_t s) {
-  if (!cc_level_supported(L.dim, L.k, L.cartesian, sizeof(T)) || L.k != K) return -1;
-  constexpr bool TRI = K == 2 && sizeof(T) == 4;
-#define SMF_CC_CASE(M)                                                       \
-  case M:                                                                    \
-    if (L.cartesian)                                                         \
-      launch_cc_mode<K, T, M, true>(L, u, p, yu, yp, s);                     \
-    else if constexpr (TRI)                                                  \
-      launch_cc_mode<K, T, M, false>(L, u, p, yu, yp, s);                    \
-    return 0;
+int launch_cell_apply_cc_k(const LevelDesc<T> &L, int mode, const T *u, const T *p, T *yu, T *yp, const T *geo,
+                           const GridBarrier *det, cudaStream_t s) {
+  if (L.k != K || !cc_serves(L, geo)) return -1;
+#define SMF_CC_CASE(M)                                                                   \
+  case M:                                                                                \
+    if (L.cartesian)                                                                     \
+      return det ? launch_cc_det_mode<K, T, M, true>(L, u, p, yu, yp, geo, *det, s)      \
+                 : (launch_cc_mode<K, T, M, true>(L, u, p, yu, yp, geo, s), 0);          \
+    if constexpr (K == 2)                                                                \
+      return det ? launch_cc_det_mode<K, T, M, false>(L, u, p, yu, yp, geo, *det, s)     \
+                 : (launch_cc_mode<K, T, M, false>(L, u, p, yu, yp, geo, s), 0);         \
+    return -1;
   switch (mode) {
     SMF_CC_CASE(kApplyA)
     SMF_CC_CASE(kApplyBT)

@@ -5,8 +5,8 @@
 
 namespace smf {
 template int launch_cell_apply_cc_k<2, float>(const LevelDesc<float> &, int, const float *, const float *, float *,
-                                              float *, cudaStream_t);
+                                              float *, const float *, const GridBarrier *, cudaStream_t);
 template int launch_cell_apply_cc_k<2, double>(const LevelDesc<double> &, int, const double *, const double *,
-                                               double *, double *, cudaStream_t);
+                                               double *, double *, const double *, const GridBarrier *, cudaStream_t);
 template int upload_cc_tables<2>(const Tab1D<double> &, cudaStream_t);
 }  // namespace smf

@@ -166,11 +166,22 @@ int launch_cell_apply_fused_k(const LevelDesc<T> &L, int mode, const T *u, const
   }
 }
 
+// 3D: one launch per colour class of cells (fixed summation order at every node).
 template <int DIM, int K, typename T, bool CART>
 static int launch_diag_dim(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dSloc, T *dMp, cudaStream_t s,
                            const T *rho, int sym) {
   using CS = CellShape<DIM, K>;
-  stokes_cell_diagonals<DIM, K, T, CART><<<(unsigned)L.n_cells, CS::NP, 0, s>>>(L, tab, dAs, dSloc, dMp, rho, sym);
+  if (DIM != 3) {
+    stokes_cell_diagonals<DIM, K, T, CART><<<(unsigned)L.n_cells, CS::NP, 0, s>>>(L, tab, dAs, dSloc, dMp, rho, sym, -1);
+    return 0;
+  }
+  for (int colour = 0; colour < 8; ++colour) {
+    const long long cells = (long long)((L.n[0] - (colour & 1) + 1) / 2) * ((L.n[1] - ((colour >> 1) & 1) + 1) / 2) *
+                            ((L.n[2] - ((colour >> 2) & 1) + 1) / 2);
+    if (cells > 0)
+      stokes_cell_diagonals<DIM, K, T, CART><<<(unsigned)cells, CS::NP, 0, s>>>(L, tab, dAs, dSloc, dMp, rho, sym,
+                                                                                colour);
+  }
   return 0;
 }
 

@@ -112,6 +112,52 @@ __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+// Grid-wide barrier of a cooperative launch with a bounded wait.  state (device, zeroed by the
+// host before a launch sequence): [0] arrivals of the current round, [1] round counter, [2] error
+// flag, [3] wait budget in clock64() cycles (as an unsigned; 0 means 2^31).  A CTA that waits longer
+// than the budget sets the error flag and returns false; every CTA that sees the flag returns false,
+// so no CTA waits for one that has left.
+struct GridBarrier {
+  unsigned *state = nullptr;
+};
+#if defined(__CUDACC__)
+__device__ __forceinline__ bool grid_barrier(const GridBarrier &B) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *st = B.state;
+    const unsigned round = st[1];
+    __threadfence();
+    int good = 1;
+    if (atomicAdd(&B.state[0], 1u) == gridDim.x - 1) {
+      atomicExch(&B.state[0], 0u);
+      __threadfence();
+      atomicAdd(&B.state[1], 1u);
+    } else {
+      const unsigned bud = st[3];
+      const long long budget = bud ? (long long)bud : (1ll << 31);
+      const long long t0 = clock64();
+      while (st[1] == round) {
+        if (st[2]) {
+          good = 0;
+          break;
+        }
+        if (clock64() - t0 > budget) {
+          atomicExch(&B.state[2], 1u);
+          good = 0;
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    ok = good && st[2] == 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+#endif
+
 // Host side: launch with the programmatic-stream-serialization attribute (PDL) where pdl_on(s)
 // says so (by default outside stream capture only).  Every kernel of the library begins with
 // pdl_enter().
