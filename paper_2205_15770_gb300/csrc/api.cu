@@ -477,27 +477,35 @@ struct Runner {
     launch_kernel(k_coarse_apply<T>, dim3((n0 * 32 + 255) / 256), dim3(256), 0, s, (const double *)C->Kinv, n0, b, x);
     note();
   }
+  // restriction out = P^T in, or P^T (in - sub) (the residual formed while restricting)
   template <int W>
-  void restrict_w(int lf, const T *in, T *out, T *zero_c) {
+  void restrict_w(int lf, const T *in, T *out, T *zero_c, const T *sub) {
     const long long n = nu(lf - 1) + np(lf - 1);
-    if (n < 32768)
-      vec(k_restrict<T, W, 8>, n * 8, L[lf].d, L[lf - 1].d, L[lf].xf, in, out, zero_c);
-    else
-      vec(k_restrict<T, W, 1>, n, L[lf].d, L[lf - 1].d, L[lf].xf, in, out, zero_c);
-  }
-  void restrict_to(int lf, const T *in, T *out, T *zero_c) {
-    switch (L[lf].d.k) {
-      case 2: restrict_w<9>(lf, in, out, zero_c); break;
-      case 3: restrict_w<13>(lf, in, out, zero_c); break;
-      default: restrict_w<17>(lf, in, out, zero_c); break;
+    if (sub) {
+      if (n < 32768)
+        vec(k_restrict<T, W, 8, true>, n * 8, L[lf].d, L[lf - 1].d, L[lf].xf, in, out, zero_c, sub);
+      else
+        vec(k_restrict<T, W, 1, true>, n, L[lf].d, L[lf - 1].d, L[lf].xf, in, out, zero_c, sub);
+    } else {
+      if (n < 32768)
+        vec(k_restrict<T, W, 8, false>, n * 8, L[lf].d, L[lf - 1].d, L[lf].xf, in, out, zero_c, sub);
+      else
+        vec(k_restrict<T, W, 1, false>, n, L[lf].d, L[lf - 1].d, L[lf].xf, in, out, zero_c, sub);
     }
   }
-  void prolongate(int lf, const T *in, T *out, int add, T *z0 = nullptr, T *z1 = nullptr) {
+  void restrict_to(int lf, const T *in, T *out, T *zero_c, const T *sub = nullptr) {
+    switch (L[lf].d.k) {
+      case 2: restrict_w<9>(lf, in, out, zero_c, sub); break;
+      case 3: restrict_w<13>(lf, in, out, zero_c, sub); break;
+      default: restrict_w<17>(lf, in, out, zero_c, sub); break;
+    }
+  }
+  void prolongate(int lf, const T *in, T *out, int add, T *z0 = nullptr, T *z1 = nullptr, T *zf = nullptr) {
     const long long n = nu(lf) + np(lf);
     switch (L[lf].d.k) {
-      case 2: vec(k_prolongate<T, 9>, n, L[lf].d, L[lf - 1].d, L[lf].xf, in, out, add, z0, z1); break;
-      case 3: vec(k_prolongate<T, 13>, n, L[lf].d, L[lf - 1].d, L[lf].xf, in, out, add, z0, z1); break;
-      default: vec(k_prolongate<T, 17>, n, L[lf].d, L[lf - 1].d, L[lf].xf, in, out, add, z0, z1); break;
+      case 2: vec(k_prolongate<T, 9>, n, L[lf].d, L[lf - 1].d, L[lf].xf, in, out, add, z0, z1, zf); break;
+      case 3: vec(k_prolongate<T, 13>, n, L[lf].d, L[lf - 1].d, L[lf].xf, in, out, add, z0, z1, zf); break;
+      default: vec(k_prolongate<T, 17>, n, L[lf].d, L[lf - 1].d, L[lf].xf, in, out, add, z0, z1, zf); break;
     }
   }
   // ---- fused smoothing: k_A = 1, 3D column kernel ------------------------------------------
@@ -522,6 +530,13 @@ struct Runner {
     return b[j];
   }
   void fapply(int l, int mode, const T *u, const T *p, T *yu, T *yp, const Fuse<T> &F) {
+    if (L[l].shape == 5) {  // the cell-component kernel's fused form where it has one (k = 2)
+      const int r = launch_cell_apply_cc_fused_k<2, T>(L[l].d, mode, u, p, yu, yp, L[l].geo, F, s);
+      if (r == 0) {
+        note();
+        return;
+      }
+    }
     const int sh = L[l].shape == 5 ? L[l].fshape : L[l].shape;
     launch_cell_apply_fused<T>(L[l].d, mode, u, p, yu, yp, s, sh, F, L[l].geo);
     note();
@@ -710,7 +725,6 @@ struct Runner {
       return;
     }
     LevelRT<T> &R = L[l];
-    const long long n = nu(l) + np(l);
     const bool fz = fused_ok(l);
     int pend = -1;
     for (int i = 0; i < C->o.m; ++i) {
@@ -719,20 +733,23 @@ struct Runner {
       else
         smooth_step(l, x, b, x_zero && i == 0);
     }
-    if (C->o.m == 0 && x_zero) {
-      vec(k_convert_zero<T, T, 1>, n, b, R.r, (T *)nullptr, n);  // r = b - K 0
+    // residual b - K x (Algorithm 1) formed inside the restriction; the K x accumulator is zeroed
+    // again by the prolongation below
+    const bool kx_used = !(C->o.m == 0 && x_zero);
+    if (!kx_used) {
+      restrict_to(l, b, L[l - 1].b, L[l - 1].x);  // r = b - K 0
     } else {
       if (fz)
         fused_residual_apply(l, x, pend);
       else
         apply_nz(l, kApplyA | kApplyBT | kApplyB, x, x + nu(l), R.kx, R.kx + nu(l));
       applyC(l, x + nu(l), R.kx + nu(l), T(-1));
-      vecp(k_residual<T, 1>, k_residual<T, VW>, {b, R.kx, R.r}, n, b, R.kx, R.r, n);
+      restrict_to(l, b, L[l - 1].b, L[l - 1].x, R.kx);
     }
-    restrict_to(l, R.r, L[l - 1].b, L[l - 1].x);
     const int gam = C->o.cycle == 1 ? 2 : 1;
     for (int j = 0; j < gam; ++j) cycle(l - 1, L[l - 1].x, L[l - 1].b, j == 0);
-    prolongate(l, L[l - 1].x, x, 1, pend >= 0 ? pairU(l, pend) : nullptr, pend >= 0 ? pairT(l, pend) : nullptr);
+    prolongate(l, L[l - 1].x, x, 1, pend >= 0 ? pairU(l, pend) : nullptr, pend >= 0 ? pairT(l, pend) : nullptr,
+               kx_used ? R.kx : nullptr);
     pend = -1;
     for (int i = 0; i < C->o.m; ++i) {
       if (fz)

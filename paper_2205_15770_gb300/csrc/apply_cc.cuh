@@ -189,10 +189,13 @@ __host__ __device__ inline long long colour_extent(const int n[3], int colour, i
 // by atomicAdd.  colour >= 0 (DET): the group-th 10 cells of that colour class, scatter by plain
 // read-modify-write through L2 (no other thread touches the node in this class), the three
 // component threads' pressure sums added in a fixed order: bitwise reproducible results.
-template <int K, typename T, int MODE, bool CART, bool DET>
+// FUSED: the inputs are the pointwise combinations of the Fuse descriptor F (the smoother's vector
+// updates, Sec. 3.3.1), evaluated while gathering; the owner of each gathered node (thread of its
+// component in the owning cell; component 0 for pressure nodes) performs F's side effects.
+template <int K, typename T, int MODE, bool CART, bool DET, bool FUSED = false>
 __device__ __forceinline__ void cc_group(const LevelDesc<T> &L, const T *__restrict__ u, const T *__restrict__ p,
                                          T *__restrict__ yu, T *__restrict__ yp, const T *__restrict__ geo,
-                                         long long group, int colour) {
+                                         long long group, int colour, const Fuse<T> &F = Fuse<T>{}) {
   constexpr int NV = K + 1, NQ = K + 1, NPR = K, CPW = kCcCells;
   constexpr bool DO_A = MODE & kApplyA, DO_BT = MODE & kApplyBT, DO_B = MODE & kApplyB;
   constexpr bool NEED_U = DO_A || DO_B;
@@ -248,7 +251,43 @@ __device__ __forceinline__ void cc_group(const LevelDesc<T> &L, const T *__restr
   // ---- gathers --------------------------------------------------------------------------------
   T uv[NV][NV][NV];
   const T *ub = u + vbase;
-  if (NEED_U && !CART) {
+  if constexpr (FUSED) {
+    bool ox[NV], oy[NV], oz[NV];  // this cell owns the node (local index below the last, or last cell)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      ox[i] = valid && (i < K || cx == L.n[0] - 1);
+      oy[i] = i < K || cy == L.n[1] - 1;
+      oz[i] = i < K || cz == L.n[2] - 1;
+    }
+#pragma unroll
+    for (int iz = 0; iz < NV; ++iz)
+#pragma unroll
+      for (int iy = 0; iy < NV; ++iy)
+#pragma unroll
+        for (int ix = 0; ix < NV; ++ix) {
+          const long long gi = vbase + iz * N01 + iy * N0 + ix;
+          const bool fr = fx[ix] && fy[iy] && fz[iz];
+          const bool own = ox[ix] && oy[iy] && oz[iz];
+          T val = T(0);
+          if ((fr && NEED_U) || (own && F.vstore)) {
+            if (F.nv > 0) {
+              T sum = F.vc[0] * F.vv[0][gi];
+#pragma unroll
+              for (int j = 1; j < kFuseVel; ++j)
+                if (j < F.nv) sum += F.vc[j] * F.vv[j][gi];
+              val = (F.vb ? F.vb[gi] : T(0)) + (F.vd ? F.vd[gi] : T(1)) * sum;
+            } else {
+              val = u[gi];
+            }
+          }
+          uv[iz][iy][ix] = fr ? val : T(0);
+          if (own) {
+            if (F.vstore) F.vstore[gi] = val;
+            if (F.vzero[0]) F.vzero[0][gi] = T(0);
+            if (F.vzero[1]) F.vzero[1][gi] = T(0);
+          }
+        }
+  } else if (NEED_U && !CART) {
     if (fast) {
 #pragma unroll
       for (int iz = 0; iz < NV; ++iz)
@@ -269,7 +308,37 @@ __device__ __forceinline__ void cc_group(const LevelDesc<T> &L, const T *__restr
   T pv[NPR][NPR][NPR];
   const long long P0 = L.Pn[0], P01 = (long long)L.Pn[0] * L.Pn[1];
   const long long pbase = ((long long)((K - 1) * cz) * L.Pn[1] + (K - 1) * cy) * P0 + (K - 1) * cx;
-  if (DO_BT && !CART) {
+  if (DO_BT && FUSED) {
+#pragma unroll
+    for (int a3 = 0; a3 < NPR; ++a3)
+#pragma unroll
+      for (int a2 = 0; a2 < NPR; ++a2)
+#pragma unroll
+        for (int a1 = 0; a1 < NPR; ++a1) {
+          const long long gi = pbase + a3 * P01 + a2 * P0 + a1;
+          T val = T(0);
+          if (valid) {
+            if (F.np > 0) {
+              T sum = T(0);
+#pragma unroll
+              for (int j = 0; j < kFusePre; ++j)
+                if (j < F.np) sum += F.pc[j] * F.pv[j][gi];
+              val = F.pd[gi] * sum;
+            } else {
+              val = p[gi];
+            }
+          }
+          pv[a3][a2][a1] = val;
+          const bool pown = valid && c == 0 && (a1 < K - 1 || cx == L.n[0] - 1) && (a2 < K - 1 || cy == L.n[1] - 1) &&
+                            (a3 < K - 1 || cz == L.n[2] - 1);
+          if (pown) {
+            if (F.pacc) F.pacc[gi] += val;
+#pragma unroll
+            for (int j = 0; j < kFusePre; ++j)
+              if (F.pzero[j]) F.pzero[j][gi] = T(0);
+          }
+        }
+  } else if (DO_BT && !CART) {
 #pragma unroll
     for (int a3 = 0; a3 < NPR; ++a3)
 #pragma unroll
@@ -322,7 +391,7 @@ __device__ __forceinline__ void cc_group(const LevelDesc<T> &L, const T *__restr
     }
     if (NEED_U) {
       // FP64 and k = 3: the slice loop stays rolled (registers for the output tensor first)
-      constexpr int SLICE_UNROLL = (K == 2 && sizeof(T) == 4) ? NV : SMF_CC_SLICE_UNROLL;
+      constexpr int SLICE_UNROLL = (K == 2 && (sizeof(T) == 4 || FUSED)) ? NV : SMF_CC_SLICE_UNROLL;
       unsigned fxm = 0;
 #pragma unroll
       for (int i = 0; i < NV; ++i) fxm |= fx[i] ? (1u << i) : 0u;
@@ -334,7 +403,7 @@ __device__ __forceinline__ void cc_group(const LevelDesc<T> &L, const T *__restr
         for (int z = 0; z < NV; ++z)
 #pragma unroll
           for (int y = 0; y < NV; ++y)
-            sl[z][y] = (fast || (fxi && fy[y] && fz[z])) ? ub[z * N01 + y * N0 + i] : T(0);
+            sl[z][y] = FUSED ? uv[z][y][i] : ((fast || (fxi && fy[y] && fz[z])) ? ub[z * N01 + y * N0 + i] : T(0));
         if (DO_B) {
           T t1[NV][NPR];
 #pragma unroll
@@ -398,7 +467,7 @@ __device__ __forceinline__ void cc_group(const LevelDesc<T> &L, const T *__restr
 #pragma unroll
         for (int c3 = 0; c3 < NPR; ++c3)
 #pragma unroll
-          for (int b = 0; b < NPR; ++b) ps[c3][b] = valid ? p[pbase + c3 * P01 + b * P0 + a] : T(0);
+          for (int b = 0; b < NPR; ++b) ps[c3][b] = FUSED ? pv[c3][b][a] : (valid ? p[pbase + c3 * P01 + b * P0 + a] : T(0));
         T t[NPR][NV];  // [c3][y]
 #pragma unroll
         for (int c3 = 0; c3 < NPR; ++c3)
@@ -698,6 +767,16 @@ __global__ void __launch_bounds__(32 * CcLaunch<K, T, MODE, CART>::WARPS, CcLaun
                                     (long long)blockIdx.x * CcLaunch<K, T, MODE, CART>::WARPS + (threadIdx.x >> 5), -1);
 }
 
+// Fused smoothing form (k = 2): inputs and owner side effects from the Fuse descriptor.
+template <int K, typename T, int MODE, bool CART>
+__global__ void __launch_bounds__(32 * CcLaunch<K, T, MODE, CART>::WARPS, CcLaunch<K, T, MODE, CART>::MINB)
+    stokes_cell_apply_cc_fused(const LevelDesc<T> L, const T *__restrict__ u, const T *__restrict__ p,
+                               T *__restrict__ yu, T *__restrict__ yp, const T *__restrict__ geo, const Fuse<T> F) {
+  pdl_enter();
+  cc_group<K, T, MODE, CART, false, true>(
+      L, u, p, yu, yp, geo, (long long)blockIdx.x * CcLaunch<K, T, MODE, CART>::WARPS + (threadIdx.x >> 5), -1, F);
+}
+
 // Deterministic form: one cooperative launch walks the 8 colour classes of cells in order, each
 // class by all CTAs (a warp per group of 10 cells), with a grid barrier between classes.  The
 // barrier waits are bounded (GridBarrier::budget); a wait that runs out sets the error flag and
@@ -728,6 +807,9 @@ static cudaError_t cc_carveout_mode() {
                                        cudaFuncAttributePreferredSharedMemoryCarveout, pc);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(stokes_cell_apply_cc_det<K, T, MODE, false>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, pc);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(stokes_cell_apply_cc_fused<K, T, MODE, false>,
                              cudaFuncAttributePreferredSharedMemoryCarveout, pc);
   return e;
 }
@@ -825,6 +907,40 @@ int launch_cell_apply_cc_k(const LevelDesc<T> &L, int mode, const T *u, const T 
     default: return -1;
   }
 #undef SMF_CC_CASE
+}
+
+// Fused smoothing applications on a level served by this kernel (k = 2); -1 otherwise.
+template <int K, typename T>
+int launch_cell_apply_cc_fused_k(const LevelDesc<T> &L, int mode, const T *u, const T *p, T *yu, T *yp,
+                                 const T *geo, const Fuse<T> &F, cudaStream_t s) {
+  if constexpr (K != 2) {
+    return -1;
+  } else {
+    if (L.k != 2 || !cc_serves(L, geo)) return -1;
+#define SMF_CCF_CASE(M)                                                                                         \
+  case M: {                                                                                                     \
+    using CL = CcLaunch<2, T, M, false>;                                                                        \
+    using CC = CcLaunch<2, T, M, true>;                                                                         \
+    const long long cpb = (long long)kCcCells * (L.cartesian ? CC::WARPS : CL::WARPS);                          \
+    const unsigned blocks = (unsigned)((L.n_cells + cpb - 1) / cpb);                                            \
+    if (L.cartesian)                                                                                            \
+      launch_kernel(stokes_cell_apply_cc_fused<2, T, M, true>, dim3(blocks), dim3(32 * CC::WARPS), CC::SMEM, s, L, \
+                    u, p, yu, yp, geo, F);                                                                      \
+    else                                                                                                        \
+      launch_kernel(stokes_cell_apply_cc_fused<2, T, M, false>, dim3(blocks), dim3(32 * CL::WARPS), CL::SMEM, s, \
+                    L, u, p, yu, yp, geo, F);                                                                   \
+    return 0;                                                                                                   \
+  }
+    switch (mode) {
+      SMF_CCF_CASE(kApplyA)
+      SMF_CCF_CASE(kApplyBT)
+      SMF_CCF_CASE(kApplyB)
+      SMF_CCF_CASE(kApplyA | kApplyBT)
+      SMF_CCF_CASE(kApplyA | kApplyBT | kApplyB)
+      default: return -1;
+    }
+#undef SMF_CCF_CASE
+  }
 }
 
 }  // namespace smf

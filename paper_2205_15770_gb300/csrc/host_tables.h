@@ -55,6 +55,9 @@ int launch_cell_apply_cc_k(const LevelDesc<T> &L, int mode, const T *u, const T 
 template <int K>
 int upload_cc_tables(const Tab1D<double> &t, cudaStream_t s);
 template <int K, typename T>
+int launch_cell_apply_cc_fused_k(const LevelDesc<T> &L, int mode, const T *u, const T *p, T *yu, T *yp,
+                                 const T *geo, const Fuse<T> &F, cudaStream_t s);
+template <int K, typename T>
 int launch_cell_diag_k(const LevelDesc<T> &L, const Tab1D<T> *tab, T *dAs, T *dSloc, T *dMp, cudaStream_t s,
                        const T *rho, int sym);
 }  // namespace smf

@@ -33,12 +33,13 @@ struct XferTabs {
 };
 
 // out (coarse) = P^T in (fine); zero_c (coarse-sized, may be null) is zeroed on the way.
+// SUB: out = P^T (in - minus), the residual b - K x of Algorithm 1 formed while restricting it.
 // LANES consecutive lanes share one coarse DoF and split its (z, y) term pairs; the partial sums
 // are combined with shuffles (LANES > 1 on small coarse levels, where there are too few DoFs to
 // fill the GPU).
-template <typename T, int W, int LANES>
+template <typename T, int W, int LANES, bool SUB = false>
 __global__ void k_restrict(const LevelDesc<T> F, const LevelDesc<T> C, const XferTabs<T> X, const T *__restrict__ in,
-                           T *__restrict__ out, T *__restrict__ zero_c) {
+                           T *__restrict__ out, T *__restrict__ zero_c, const T *__restrict__ minus = nullptr) {
   pdl_enter();
   const long long total = (C.n_u + C.n_p) * LANES;
   const int sub = threadIdx.x & (LANES - 1);
@@ -55,7 +56,9 @@ __global__ void k_restrict(const LevelDesc<T> F, const LevelDesc<T> C, const Xfe
       const int *Nc = vel ? C.N : C.Pn, *Nf = vel ? F.N : F.Pn;
       const long long j = vel ? i % C.nv : i - C.n_u;
       const int G0 = (int)(j % Nc[0]), G1 = (int)((j / Nc[0]) % Nc[1]), G2 = (int)(j / ((long long)Nc[0] * Nc[1]));
-      const T *src = in + (vel ? (i / C.nv) * F.nv : F.n_u);
+      const long long off = vel ? (i / C.nv) * F.nv : F.n_u;
+      const T *src = in + off;
+      const T *ssrc = SUB ? minus + off : nullptr;
       const Xfer1D<T> &ax = X.r[sp][0], &ay = X.r[sp][1], &az = X.r[sp][2];
       const int n0 = ax.cnt[G0], n1 = ay.cnt[G1], n2 = az.cnt[G2];
       int f0[W];
@@ -69,11 +72,19 @@ __global__ void k_restrict(const LevelDesc<T> F, const LevelDesc<T> C, const Xfe
         const int a1 = t % n1, a2 = t / n1;
         const int f1 = ay.idx[G1 * W + a1], f2 = az.idx[G2 * W + a2];
         const T w21 = ay.w[G1 * W + a1] * az.w[G2 * W + a2];
-        const T *row = src + ((long long)f2 * Nf[1] + f1) * Nf[0];
+        const long long ro = ((long long)f2 * Nf[1] + f1) * Nf[0];
+        const T *row = src + ro;
         T r = T(0);
+        if (SUB) {
+          const T *srow = ssrc + ro;
 #pragma unroll
-        for (int a = 0; a < W; ++a)
-          if (a < n0) r += w0[a] * row[f0[a]];
+          for (int a = 0; a < W; ++a)
+            if (a < n0) r += w0[a] * (row[f0[a]] - srow[f0[a]]);
+        } else {
+#pragma unroll
+          for (int a = 0; a < W; ++a)
+            if (a < n0) r += w0[a] * row[f0[a]];
+        }
         s += w21 * r;
       }
     }
@@ -87,13 +98,16 @@ __global__ void k_restrict(const LevelDesc<T> F, const LevelDesc<T> C, const Xfe
 }
 
 // out (fine) = P in (coarse); add != 0: out += P in.  Covers velocity and pressure.  z0 / z1
-// (fine velocity-sized, may be null) are zeroed on the way.
+// (fine velocity-sized, may be null) and zf (fine full-sized, may be null: the residual's K x
+// accumulator) are zeroed on the way.
 template <typename T, int W>
 __global__ void k_prolongate(const LevelDesc<T> F, const LevelDesc<T> C, const XferTabs<T> X, const T *__restrict__ in,
-                             T *__restrict__ out, int add, T *__restrict__ z0, T *__restrict__ z1) {
+                             T *__restrict__ out, int add, T *__restrict__ z0, T *__restrict__ z1,
+                             T *__restrict__ zf = nullptr) {
   pdl_enter();
   SMF_GRID_LOOP(i, F.n_u + F.n_p) {
     const bool vel = i < F.n_u;
+    if (zf) zf[i] = T(0);
     if (vel) {
       if (z0) z0[i] = T(0);
       if (z1) z1[i] = T(0);

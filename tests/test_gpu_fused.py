@@ -38,6 +38,17 @@ def _oracle_mg(case, **kw):
     return H, Multigrid(H, mu=case.get("mu", 1.0), gamma_rho=case.get("gamma_rho", 0.0), **kw)
 
 
+def _solver(case, shape, **kw):
+    """gpu_solver with the launch shape pinned on every level (0: the default column kernel; 5: the
+    cell-component kernel, whose fused form then runs wherever it serves the level)."""
+    S = gpu_solver(case, **kw)
+    if shape:
+        for prec in (32, 64):
+            for l in range(case["levels"]):
+                S.set_launch_shape(l, shape, precision=prec)
+    return S
+
+
 def _unfused(monkeypatch, case, **kw):
     monkeypatch.setenv("STOKES_NO_FUSE", "1")
     S = gpu_solver(case, **kw)
@@ -45,14 +56,16 @@ def _unfused(monkeypatch, case, **kw):
     return S
 
 
+@pytest.mark.parametrize("shape", [0, 5])
 @pytest.mark.parametrize("name", FUSED_CASES)
 @pytest.mark.parametrize("kS", [1, 2, 3, 4])
-def test_fused_smoothing_matches_oracle(name, kS):
+def test_fused_smoothing_matches_oracle(name, kS, shape):
     case = CASES[name]
     H, mg = _oracle_mg(case, kA=1, kS=kS, m=2)
     l = len(H.levels) - 1
     lev = H.levels[l]
-    S = gpu_solver(case, kA=1, kS=kS, m=2)
+    S = _solver(case, shape, kA=1, kS=kS, m=2)
+    assert S.fused_levels(64)[l] and S.fused_levels(32)[l]
     b = random_full(lev, 6, constrained_zero=True)
     x0 = random_full(lev, 7, constrained_zero=True)
     ref = mg.smoothers[l].smooth(x0.copy(), b, 3)
@@ -64,13 +77,14 @@ def test_fused_smoothing_matches_oracle(name, kS):
     assert rel_err(_n(x32), ref) < 1e-4
 
 
+@pytest.mark.parametrize("shape", [0, 5])
 @pytest.mark.parametrize("name", FUSED_CASES)
 @pytest.mark.parametrize("cycle", ["V", "W"])
-def test_fused_cycle_matches_oracle(name, cycle):
+def test_fused_cycle_matches_oracle(name, cycle, shape):
     case = CASES[name]
     H, mg = _oracle_mg(case, kA=1, kS=2, m=2, cycle=cycle)
     lev = H.levels[-1]
-    S = gpu_solver(case, kA=1, kS=2, m=2, cycle=cycle)
+    S = _solver(case, shape, kA=1, kS=2, m=2, cycle=cycle)
     b = random_full(lev, 8, constrained_zero=True)
     x0 = random_full(lev, 9, constrained_zero=True)
     for start in (np.zeros(lev.size), x0):
@@ -128,7 +142,7 @@ def test_fused_every_launch_shape(monkeypatch):
     S = gpu_solver(case, kA=1, kS=2, m=2)
     b = _t(random_full(lev, 15, constrained_zero=True))
     ref = _n(S.vcycle(b))
-    for shape in (1, 3, 4, -1):  # -1: point kernel, unfused smoother on that level
+    for shape in (1, 3, 4, -1, 5):  # -1: point kernel, unfused smoother on that level
         for l in range(1, case["levels"]):
             S.set_launch_shape(l, shape, precision=64)
         assert rel_err(_n(S.vcycle(b)), ref) < 1e-12, shape
