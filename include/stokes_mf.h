@@ -258,11 +258,11 @@ int stokes_time_apply(stokes_ctx *ctx, int level, int precision, int blocks, int
                       void *stream);
 
 /* Measurement helper (no counterpart in the paper): FMA throughput of the current device in
- * `precision` (32 or 64), from 5 launches of a kernel running 8 independent multiply-add chains
- * per thread on 8 x 256-thread CTAs per SM, timed by CUDA events on `stream` (NULL: the legacy
- * default stream); *tflops (HOST) = 2 x FMAs / elapsed / 1e12.  No context; allocates and frees
- * a small output buffer; synchronises the stream.  STOKES_EINVAL on a bad precision or a NULL
- * output. */
+ * `precision` (32 or 64; 2: FP32 in packed pairs, one paired multiply-add instruction per two
+ * FMAs), from 5 launches of a kernel running 8 independent multiply-add chains per thread on
+ * 8 x 256-thread CTAs per SM, timed by CUDA events on `stream` (NULL: the legacy default stream);
+ * *tflops (HOST) = 2 x FMAs / elapsed / 1e12.  No context; allocates and frees a small output
+ * buffer; synchronises the stream.  STOKES_EINVAL on a bad precision or a NULL output. */
 int stokes_fma_peak(int precision, double *tflops, void *stream);
 
 /* Batched solves of independent meshes (no counterpart in the paper; a layer on its method).

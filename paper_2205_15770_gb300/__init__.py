@@ -46,7 +46,8 @@ def _ptr(t, dtype):
 
 
 def fma_peak(precision=32):
-    """Measured FMA throughput of the current device in TFLOP/s (stokes_fma_peak)."""
+    """Measured FMA throughput of the current device in TFLOP/s (stokes_fma_peak; precision 32, 64, or 2 for
+    FP32 in packed pairs)."""
     torch = _torch()
     lib = L.load()
     out = C.c_double()

@@ -209,6 +209,25 @@ __global__ void k_fma_peak(T *out, int iters, T seed) {
   for (int j = 0; j < 8; ++j) sum += a[j];
   if (sum == T(-1)) out[(long long)blockIdx.x * blockDim.x + threadIdx.x] = sum;
 }
+// The same chains in packed pairs: 4 float2 chains per thread, each step one paired FP32
+// multiply-add (two FMAs per instruction).
+__global__ void k_fma_peak_x2(float *out, int iters, float seed) {
+  float2 a[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    a[j] = make_float2(seed + float(threadIdx.x + 2 * j) * 1e-7f, seed + float(threadIdx.x + 2 * j + 1) * 1e-7f);
+  const float2 m = make_float2(0.999999f, 0.999999f), c = make_float2(1e-7f, 1e-7f);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) a[j] = __ffma2_rn(a[j], m, c);
+  }
+  float sum = 0.f;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) sum += a[j].x + a[j].y;
+  if (sum == -1.f) out[(long long)blockIdx.x * blockDim.x + threadIdx.x] = sum;
+}
 
 }  // namespace smf
 
@@ -1505,24 +1524,6 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
       SMF_CUDA_OK(cudaStreamSynchronize(C->s));
       d.vert = dv;
       f.vert = fv;
-      // per-point geometry of the FP64 column kernel, precomputed once (the geometry is a quarter
-      // of the FP64 flops of an application; STOKES_GEO=none keeps it on the fly)
-      if (dim == 3) {
-        const char *gs = getenv("STOKES_GEO");
-        const bool g64 = !(gs && std::strcmp(gs, "none") == 0);
-        const long long per = 16LL * (k + 1) * (k + 1) * (k + 1), cells = d.n_cells;
-        // stored when it takes at most 1/16 of the device's memory (17.8 GB on a GB300; 7.2 GB for
-        // a trilinear 128^3 level), a fixed budget so that the choice does not depend on what other
-        // processes hold; skipped only when it would take more than half of the memory still free
-        size_t free_b = 0, total_b = 0;
-        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = total_b = 0;
-        const long long gbytes = cells * per * (long long)sizeof(double);
-        if (g64 && gbytes <= (long long)(total_b / 16) && gbytes <= (long long)(free_b / 2)) {
-          if ((st = dalloc(C, &geo_l, cells * per))) return st;
-          launch_col_geometry<double>(d, geo_l, C->s);
-          SMF_CUDA_OK(cudaGetLastError());
-        }
-      }
     }
     if (mu_cell) {
       std::vector<double> &m = mu_levels[l];
@@ -1549,6 +1550,25 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
       SMF_CUDA_OK(cudaStreamSynchronize(C->s));
       C->L64[l].rho = dr;
       C->L32[l].rho = fr;
+    }
+    // per-point geometry of the FP64 column kernel (mu and gamma rho folded in), precomputed once
+    // (the geometry is a quarter of the FP64 flops of an application; STOKES_GEO=none keeps it on
+    // the fly); after the level's viscosity is in place
+    if (mesh->vertices && dim == 3) {
+      const char *gs = getenv("STOKES_GEO");
+      const bool g64 = !(gs && std::strcmp(gs, "none") == 0);
+      const long long per = 16LL * (k + 1) * (k + 1) * (k + 1), cells = d.n_cells;
+      // stored when it takes at most 1/16 of the device's memory (17.8 GB on a GB300; 7.2 GB for
+      // a trilinear 128^3 level), a fixed budget so that the choice does not depend on what other
+      // processes hold; skipped only when it would take more than half of the memory still free
+      size_t free_b = 0, total_b = 0;
+      if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = total_b = 0;
+      const long long gbytes = cells * per * (long long)sizeof(double);
+      if (g64 && gbytes <= (long long)(total_b / 16) && gbytes <= (long long)(free_b / 2)) {
+        if ((st = dalloc(C, &geo_l, cells * per))) return st;
+        launch_col_geometry<double>(d, geo_l, C->s);
+        SMF_CUDA_OK(cudaGetLastError());
+      }
     }
     C->L64[l].d = d;
     C->L32[l].d = f;
@@ -2956,7 +2976,7 @@ int stokes_mg_iterate(stokes_ctx *C, const double *b, double *x, int max_iter, d
 }
 
 int stokes_fma_peak(int precision, double *tflops, void *stream) {
-  if ((precision != 32 && precision != 64) || !tflops) {
+  if ((precision != 32 && precision != 64 && precision != 2) || !tflops) {
     set_error("invalid stokes_fma_peak arguments");
     return STOKES_EINVAL;
   }
@@ -2965,7 +2985,7 @@ int stokes_fma_peak(int precision, double *tflops, void *stream) {
   SMF_CUDA_OK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   cudaStream_t s = (cudaStream_t)stream;
   const int threads = 256, blocks = sms * 8;
-  const int iters = precision == 32 ? 4000 : 100;  // about 5-10 ms per launch on GB300
+  const int iters = precision == 64 ? 100 : 4000;  // about 5-10 ms per launch on GB300
   void *out = nullptr;
   SMF_CUDA_OK(cudaMalloc(&out, (size_t)blocks * threads * 8));
   cudaEvent_t e0, e1;
@@ -2974,6 +2994,8 @@ int stokes_fma_peak(int precision, double *tflops, void *stream) {
   auto launch = [&]() {
     if (precision == 32)
       k_fma_peak<float><<<blocks, threads, 0, s>>>((float *)out, iters, 1.0f);
+    else if (precision == 2)
+      k_fma_peak_x2<<<blocks, threads, 0, s>>>((float *)out, iters, 1.0f);
     else
       k_fma_peak<double><<<blocks, threads, 0, s>>>((double *)out, iters, 1.0);
   };

@@ -573,11 +573,10 @@ __device__ __forceinline__ void cc_group(const LevelDesc<T> &L, const T *__restr
       }
       __syncwarp();
     }
-    // FP64: the per-point factors stored at setup, [cell][field][qz][qy][qx]: G (6, times mu
-    // here), w adj (9, row-major), w det (1, times gamma rho here)
+    // FP64: the per-point factors stored at setup, [cell][field][qz][qy][qx]: G (6, mu
+    // included), w adj (9, row-major), gamma rho w det (1)
     constexpr int GST = NQ * NQ * NQ;
     const T *gc = CL::SMEM_GEO ? nullptr : geo + cell * (long long)(16 * GST);
-    const T grho_g = L.gamma_rho;
 
     // ---- this component at the Gauss points --------------------------------------------------
     auto Sf = [&](int i, int j) { return tb.S[i * NV + j]; };
@@ -620,8 +619,8 @@ __device__ __forceinline__ void cc_group(const LevelDesc<T> &L, const T *__restr
               gg[0] = g0.x; gg[1] = g0.y; gg[2] = g0.z; gg[3] = g0.w; gg[4] = g1.x; gg[5] = g1.y; gg[6] = g1.z;
             } else {
 #pragma unroll
-              for (int i = 0; i < 6; ++i) gg[i] = mu * gc[i * GST + pt];
-              gg[6] = grho_g * gc[15 * GST + pt];
+              for (int i = 0; i < 6; ++i) gg[i] = gc[i * GST + pt];
+              gg[6] = gc[15 * GST + pt];
             }
           };
           auto geo_C = [&](T(&cc)[3]) {

@@ -79,13 +79,15 @@ __device__ __forceinline__ T sel3(int c, T a, T b, T d) {
 }
 
 // Geometry of a column's Gauss points (qx = ix, qy = iy, qz = 0..NQ-1) of cell (cx, cy, cz):
-// G = w adj(J) adj(J)^T / det J (symmetric, 00 01 02 11 12 22), Cm = w adj(J) (when NEED_C),
-// Wd = w det J, w the tensor Gauss weight.  Trilinear cells: the first two Jacobian columns are
-// linear in zeta along the column and the third is constant, so they are set up once from the
-// 8 vertices and evaluated per point.
+// G = mu w adj(J) adj(J)^T / det J (symmetric, 00 01 02 11 12 22), Cm = w adj(J) (when NEED_C),
+// Wd = gamma rho w det J, w the tensor Gauss weight: the coefficients of the two terms of the
+// viscous block are folded into the per-point factors.  Trilinear cells: the first two Jacobian
+// columns are linear in zeta along the column and the third is constant, so they are set up once
+// from the 8 vertices and evaluated per point.
 template <int K, typename T, bool CART, bool NEED_C>
-__device__ __forceinline__ void col_geometry(const LevelDesc<T> &L, int ix, int iy, int cx, int cy, int cz,
-                                             T (&G)[K + 1][6], T (&Cm)[NEED_C ? K + 1 : 1][9], T (&Wd)[K + 1]) {
+__device__ __forceinline__ void col_geometry(const LevelDesc<T> &L, int ix, int iy, int cx, int cy, int cz, T mu,
+                                             T grho, T (&G)[K + 1][6], T (&Cm)[NEED_C ? K + 1 : 1][9],
+                                             T (&Wd)[K + 1]) {
   using CT = CTab<T>;
   constexpr int NQ = K + 1;
   {
@@ -95,14 +97,14 @@ __device__ __forceinline__ void col_geometry(const LevelDesc<T> &L, int ix, int 
       const T a0 = h1 * h2, a1 = h0 * h2, a2 = h0 * h1, det = h0 * h1 * h2;
 #pragma unroll
       for (int qz = 0; qz < NQ; ++qz) {
-        const T w = wxy * CT::W(qz);
-        G[qz][0] = w * a0 * a0 / det;
+        const T w = wxy * CT::W(qz), wm = mu * w;
+        G[qz][0] = wm * a0 * a0 / det;
         G[qz][1] = T(0);
         G[qz][2] = T(0);
-        G[qz][3] = w * a1 * a1 / det;
+        G[qz][3] = wm * a1 * a1 / det;
         G[qz][4] = T(0);
-        G[qz][5] = w * a2 * a2 / det;
-        Wd[qz] = w * det;
+        G[qz][5] = wm * a2 * a2 / det;
+        Wd[qz] = grho * w * det;
         if (NEED_C) {
 #pragma unroll
           for (int i = 0; i < 9; ++i) Cm[qz][i] = T(0);
@@ -161,14 +163,14 @@ __device__ __forceinline__ void col_geometry(const LevelDesc<T> &L, int ix, int 
         adj[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
         const T det = J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
         const T w = wxy * CT::W(qz);
-        const T wd = w / det;
+        const T wd = mu * w / det;
         G[qz][0] = wd * (adj[0][0] * adj[0][0] + adj[0][1] * adj[0][1] + adj[0][2] * adj[0][2]);
         G[qz][1] = wd * (adj[0][0] * adj[1][0] + adj[0][1] * adj[1][1] + adj[0][2] * adj[1][2]);
         G[qz][2] = wd * (adj[0][0] * adj[2][0] + adj[0][1] * adj[2][1] + adj[0][2] * adj[2][2]);
         G[qz][3] = wd * (adj[1][0] * adj[1][0] + adj[1][1] * adj[1][1] + adj[1][2] * adj[1][2]);
         G[qz][4] = wd * (adj[1][0] * adj[2][0] + adj[1][1] * adj[2][1] + adj[1][2] * adj[2][2]);
         G[qz][5] = wd * (adj[2][0] * adj[2][0] + adj[2][1] * adj[2][1] + adj[2][2] * adj[2][2]);
-        Wd[qz] = w * det;
+        Wd[qz] = grho * w * det;
         if (NEED_C) {
 #pragma unroll
           for (int a = 0; a < 3; ++a)
@@ -275,9 +277,12 @@ __global__ void __launch_bounds__(32 * WARPS)
   if (NEED_U) load_comp(c_begin);
 
   // ---- geometry at the column's Gauss points (qx = ix, qy = iy, qz = 0..NQ-1) --------------
-  T G[NQ][6];                 // w adj adj^T / det, symmetric: 00 01 02 11 12 22
+  T G[NQ][6];                 // mu w adj adj^T / det, symmetric: 00 01 02 11 12 22
   T Cm[NEED_C ? NQ : 1][9];   // w adj
-  T Wd[NQ];                   // w det
+  T Wd[NQ];                   // gamma rho w det
+  // mu and gamma rho enter the per-point factors (G, Wd) where they are formed
+  const T mu = L.mu_cell ? (valid ? L.mu_cell[cell] : T(0)) : L.mu;
+  const T grho = L.gamma_rho;
   // geo (FP64 trilinear levels): precomputed at setup, the geometry being a quarter of the FP64
   // flops; otherwise evaluated on the fly.  (A separate kernel argument: a larger level
   // descriptor changes the register allocation of the FP32 kernels.)
@@ -307,14 +312,14 @@ __global__ void __launch_bounds__(32 * WARPS)
         const T a0 = h1 * h2, a1 = h0 * h2, a2 = h0 * h1, det = h0 * h1 * h2;
   #pragma unroll
         for (int qz = 0; qz < NQ; ++qz) {
-          const T w = wxy * CT::W(qz);
-          G[qz][0] = w * a0 * a0 / det;
+          const T w = wxy * CT::W(qz), wm = mu * w;
+          G[qz][0] = wm * a0 * a0 / det;
           G[qz][1] = T(0);
           G[qz][2] = T(0);
-          G[qz][3] = w * a1 * a1 / det;
+          G[qz][3] = wm * a1 * a1 / det;
           G[qz][4] = T(0);
-          G[qz][5] = w * a2 * a2 / det;
-          Wd[qz] = w * det;
+          G[qz][5] = wm * a2 * a2 / det;
+          Wd[qz] = grho * w * det;
           if (NEED_C) {
   #pragma unroll
             for (int i = 0; i < 9; ++i) Cm[qz][i] = T(0);
@@ -373,14 +378,14 @@ __global__ void __launch_bounds__(32 * WARPS)
           adj[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
           const T det = J[0][0] * adj[0][0] + J[0][1] * adj[1][0] + J[0][2] * adj[2][0];
           const T w = wxy * CT::W(qz);
-          const T wd = w / det;
+          const T wd = mu * w / det;
           G[qz][0] = wd * (adj[0][0] * adj[0][0] + adj[0][1] * adj[0][1] + adj[0][2] * adj[0][2]);
           G[qz][1] = wd * (adj[0][0] * adj[1][0] + adj[0][1] * adj[1][1] + adj[0][2] * adj[1][2]);
           G[qz][2] = wd * (adj[0][0] * adj[2][0] + adj[0][1] * adj[2][1] + adj[0][2] * adj[2][2]);
           G[qz][3] = wd * (adj[1][0] * adj[1][0] + adj[1][1] * adj[1][1] + adj[1][2] * adj[1][2]);
           G[qz][4] = wd * (adj[1][0] * adj[2][0] + adj[1][1] * adj[2][1] + adj[1][2] * adj[2][2]);
           G[qz][5] = wd * (adj[2][0] * adj[2][0] + adj[2][1] * adj[2][1] + adj[2][2] * adj[2][2]);
-          Wd[qz] = w * det;
+          Wd[qz] = grho * w * det;
           if (NEED_C) {
   #pragma unroll
             for (int a = 0; a < 3; ++a)
@@ -391,8 +396,6 @@ __global__ void __launch_bounds__(32 * WARPS)
       }
     }
   }
-  const T mu = L.mu_cell ? (valid ? L.mu_cell[cell] : T(0)) : L.mu;
-  const T grho = L.gamma_rho;
 
   // ---- pressure at the column's Gauss points ---------------------------------------------------
   T pq[NQ];
@@ -569,10 +572,10 @@ __global__ void __launch_bounds__(32 * WARPS)
       for (int q = 0; q < NQ; ++q) {
         T f0 = T(0), f1 = T(0), f2 = T(0), mv = T(0);
         if (DO_A) {
-          f0 = mu * (G[q][0] * gxv[q] + G[q][1] * gyv[q] + G[q][2] * gzv[q]);
-          f1 = mu * (G[q][1] * gxv[q] + G[q][3] * gyv[q] + G[q][4] * gzv[q]);
-          f2 = mu * (G[q][2] * gxv[q] + G[q][4] * gyv[q] + G[q][5] * gzv[q]);
-          mv = grho * Wd[q] * v[q];
+          f0 = G[q][0] * gxv[q] + G[q][1] * gyv[q] + G[q][2] * gzv[q];
+          f1 = G[q][1] * gxv[q] + G[q][3] * gyv[q] + G[q][4] * gzv[q];
+          f2 = G[q][2] * gxv[q] + G[q][4] * gyv[q] + G[q][5] * gzv[q];
+          mv = Wd[q] * v[q];
         }
         if (DO_BT) {
           f0 -= pq[q] * cc0[q];
@@ -662,7 +665,8 @@ __global__ void __launch_bounds__(32 * WARPS)
 namespace smf {
 
 // Per-point geometry of every cell for the column kernel, written once at setup:
-// geo[cell][field][qz][iy][ix], fields G (6), Cm (9), Wd (1) as in col_geometry.
+// geo[cell][field][qz][iy][ix], fields G (6), Cm (9), Wd (1) as in col_geometry (mu and gamma rho
+// included).
 template <int K, typename T>
 __global__ void k_col_geometry(const LevelDesc<T> L, T *__restrict__ geo) {
   pdl_enter();
@@ -674,7 +678,8 @@ __global__ void k_col_geometry(const LevelDesc<T> L, T *__restrict__ geo) {
     const long long rr = cell / L.n[0];
     const int cy = (int)(rr % L.n[1]), cz = (int)(rr / L.n[1]);
     T G[NQ][6], Cm[NQ][9], Wd[NQ];
-    col_geometry<K, T, false, true>(L, ix, iy, cx, cy, cz, G, Cm, Wd);
+    const T mu = L.mu_cell ? L.mu_cell[cell] : L.mu;
+    col_geometry<K, T, false, true>(L, ix, iy, cx, cy, cz, mu, L.gamma_rho, G, Cm, Wd);
     T *base = geo + cell * (long long)(16 * ST) + iy * NV + ix;
 #pragma unroll
     for (int qz = 0; qz < NQ; ++qz) {
