@@ -276,8 +276,11 @@ int stokes_setup_batch(int n_meshes, const stokes_mesh *meshes, const int *k, co
 int stokes_batch_context(stokes_batch *batch, int mesh, stokes_ctx **ctx);
 
 /* Solve every member: b[i], x[i] are device double vectors of member i (x[i] = initial guess
- * in, solution out).  FP64 FGMRES of all members in lockstep; the FP32 cycles of one iteration of
- * all members run as one CUDA-graph launch with one parallel branch per member.  iters,
+ * in, solution out).  FP64 FGMRES of every member; with the iterations on the device
+ * (stokes_batch_krylov_mode 1) one restart cycle of all members is one CUDA-graph launch holding
+ * one conditional while node per member as independent branches, so each member iterates to its
+ * own stopping test without waiting for the others; host-driven (mode 0), the members advance in
+ * lockstep, the FP32 cycles of one iteration of all members as one graph launch.  iters,
  * final_rel_res: HOST arrays of n_meshes entries (nullable).  Synchronises the stream.  Returns
  * the first non-OK member status (STOKES_ENOTCONV / STOKES_EBREAKDOWN). */
 int stokes_solve_batch(stokes_batch *batch, const double *const *b, double *const *x, double rtol,

@@ -464,8 +464,9 @@ class StokesBatch:
 
     @property
     def krylov_mode(self):
-        """1: every member's inner FGMRES iterations on the device in one graph launch per restart cycle,
-        0: host-driven lockstep, -1: no solve yet (stokes_batch_krylov_mode)."""
+        """1: every member's inner FGMRES iterations on the device in one graph launch per restart cycle
+        (one while node per member, independent branches), 0: host-driven lockstep, -1: no solve yet
+        (stokes_batch_krylov_mode)."""
         return int(self._lib.stokes_batch_krylov_mode(self._bt))
 
     def close(self):

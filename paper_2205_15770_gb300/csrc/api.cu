@@ -2094,9 +2094,11 @@ static void dot64_async(stokes_ctx *C, const double *a, const double *b, long lo
   C->launches += 2;
 }
 
-// The device Arnoldi graph of a batch: a while node (runs while any member does) whose body is
-// k_batch_select, one conditional if node per member holding that member's krylov_body, and
-// k_batch_any after all of them.  Members' bodies are independent branches of the body graph.
+// The device Arnoldi graph of a batch: k_batch_select (each member's condition from its stop
+// flag), then one conditional while node per member, each holding that member's krylov_body, as
+// independent branches with no edge between members: every member runs its inner iterations to
+// its own stopping test at its own pace, so a member that needs fewer iterations, or a small mesh,
+// never waits for the others inside the launch.
 static bool batch_kbuild(stokes_batch *Bt) {
   const int nm = (int)Bt->ctx.size();
   Bt->kmode = 0;
@@ -2106,23 +2108,11 @@ static bool batch_kbuild(stokes_batch *Bt) {
   BatchCond bc;
   bc.n = nm;
   bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
-  if (ok) ok = cudaGraphConditionalHandleCreate(&bc.loop, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
-  cudaGraphNodeParams wp = {};
-  cudaGraphNode_t wn = nullptr;
-  if (ok) {
-    wp.type = cudaGraphNodeTypeConditional;
-    wp.conditional.handle = bc.loop;
-    wp.conditional.type = cudaGraphCondTypeWhile;
-    wp.conditional.size = 1;
-    ok = cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, &wp) == cudaSuccess;
-  }
-  cudaGraph_t body = ok ? wp.conditional.phGraph_out[0] : nullptr;
   for (int i = 0; i < nm && ok; ++i) {
-    ok = cudaGraphConditionalHandleCreate(&bc.member[i], body, 0, 0) == cudaSuccess;
+    ok = cudaGraphConditionalHandleCreate(&bc.member[i], g, 0, 0) == cudaSuccess;
     bc.ctl[i] = Bt->ctx[i]->kd.ctl;
   }
-  cudaGraphNode_t seln = nullptr, anyn = nullptr;
-  std::vector<cudaGraphNode_t> ifn(nm, nullptr);
+  cudaGraphNode_t seln = nullptr;
   void *args[1] = {&bc};
   if (ok) {
     cudaKernelNodeParams kp = {};
@@ -2130,36 +2120,29 @@ static bool batch_kbuild(stokes_batch *Bt) {
     kp.gridDim = dim3(1);
     kp.blockDim = dim3(kBatchMax);
     kp.kernelParams = args;
-    ok = cudaGraphAddKernelNode(&seln, body, nullptr, 0, &kp) == cudaSuccess;
+    ok = cudaGraphAddKernelNode(&seln, g, nullptr, 0, &kp) == cudaSuccess;
   }
   Bt->kbody.assign(nm, 0);
   for (int i = 0; i < nm && ok; ++i) {
     stokes_ctx *C = Bt->ctx[i];
-    cudaGraphNodeParams ip = {};
-    ip.type = cudaGraphNodeTypeConditional;
-    ip.conditional.handle = bc.member[i];
-    ip.conditional.type = cudaGraphCondTypeIf;
-    ip.conditional.size = 1;
-    ok = cudaGraphAddNode(&ifn[i], body, &seln, nullptr, 1, &ip) == cudaSuccess;
+    cudaGraphNodeParams wp = {};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = bc.member[i];
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wn = nullptr;
+    ok = cudaGraphAddNode(&wn, g, &seln, nullptr, 1, &wp) == cudaSuccess;
     if (!ok) break;
-    cudaGraph_t ib = ip.conditional.phGraph_out[0];
-    ok = cudaStreamBeginCaptureToGraph(C->s, ib, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    cudaGraph_t wb = wp.conditional.phGraph_out[0];
+    ok = cudaStreamBeginCaptureToGraph(C->s, wb, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (!ok) break;
     C->capturing = true;
     C->cap_count = 0;
-    krylov_body(C, cudaGraphConditionalHandle{}, false);
+    krylov_body(C, bc.member[i], true);
     C->capturing = false;
-    cudaGraph_t out = ib;
+    cudaGraph_t out = wb;
     ok = cudaStreamEndCapture(C->s, &out) == cudaSuccess;
     Bt->kbody[i] = C->cap_count;
-  }
-  if (ok) {
-    cudaKernelNodeParams kp = {};
-    kp.func = (void *)k_batch_any;
-    kp.gridDim = dim3(1);
-    kp.blockDim = dim3(32);
-    kp.kernelParams = args;
-    ok = cudaGraphAddKernelNode(&anyn, body, ifn.data(), nm, &kp) == cudaSuccess;
   }
   if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
   if (g) cudaGraphDestroy(g);
@@ -2266,7 +2249,7 @@ static int batch_solve(stokes_batch *Bt, const double *const *b, double *const *
     for (auto &st : S) nactive += st.done ? 0 : 1;
     if (nactive == 0) break;
     if (Bt->kmode == 1) {
-      // (b') every active member's inner iterations in one graph launch; stopped members idle
+      // (b') every active member's inner iterations in one graph launch, members independent
       for (auto &st : S) {
         stokes_ctx *C = st.C;
         int hctl[4] = {0, st.it, st.done ? 5 : 0, maxit};

@@ -412,12 +412,10 @@ __global__ void k_fgmres_givens(KrylovDev K, cudaGraphConditionalHandle cond, in
 constexpr int kBatchMax = 64;
 struct BatchCond {
   int n = 0;
-  cudaGraphConditionalHandle loop{};
   cudaGraphConditionalHandle member[kBatchMax] = {};
   const int *ctl[kBatchMax] = {};
 };
 __global__ void k_batch_select(const BatchCond B);  // member conditions from their stop flags
-__global__ void k_batch_any(const BatchCond B);     // loop condition: any member still running
 // y = R^{-1} g on the first ctl[0] columns (R the rotated Hessenberg, upper triangular)
 __global__ void k_fgmres_trisolve(KrylovDev K);
 
