@@ -227,27 +227,6 @@ __global__ void k_fused_finish(const T *__restrict__ uhat, const T *__restrict__
   }
 }
 
-// r = b - kx; kx is zeroed after it is read (residual of Algorithm 1).
-template <typename T, int V>
-__global__ void k_residual(const T *__restrict__ b, T *__restrict__ kx, T *__restrict__ r, long long n) {
-  pdl_enter();
-  SMF_PACK_LOOP(j, n, V) {
-    const Pack<T, V> B = ldp<V>(b, j), K = ldp<V>(kx, j);
-    Pack<T, V> R, Z;
-#pragma unroll
-    for (int k = 0; k < V; ++k) {
-      R.v[k] = B.v[k] - K.v[k];
-      Z.v[k] = T(0);
-    }
-    stp<V>(r, j, R);
-    stp<V>(kx, j, Z);
-  }
-  SMF_TAIL_LOOP(i, n, V) {
-    r[i] = b[i] - kx[i];
-    kx[i] = T(0);
-  }
-}
-
 // out = (Tout) a; zero (may be null) is zeroed.
 template <typename Tin, typename Tout, int V>
 __global__ void k_convert_zero(const Tin *__restrict__ a, Tout *__restrict__ out, Tout *__restrict__ zero, long long n) {
