@@ -199,7 +199,31 @@ int stokes_krylov_mode(const stokes_ctx *ctx);
  * (clock64() cycles; 0 = 2^31).  Synchronises the context stream; STOKES_EINVAL for a context not in
  * deterministic mode.  No counterpart in the paper. */
 int stokes_set_wait_cycles(stokes_ctx *ctx, unsigned int cycles);
+
+/* Where stokes_solve_batch runs: 1 = device iterations, one while node per member as independent
+ * graph branches; 2 = device iterations in lockstep with the members' FP32 cycles run by ONE
+ * persistent work-queue kernel per iteration (STOKES_BATCH_QUEUE=1 at the first solve; every
+ * member 3D, k = 2, FP32 cycle, no stabilisation / symmetric gradient / rho term; otherwise 1):
+ * each cycle is recorded once as its operation list (cell-kernel applications, Chebyshev-Jacobi
+ * vector steps, restriction with the residual, prolongation, coarse solve), split into work items
+ * (bricks of 40 cells, ranges of DoFs), and the kernel's CTAs take items from one queue (a list
+ * schedule: each operation at the time it could start were its member alone), each waiting until
+ * the member's previous operation has finished; 0 =
+ * host-driven lockstep; -1 = no solve yet.  No counterpart in the paper (a layer on Algorithm 1). */
 int stokes_batch_krylov_mode(const stokes_batch *batch);
+
+/* Work-queue mode (2): the budget of every dependency wait in clock64() cycles (0 = 2^31, about a
+ * second); a wait that runs out ends the launch, and stokes_solve_batch returns STOKES_ETIMEOUT
+ * (the batch stays usable).  Stored for a later build of the queue if called before the first
+ * solve; synchronises.  No counterpart in the paper. */
+int stokes_batch_set_wait_cycles(stokes_batch *batch, unsigned int cycles);
+
+/* One FP32 cycle (Algorithm 1, from x = 0) of every member in ONE launch of the persistent
+ * work-queue kernel: b[i] / x[i] are device float vectors of member i (right-hand side in,
+ * cycle result out).  Builds the queue on first use; STOKES_EINVAL where the work-queue form does
+ * not serve the batch (see stokes_batch_krylov_mode), STOKES_ETIMEOUT when a dependency wait ran
+ * out.  Synchronises the stream.  No counterpart in the paper (the batch layer). */
+int stokes_batch_vcycle(stokes_batch *batch, const float *const *b, float *const *x, void *stream);
 
 /* stokes_solve with HOST vectors: copies b in, solves from x = 0, copies x out. */
 int stokes_solve_host(stokes_ctx *ctx, const double *b_host, double *x_host, double rtol, int maxit,
@@ -279,10 +303,12 @@ int stokes_batch_context(stokes_batch *batch, int mesh, stokes_ctx **ctx);
  * in, solution out).  FP64 FGMRES of every member; with the iterations on the device
  * (stokes_batch_krylov_mode 1) one restart cycle of all members is one CUDA-graph launch holding
  * one conditional while node per member as independent branches, so each member iterates to its
- * own stopping test without waiting for the others; host-driven (mode 0), the members advance in
+ * own stopping test without waiting for the others; in mode 2 the members' FP32 cycles of an
+ * iteration are one persistent work-queue kernel; host-driven (mode 0), the members advance in
  * lockstep, the FP32 cycles of one iteration of all members as one graph launch.  iters,
  * final_rel_res: HOST arrays of n_meshes entries (nullable).  Synchronises the stream.  Returns
- * the first non-OK member status (STOKES_ENOTCONV / STOKES_EBREAKDOWN). */
+ * the first non-OK member status (STOKES_ENOTCONV / STOKES_EBREAKDOWN), or STOKES_ETIMEOUT when a
+ * work-queue wait ran out. */
 int stokes_solve_batch(stokes_batch *batch, const double *const *b, double *const *x, double rtol,
                        int maxit, int *iters, double *final_rel_res, void *stream);
 

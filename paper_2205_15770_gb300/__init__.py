@@ -465,9 +465,29 @@ class StokesBatch:
     @property
     def krylov_mode(self):
         """1: every member's inner FGMRES iterations on the device in one graph launch per restart cycle
-        (one while node per member, independent branches), 0: host-driven lockstep, -1: no solve yet
-        (stokes_batch_krylov_mode)."""
+        (one while node per member, independent branches), 2: device iterations in lockstep with the
+        members' FP32 cycles in one persistent work-queue kernel per iteration (STOKES_BATCH_QUEUE=1),
+        0: host-driven lockstep, -1: no solve yet (stokes_batch_krylov_mode)."""
         return int(self._lib.stokes_batch_krylov_mode(self._bt))
+
+    def vcycle(self, bs, xs=None):
+        """One FP32 cycle of every member in one launch of the persistent work-queue kernel
+        (stokes_batch_vcycle); bs, xs: lists of float32 CUDA tensors.  Returns xs."""
+        torch = _torch()
+        xs = [torch.empty_like(b) for b in bs] if xs is None else xs
+        nm = self.n_meshes
+        bp = (C.c_void_p * nm)(*[_ptr(b, torch.float32).value for b in bs])
+        xp = (C.c_void_p * nm)(*[_ptr(x, torch.float32).value for x in xs])
+        st = self._lib.stokes_batch_vcycle(self._bt, bp, xp, StokesMG._stream())
+        if st != 0:
+            raise StokesError(st, self._lib.stokes_global_last_error().decode())
+        return xs
+
+    def set_wait_cycles(self, cycles):
+        """Work-queue mode: the clock64() budget of each dependency wait (0: 2^31); a wait that runs out
+        makes solve() raise STOKES_ETIMEOUT (stokes_batch_set_wait_cycles)."""
+        st = self._lib.stokes_batch_set_wait_cycles(self._bt, int(cycles))
+        self._check(st)
 
     def close(self):
         if getattr(self, "_bt", None):

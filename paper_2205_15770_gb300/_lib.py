@@ -70,6 +70,8 @@ SIGNATURES = {
     "stokes_krylov_mode": (C.c_int, [P]),
     "stokes_set_wait_cycles": (C.c_int, [P, C.c_uint]),
     "stokes_batch_krylov_mode": (C.c_int, [P]),
+    "stokes_batch_set_wait_cycles": (C.c_int, [P, C.c_uint]),
+    "stokes_batch_vcycle": (C.c_int, [P, C.POINTER(P), C.POINTER(P), P]),
     "stokes_last_error": (C.c_char_p, [P]),
     "stokes_global_last_error": (C.c_char_p, []),
     "stokes_destroy": (None, [P]),

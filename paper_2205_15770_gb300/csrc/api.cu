@@ -5,12 +5,15 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/stokes_mf.h"
 #include "common.cuh"
 #include "host_tables.h"
+#include "queue.h"
 #include "transfer.cuh"
 #include "vec.cuh"
 
@@ -260,6 +263,10 @@ struct stokes_ctx {
   long long launches = 0;
   bool capturing = false;
   long long cap_count = 0;
+  // recording of the FP32 cycle for the batched work-queue kernel (queue.h): while set, the FP32
+  // Runner appends its operations here instead of launching them
+  std::vector<PqOp> *pq = nullptr;
+  int pq_member = 0;
   bool use_graphs = true;
   bool fuse = true;  // fused smoothing where eligible (STOKES_NO_FUSE=1: the unfused path)
   GraphSlot g32[2], g64[2];  // [x_zero]
@@ -394,9 +401,37 @@ struct Runner {
     if (yp) zero(yp, np(l));
     apply_nz(l, mode, u, p, yu, yp);
   }
+  // Recording for the work-queue kernel (FP32 only): the operation is appended instead of launched.
+  bool rec() const { return std::is_same<T, float>::value && C->pq != nullptr; }
+  PqOp &rec_op(int type, int l) {
+    C->pq->emplace_back();
+    PqOp &o = C->pq->back();
+    o.type = type;
+    o.member = C->pq_member;
+    if constexpr (std::is_same<T, float>::value) o.F = L[l].d;
+    return o;
+  }
+  void rec_xfer(PqOp &o, int lf) {
+    if constexpr (std::is_same<T, float>::value) {
+      o.Cd = L[lf - 1].d;
+      o.X = L[lf].xf;
+    }
+  }
+  static float *fp(T *p) { return reinterpret_cast<float *>(p); }
+  static const float *fp(const T *p) { return reinterpret_cast<const float *>(p); }
   // Cycle form: the outputs are already zero (work buffers are zeroed by the kernel that
   // consumes them, so the captured cycle contains kernels only).
   void apply_nz(int l, int mode, const T *u, const T *p, T *yu, T *yp) {
+    if (rec()) {
+      PqOp &o = rec_op(kPqCell, l);
+      o.mode = mode;
+      o.in[0] = fp(u);
+      o.in[1] = fp(p);
+      o.out[0] = fp(yu);
+      o.out[1] = fp(yp);
+      o.items = pq_items(o);
+      return;
+    }
     launch_cell_apply<T>(L[l].d, tab, form(mode), u, p, yu, yp, s, L[l].shape, L[l].geo, L[l].rho,
                          C->det ? &C->gb : nullptr);
     note();
@@ -447,12 +482,11 @@ struct Runner {
       tb = R.ps;
     }
     if (kd == 0) {
-      vecp(k_cheb_init<T, 1>, k_cheb_init<T, VW>, {a, b, Dinv, db, xb, base, out, acc, za, zb}, n, a, b, sr, Dinv,
-           (T)cc.c0, (T *)nullptr, db, xb, base, scale, out, acc, za, zb, n);
+      cheb_init_op(l, n, a, b, sr, Dinv, (T)cc.c0, (T *)nullptr, db, xb, base, scale, out, acc, za, zb);
       return;
     }
-    vecp(k_cheb_init<T, 1>, k_cheb_init<T, VW>, {a, b, Dinv, rb, db, xb, za, zb}, n, a, b, sr, Dinv, (T)cc.c0, rb, db,
-         xb, (const T *)nullptr, T(0), (T *)nullptr, (T *)nullptr, za, zb, n);
+    cheb_init_op(l, n, a, b, sr, Dinv, (T)cc.c0, rb, db, xb, (const T *)nullptr, T(0), (T *)nullptr, (T *)nullptr, za,
+                 zb);
     for (int j = 1; j <= kd; ++j) {
       if (velocity)
         apply_nz(l, kApplyA, xb, nullptr, tb, nullptr);
@@ -461,9 +495,48 @@ struct Runner {
       const bool last = j == kd;
       const T *bs = last ? base : nullptr;
       T *fo = last ? out : nullptr, *ac = last ? acc : nullptr;
-      vecp(k_cheb_step<T, 1>, k_cheb_step<T, VW>, {rb, tb, Dinv, db, xb, bs, fo, ac}, n, (const T *)rb, tb, Dinv,
-           (T)cc.c1[j], (T)cc.c2[j], db, xb, bs, scale, fo, ac, n);
+      cheb_step_op(l, n, rb, tb, Dinv, (T)cc.c1[j], (T)cc.c2[j], db, xb, bs, scale, fo, ac);
     }
+  }
+  // The two Chebyshev vector kernels (k_cheb_init / k_cheb_step), launched or recorded.
+  void cheb_init_op(int l, long long n, const T *a, const T *b, T sr, const T *Dinv, T c0, T *r_out, T *d, T *x,
+                    const T *base, T fscale, T *final_out, T *acc_out, T *za, T *zb) {
+    if (rec()) {
+      PqOp &o = rec_op(kPqChebInit, l);
+      o.n = n;
+      const float *in[4] = {fp(a), fp(b), fp(Dinv), fp(base)};
+      float *out[7] = {fp(r_out), fp(d), fp(x), fp(final_out), fp(acc_out), fp(za), fp(zb)};
+      std::copy(in, in + 4, o.in);
+      std::copy(out, out + 7, o.out);
+      o.sc[0] = (float)sr;
+      o.sc[1] = (float)c0;
+      o.sc[2] = (float)fscale;
+      o.vec4 = all_aligned(16, {a, b, Dinv, r_out, d, x, base, final_out, acc_out, za, zb}) ? 1 : 0;
+      o.items = pq_items(o);
+      return;
+    }
+    vecp(k_cheb_init<T, 1>, k_cheb_init<T, VW>, {a, b, Dinv, r_out, d, x, base, final_out, acc_out, za, zb}, n, a, b,
+         sr, Dinv, c0, r_out, d, x, base, fscale, final_out, acc_out, za, zb, n);
+  }
+  void cheb_step_op(int l, long long n, const T *r, T *t, const T *Dinv, T c1, T c2, T *d, T *x, const T *base,
+                    T fscale, T *final_out, T *acc_out) {
+    if (rec()) {
+      PqOp &o = rec_op(kPqChebStep, l);
+      o.n = n;
+      o.in[0] = fp(r);
+      o.in[1] = fp(Dinv);
+      o.in[2] = fp(base);
+      float *out[5] = {fp(t), fp(d), fp(x), fp(final_out), fp(acc_out)};
+      std::copy(out, out + 5, o.out);
+      o.sc[0] = (float)c1;
+      o.sc[1] = (float)c2;
+      o.sc[2] = (float)fscale;
+      o.vec4 = all_aligned(16, {r, t, Dinv, d, x, base, final_out, acc_out}) ? 1 : 0;
+      o.items = pq_items(o);
+      return;
+    }
+    vecp(k_cheb_step<T, 1>, k_cheb_step<T, VW>, {r, t, Dinv, d, x, base, final_out, acc_out}, n, r, t, Dinv, c1, c2,
+         d, x, base, fscale, final_out, acc_out, n);
   }
   // y = B A^-1_hat B^T q   (y zero on entry)
   void S_tilde(int l, const T *q, T *y) {
@@ -493,6 +566,15 @@ struct Runner {
   }
   void coarse(const T *b, T *x) {
     const int n0 = C->n0;
+    if (rec()) {
+      PqOp &o = rec_op(kPqCoarse, 0);
+      o.in[0] = fp(b);
+      o.out[0] = fp(x);
+      o.Kinv = (const double *)C->Kinv;
+      o.n0 = n0;
+      o.items = pq_items(o);
+      return;
+    }
     launch_kernel(k_coarse_apply<T>, dim3((n0 * 32 + 255) / 256), dim3(256), 0, s, (const double *)C->Kinv, n0, b, x);
     note();
   }
@@ -500,6 +582,17 @@ struct Runner {
   template <int W>
   void restrict_w(int lf, const T *in, T *out, T *zero_c, const T *sub) {
     const long long n = nu(lf - 1) + np(lf - 1);
+    if (rec()) {
+      PqOp &o = rec_op(kPqRestrict, lf);
+      rec_xfer(o, lf);
+      o.W = W;
+      o.in[0] = fp(in);
+      o.in[1] = fp(sub);
+      o.out[0] = fp(out);
+      o.out[1] = fp(zero_c);
+      o.items = pq_items(o);
+      return;
+    }
     if (sub) {
       if (n < 32768)
         vec(k_restrict<T, W, 8, true>, n * 8, L[lf].d, L[lf - 1].d, L[lf].xf, in, out, zero_c, sub);
@@ -521,6 +614,19 @@ struct Runner {
   }
   void prolongate(int lf, const T *in, T *out, int add, T *z0 = nullptr, T *z1 = nullptr, T *zf = nullptr) {
     const long long n = nu(lf) + np(lf);
+    if (rec()) {
+      PqOp &o = rec_op(kPqProlong, lf);
+      rec_xfer(o, lf);
+      o.W = L[lf].xf.W;
+      o.in[0] = fp(in);
+      o.out[0] = fp(out);
+      o.out[1] = fp(z0);
+      o.out[2] = fp(z1);
+      o.out[3] = fp(zf);
+      o.add = add;
+      o.items = pq_items(o);
+      return;
+    }
     switch (L[lf].d.k) {
       case 2: vec(k_prolongate<T, 9>, n, L[lf].d, L[lf - 1].d, L[lf].xf, in, out, add, z0, z1, zf); break;
       case 3: vec(k_prolongate<T, 13>, n, L[lf].d, L[lf - 1].d, L[lf].xf, in, out, add, z0, z1, zf); break;
@@ -1794,24 +1900,44 @@ static void drop_graphs(stokes_ctx *C) {
 // The inner FGMRES iteration on the device (one Arnoldi step, Sec. 4 outer loop around the
 // multigrid preconditioner of Algorithm 1): z_j = MG(0, v_j) into zcur and Z_j, w = K z_j (FP64),
 // CGS2 against v_0..v_j, v_{j+1} = w / ||w||, then the Givens update that sets `cond`.
+// Split at the FP32 cycle for the batched work-queue form: krylov_pre converts v_j into the
+// cycle's right-hand side (and zeroes x), krylov_post takes the cycle's result from there on.
+static void krylov_pre(stokes_ctx *C) {
+  Runner<float> R32(C);
+  const int top = C->nl - 1;
+  const long long N = C->L64[top].d.n_u + C->L64[top].d.n_p;
+  LevelRT<float> &T32 = C->L32[top];
+  R32.vec(k_slot_convert<float>, N, (const double *)C->V, N, (const int *)C->kd.ctl, T32.b, T32.x, N);
+}
+static void krylov_post(stokes_ctx *C, cudaGraphConditionalHandle cond, bool set_cond, bool from_fp32);
 static void krylov_body(stokes_ctx *C, cudaGraphConditionalHandle cond, bool set_cond) {
+  Runner<double> R64(C);
+  Runner<float> R32(C);
+  const int top = C->nl - 1;
+  const long long N = C->L64[top].d.n_u + C->L64[top].d.n_p;
+  const int *ctl = C->kd.ctl;
+  if (C->o.vcycle_fp32) {
+    LevelRT<float> &T32 = C->L32[top];
+    krylov_pre(C);
+    R32.cycle(top, T32.x, T32.b, true);
+  } else {
+    LevelRT<double> &T64 = C->L64[top];
+    R64.vec(k_slot_convert<double>, N, (const double *)C->V, N, ctl, T64.b, T64.x, N);
+    R64.cycle(top, T64.x, T64.b, true);
+  }
+  krylov_post(C, cond, set_cond, C->o.vcycle_fp32 != 0);
+}
+static void krylov_post(stokes_ctx *C, cudaGraphConditionalHandle cond, bool set_cond, bool from_fp32) {
   Runner<double> R64(C);
   Runner<float> R32(C);
   const int top = C->nl - 1;
   const long long N = C->L64[top].d.n_u + C->L64[top].d.n_p;
   const int nb = vec_blocks(N), m = C->restart;
   const int *ctl = C->kd.ctl;
-  if (C->o.vcycle_fp32) {
-    LevelRT<float> &T32 = C->L32[top];
-    R32.vec(k_slot_convert<float>, N, (const double *)C->V, N, ctl, T32.b, T32.x, N);
-    R32.cycle(top, T32.x, T32.b, true);
-    R32.vec(k_convert_to_slot<float>, N, (const float *)T32.x, C->zcur, C->Z, N, ctl, N);
-  } else {
-    LevelRT<double> &T64 = C->L64[top];
-    R64.vec(k_slot_convert<double>, N, (const double *)C->V, N, ctl, T64.b, T64.x, N);
-    R64.cycle(top, T64.x, T64.b, true);
-    R64.vec(k_convert_to_slot<double>, N, (const double *)T64.x, C->zcur, C->Z, N, ctl, N);
-  }
+  if (from_fp32)
+    R32.vec(k_convert_to_slot<float>, N, (const float *)C->L32[top].x, C->zcur, C->Z, N, ctl, N);
+  else
+    R64.vec(k_convert_to_slot<double>, N, (const double *)C->L64[top].x, C->zcur, C->Z, N, ctl, N);
   R64.vmult(top, C->zcur, C->w, true);
   for (int pass = 0; pass < 2; ++pass) {
     k_mdot_partial_cnt<<<kRedBlocks, kVecThreads, 0, C->s>>>(C->V, N, ctl, 1, C->w, N, C->partial);
@@ -2057,6 +2183,12 @@ struct stokes_batch {
   cudaGraphExec_t kgraph = nullptr;
   std::vector<long long> kbody;
   int kmode = -1;
+  // work-queue form (kmode 2, queue.h): the members' FP32 cycles as one persistent kernel launch
+  // per iteration; qmem holds the operations, segments, member control pointers and queue state
+  void *qmem = nullptr;
+  PqRun qrun{};
+  size_t qsmem = 0;
+  unsigned qbudget = 0;
 };
 
 namespace smf {
@@ -2156,14 +2288,246 @@ static bool batch_kbuild(stokes_batch *Bt) {
   return true;
 }
 
+// The work-queue form of the batch (kmode 2).  Every member's FP32 cycle is recorded once as its
+// operation list (unfused smoothing, the same arithmetic as the launched cycle) and queued by a
+// list schedule (batch_qrecord).  The device Arnoldi graph is then a while node whose body runs
+// k_batch_select, per member an if node with the conversion of v_j, the queue state reset and
+// ONE launch of the persistent queue kernel (every active member's cycle), per member an if node
+// with the rest of its iteration (FP64 operator, CGS2, Givens) and k_batch_any.  Served: every
+// member 3D, k = 2, FP32 cycle, no stabilisation, symmetric-gradient or rho term.
+static bool batch_qrecord(stokes_batch *Bt) {
+  const int nm = (int)Bt->ctx.size();
+  bool tri = false;
+  for (auto *C : Bt->ctx) {
+    if (C->dim != 3 || C->k != 2 || !C->o.vcycle_fp32 || C->sym || C->c_mass != 0.0 || C->c_grad != 0.0 || C->det)
+      return false;
+    for (int l = 0; l < C->nl; ++l) {
+      if (C->L32[l].rho) return false;
+      tri = tri || !C->L32[l].d.cartesian;
+    }
+  }
+  std::vector<std::vector<PqOp>> rec(nm);
+  for (int m = 0; m < nm; ++m) {
+    stokes_ctx *C = Bt->ctx[m];
+    std::vector<bool> fz(C->nl);
+    for (int l = 0; l < C->nl; ++l) {
+      fz[l] = C->L32[l].fuse;
+      C->L32[l].fuse = false;
+    }
+    C->pq = &rec[m];
+    C->pq_member = m;
+    const int top = C->nl - 1;
+    Runner<float>(C).cycle(top, C->L32[top].x, C->L32[top].b, true);
+    C->pq = nullptr;
+    for (int l = 0; l < C->nl; ++l) C->L32[l].fuse = fz[l];
+  }
+  // flatten: global operation index = member offset + operation.  Queue order: a list schedule,
+  // each operation at the time it could start if its member ran alone (a latency plus its items
+  // spread over the resident CTAs), so a small member's later operations come before a large
+  // member's; an operation always follows its member's previous one.
+  std::vector<int> off(nm + 1, 0);
+  for (int m = 0; m < nm; ++m) off[m + 1] = off[m] + (int)rec[m].size();
+  const int nops = off[nm];
+  std::vector<PqOp> ops((size_t)nops);
+  for (int m = 0; m < nm; ++m) std::copy(rec[m].begin(), rec[m].end(), ops.begin() + off[m]);
+  const double ctas = std::max(1, queue_resident_ctas(queue_smem_bytes(tri, kPqSmemSegments)));
+  struct Slot {
+    double t;
+    int m, o;
+  };
+  std::vector<Slot> order;
+  order.reserve((size_t)nops);
+  for (int m = 0; m < nm; ++m) {
+    double t = 0.0;
+    for (int o = 0; o < (int)rec[m].size(); ++o) {
+      order.push_back({t, m, o});
+      t += 1.0 + std::ceil((double)rec[m][(size_t)o].items / ctas);  // in units of one item's duration
+    }
+  }
+  std::stable_sort(order.begin(), order.end(), [](const Slot &a, const Slot &b) {
+    return a.t < b.t || (a.t == b.t && (a.o < b.o || (a.o == b.o && a.m < b.m)));
+  });
+  std::vector<long long> start, need;
+  std::vector<int> sop, sdep;
+  long long total = 0;
+  for (const Slot &sl : order) {
+    const int g = off[sl.m] + sl.o;
+    start.push_back(total);
+    sop.push_back(g);
+    sdep.push_back(sl.o > 0 ? g - 1 : -1);
+    need.push_back(sl.o > 0 ? ops[(size_t)g - 1].items : 0);
+    total += ops[(size_t)g].items;
+  }
+  const int nseg = (int)sop.size();
+  start.push_back(total);
+  // one device block: ops | seg_start | seg_need | seg_op | seg_dep | active | state
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t b_ops = al(sizeof(PqOp) * nops), b_start = al(sizeof(long long) * (nseg + 1)),
+               b_need = al(sizeof(long long) * nseg), b_op = al(sizeof(int) * nseg), b_dep = al(sizeof(int) * nseg),
+               b_act = al(sizeof(int *) * nm), b_state = al(sizeof(unsigned) * (5 + nops));
+  char *mem = nullptr;
+  if (cudaMalloc(&mem, b_ops + b_start + b_need + b_op + b_dep + b_act + b_state) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  Bt->qmem = mem;
+  std::vector<const int *> act(nm);
+  for (int m = 0; m < nm; ++m) act[m] = Bt->ctx[m]->kd.ctl;
+  std::vector<unsigned> st(5 + nops, 0u);
+  st[4 + nops] = Bt->qbudget;
+  char *p = mem;
+  PqRun R;
+  bool ok = true;
+  auto put = [&](const void *src, size_t n, size_t span) {
+    void *dst = p;
+    if (n) ok = ok && cudaMemcpy(dst, src, n, cudaMemcpyHostToDevice) == cudaSuccess;
+    p += span;
+    return dst;
+  };
+  R.ops = (const PqOp *)put(ops.data(), sizeof(PqOp) * nops, b_ops);
+  R.seg_start = (const long long *)put(start.data(), sizeof(long long) * (nseg + 1), b_start);
+  R.seg_need = (const long long *)put(need.data(), sizeof(long long) * nseg, b_need);
+  R.seg_op = (const int *)put(sop.data(), sizeof(int) * nseg, b_op);
+  R.seg_dep = (const int *)put(sdep.data(), sizeof(int) * nseg, b_dep);
+  R.active = (const int *const *)put(act.data(), sizeof(int *) * nm, b_act);
+  R.state = (unsigned *)put(st.data(), sizeof(unsigned) * (5 + nops), b_state);
+  R.nseg = nseg;
+  R.nops = nops;
+  R.total = total;
+  R.geo_smem = (unsigned)queue_geo_smem_bytes(tri);
+  Bt->qrun = R;
+  Bt->qsmem = queue_smem_bytes(tri, nseg);
+  if (!ok || queue_resident_ctas(Bt->qsmem) <= 0) {
+    cudaGetLastError();
+    cudaFree(Bt->qmem);
+    Bt->qmem = nullptr;
+    return false;
+  }
+  return true;
+}
+
+static bool batch_qbuild(stokes_batch *Bt) {
+  const int nm = (int)Bt->ctx.size();
+  Bt->kmode = 0;
+  if (nm > kBatchMax || !batch_qrecord(Bt)) return false;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  BatchCond bc;
+  bc.n = nm;
+  bc.has_post = 1;
+  bool ok = cudaGraphCreate(&g, 0) == cudaSuccess;
+  if (ok) ok = cudaGraphConditionalHandleCreate(&bc.loop, g, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  cudaGraphNodeParams wp = {};
+  cudaGraphNode_t wn = nullptr;
+  if (ok) {
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = bc.loop;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    ok = cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, &wp) == cudaSuccess;
+  }
+  cudaGraph_t body = ok ? wp.conditional.phGraph_out[0] : nullptr;
+  for (int i = 0; i < nm && ok; ++i) {
+    ok = cudaGraphConditionalHandleCreate(&bc.member[i], body, 0, 0) == cudaSuccess &&
+         cudaGraphConditionalHandleCreate(&bc.post[i], body, 0, 0) == cudaSuccess;
+    bc.ctl[i] = Bt->ctx[i]->kd.ctl;
+  }
+  void *args[1] = {&bc};
+  cudaGraphNode_t seln = nullptr, anyn = nullptr;
+  if (ok) {
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)k_batch_select;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(kBatchMax);
+    kp.kernelParams = args;
+    ok = cudaGraphAddKernelNode(&seln, body, nullptr, 0, &kp) == cudaSuccess;
+  }
+  // an if node per member on its own stream, `capture` filling its body
+  auto add_if = [&](cudaGraphConditionalHandle h, const cudaGraphNode_t *deps, size_t nd, stokes_ctx *C,
+                    const std::function<void()> &capture, cudaGraphNode_t *node) {
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = h;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    bool r = cudaGraphAddNode(node, body, deps, nullptr, nd, &ip) == cudaSuccess;
+    if (r) {
+      cudaGraph_t ib = ip.conditional.phGraph_out[0];
+      r = cudaStreamBeginCaptureToGraph(C->s, ib, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+          cudaSuccess;
+      if (r) {
+        C->capturing = true;
+        C->cap_count = 0;
+        capture();
+        C->capturing = false;
+        cudaGraph_t out = ib;
+        r = cudaStreamEndCapture(C->s, &out) == cudaSuccess;
+      }
+    }
+    return r;
+  };
+  std::vector<cudaGraphNode_t> pre(nm, nullptr), post(nm, nullptr);
+  Bt->kbody.assign(nm, 0);
+  for (int i = 0; i < nm && ok; ++i) {
+    stokes_ctx *C = Bt->ctx[i];
+    ok = add_if(bc.member[i], &seln, 1, C, [&] { krylov_pre(C); }, &pre[i]);
+    Bt->kbody[i] = C->cap_count;
+  }
+  // queue state reset and the persistent kernel, after every member's conversion
+  cudaGraphNode_t qnode = nullptr;
+  if (ok) {
+    ok = cudaStreamBeginCaptureToGraph(Bt->s, body, pre.data(), nullptr, nm, cudaStreamCaptureModeThreadLocal) ==
+         cudaSuccess;
+    if (ok) {
+      cudaMemsetAsync(Bt->qrun.state, 0, sizeof(unsigned) * (4 + Bt->qrun.nops), Bt->s);
+      const int e = launch_queue(Bt->qrun, Bt->qsmem, Bt->s);
+      cudaStreamCaptureStatus cs;
+      const cudaGraphNode_t *deps = nullptr;
+      size_t nd = 0;
+      ok = e == 0 && cudaStreamGetCaptureInfo(Bt->s, &cs, nullptr, nullptr, &deps, nullptr, &nd) == cudaSuccess &&
+           nd == 1;
+      if (ok) qnode = deps[0];
+      cudaGraph_t out = body;
+      ok = cudaStreamEndCapture(Bt->s, &out) == cudaSuccess && ok;
+    }
+  }
+  for (int i = 0; i < nm && ok; ++i) {
+    stokes_ctx *C = Bt->ctx[i];
+    ok = add_if(bc.post[i], &qnode, 1, C, [&] { krylov_post(C, cudaGraphConditionalHandle{}, false, true); },
+                &post[i]);
+    Bt->kbody[i] += C->cap_count;
+  }
+  if (ok) {
+    cudaKernelNodeParams kp = {};
+    kp.func = (void *)k_batch_any;
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(32);
+    kp.kernelParams = args;
+    ok = cudaGraphAddKernelNode(&anyn, body, post.data(), nm, &kp) == cudaSuccess;
+  }
+  if (ok) ok = cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {
+    if (ex) cudaGraphExecDestroy(ex);
+    cudaGetLastError();
+    if (Bt->qmem) cudaFree(Bt->qmem);
+    Bt->qmem = nullptr;
+    return false;
+  }
+  Bt->kgraph = ex;
+  Bt->kmode = 2;
+  return true;
+}
+
 static int batch_solve(stokes_batch *Bt, const double *const *b, double *const *x, double rtol, int maxit, int *iters,
                        double *final_rel) {
   const int nm = (int)Bt->ctx.size();
   if (Bt->kmode < 0) {
     const char *hk = getenv("STOKES_HOST_KRYLOV");
+    const char *qe = getenv("STOKES_BATCH_QUEUE");
     if ((hk && hk[0] == '1') || !Bt->ctx[0]->use_graphs)
       Bt->kmode = 0;
-    else
+    else if (!(qe && qe[0] == '1' && batch_qbuild(Bt)))
       batch_kbuild(Bt);
   }
   std::vector<BatchState> S(nm);
@@ -2248,8 +2612,9 @@ static int batch_solve(stokes_batch *Bt, const double *const *b, double *const *
     int nactive = 0;
     for (auto &st : S) nactive += st.done ? 0 : 1;
     if (nactive == 0) break;
-    if (Bt->kmode == 1) {
-      // (b') every active member's inner iterations in one graph launch, members independent
+    if (Bt->kmode >= 1) {
+      // (b') every active member's inner iterations in one graph launch: members independent
+      // (kmode 1), or in lockstep around the work-queue kernel of their cycles (kmode 2)
       for (auto &st : S) {
         stokes_ctx *C = st.C;
         int hctl[4] = {0, st.it, st.done ? 5 : 0, maxit};
@@ -2285,6 +2650,15 @@ static int batch_solve(stokes_batch *Bt, const double *const *b, double *const *
         st.C->launches += Bt->kbody[i] * (long long)(hctl[1] - st.it) + 2;
         st.it = hctl[1];
         st.need_start = true;
+      }
+      if (Bt->kmode == 2) {
+        unsigned qerr = 0;
+        SMF_CUDA_OK(cudaMemcpyAsync(&qerr, Bt->qrun.state + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, Bt->s));
+        SMF_CUDA_OK(cudaStreamSynchronize(Bt->s));
+        if (qerr) {
+          set_error("batched work-queue kernel: a dependency wait exceeded its budget");
+          return STOKES_ETIMEOUT;
+        }
       }
       continue;
     }
@@ -3127,6 +3501,7 @@ void stokes_destroy_batch(stokes_batch *Bt) {
   if (Bt->s) cudaStreamSynchronize(Bt->s);
   if (Bt->graph) cudaGraphExecDestroy(Bt->graph);
   if (Bt->kgraph) cudaGraphExecDestroy(Bt->kgraph);
+  if (Bt->qmem) cudaFree(Bt->qmem);
   for (auto *C : Bt->ctx) stokes_destroy(C);
   for (auto *h : Bt->pinned)
     if (h) cudaFreeHost(h);
@@ -3198,6 +3573,65 @@ int stokes_set_wait_cycles(stokes_ctx *C, unsigned int cycles) {
   return STOKES_OK;
 }
 int stokes_batch_krylov_mode(const stokes_batch *Bt) { return Bt ? Bt->kmode : -1; }
+int stokes_batch_vcycle(stokes_batch *Bt, const float *const *b, float *const *x, void *stream) {
+  if (!Bt || !b || !x) {
+    set_error("invalid stokes_batch_vcycle arguments");
+    return STOKES_EINVAL;
+  }
+  const int nm = (int)Bt->ctx.size();
+  for (int i = 0; i < nm; ++i)
+    if (!b[i] || !x[i]) {
+      set_error("null vector in stokes_batch_vcycle");
+      return STOKES_EINVAL;
+    }
+  if (!Bt->qmem && !batch_qrecord(Bt)) {
+    set_error("stokes_batch_vcycle: the work-queue form does not serve this batch (every member 3D, k = 2, FP32 "
+              "cycle, no stabilisation, symmetric gradient or rho term)");
+    return STOKES_EINVAL;
+  }
+  cudaStream_t user = (cudaStream_t)stream;
+  SMF_CUDA_OK(cudaEventRecord(Bt->fork, user));
+  SMF_CUDA_OK(cudaStreamWaitEvent(Bt->s, Bt->fork, 0));
+  for (int i = 0; i < nm; ++i) {
+    stokes_ctx *C = Bt->ctx[i];
+    const int top = C->nl - 1;
+    const long long n = C->L32[top].d.n_u + C->L32[top].d.n_p;
+    SMF_CUDA_OK(cudaMemcpyAsync(C->L32[top].b, b[i], n * sizeof(float), cudaMemcpyDeviceToDevice, Bt->s));
+    SMF_CUDA_OK(cudaMemsetAsync(C->L32[top].x, 0, n * sizeof(float), Bt->s));
+  }
+  PqRun R = Bt->qrun;
+  R.active = nullptr;  // every member
+  SMF_CUDA_OK(cudaMemsetAsync(R.state, 0, sizeof(unsigned) * (4 + R.nops), Bt->s));
+  const int e = launch_queue(R, Bt->qsmem, Bt->s);
+  if (e) return cuda_fail((cudaError_t)e, "launch_queue", __FILE__, __LINE__);
+  for (int i = 0; i < nm; ++i) {
+    stokes_ctx *C = Bt->ctx[i];
+    const int top = C->nl - 1;
+    const long long n = C->L32[top].d.n_u + C->L32[top].d.n_p;
+    SMF_CUDA_OK(cudaMemcpyAsync(x[i], C->L32[top].x, n * sizeof(float), cudaMemcpyDeviceToDevice, Bt->s));
+  }
+  unsigned qerr = 0;
+  SMF_CUDA_OK(cudaMemcpyAsync(&qerr, R.state + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, Bt->s));
+  SMF_CUDA_OK(cudaStreamSynchronize(Bt->s));
+  if (qerr) {
+    set_error("batched work-queue kernel: a dependency wait exceeded its budget");
+    return STOKES_ETIMEOUT;
+  }
+  return STOKES_OK;
+}
+int stokes_batch_set_wait_cycles(stokes_batch *Bt, unsigned int cycles) {
+  if (!Bt) {
+    set_error("invalid stokes_batch_set_wait_cycles arguments");
+    return STOKES_EINVAL;
+  }
+  Bt->qbudget = cycles;
+  if (Bt->qmem) {
+    SMF_CUDA_OK(cudaMemcpyAsync(Bt->qrun.state + 4 + Bt->qrun.nops, &cycles, sizeof(unsigned), cudaMemcpyHostToDevice,
+                                Bt->s));
+    SMF_CUDA_OK(cudaStreamSynchronize(Bt->s));
+  }
+  return STOKES_OK;
+}
 
 const char *stokes_last_error(const stokes_ctx *C) { return C ? C->err.c_str() : g_last_error.c_str(); }
 const char *stokes_global_last_error(void) { return g_last_error.c_str(); }

@@ -192,7 +192,8 @@ __host__ __device__ inline long long colour_extent(const int n[3], int colour, i
 // FUSED: the inputs are the pointwise combinations of the Fuse descriptor F (the smoother's vector
 // updates, Sec. 3.3.1), evaluated while gathering; the owner of each gathered node (thread of its
 // component in the owning cell; component 0 for pressure nodes) performs F's side effects.
-template <int K, typename T, int MODE, bool CART, bool DET, bool FUSED = false>
+// COH: inputs read through L2 only (see ld_in).
+template <int K, typename T, int MODE, bool CART, bool DET, bool FUSED = false, bool COH = false>
 __device__ __forceinline__ void cc_group(const LevelDesc<T> &L, const T *__restrict__ u, const T *__restrict__ p,
                                          T *__restrict__ yu, T *__restrict__ yp, const T *__restrict__ geo,
                                          long long group, int colour, const Fuse<T> &F = Fuse<T>{}) {
@@ -201,6 +202,7 @@ __device__ __forceinline__ void cc_group(const LevelDesc<T> &L, const T *__restr
   constexpr bool NEED_U = DO_A || DO_B;
   using CL = CcLaunch<K, T, MODE, CART>;
   static_assert(CART || K == 2, "trilinear cell-component kernel: k = 2");
+  static_assert(!(COH && (FUSED || DET)), "coherent loads: plain form only");
   const CCTab<T> &tb = cct<T>();
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -294,7 +296,7 @@ __device__ __forceinline__ void cc_group(const LevelDesc<T> &L, const T *__restr
 #pragma unroll
         for (int iy = 0; iy < NV; ++iy)
 #pragma unroll
-          for (int ix = 0; ix < NV; ++ix) uv[iz][iy][ix] = ub[iz * N01 + iy * N0 + ix];
+          for (int ix = 0; ix < NV; ++ix) uv[iz][iy][ix] = ld_in<COH>(ub + iz * N01 + iy * N0 + ix);
     } else {
 #pragma unroll
       for (int iz = 0; iz < NV; ++iz)
@@ -302,7 +304,7 @@ __device__ __forceinline__ void cc_group(const LevelDesc<T> &L, const T *__restr
         for (int iy = 0; iy < NV; ++iy)
 #pragma unroll
           for (int ix = 0; ix < NV; ++ix)
-            uv[iz][iy][ix] = (fx[ix] && fy[iy] && fz[iz]) ? ub[iz * N01 + iy * N0 + ix] : T(0);
+            uv[iz][iy][ix] = (fx[ix] && fy[iy] && fz[iz]) ? ld_in<COH>(ub + iz * N01 + iy * N0 + ix) : T(0);
     }
   }
   T pv[NPR][NPR][NPR];
@@ -344,7 +346,8 @@ __device__ __forceinline__ void cc_group(const LevelDesc<T> &L, const T *__restr
 #pragma unroll
       for (int a2 = 0; a2 < NPR; ++a2)
 #pragma unroll
-        for (int a1 = 0; a1 < NPR; ++a1) pv[a3][a2][a1] = valid ? p[pbase + a3 * P01 + a2 * P0 + a1] : T(0);
+        for (int a1 = 0; a1 < NPR; ++a1)
+          pv[a3][a2][a1] = valid ? ld_in<COH>(p + pbase + a3 * P01 + a2 * P0 + a1) : T(0);
   }
   const T mu = L.mu_cell ? L.mu_cell[cell] : L.mu;
 
@@ -403,7 +406,8 @@ __device__ __forceinline__ void cc_group(const LevelDesc<T> &L, const T *__restr
         for (int z = 0; z < NV; ++z)
 #pragma unroll
           for (int y = 0; y < NV; ++y)
-            sl[z][y] = FUSED ? uv[z][y][i] : ((fast || (fxi && fy[y] && fz[z])) ? ub[z * N01 + y * N0 + i] : T(0));
+            sl[z][y] = FUSED ? uv[z][y][i]
+                             : ((fast || (fxi && fy[y] && fz[z])) ? ld_in<COH>(ub + z * N01 + y * N0 + i) : T(0));
         if (DO_B) {
           T t1[NV][NPR];
 #pragma unroll
@@ -467,7 +471,8 @@ __device__ __forceinline__ void cc_group(const LevelDesc<T> &L, const T *__restr
 #pragma unroll
         for (int c3 = 0; c3 < NPR; ++c3)
 #pragma unroll
-          for (int b = 0; b < NPR; ++b) ps[c3][b] = FUSED ? pv[c3][b][a] : (valid ? p[pbase + c3 * P01 + b * P0 + a] : T(0));
+          for (int b = 0; b < NPR; ++b)
+            ps[c3][b] = FUSED ? pv[c3][b][a] : (valid ? ld_in<COH>(p + pbase + c3 * P01 + b * P0 + a) : T(0));
         T t[NPR][NV];  // [c3][y]
 #pragma unroll
         for (int c3 = 0; c3 < NPR; ++c3)

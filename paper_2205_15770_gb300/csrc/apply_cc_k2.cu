@@ -1,7 +1,9 @@
 // Cell-component kernel instantiations for velocity degree k = 2 (own translation unit: its
-// 1D tables live in this unit's constant memory).
+// 1D tables live in this unit's constant memory), and the batched work-queue kernel, whose cell
+// items use the same tables.
 #include "apply_cc.cuh"
 #include "host_tables.h"
+#include "queue.cuh"
 
 namespace smf {
 template int launch_cell_apply_cc_k<2, float>(const LevelDesc<float> &, int, const float *, const float *, float *,

@@ -253,7 +253,19 @@ namespace smf {
 __global__ void k_batch_select(const BatchCond B) {
   pdl_enter();
   const int i = threadIdx.x;
-  if (blockIdx.x == 0 && i < B.n) cudaGraphSetConditional(B.member[i], B.ctl[i][2] == 0 ? 1u : 0u);
+  if (blockIdx.x == 0 && i < B.n) {
+    const unsigned on = B.ctl[i][2] == 0 ? 1u : 0u;
+    cudaGraphSetConditional(B.member[i], on);
+    if (B.has_post) cudaGraphSetConditional(B.post[i], on);
+  }
+}
+
+__global__ void k_batch_any(const BatchCond B) {
+  pdl_enter();
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  int any = 0;
+  for (int i = 0; i < B.n; ++i) any |= B.ctl[i][2] == 0;
+  cudaGraphSetConditional(B.loop, any ? 1u : 0u);
 }
 
 

@@ -32,6 +32,51 @@ struct XferTabs {
   int W = 0;
 };
 
+// Restriction row of coarse DoF i (P^T in, or P^T (in - minus) with SUB), summed over its (z, y)
+// term pairs t = t0, t0 + dt, ... (all of them for t0 = 0, dt = 1).
+template <typename T, int W, bool SUB, bool COH = false>
+__device__ __forceinline__ T restrict_terms(const LevelDesc<T> &F, const LevelDesc<T> &C, const XferTabs<T> &X,
+                                            const T *in, const T *minus, long long i, int t0, int dt) {
+  const bool vel = i < C.n_u;
+  const int sp = vel ? 0 : 1;
+  const int *Nc = vel ? C.N : C.Pn, *Nf = vel ? F.N : F.Pn;
+  const long long j = vel ? i % C.nv : i - C.n_u;
+  const int G0 = (int)(j % Nc[0]), G1 = (int)((j / Nc[0]) % Nc[1]), G2 = (int)(j / ((long long)Nc[0] * Nc[1]));
+  const long long off = vel ? (i / C.nv) * F.nv : F.n_u;
+  const T *src = in + off;
+  const T *ssrc = SUB ? minus + off : nullptr;
+  const Xfer1D<T> &ax = X.r[sp][0], &ay = X.r[sp][1], &az = X.r[sp][2];
+  const int n0 = ax.cnt[G0], n1 = ay.cnt[G1], n2 = az.cnt[G2];
+  int f0[W];
+  T w0[W];
+#pragma unroll
+  for (int a = 0; a < W; ++a) {
+    f0[a] = a < n0 ? ax.idx[G0 * W + a] : 0;
+    w0[a] = a < n0 ? ax.w[G0 * W + a] : T(0);
+  }
+  T s = T(0);
+  for (int t = t0; t < n1 * n2; t += dt) {
+    const int a1 = t % n1, a2 = t / n1;
+    const int f1 = ay.idx[G1 * W + a1], f2 = az.idx[G2 * W + a2];
+    const T w21 = ay.w[G1 * W + a1] * az.w[G2 * W + a2];
+    const long long ro = ((long long)f2 * Nf[1] + f1) * Nf[0];
+    const T *row = src + ro;
+    T r = T(0);
+    if (SUB) {
+      const T *srow = ssrc + ro;
+#pragma unroll
+      for (int a = 0; a < W; ++a)
+        if (a < n0) r += w0[a] * (ld_in<COH>(row + f0[a]) - ld_in<COH>(srow + f0[a]));
+    } else {
+#pragma unroll
+      for (int a = 0; a < W; ++a)
+        if (a < n0) r += w0[a] * ld_in<COH>(row + f0[a]);
+    }
+    s += w21 * r;
+  }
+  return s;
+}
+
 // out (coarse) = P^T in (fine); zero_c (coarse-sized, may be null) is zeroed on the way.
 // SUB: out = P^T (in - minus), the residual b - K x of Algorithm 1 formed while restricting it.
 // LANES consecutive lanes share one coarse DoF and split its (z, y) term pairs; the partial sums
@@ -49,45 +94,7 @@ __global__ void k_restrict(const LevelDesc<T> F, const LevelDesc<T> C, const Xfe
        gid += (long long)gridDim.x * blockDim.x) {
     const long long i = gid / LANES;
     const bool active = i < C.n_u + C.n_p;
-    T s = T(0);
-    if (active) {
-      const bool vel = i < C.n_u;
-      const int sp = vel ? 0 : 1;
-      const int *Nc = vel ? C.N : C.Pn, *Nf = vel ? F.N : F.Pn;
-      const long long j = vel ? i % C.nv : i - C.n_u;
-      const int G0 = (int)(j % Nc[0]), G1 = (int)((j / Nc[0]) % Nc[1]), G2 = (int)(j / ((long long)Nc[0] * Nc[1]));
-      const long long off = vel ? (i / C.nv) * F.nv : F.n_u;
-      const T *src = in + off;
-      const T *ssrc = SUB ? minus + off : nullptr;
-      const Xfer1D<T> &ax = X.r[sp][0], &ay = X.r[sp][1], &az = X.r[sp][2];
-      const int n0 = ax.cnt[G0], n1 = ay.cnt[G1], n2 = az.cnt[G2];
-      int f0[W];
-      T w0[W];
-#pragma unroll
-      for (int a = 0; a < W; ++a) {
-        f0[a] = a < n0 ? ax.idx[G0 * W + a] : 0;
-        w0[a] = a < n0 ? ax.w[G0 * W + a] : T(0);
-      }
-      for (int t = sub; t < n1 * n2; t += LANES) {
-        const int a1 = t % n1, a2 = t / n1;
-        const int f1 = ay.idx[G1 * W + a1], f2 = az.idx[G2 * W + a2];
-        const T w21 = ay.w[G1 * W + a1] * az.w[G2 * W + a2];
-        const long long ro = ((long long)f2 * Nf[1] + f1) * Nf[0];
-        const T *row = src + ro;
-        T r = T(0);
-        if (SUB) {
-          const T *srow = ssrc + ro;
-#pragma unroll
-          for (int a = 0; a < W; ++a)
-            if (a < n0) r += w0[a] * (row[f0[a]] - srow[f0[a]]);
-        } else {
-#pragma unroll
-          for (int a = 0; a < W; ++a)
-            if (a < n0) r += w0[a] * row[f0[a]];
-        }
-        s += w21 * r;
-      }
-    }
+    T s = active ? restrict_terms<T, W, SUB>(F, C, X, in, minus, i, sub, LANES) : T(0);
 #pragma unroll
     for (int o = LANES / 2; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, LANES);
     if (active && sub == 0) {
@@ -95,6 +102,32 @@ __global__ void k_restrict(const LevelDesc<T> F, const LevelDesc<T> C, const Xfe
       if (zero_c) zero_c[i] = T(0);
     }
   }
+}
+
+// Prolongation row of fine DoF i: (P in)_i.
+template <typename T, int W, bool COH = false>
+__device__ __forceinline__ T prolong_entry(const LevelDesc<T> &F, const LevelDesc<T> &C, const XferTabs<T> &X,
+                                           const T *in, long long i) {
+  const bool vel = i < F.n_u;
+  const int sp = vel ? 0 : 1;
+  const int *Nc = vel ? C.N : C.Pn, *Nf = vel ? F.N : F.Pn;
+  const long long j = vel ? i % F.nv : i - F.n_u;
+  const int g0 = (int)(j % Nf[0]), g1 = (int)((j / Nf[0]) % Nf[1]), g2 = (int)(j / ((long long)Nf[0] * Nf[1]));
+  const T *src = in + (vel ? (i / F.nv) * C.nv : C.n_u);
+  const Xfer1D<T> &ax = X.p[sp][0], &ay = X.p[sp][1], &az = X.p[sp][2];
+  const int n0 = ax.cnt[g0], n1 = ay.cnt[g1], n2 = az.cnt[g2];
+  T s = T(0);
+  for (int a2 = 0; a2 < n2; ++a2) {
+    const int G2 = az.idx[g2 * W + a2];
+    const T w2 = az.w[g2 * W + a2];
+    for (int a1 = 0; a1 < n1; ++a1) {
+      const T *row = src + ((long long)G2 * Nc[1] + ay.idx[g1 * W + a1]) * Nc[0];
+      T r = T(0);
+      for (int a0 = 0; a0 < n0; ++a0) r += ax.w[g0 * W + a0] * ld_in<COH>(row + ax.idx[g0 * W + a0]);
+      s += w2 * ay.w[g1 * W + a1] * r;
+    }
+  }
+  return s;
 }
 
 // out (fine) = P in (coarse); add != 0: out += P in.  Covers velocity and pressure.  z0 / z1
@@ -112,24 +145,7 @@ __global__ void k_prolongate(const LevelDesc<T> F, const LevelDesc<T> C, const X
       if (z0) z0[i] = T(0);
       if (z1) z1[i] = T(0);
     }
-    const int sp = vel ? 0 : 1;
-    const int *Nc = vel ? C.N : C.Pn, *Nf = vel ? F.N : F.Pn;
-    const long long j = vel ? i % F.nv : i - F.n_u;
-    const int g0 = (int)(j % Nf[0]), g1 = (int)((j / Nf[0]) % Nf[1]), g2 = (int)(j / ((long long)Nf[0] * Nf[1]));
-    const T *src = in + (vel ? (i / F.nv) * C.nv : C.n_u);
-    const Xfer1D<T> &ax = X.p[sp][0], &ay = X.p[sp][1], &az = X.p[sp][2];
-    const int n0 = ax.cnt[g0], n1 = ay.cnt[g1], n2 = az.cnt[g2];
-    T s = T(0);
-    for (int a2 = 0; a2 < n2; ++a2) {
-      const int G2 = az.idx[g2 * W + a2];
-      const T w2 = az.w[g2 * W + a2];
-      for (int a1 = 0; a1 < n1; ++a1) {
-        const T *row = src + ((long long)G2 * Nc[1] + ay.idx[g1 * W + a1]) * Nc[0];
-        T r = T(0);
-        for (int a0 = 0; a0 < n0; ++a0) r += ax.w[g0 * W + a0] * row[ax.idx[g0 * W + a0]];
-        s += w2 * ay.w[g1 * W + a1] * r;
-      }
-    }
+    const T s = prolong_entry<T, W>(F, C, X, in, i);
     out[i] = add ? out[i] + s : s;
   }
 }

@@ -96,6 +96,29 @@ __device__ __forceinline__ Pack<T, V> ldp_or0(const T *p, long long j) {
   }
   return r;
 }
+// 16-byte packs read through L2 only (COH, see ld_in) or plainly.
+template <int V, bool COH, typename T>
+__device__ __forceinline__ Pack<T, V> ldpc(const T *p, long long j) {
+  if constexpr (COH) {
+    static_assert(sizeof(T) * V == 16, "16-byte packs");
+    Pack<T, V> r;
+    *reinterpret_cast<float4 *>(&r) = __ldcg(reinterpret_cast<const float4 *>(p + j * V));
+    return r;
+  } else {
+    return ldp<V>(p, j);
+  }
+}
+template <int V, bool COH, typename T>
+__device__ __forceinline__ Pack<T, V> ldpc_or0(const T *p, long long j) {
+  Pack<T, V> r;
+  if (p) {
+    r = ldpc<V, COH>(p, j);
+  } else {
+#pragma unroll
+    for (int k = 0; k < V; ++k) r.v[k] = T(0);
+  }
+  return r;
+}
 // Elements [0, n) as n/V packs plus a scalar tail handled by the first threads of the grid.
 #define SMF_PACK_LOOP(j, n, V) SMF_GRID_LOOP(j, (n) / (V))
 #define SMF_TAIL_LOOP(i, n, V)                                                                       \
@@ -106,6 +129,37 @@ __device__ __forceinline__ Pack<T, V> ldp_or0(const T *p, long long j) {
 // d = x = c0 * Dinv * r; r is stored if r_out != null.  za / zb (may alias a / b) are zeroed
 // after they are read: apply targets are kept zero between uses, so the cycle needs no memset.
 // With final_out / acc_out the degree-0 result f = base + fscale * x is written / accumulated.
+// One element of k_cheb_init / k_cheb_step (the scalar tail of the packed kernels, and the work
+// items of the persistent queue kernel with COH loads).
+template <typename T, bool COH = false>
+__device__ __forceinline__ void cheb_init_elem(long long i, const T *a, const T *b, T sr, const T *Dinv, T c0, T *r_out,
+                                               T *d, T *x, const T *base, T fscale, T *final_out, T *acc_out, T *za,
+                                               T *zb) {
+  const T av = a ? ld_in<COH>(a + i) : T(0), bv = b ? ld_in<COH>(b + i) : T(0);
+  if (za) za[i] = T(0);
+  if (zb) zb[i] = T(0);
+  const T r = sr * (av - bv);
+  if (r_out) r_out[i] = r;
+  const T v = c0 * ld_in<COH>(Dinv + i) * r;
+  d[i] = v;
+  x[i] = v;
+  const T f = (base ? ld_in<COH>(base + i) : T(0)) + fscale * v;
+  if (final_out) final_out[i] = f;
+  if (acc_out) acc_out[i] = ld_in<COH>(acc_out + i) + f;
+}
+template <typename T, bool COH = false>
+__device__ __forceinline__ void cheb_step_elem(long long i, const T *r, T *t, const T *Dinv, T c1, T c2, T *d, T *x,
+                                               const T *base, T fscale, T *final_out, T *acc_out) {
+  const T tv = ld_in<COH>(t + i);
+  t[i] = T(0);
+  const T dn = c1 * ld_in<COH>(d + i) + c2 * ld_in<COH>(Dinv + i) * (ld_in<COH>(r + i) - tv);
+  const T xn = ld_in<COH>(x + i) + dn;
+  d[i] = dn;
+  x[i] = xn;
+  const T f = (base ? ld_in<COH>(base + i) : T(0)) + fscale * xn;
+  if (final_out) final_out[i] = f;
+  if (acc_out) acc_out[i] = ld_in<COH>(acc_out + i) + f;
+}
 template <typename T, int V>
 __device__ __forceinline__ void cheb_init_pack(const Pack<T, V> &A, const Pack<T, V> &B, T sr, const Pack<T, V> &Di,
                                                T c0, Pack<T, V> &R, Pack<T, V> &X) {
@@ -115,14 +169,14 @@ __device__ __forceinline__ void cheb_init_pack(const Pack<T, V> &A, const Pack<T
     X.v[k] = c0 * Di.v[k] * R.v[k];
   }
 }
-template <typename T, int V>
-__global__ void k_cheb_init(const T *__restrict__ a, const T *__restrict__ b, T sr, const T *__restrict__ Dinv,
-                            T c0, T *__restrict__ r_out, T *__restrict__ d, T *__restrict__ x, const T *__restrict__ base,
-                            T fscale, T *__restrict__ final_out, T *__restrict__ acc_out, T *za, T *zb, long long n) {
-  pdl_enter();
-  SMF_PACK_LOOP(j, n, V) {
-    const Pack<T, V> A = ldp_or0<V>(a, j), B = ldp_or0<V>(b, j), Di = ldp<V>(Dinv, j);
-    const Pack<T, V> Bs = ldp_or0<V>(base, j), Ac = ldp_or0<V>(acc_out, j);
+// Pack j of k_cheb_init (also a work item of the persistent queue kernel, COH).
+template <typename T, int V, bool COH = false>
+__device__ __forceinline__ void cheb_init_packj(long long j, const T *a, const T *b, T sr, const T *Dinv, T c0,
+                                                T *r_out, T *d, T *x, const T *base, T fscale, T *final_out,
+                                                T *acc_out, T *za, T *zb) {
+  {
+    const Pack<T, V> A = ldpc_or0<V, COH>(a, j), B = ldpc_or0<V, COH>(b, j), Di = ldpc<V, COH>(Dinv, j);
+    const Pack<T, V> Bs = ldpc_or0<V, COH>(base, j), Ac = ldpc_or0<V, COH>(acc_out, j);
     Pack<T, V> R, X, Z;
     cheb_init_pack(A, B, sr, Di, c0, R, X);
 #pragma unroll
@@ -143,31 +197,26 @@ __global__ void k_cheb_init(const T *__restrict__ a, const T *__restrict__ b, T 
       if (acc_out) stp<V>(acc_out, j, Anew);
     }
   }
-  SMF_TAIL_LOOP(i, n, V) {
-    const T av = a ? a[i] : T(0), bv = b ? b[i] : T(0);
-    if (za) za[i] = T(0);
-    if (zb) zb[i] = T(0);
-    const T r = sr * (av - bv);
-    if (r_out) r_out[i] = r;
-    const T v = c0 * Dinv[i] * r;
-    d[i] = v;
-    x[i] = v;
-    const T f = (base ? base[i] : T(0)) + fscale * v;
-    if (final_out) final_out[i] = f;
-    if (acc_out) acc_out[i] += f;
-  }
+}
+template <typename T, int V>
+__global__ void k_cheb_init(const T *__restrict__ a, const T *__restrict__ b, T sr, const T *__restrict__ Dinv,
+                            T c0, T *__restrict__ r_out, T *__restrict__ d, T *__restrict__ x, const T *__restrict__ base,
+                            T fscale, T *__restrict__ final_out, T *__restrict__ acc_out, T *za, T *zb, long long n) {
+  pdl_enter();
+  SMF_PACK_LOOP(j, n, V)
+  cheb_init_packj<T, V>(j, a, b, sr, Dinv, c0, r_out, d, x, base, fscale, final_out, acc_out, za, zb);
+  SMF_TAIL_LOOP(i, n, V) cheb_init_elem(i, a, b, sr, Dinv, c0, r_out, d, x, base, fscale, final_out, acc_out, za, zb);
 }
 
 // One Chebyshev step: d = c1 d + c2 Dinv (r - t); x += d; t is zeroed after it is read.  With
 // final_out / acc_out, f = base + fscale * x_new is written / accumulated.
-template <typename T, int V>
-__global__ void k_cheb_step(const T *__restrict__ r, T *__restrict__ t, const T *__restrict__ Dinv, T c1, T c2,
-                            T *__restrict__ d, T *__restrict__ x, const T *__restrict__ base, T fscale,
-                            T *__restrict__ final_out, T *__restrict__ acc_out, long long n) {
-  pdl_enter();
-  SMF_PACK_LOOP(j, n, V) {
-    const Pack<T, V> R = ldp<V>(r, j), Tt = ldp<V>(t, j), Di = ldp<V>(Dinv, j), Dd = ldp<V>(d, j), X = ldp<V>(x, j);
-    const Pack<T, V> Bs = ldp_or0<V>(base, j), Ac = ldp_or0<V>(acc_out, j);
+template <typename T, int V, bool COH = false>
+__device__ __forceinline__ void cheb_step_packj(long long j, const T *r, T *t, const T *Dinv, T c1, T c2, T *d, T *x,
+                                                const T *base, T fscale, T *final_out, T *acc_out) {
+  {
+    const Pack<T, V> R = ldpc<V, COH>(r, j), Tt = ldpc<V, COH>(t, j), Di = ldpc<V, COH>(Dinv, j),
+                     Dd = ldpc<V, COH>(d, j), X = ldpc<V, COH>(x, j);
+    const Pack<T, V> Bs = ldpc_or0<V, COH>(base, j), Ac = ldpc_or0<V, COH>(acc_out, j);
     Pack<T, V> Dn, Xn, Z;
 #pragma unroll
     for (int k = 0; k < V; ++k) {
@@ -189,17 +238,14 @@ __global__ void k_cheb_step(const T *__restrict__ r, T *__restrict__ t, const T 
       if (acc_out) stp<V>(acc_out, j, Anew);
     }
   }
-  SMF_TAIL_LOOP(i, n, V) {
-    const T tv = t[i];
-    t[i] = T(0);
-    const T dn = c1 * d[i] + c2 * Dinv[i] * (r[i] - tv);
-    const T xn = x[i] + dn;
-    d[i] = dn;
-    x[i] = xn;
-    const T f = (base ? base[i] : T(0)) + fscale * xn;
-    if (final_out) final_out[i] = f;
-    if (acc_out) acc_out[i] += f;
-  }
+}
+template <typename T, int V>
+__global__ void k_cheb_step(const T *__restrict__ r, T *__restrict__ t, const T *__restrict__ Dinv, T c1, T c2,
+                            T *__restrict__ d, T *__restrict__ x, const T *__restrict__ base, T fscale,
+                            T *__restrict__ final_out, T *__restrict__ acc_out, long long n) {
+  pdl_enter();
+  SMF_PACK_LOOP(j, n, V) cheb_step_packj<T, V>(j, r, t, Dinv, c1, c2, d, x, base, fscale, final_out, acc_out);
+  SMF_TAIL_LOOP(i, n, V) cheb_step_elem(i, r, t, Dinv, c1, c2, d, x, base, fscale, final_out, acc_out);
 }
 
 // End of a fused smoothing sequence: the last line of the compact Uzawa step,
@@ -391,10 +437,14 @@ __global__ void k_fgmres_givens(KrylovDev K, cudaGraphConditionalHandle cond, in
 constexpr int kBatchMax = 64;
 struct BatchCond {
   int n = 0;
-  cudaGraphConditionalHandle member[kBatchMax] = {};
+  int has_post = 0;                                    // post[] in use (work-queue form)
+  cudaGraphConditionalHandle loop{};                   // work-queue form: the iteration loop
+  cudaGraphConditionalHandle member[kBatchMax] = {};  // a member's iterations (or its part before the queue)
+  cudaGraphConditionalHandle post[kBatchMax] = {};    // work-queue form: its part after the queue
   const int *ctl[kBatchMax] = {};
 };
 __global__ void k_batch_select(const BatchCond B);  // member conditions from their stop flags
+__global__ void k_batch_any(const BatchCond B);     // loop condition: any member still running
 // y = R^{-1} g on the first ctl[0] columns (R the rotated Hessenberg, upper triangular)
 __global__ void k_fgmres_trisolve(KrylovDev K);
 

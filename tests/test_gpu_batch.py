@@ -139,3 +139,105 @@ def test_tuning_string_pins_shapes_and_smoother_forms(monkeypatch):
     monkeypatch.setenv("STOKES_TUNING", "s32=4,4;s64=4,4,4;f32=0,1,1;f64=0,1,1")  # wrong length
     with pytest.raises(StokesError):
         StokesMG(dim=3, n=(8, 8, 8), n_levels=3, k=2, kA=1, kS=2, m=2)
+
+
+def _queue_members():
+    return [dict(dim=3, n=(4, 4, 4), n_levels=2, gamma_rho=0.0),
+            dict(dim=3, n=(8, 8, 8), n_levels=3, gamma_rho=1e3),
+            dict(dim=3, n=(6, 6, 6), n_levels=2, gamma_rho=10.0),
+            dict(dim=3, n=(8, 8, 8), n_levels=3, gamma_rho=0.0, vertices=W.perturbed_vertices(3, (8, 8, 8), seed=7)),
+            dict(dim=3, n=(16, 16, 16), n_levels=4, gamma_rho=1e2)]
+
+
+@pytest.mark.parametrize("restart", [30, 3])
+def test_batch_work_queue_solves(monkeypatch, restart):
+    """Work-queue mode (krylov_mode 2): every member's FP32 cycle of an iteration is run by one
+    persistent kernel taking (member, operation, brick) items from one queue.  Each member reaches
+    the FP64 residual rtol (checked through the member's own FP64 operator) in the iteration count of
+    its single-mesh solve, give or take one (the queue records the unfused smoother, the single solve
+    may fuse some levels: the FP32 cycles differ by rounding), with Cartesian and trilinear members
+    of different depths and a short restart that forces several restart cycles."""
+    from paper_2205_15770_gb300 import StokesBatch, StokesMG
+    monkeypatch.setenv("STOKES_BATCH_QUEUE", "1")
+    members = _queue_members()
+    kw = dict(kA=1, kS=1, m=2, schur_diag="d", restart=restart)
+    Bt = StokesBatch(members, **kw)
+    bs = [mv.mass_rhs(torch.as_tensor(W.fourier_forcing(3, 2, mb["n"], seed=30 + i).reshape(-1), device="cuda"))
+          for i, (mb, mv) in enumerate(zip(members, Bt.members))]
+    for rep in range(2):  # the second solve replays the built graph
+        xs, its, rels = Bt.solve(bs, rtol=1e-10)
+        assert Bt.krylov_mode == 2
+        for i, (mb, mv) in enumerate(zip(members, Bt.members)):
+            r = bs[i] - mv.vmult(xs[i])
+            assert torch.linalg.norm(r).item() <= 1.01e-10 * torch.linalg.norm(bs[i]).item(), (rep, i)
+            if rep == 0:
+                S = StokesMG(dim=3, n=mb["n"], n_levels=mb["n_levels"], gamma_rho=mb["gamma_rho"],
+                             vertices=mb.get("vertices"), **kw)
+                _, its1, _ = S.solve(bs[i], rtol=1e-10)
+                assert abs(its[i] - its1) <= 1, (i, its, its1)
+                S.close()
+    Bt.close()
+
+
+def test_batch_work_queue_matches_graph_branches(monkeypatch):
+    """The same batch in work-queue mode and in graph-branch mode (krylov_mode 1): solutions within the
+    solver tolerance of each other."""
+    from paper_2205_15770_gb300 import StokesBatch
+    members = _queue_members()
+    kw = dict(kA=1, kS=1, m=2, schur_diag="d")
+    out = {}
+    for mode in ("0", "1"):
+        monkeypatch.setenv("STOKES_BATCH_QUEUE", mode)
+        Bt = StokesBatch(members, **kw)
+        bs = [mv.mass_rhs(torch.as_tensor(W.fourier_forcing(3, 2, mb["n"], seed=40 + i).reshape(-1), device="cuda"))
+              for i, (mb, mv) in enumerate(zip(members, Bt.members))]
+        xs, its, rels = Bt.solve(bs, rtol=1e-10)
+        assert Bt.krylov_mode == (2 if mode == "1" else 1)
+        out[mode] = [x.cpu().numpy() for x in xs]
+        Bt.close()
+    for a, b in zip(out["0"], out["1"]):
+        assert np.abs(a - b).max() <= 1e-7 * np.abs(a).max()
+
+
+def test_batch_work_queue_wait_budget_returns_etimeout(monkeypatch):
+    """A one-cycle budget makes the first dependency wait of the queue kernel run out: the launch
+    ends (no GPU fault), solve reports STOKES_ETIMEOUT, and the batch solves normally once the
+    budget is restored."""
+    from paper_2205_15770_gb300 import StokesBatch
+    monkeypatch.setenv("STOKES_BATCH_QUEUE", "1")
+    members = [dict(dim=3, n=(16, 16, 16), n_levels=4, gamma_rho=0.0), dict(dim=3, n=(8, 8, 8), n_levels=3)]
+    Bt = StokesBatch(members, kA=1, kS=1, m=2, schur_diag="d")
+    bs = [mv.mass_rhs(torch.as_tensor(W.fourier_forcing(3, 2, mb["n"], seed=50 + i).reshape(-1), device="cuda"))
+          for i, (mb, mv) in enumerate(zip(members, Bt.members))]
+    Bt.set_wait_cycles(1)
+    _, _, _, st = Bt.solve(bs, rtol=1e-8, check=False)
+    assert st == 6 and "budget" in Bt.last_error
+    Bt.set_wait_cycles(0)
+    xs, its, rels = Bt.solve(bs, rtol=1e-8)
+    assert Bt.krylov_mode == 2 and max(rels) <= 1e-8
+    Bt.close()
+
+
+def test_batch_work_queue_vcycle_matches_member_cycles():
+    """stokes_batch_vcycle: one launch of the work-queue kernel runs the FP32 cycle of every member
+    (Cartesian and trilinear, different depths).  Measured against the member's own FP64 cycle, each
+    queue result is as accurate as the member's own FP32 cycle (within twice its error; FP32 cycles
+    of these small pure-Stokes members drift by up to ~1e-2 in the pressure), and the queue cycle is
+    a fixed function of its input (two launches agree up to the order of the atomic sums: 1e-5)."""
+    from paper_2205_15770_gb300 import StokesBatch
+    members = _queue_members()
+    Bt = StokesBatch(members, kA=1, kS=1, m=2, schur_diag="d")
+    b64 = [mv.mass_rhs(torch.as_tensor(W.fourier_forcing(3, 2, mb["n"], seed=60 + i).reshape(-1), device="cuda"))
+           for i, (mb, mv) in enumerate(zip(members, Bt.members))]
+    bs = [b.float() for b in b64]
+    first = Bt.vcycle(bs)
+    first = [x.clone() for x in first]
+    xs = Bt.vcycle(bs)
+    for i, (mv, b) in enumerate(zip(Bt.members, b64)):
+        ref = mv.vcycle(b, torch.zeros_like(b))
+        own = mv.vcycle(bs[i], torch.zeros_like(bs[i])).double()
+        scale = ref.abs().max().item()
+        err_own = (own - ref).abs().max().item()
+        assert (xs[i].double() - ref).abs().max().item() <= max(2 * err_own, 1e-5 * scale), i
+        assert (xs[i] - first[i]).abs().max().item() <= 1e-5 * scale, i
+    Bt.close()
