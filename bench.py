@@ -586,6 +586,7 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk,
         "launch_shapes_fp32": S32[0].launch_shapes(32),
+        "fp64_geometry_stored": S32[0].geometry_stored(),
         "fused_smoothing_levels": {"fp32": S32[0].fused_levels(32), "fp64": S32[0].fused_levels(64)},
         "tuning": tuning_string(S32[0]),
         "batched": batched,

@@ -328,6 +328,12 @@ void stokes_destroy_batch(stokes_batch *batch);
  * STOKES_EINVAL.  HOST output. */
 int stokes_get_launch_shape(const stokes_ctx *ctx, int level, int precision, int *shape);
 
+/* 1 if the FP64 per-point geometry of `level` (G, w adj(J), w det J per Gauss point with mu and
+ * gamma rho folded in; 3D trilinear levels) was stored at setup, 0 if the FP64 kernels evaluate it
+ * on the fly (Cartesian levels, STOKES_GEO=none, or a level larger than the budget: 1/16 of the
+ * device memory, and at most half of the memory free at setup).  HOST output. */
+int stokes_get_geometry_stored(const stokes_ctx *ctx, int level, int *stored);
+
 /* 1 if smoothing on `level` / `precision` runs in the fused form (k_A = 1, 3D, column kernel: the
  * Chebyshev-Jacobi and Uzawa vector updates of Sec. 3.3.1 evaluated inside the cell-kernel
  * gathers, 5 + 3 k_S launches per step), 0 if in the unfused form (separate vector kernels).

@@ -346,6 +346,15 @@ class StokesMG:
             out.append(v.value)
         return out
 
+    def geometry_stored(self):
+        """Per level: True where the FP64 per-point geometry is stored (stokes_get_geometry_stored)."""
+        out = []
+        for l in range(self.n_levels):
+            v = C.c_int()
+            self._check(self._lib.stokes_get_geometry_stored(self._ctx, l, C.byref(v)))
+            out.append(bool(v.value))
+        return out
+
     def fused_levels(self, precision=32):
         """Per level: True where smoothing runs in the fused form (stokes_get_smoother_fusion)."""
         out = []

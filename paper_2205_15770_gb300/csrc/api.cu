@@ -3512,6 +3512,15 @@ void stokes_destroy_batch(stokes_batch *Bt) {
   delete Bt;
 }
 
+int stokes_get_geometry_stored(const stokes_ctx *C, int level, int *stored) {
+  if (!C || level < 0 || level >= C->nl || !stored) {
+    set_error("invalid stokes_get_geometry_stored arguments");
+    return STOKES_EINVAL;
+  }
+  *stored = C->L64[level].geo ? 1 : 0;
+  return STOKES_OK;
+}
+
 int stokes_get_launch_shape(const stokes_ctx *C, int level, int precision, int *shape) {
   if (!C || level < 0 || level >= C->nl || !shape || (precision != 32 && precision != 64)) {
     set_error("invalid stokes_get_launch_shape arguments");
