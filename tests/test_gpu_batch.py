@@ -241,3 +241,39 @@ def test_batch_work_queue_vcycle_matches_member_cycles():
         assert (xs[i].double() - ref).abs().max().item() <= max(2 * err_own, 1e-5 * scale), i
         assert (xs[i] - first[i]).abs().max().item() <= 1e-5 * scale, i
     Bt.close()
+
+
+def test_batch_work_queue_w_cycle(monkeypatch):
+    """Work-queue mode with W-cycles (the recorded cycle visits the coarser levels twice): every
+    member reaches rtol through its own FP64 operator."""
+    from paper_2205_15770_gb300 import StokesBatch
+    monkeypatch.setenv("STOKES_BATCH_QUEUE", "1")
+    members = _queue_members()[:4]
+    Bt = StokesBatch(members, kA=1, kS=1, m=2, schur_diag="d", cycle="W")
+    bs = [mv.mass_rhs(torch.as_tensor(W.fourier_forcing(3, 2, mb["n"], seed=70 + i).reshape(-1), device="cuda"))
+          for i, (mb, mv) in enumerate(zip(members, Bt.members))]
+    xs, its, rels = Bt.solve(bs, rtol=1e-10)
+    assert Bt.krylov_mode == 2
+    for i, mv in enumerate(Bt.members):
+        r = bs[i] - mv.vmult(xs[i])
+        assert torch.linalg.norm(r).item() <= 1.01e-10 * torch.linalg.norm(bs[i]).item(), i
+    Bt.close()
+
+
+def test_batch_work_queue_not_served_falls_back(monkeypatch):
+    """A member the work-queue kernel does not serve (k = 3) keeps the batch on the graph branches
+    (krylov_mode 1), and stokes_batch_vcycle reports STOKES_EINVAL."""
+    from paper_2205_15770_gb300 import StokesBatch, StokesError
+    monkeypatch.setenv("STOKES_BATCH_QUEUE", "1")
+    members = [dict(dim=3, n=(4, 4, 4), n_levels=2, gamma_rho=0.0),
+               dict(dim=3, n=(4, 4, 4), n_levels=2, gamma_rho=1.0, k=3)]
+    Bt = StokesBatch(members, kA=1, kS=1, m=2, schur_diag="d")
+    bs = [mv.mass_rhs(torch.as_tensor(W.fourier_forcing(3, mb.get("k", 2), mb["n"], seed=80 + i).reshape(-1),
+                                      device="cuda"))
+          for i, (mb, mv) in enumerate(zip(members, Bt.members))]
+    xs, its, rels = Bt.solve(bs, rtol=1e-9)
+    assert Bt.krylov_mode == 1 and max(rels) <= 1e-9
+    with pytest.raises(StokesError) as e:
+        Bt.vcycle([b.float() for b in bs])
+    assert e.value.status == 1
+    Bt.close()
