@@ -2296,6 +2296,7 @@ static bool batch_kbuild(stokes_batch *Bt) {
 // with the rest of its iteration (FP64 operator, CGS2, Givens) and k_batch_any.  Served: every
 // member 3D, k = 2, FP32 cycle, no stabilisation, symmetric-gradient or rho term.
 static bool batch_qrecord(stokes_batch *Bt) {
+  if (Bt->qmem) return true;  // recorded before (stokes_batch_vcycle or an earlier build)
   const int nm = (int)Bt->ctx.size();
   bool tri = false;
   for (auto *C : Bt->ctx) {
