@@ -1058,6 +1058,42 @@ def run_channel(args):
     print(json.dumps(out))
 
 
+def run_channel_smoothers(args):
+    """The Q3 channel solve of run_channel (64^3 cells of aspect 4:1:1, lifted inflow, rtol 1e-8,
+    FP32 V-cycle in FP64 FGMRES(30), Schur diagonal d) for several smoothers (k_A, k_S, m): FGMRES
+    iterations and ms per solve.  The paper's best settings for its channel benchmark (Schafer-Turek,
+    Sec. 4.4) use higher Chebyshev degrees than the cube's (1, 1, 2)."""
+    import torch
+    from paper_2205_15770_gb300 import StokesMG
+    n, k, nl = 64, 3, 6
+    for kA, kS, m in ((1, 1, 2), (2, 1, 2), (3, 1, 2), (2, 2, 2), (3, 2, 2), (3, 3, 2)):
+        S = StokesMG(dim=3, n=(n, n, n), n_levels=nl, k=k, mu=1e-3, hi=(4.0, 1.0, 1.0), dirichlet_faces=0x3D,
+                     kA=kA, kS=kS, m=m, schur_diag="d")
+        N = S.size()
+        nodes = S.velocity_nodes()
+        nu, _ = S.sizes()
+        nv = nu // 3
+        uD = torch.zeros(N, dtype=torch.float64, device="cuda")
+        inflow = nodes[:, 0] == 0.0
+        yy, zz = nodes[:, 1], nodes[:, 2]
+        uD[:nv] = torch.where(inflow, 16 * yy * (1 - yy) * zz * (1 - zz), torch.zeros_like(yy))
+        b = S.lift_rhs(uD, torch.zeros_like(uD))
+        xs = torch.zeros_like(b)
+        S.solve(b, xs, rtol=WL["rtol"])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        xs.zero_()
+        e0.record()
+        _, its, rel = S.solve(b, xs, rtol=WL["rtol"])
+        e1.record()
+        e1.synchronize()
+        print(json.dumps({"kA": kA, "kS": kS, "m": m, "schur_diag": "d", "dofs": N, "iterations": its,
+                          "ms_per_solve": round(e0.elapsed_time(e1), 2), "rel_residual": rel}), flush=True)
+        S.close()
+        del S
+        torch.cuda.empty_cache()
+
+
 def run_kernel_only(args):
     """Set up one context of the workload (gamma = 1e2) and launch one cell kernel of the finest
     level a few times inside a cudaProfilerStart/Stop range, for ncu: the FP32 A-block apply
@@ -1127,6 +1163,8 @@ def main():
                     help="bracket the timed steps by cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--channel", action="store_true",
                     help="64^3 channel (Q2..Q4): vmult throughput, HBM fraction, Q3 solve of the lifted problem")
+    ap.add_argument("--channel-smoothers", action="store_true",
+                    help="Q3 channel solve for several smoother settings (k_A, k_S, m)")
     ap.add_argument("--paper-sweep", action="store_true",
                     help="the paper's (k_A, k_S, m) rate study on the lid-driven cavities (stationary FP64 MG)")
     ap.add_argument("--smoother-sweep", action="store_true",
@@ -1157,6 +1195,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.channel:
         run_channel(args)
+    elif args.channel_smoothers:
+        run_channel_smoothers(args)
     elif args.paper_sweep:
         run_paper_sweep(args)
     elif args.smoother_sweep:
