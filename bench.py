@@ -613,12 +613,13 @@ def run_ours(args):
 
 
 def run_deterministic(S_atomic, b, common):
-    """The workload's gamma = 1e2 solve and vmults in deterministic mode against the default (atomic)
-    context: time per FP32-MG solve, FP32 / FP64 vmult, and whether two solves repeat bitwise."""
+    """The workload's gamma = 1e2 solve and vmults in deterministic mode (owner-computes; the colour-class
+    form beside it) against the default (atomic) context: time per FP32-MG solve, FP32 / FP64 vmult, and
+    whether two solves repeat bitwise."""
     import torch
     from paper_2205_15770_gb300 import StokesMG
     kw = dict(common)
-    S = StokesMG(gamma_rho=1e2, vcycle_fp32=True, deterministic=True, **kw)
+    S = StokesMG(gamma_rho=1e2, vcycle_fp32=True, deterministic=1, **kw)
 
     def t_solve(Sx, reps=3):
         x = torch.zeros_like(b)
@@ -655,6 +656,11 @@ def run_deterministic(S_atomic, b, common):
         out[f"vmult_fp{prec}_us"] = round(t_vmult(S, dt, reps), 2)
         out[f"atomic_vmult_fp{prec}_us"] = round(t_vmult(S_atomic, dt, reps), 2)
     S.close()
+    S2 = StokesMG(gamma_rho=1e2, vcycle_fp32=True, deterministic=2, **kw)
+    ms_col, it_col, _ = t_solve(S2, reps=1)
+    out["colour_classes"] = {"solve_ms": round(ms_col, 3), "iterations": it_col,
+                             "vmult_fp32_us": round(t_vmult(S2, torch.float32, 20), 2)}
+    S2.close()
     return out
 
 

@@ -92,16 +92,19 @@ typedef struct {
   const double *rho_cell; /* HOST, nullable: per-cell rho of the gamma rho u.v term on the finest level
                            (n cells, x fastest; copied at setup; coarse levels take the mean of the
                            2^d children); null: rho = 1.  Entries must be > 0 */
-  int deterministic;    /* 1: bitwise-reproducible operator applications.  Every cell-kernel launch of
-                           the solver runs as one cooperative launch that walks the 8 classes of cells
-                           with equal index parities (no two cells of a class share a node; the paper's
-                           K x = sum_tau P_tau K_tau P_tau^T x summed class by class) with a grid barrier
-                           between classes, and scatters by plain read-modify-write instead of atomic
-                           adds; the smoother is the unfused one.  3D, k = 2 (any mesh) or k = 3
-                           (Cartesian), Laplacian form, constant rho, C = 0 (else STOKES_EINVAL) */
-  unsigned int wait_cycles; /* deterministic mode: clock64() cycles a CTA waits at a grid barrier before
-                           it gives up, flags the error and returns (0: 2^31, about 1 s); calls then
-                           return STOKES_ETIMEOUT */
+  int deterministic;    /* bitwise-reproducible operator applications (no atomic scatter; the smoother is
+                           the unfused one).  1 (owner-computes): every cell-kernel application is two
+                           launches, the cell-component kernel storing each cell's local results
+                           (K_tau P_tau^T x of the paper's K x = sum_tau P_tau K_tau P_tau^T x) and a
+                           per-DoF pass summing the results of the cells that hold the DoF in a fixed
+                           order.  2 (colour classes): one cooperative launch walks the 8 classes of
+                           cells with equal index parities (no two cells of a class share a node) with
+                           a grid barrier between classes and scatters by plain read-modify-write.
+                           3D, k = 2 (any mesh) or k = 3 (Cartesian), Laplacian form, constant rho,
+                           C = 0 (else STOKES_EINVAL); 0: atomic scatter */
+  unsigned int wait_cycles; /* deterministic mode 2: clock64() cycles a CTA waits at a grid barrier
+                           before it gives up, flags the error and returns (0: 2^31, about 1 s); calls
+                           then return STOKES_ETIMEOUT */
 } stokes_opts;
 
 /* Fill *o with kA = kS = 3, m = 2, V-cycle, local Schur diagonal, FP32 cycle,

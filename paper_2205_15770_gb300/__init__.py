@@ -99,7 +99,8 @@ class StokesMG:
         opts.seed = seed
         opts.c_mass, opts.c_grad = float(c_mass), float(c_grad)
         opts.sym_grad = 1 if sym_grad else 0
-        opts.deterministic = 1 if deterministic else 0
+        # True / 1: owner-computes, 2 or "colour": colour classes with bounded grid barriers
+        opts.deterministic = {False: 0, True: 1, 0: 0, 1: 1, 2: 2, "owner": 1, "colour": 2}[deterministic]
         opts.wait_cycles = int(wait_cycles)
         if rho_cell is not None:
             rc = np.ascontiguousarray(np.asarray(rho_cell, dtype=np.float64).reshape(-1))

@@ -1483,6 +1483,10 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
   C->c_grad = C->o.c_grad;
   C->sym = C->o.sym_grad != 0;
   C->det = C->o.deterministic != 0;
+  if (C->o.deterministic < 0 || C->o.deterministic > 2) {
+    set_error("opts.deterministic must be 0, 1 (owner-computes) or 2 (colour classes)");
+    return STOKES_EINVAL;
+  }
   if (C->det && (dim != 3 || (k != 2 && k != 3) || (k == 3 && mesh->vertices) || C->sym || C->o.rho_cell ||
                  C->c_mass != 0.0 || C->c_grad != 0.0)) {
     set_error("deterministic mode needs 3D, k = 2 (any mesh) or k = 3 (Cartesian), the Laplacian form with a "
@@ -1721,6 +1725,19 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
         return STOKES_EINVAL;
       }
     if ((st = dalloc(C, &C->gb.state, 4))) return st;
+    if (C->o.deterministic == 1) {
+      // owner-computes form: per-cell local results of the largest level, both precisions
+      long long cells = 0;
+      for (int l = 0; l < nl; ++l) cells = std::max(cells, C->L64[l].d.n_cells);
+      const long long per = 3LL * ((k + 1) * (k + 1) * (k + 1) + k * k * k);
+      float *l32 = nullptr;
+      double *l64 = nullptr;
+      if ((st = dalloc(C, &l32, per * cells))) return st;
+      if ((st = dalloc(C, &l64, per * cells))) return st;
+      C->gb.owner = 1;
+      C->gb.loc32 = l32;
+      C->gb.loc64 = l64;
+    }
     // setup runs with the default budget; opts.wait_cycles applies from the end of setup on
     const unsigned hs[4] = {0u, 0u, 0u, 0u};
     SMF_CUDA_OK(cudaMemcpyAsync(C->gb.state, hs, sizeof(hs), cudaMemcpyHostToDevice, C->s));

@@ -192,8 +192,12 @@ __host__ __device__ inline long long colour_extent(const int n[3], int colour, i
 // FUSED: the inputs are the pointwise combinations of the Fuse descriptor F (the smoother's vector
 // updates, Sec. 3.3.1), evaluated while gathering; the owner of each gathered node (thread of its
 // component in the owning cell; component 0 for pressure nodes) performs F's side effects.
-// COH: inputs read through L2 only (see ld_in).
-template <int K, typename T, int MODE, bool CART, bool DET, bool FUSED = false, bool COH = false>
+// COH: inputs read through L2 only (see ld_in).  LOCAL (owner-computes deterministic form): yu / yp
+// receive this thread's local results instead of the scatter, yu[(i * 3 + c) * n_cells + cell] for
+// the velocity node i of the cell (z, y, x lexicographic) and yp[(a * 3 + c) * n_cells + cell] for
+// the pressure node a (component c's part of B u); k_cc_owner_gather sums them per DoF.
+template <int K, typename T, int MODE, bool CART, bool DET, bool FUSED = false, bool COH = false,
+          bool LOCAL = false>
 __device__ __forceinline__ void cc_group(const LevelDesc<T> &L, const T *__restrict__ u, const T *__restrict__ p,
                                          T *__restrict__ yu, T *__restrict__ yp, const T *__restrict__ geo,
                                          long long group, int colour, const Fuse<T> &F = Fuse<T>{}) {
@@ -203,6 +207,7 @@ __device__ __forceinline__ void cc_group(const LevelDesc<T> &L, const T *__restr
   using CL = CcLaunch<K, T, MODE, CART>;
   static_assert(CART || K == 2, "trilinear cell-component kernel: k = 2");
   static_assert(!(COH && (FUSED || DET)), "coherent loads: plain form only");
+  static_assert(!(LOCAL && (FUSED || DET || COH)), "owner-computes form: plain gathers");
   const CCTab<T> &tb = cct<T>();
 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -689,6 +694,31 @@ __device__ __forceinline__ void cc_group(const LevelDesc<T> &L, const T *__restr
   }
 
   // ---- scatter ---------------------------------------------------------------------------------
+  if constexpr (LOCAL) {
+    if (valid) {
+      const long long nc = L.n_cells;
+      if (DO_A || DO_BT) {
+#pragma unroll
+        for (int iz = 0; iz < NV; ++iz)
+#pragma unroll
+          for (int iy = 0; iy < NV; ++iy)
+#pragma unroll
+            for (int ix = 0; ix < NV; ++ix)
+              yu[((long long)((iz * NV + iy) * NV + ix) * 3 + c) * nc + cell] = yv[iz][iy][ix];
+      }
+      if (DO_B) {
+#pragma unroll
+        for (int a3 = 0; a3 < NPR; ++a3)
+#pragma unroll
+          for (int a2 = 0; a2 < NPR; ++a2)
+#pragma unroll
+            for (int a1 = 0; a1 < NPR; ++a1)
+              yp[((long long)((a3 * NPR + a2) * NPR + a1) * 3 + c) * nc + cell] = qn[a3][a2][a1];
+      }
+    }
+    __syncwarp();
+    return;
+  }
   if (DO_A || DO_BT) {
     T *yb = yu + vbase;
     if (DET) {
@@ -781,6 +811,87 @@ __global__ void __launch_bounds__(32 * CcLaunch<K, T, MODE, CART>::WARPS, CcLaun
       L, u, p, yu, yp, geo, (long long)blockIdx.x * CcLaunch<K, T, MODE, CART>::WARPS + (threadIdx.x >> 5), -1, F);
 }
 
+// Owner-computes deterministic form, pass 1: every (cell, component) thread stores its local results.
+template <int K, typename T, int MODE, bool CART>
+__global__ void __launch_bounds__(32 * CcLaunch<K, T, MODE, CART>::WARPS, CcLaunch<K, T, MODE, CART>::MINB)
+    stokes_cell_apply_cc_local(const LevelDesc<T> L, const T *__restrict__ u, const T *__restrict__ p,
+                               T *__restrict__ lu, T *__restrict__ lp, const T *__restrict__ geo) {
+  pdl_enter();
+  cc_group<K, T, MODE, CART, false, false, false, true>(
+      L, u, p, lu, lp, geo, (long long)blockIdx.x * CcLaunch<K, T, MODE, CART>::WARPS + (threadIdx.x >> 5), -1);
+}
+
+// The cells holding global node g along one axis (node spacing s = k for velocity, k - 1 for
+// pressure, n cells): g = s c + a.  Interior-of-cell nodes have one (cell, local index), nodes on a
+// cell boundary two (the lower cell's last index first), the domain ends one.
+__device__ __forceinline__ int owner_cells(int g, int s, int n, int (&cell)[2], int (&loc)[2]) {
+  const int c = g / s, a = g - c * s;
+  if (a != 0) {
+    cell[0] = c;
+    loc[0] = a;
+    return 1;
+  }
+  int m = 0;
+  if (c > 0) {
+    cell[m] = c - 1;
+    loc[m] = s;
+    ++m;
+  }
+  if (c < n) {
+    cell[m] = c;
+    loc[m] = 0;
+    ++m;
+  }
+  return m;
+}
+
+// Pass 2: y += the sum of the local results of every cell holding the DoF, cells in a fixed
+// (z, y, x) order and, for pressure, the three component parts of a cell summed first: the same
+// operator as the atomic scatter (the paper's K x = sum_tau P_tau K_tau P_tau^T x), bitwise
+// reproducible.  Constrained velocity DoFs are left alone.
+template <int K, typename T>
+__global__ void k_cc_owner_gather(const LevelDesc<T> L, const T *__restrict__ lu, const T *__restrict__ lp,
+                                  T *__restrict__ yu, T *__restrict__ yp, int do_u, int do_p) {
+  pdl_enter();
+  constexpr int NV = K + 1, NPR = K;
+  const long long nc = L.n_cells, nu = do_u ? L.n_u : 0, np = do_p ? L.n_p : 0;
+  SMF_GRID_LOOP(i, nu + np) {
+    int cx[2], ax[2], cy[2], ay[2], cz[2], az[2];
+    if (i < nu) {
+      const int c = (int)(i / L.nv);
+      const long long j = i - c * L.nv;
+      const int gx = (int)(j % L.N[0]), gy = (int)((j / L.N[0]) % L.N[1]), gz = (int)(j / ((long long)L.N[0] * L.N[1]));
+      if (vel_constrained(L.N, L.faces, 3, gx, gy, gz)) continue;
+      const int mx = owner_cells(gx, K, L.n[0], cx, ax), my = owner_cells(gy, K, L.n[1], cy, ay),
+                mz = owner_cells(gz, K, L.n[2], cz, az);
+      T s = T(0);
+      for (int z = 0; z < mz; ++z)
+        for (int y = 0; y < my; ++y)
+          for (int x = 0; x < mx; ++x) {
+            const long long cell = ((long long)cz[z] * L.n[1] + cy[y]) * L.n[0] + cx[x];
+            const int loc = (az[z] * NV + ay[y]) * NV + ax[x];
+            s += lu[((long long)loc * 3 + c) * nc + cell];
+          }
+      yu[i] += s;
+    } else {
+      const long long j = i - nu;
+      const int px = (int)(j % L.Pn[0]), py = (int)((j / L.Pn[0]) % L.Pn[1]),
+                pz = (int)(j / ((long long)L.Pn[0] * L.Pn[1]));
+      const int mx = owner_cells(px, K - 1, L.n[0], cx, ax), my = owner_cells(py, K - 1, L.n[1], cy, ay),
+                mz = owner_cells(pz, K - 1, L.n[2], cz, az);
+      T s = T(0);
+      for (int z = 0; z < mz; ++z)
+        for (int y = 0; y < my; ++y)
+          for (int x = 0; x < mx; ++x) {
+            const long long cell = ((long long)cz[z] * L.n[1] + cy[y]) * L.n[0] + cx[x];
+            const long long base = (long long)((az[z] * NPR + ay[y]) * NPR + ax[x]) * 3 * nc + cell;
+            s += (lp[base] + lp[base + nc]) + lp[base + 2 * nc];
+          }
+      yp[j] += s;
+    }
+  }
+}
+
 // Deterministic form: one cooperative launch walks the 8 colour classes of cells in order, each
 // class by all CTAs (a warp per group of 10 cells), with a grid barrier between classes.  The
 // barrier waits are bounded (GridBarrier::budget); a wait that runs out sets the error flag and
@@ -815,6 +926,9 @@ static cudaError_t cc_carveout_mode() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(stokes_cell_apply_cc_fused<K, T, MODE, false>,
                              cudaFuncAttributePreferredSharedMemoryCarveout, pc);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(stokes_cell_apply_cc_local<K, T, MODE, false>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout, pc);
   return e;
 }
 template <int K>
@@ -847,6 +961,17 @@ template <int K, typename T, int MODE, bool CART>
 static int launch_cc_det_mode(const LevelDesc<T> &L, const T *u, const T *p, T *yu, T *yp, const T *geo,
                               const GridBarrier &gb, cudaStream_t s) {
   using CL = CcLaunch<K, T, MODE, CART>;
+  if (gb.owner) {  // owner-computes: local results, then the per-DoF sums
+    T *lu = static_cast<T *>(sizeof(T) == 4 ? gb.loc32 : gb.loc64);
+    T *lp = lu + (long long)3 * (K + 1) * (K + 1) * (K + 1) * L.n_cells;
+    const long long cpb = (long long)kCcCells * CL::WARPS;
+    launch_kernel(stokes_cell_apply_cc_local<K, T, MODE, CART>, dim3((unsigned)((L.n_cells + cpb - 1) / cpb)),
+                  dim3(32 * CL::WARPS), CL::SMEM, s, L, u, p, lu, lp, geo);
+    constexpr bool DU = MODE & (kApplyA | kApplyBT), DP = MODE & kApplyB;
+    launch_kernel(k_cc_owner_gather<K, T>, dim3(vec_blocks((DU ? L.n_u : 0) + (DP ? L.n_p : 0))), dim3(kVecThreads), 0,
+                  s, L, (const T *)lu, (const T *)lp, yu, yp, DU ? 1 : 0, DP ? 1 : 0);
+    return (int)cudaGetLastError();
+  }
   static int resident = -1;
   if (resident < 0) {
     int dev = 0, sms = 0, per_sm = 0;

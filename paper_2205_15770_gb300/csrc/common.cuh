@@ -119,6 +119,10 @@ __device__ __forceinline__ void pdl_enter() {
 // so no CTA waits for one that has left.
 struct GridBarrier {
   unsigned *state = nullptr;
+  // owner-computes form (owner != 0): no barrier; per-cell local results in loc32 / loc64 (by
+  // precision), summed per DoF in a fixed order by a second pass
+  int owner = 0;
+  void *loc32 = nullptr, *loc64 = nullptr;
 };
 #if defined(__CUDACC__)
 // Input loads of the kernels: plain (the compiler may use the read-only path) or, in the
