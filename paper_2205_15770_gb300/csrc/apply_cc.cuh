@@ -147,12 +147,14 @@ __device__ __forceinline__ void cc_sweep2(const T (&in)[NI][E1][E0], T (&out)[NO
       }
 }
 
-// Shared-memory geometry record of one Gauss point of one cell (trilinear, FP32): NF float4,
-// [0] = (G00, G01, G02, G11), [1] = (G12, G22, gamma rho w det, 0) with G = mu w adj adj^T / det,
-// [2 + j] = column j of w adj(J) (present when a B block is applied).
+// Shared-memory geometry record of one Gauss point of one cell (trilinear, FP32): NF = NA + NB
+// float4, with the A block [0] = (G00, G01, G02, G11), [1] = (G12, G22, gamma rho w det, 0),
+// G = mu w adj adj^T / det (NA = 2), and with a B block [NA + j] = column j of w adj(J) (NB = 3).
 template <int MODE>
 struct CcGeo {
-  static constexpr int NF = (MODE & (kApplyB | kApplyBT)) ? 5 : 2;
+  static constexpr int NA = (MODE & kApplyA) ? 2 : 0;
+  static constexpr int NB = (MODE & (kApplyB | kApplyBT)) ? 3 : 0;
+  static constexpr int NF = NA + NB;
 };
 
 #ifndef SMF_CC_SLICE_UNROLL
@@ -167,7 +169,7 @@ struct CcLaunch {
   // trilinear cells: FP32 shares the geometry through shared memory, FP64 reads the per-point
   // geometry stored at setup (the column kernel's layout)
   static constexpr bool SMEM_GEO = !CART && sizeof(T) == 4;
-  static constexpr int WARPS = (SMEM_GEO && (MODE & (kApplyB | kApplyBT))) ? 2 : 4;
+  static constexpr int WARPS = (SMEM_GEO && CcGeo<MODE>::NF > 3) ? 2 : 4;
   static constexpr size_t GEO_BYTES =
       SMEM_GEO ? (size_t)WARPS * NQ * NQ * NQ * CcGeo<MODE>::NF * kCcCells * sizeof(float4) : 0;
   // deterministic launches: the three component threads' pressure sums of a cell meet here
@@ -565,18 +567,21 @@ __device__ __forceinline__ void cc_group(const LevelDesc<T> &L, const T *__restr
           r[2][0] = c0[1] * c1[2] - c0[2] * c1[1];
           r[2][1] = c0[2] * c1[0] - c0[0] * c1[2];
           r[2][2] = c0[0] * c1[1] - c0[1] * c1[0];
-          const T det = c0[0] * r[0][0] + c0[1] * r[0][1] + c0[2] * r[0][2];
           const T w = tb.W[qx] * tb.W[qy] * wz;
-          const T wd = __fdividef(mu * w, det);
-          auto dot = [&](int i, int j) { return r[i][0] * r[j][0] + r[i][1] * r[j][1] + r[i][2] * r[j][2]; };
           const int pt = (c * NQ + qy) * NQ + qx;
+          constexpr int NA = CcGeo<MODE>::NA;
           if (!pad) {
             float4 *g = gs + (size_t)pt * NF * CPW + s;
-            g[0] = make_float4(wd * dot(0, 0), wd * dot(0, 1), wd * dot(0, 2), wd * dot(1, 1));
-            g[CPW] = make_float4(wd * dot(1, 2), wd * dot(2, 2), grho * w * det, 0.f);
-            if (NF > 2) {
+            if constexpr (NA > 0) {  // the A block's metric (the B blocks need only w adj(J))
+              const T det = c0[0] * r[0][0] + c0[1] * r[0][1] + c0[2] * r[0][2];
+              const T wd = __fdividef(mu * w, det);
+              auto dot = [&](int i, int j) { return r[i][0] * r[j][0] + r[i][1] * r[j][1] + r[i][2] * r[j][2]; };
+              g[0] = make_float4(wd * dot(0, 0), wd * dot(0, 1), wd * dot(0, 2), wd * dot(1, 1));
+              g[CPW] = make_float4(wd * dot(1, 2), wd * dot(2, 2), grho * w * det, 0.f);
+            }
+            if constexpr (CcGeo<MODE>::NB > 0) {
 #pragma unroll
-              for (int j = 0; j < 3; ++j) g[(2 + j) * CPW] = make_float4(w * r[0][j], w * r[1][j], w * r[2][j], 0.f);
+              for (int j = 0; j < 3; ++j) g[(NA + j) * CPW] = make_float4(w * r[0][j], w * r[1][j], w * r[2][j], 0.f);
             }
           }
         }
@@ -635,7 +640,7 @@ __device__ __forceinline__ void cc_group(const LevelDesc<T> &L, const T *__restr
           };
           auto geo_C = [&](T(&cc)[3]) {
             if constexpr (CL::SMEM_GEO) {
-              const float4 v = g[(2 + c) * CPW];
+              const float4 v = g[(CcGeo<MODE>::NA + c) * CPW];
               cc[0] = v.x; cc[1] = v.y; cc[2] = v.z;
             } else {
 #pragma unroll
@@ -914,21 +919,23 @@ __global__ void __launch_bounds__(32 * CcLaunch<K, T, MODE, CART>::WARPS, CcLaun
 }
 
 // The trilinear kernels keep their geometry in shared memory: ask for the largest shared-memory
-// carveout so that occupancy is set by registers, not by the default L1 / shared split.
+// carveout so that occupancy is set by registers, not by the default L1 / shared split, and allow
+// the launch's dynamic shared memory where it exceeds the default 48 KB.
+template <typename F>
+static cudaError_t cc_smem_attrs(F *kern, size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       (int)cudaSharedmemCarveoutMaxShared);
+  if (e == cudaSuccess && smem > 48 * 1024)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return e;
+}
 template <int K, typename T, int MODE>
 static cudaError_t cc_carveout_mode() {
-  const int pc = (int)cudaSharedmemCarveoutMaxShared;
-  cudaError_t e = cudaFuncSetAttribute(stokes_cell_apply_cc<K, T, MODE, false>,
-                                       cudaFuncAttributePreferredSharedMemoryCarveout, pc);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(stokes_cell_apply_cc_det<K, T, MODE, false>,
-                             cudaFuncAttributePreferredSharedMemoryCarveout, pc);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(stokes_cell_apply_cc_fused<K, T, MODE, false>,
-                             cudaFuncAttributePreferredSharedMemoryCarveout, pc);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(stokes_cell_apply_cc_local<K, T, MODE, false>,
-                             cudaFuncAttributePreferredSharedMemoryCarveout, pc);
+  using CL = CcLaunch<K, T, MODE, false>;
+  cudaError_t e = cc_smem_attrs(stokes_cell_apply_cc<K, T, MODE, false>, CL::SMEM);
+  if (e == cudaSuccess) e = cc_smem_attrs(stokes_cell_apply_cc_det<K, T, MODE, false>, CL::SMEM_DET);
+  if (e == cudaSuccess) e = cc_smem_attrs(stokes_cell_apply_cc_fused<K, T, MODE, false>, CL::SMEM);
+  if (e == cudaSuccess) e = cc_smem_attrs(stokes_cell_apply_cc_local<K, T, MODE, false>, CL::SMEM);
   return e;
 }
 template <int K>
