@@ -1100,6 +1100,48 @@ def run_channel_smoothers(args):
         torch.cuda.empty_cache()
 
 
+def run_level_times(args):
+    """Where a V-cycle's time goes: the FP32 V-cycle of the workload's family (perturbed unit cube,
+    gamma 1e2, the bench smoother) on 4^3 .. 32^3 cells (coarsest 2^3), each timed over 50 cycles
+    (CUDA events, captured cycle graphs), and on the 32^3 hierarchy the cell kernel's duration per
+    level, block set (A, B^T, B, A + B^T, full) and launch shape (stokes_time_apply, 200 launches)."""
+    import torch
+    import workloads as W
+    from paper_2205_15770_gb300 import StokesMG
+    for n in (4, 8, 16, 32):
+        nl = {4: 2, 8: 3, 16: 4, 32: 5}[n]
+        V = W.perturbed_vertices(3, (n,) * 3, seed=WL["seed"], amplitude=WL["amplitude"])
+        S = StokesMG(dim=3, n=(n,) * 3, n_levels=nl, k=2, vertices=V, gamma_rho=1e2,
+                     kA=WL["kA"], kS=WL["kS"], m=WL["m"], schur_diag=WL["schur_diag"])
+        f = torch.as_tensor(W.fourier_forcing(3, 2, (n,) * 3, seed=WL["seed"]).reshape(-1), device="cuda")
+        b = S.mass_rhs(f).float()
+        x = torch.zeros_like(b)
+        for _ in range(5):
+            x.zero_()
+            S.vcycle(b, x)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(50):
+            x.zero_()
+            S.vcycle(b, x)
+        e1.record()
+        e1.synchronize()
+        row = {"n": n, "levels": nl, "vcycle_fp32_ms": round(e0.elapsed_time(e1) / 50, 4),
+               "launch_shapes_fp32": S.launch_shapes(32), "fused_smoothing_levels": S.fused_levels(32)}
+        if n == 32:
+            apply_us = {}
+            for l in range(1, nl):
+                for sh in sorted({S.launch_shapes(32)[l], 5}):
+                    S.set_launch_shape(l, sh, precision=32)
+                    apply_us[f"level{l}_shape{sh}"] = {
+                        name: round(S.time_apply(blk, level=l, precision=32, reps=200) * 1e3, 2)
+                        for name, blk in (("A", 1), ("BT", 2), ("B", 4), ("A+BT", 3), ("full", 7))}
+            row["apply_us"] = apply_us
+        print(json.dumps(row), flush=True)
+        S.close()
+
+
 def run_kernel_only(args):
     """Set up one context of the workload (gamma = 1e2) and launch one cell kernel of the finest
     level a few times inside a cudaProfilerStart/Stop range, for ncu: the FP32 A-block apply
@@ -1169,6 +1211,8 @@ def main():
                     help="bracket the timed steps by cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--channel", action="store_true",
                     help="64^3 channel (Q2..Q4): vmult throughput, HBM fraction, Q3 solve of the lifted problem")
+    ap.add_argument("--level-times", action="store_true",
+                    help="FP32 V-cycle time on 4^3..32^3 and the cell kernel's duration per level and block set")
     ap.add_argument("--channel-smoothers", action="store_true",
                     help="Q3 channel solve for several smoother settings (k_A, k_S, m)")
     ap.add_argument("--paper-sweep", action="store_true",
@@ -1203,6 +1247,8 @@ def main():
         run_channel(args)
     elif args.channel_smoothers:
         run_channel_smoothers(args)
+    elif args.level_times:
+        run_level_times(args)
     elif args.paper_sweep:
         run_paper_sweep(args)
     elif args.smoother_sweep:
