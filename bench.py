@@ -1149,21 +1149,27 @@ def run_kernel_only(args):
     import torch
     from paper_2205_15770_gb300 import StokesMG
     torch.cuda.set_device(0)
-    S = StokesMG(dim=3, n=WL["n"], n_levels=WL["levels"], k=WL["k"], vertices=perturbed_vertices(), gamma_rho=1e2,
-                 kA=WL["kA"], kS=WL["kS"], m=WL["m"], schur_diag=WL["schur_diag"])
+    if args.kernel_case == "channel-q2-128":  # the channel's Q2 point at 128^3 Cartesian cells (53.1M DoFs)
+        nl, cells = 7, 128 ** 3
+        S = StokesMG(dim=3, n=(128, 128, 128), n_levels=nl, k=2, mu=1e-3, hi=(4.0, 1.0, 1.0), dirichlet_faces=0x3D,
+                     kA=WL["kA"], kS=WL["kS"], m=WL["m"], schur_diag=WL["schur_diag"])
+    else:
+        nl, cells = WL["levels"], WL["n"][0] * WL["n"][1] * WL["n"][2]
+        S = StokesMG(dim=3, n=WL["n"], n_levels=nl, k=WL["k"], vertices=perturbed_vertices(), gamma_rho=1e2,
+                     kA=WL["kA"], kS=WL["kS"], m=WL["m"], schur_diag=WL["schur_diag"])
     prec = args.kernel_precision
     mode = args.kernel_mode if args.kernel_mode else (1 if prec == 32 else 7)
     # the finest level's launch shape is pinned (a profiler changes the setup's timings): the
     # cell-component kernel in FP32, the 4-warp column kernel with stored geometry in FP64
     shape = args.kernel_shape if args.kernel_shape else (5 if prec == 32 else 4)
-    S.set_launch_shape(WL["levels"] - 1, shape, precision=prec)
+    S.set_launch_shape(nl - 1, shape, precision=prec)
     S.time_apply(mode, precision=prec, reps=3)
     torch.cuda.synchronize()
     torch.cuda.profiler.start()
     ms = S.time_apply(mode, precision=prec, reps=3)
     torch.cuda.profiler.stop()
     print(json.dumps({"kernel": f"cell kernel, blocks {mode}, FP{prec}, launch shape {S.launch_shapes(prec)[-1]}",
-                      "avg_launch_us": ms * 1e3, "cells": WL["n"][0] * WL["n"][1] * WL["n"][2]}))
+                      "avg_launch_us": ms * 1e3, "cells": cells}))
     S.close()
 
 
@@ -1225,6 +1231,8 @@ def main():
                     help="with --kernel-only: the block bit set (1 A, 2 B^T, 4 B, 7 full; default 1 / 7 by precision)")
     ap.add_argument("--kernel-shape", type=int, default=0,
                     help="with --kernel-only: the finest level's launch shape (default 5 in FP32, 4 in FP64)")
+    ap.add_argument("--kernel-case", choices=("workload", "channel-q2-128"), default="workload",
+                    help="--kernel-only: the 32^3 workload, or the channel's Q2 point at 128^3 cells")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only launch the dominant kernel inside a profiler range (for ncu --set full)")
     ap.add_argument("--cpu-table", action="store_true",
