@@ -30,6 +30,11 @@ constexpr int kCcCells = 10;  // cells per warp of the cell-component kernel
 // 1D tables of this translation unit's degree for the cell-component kernel.
 template <typename T>
 struct CCTab {
+  // pairs for the packed (two FMAs per instruction) FP32 sweeps of the Cartesian A block, first in
+  // the struct so that they are 8-byte aligned: MK[2(i*NV+j) + 0 / 1] = (Mh, Kh)[i*NV+j],
+  // MM[2(i*NV+j) + 0 / 1] = Mh[i*NV+j] twice
+  T MK[2 * kMaxN1 * kMaxN1];
+  T MM[2 * kMaxN1 * kMaxN1];
   T S[kMaxN1 * kMaxN1];    // S[q*NV+m]  = l_m(x_q)   velocity basis at the Gauss points
   T D[kMaxN1 * kMaxN1];    // D[q*NQ+m]  = g_m'(x_q)  collocation derivative at the Gauss points
   T P[kMaxN1 * kMaxDeg];   // P[q*NPR+a] = psi_a(x_q) pressure basis at the Gauss points
@@ -40,8 +45,8 @@ struct CCTab {
   T Gh[kMaxDeg * kMaxN1];  // Gh[a*NV+j] = int_0^1 psi_a l_j'
   T Nh[kMaxDeg * kMaxN1];  // Nh[a*NV+j] = int_0^1 psi_a l_j
 };
-static __constant__ CCTab<float> c_ccf;
-static __constant__ CCTab<double> c_ccd;
+static __constant__ __align__(16) CCTab<float> c_ccf;
+static __constant__ __align__(16) CCTab<double> c_ccd;
 template <typename T>
 __device__ __forceinline__ const CCTab<T> &cct();
 template <>
@@ -78,6 +83,10 @@ int upload_cc_tables(const Tab1D<double> &t, cudaStream_t s) {
       }
       h.Kh[i * NV + j] = kk;
       h.Mh[i * NV + j] = mm;
+      h.MK[2 * (i * NV + j)] = mm;
+      h.MK[2 * (i * NV + j) + 1] = kk;
+      h.MM[2 * (i * NV + j)] = mm;
+      h.MM[2 * (i * NV + j) + 1] = mm;
     }
   for (int a = 0; a < NPR; ++a)
     for (int j = 0; j < NV; ++j) {
@@ -437,7 +446,38 @@ __device__ __forceinline__ void cc_group(const LevelDesc<T> &L, const T *__restr
               for (int a = 0; a < NPR; ++a) qn[a3][b][a] += Bx[a][i] * q;
             }
         }
-        if (DO_A) {
+        if constexpr (DO_A && sizeof(T) == 4) {
+          // the same sweeps with the Mh and Kh results of a node in one register pair: packed
+          // FP32 multiply-adds (two per instruction, the same roundings)
+          const float2 *MK = reinterpret_cast<const float2 *>(tb.MK);
+          const float2 *MM = reinterpret_cast<const float2 *>(tb.MM);
+          float2 a12[NV][NV];  // [z][y']: (Mh, Kh) along y
+#pragma unroll
+          for (int z = 0; z < NV; ++z)
+#pragma unroll
+            for (int yo = 0; yo < NV; ++yo) {
+              float2 acc = __fmul2_rn(MK[yo * NV], make_float2(sl[z][0], sl[z][0]));
+#pragma unroll
+              for (int y = 1; y < NV; ++y) acc = __ffma2_rn(MK[yo * NV + y], make_float2(sl[z][y], sl[z][y]), acc);
+              a12[z][yo] = acc;
+            }
+#pragma unroll
+          for (int zo = 0; zo < NV; ++zo)
+#pragma unroll
+            for (int y = 0; y < NV; ++y) {
+              float2 vt = __fmul2_rn(MM[zo * NV], a12[0][y]);  // (v, t2): Mh along z of (a1, a2)
+              T t3 = tb.Kh[zo * NV] * a12[0][y].x;
+#pragma unroll
+              for (int z = 1; z < NV; ++z) {
+                vt = __ffma2_rn(MM[zo * NV + z], a12[z][y], vt);
+                t3 += tb.Kh[zo * NV + z] * a12[z][y].x;
+              }
+              const T w = ay * vt.y + az * t3 + be * vt.x;
+              const T av = ax * vt.x;
+#pragma unroll
+              for (int j = 0; j < NV; ++j) yv[zo][y][j] += tb.Kh[j * NV + i] * av + tb.Mh[j * NV + i] * w;
+            }
+        } else if (DO_A) {
           T a1[NV][NV], a2[NV][NV];  // [z][y']: Mh and Kh along y
 #pragma unroll
           for (int z = 0; z < NV; ++z)
