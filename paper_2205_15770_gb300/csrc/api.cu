@@ -1793,6 +1793,7 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
     if ((st = dalloc(C, &K.y, m))) return st;
     if ((st = dalloc(C, &K.thresh, 1))) return st;
     if ((st = dalloc(C, &K.ctl, 4))) return st;
+    if ((st = dalloc(C, &K.ticket, 1))) return st;
     K.hcol = C->hdev;
     if ((st = dalloc(C, &C->zcur, N))) return st;
   }
@@ -1951,21 +1952,27 @@ static void krylov_post(stokes_ctx *C, cudaGraphConditionalHandle cond, bool set
   const long long N = C->L64[top].d.n_u + C->L64[top].d.n_p;
   const int nb = vec_blocks(N), m = C->restart;
   const int *ctl = C->kd.ctl;
+  // w = K z_j: the conversion writes the operator's identity rows too (no separate k_init_identity)
+  const LevelDesc<double> &Lt = C->L64[top].d;
   if (from_fp32)
-    R32.vec(k_convert_to_slot<float>, N, (const float *)C->L32[top].x, C->zcur, C->Z, N, ctl, N);
+    launch_kernel(k_convert_to_slot_id<float>, dim3(nb), dim3(kVecThreads), 0, C->s, Lt,
+                  (const float *)C->L32[top].x, C->zcur, C->Z, N, ctl, C->w);
   else
-    R64.vec(k_convert_to_slot<double>, N, (const double *)C->L64[top].x, C->zcur, C->Z, N, ctl, N);
-  R64.vmult(top, C->zcur, C->w, true);
+    launch_kernel(k_convert_to_slot_id<double>, dim3(nb), dim3(kVecThreads), 0, C->s, Lt,
+                  (const double *)C->L64[top].x, C->zcur, C->Z, N, ctl, C->w);
+  R64.apply_nz(top, kApplyA | kApplyBT | kApplyB, C->zcur, C->zcur + Lt.n_u, C->w, C->w + Lt.n_u);
+  R64.applyC(top, C->zcur + Lt.n_u, C->w + Lt.n_u, -1.0);
+  // CGS2 (two passes) and ||w||^2, each dot set with its final sums in the same launch
   for (int pass = 0; pass < 2; ++pass) {
-    k_mdot_partial_cnt<<<kRedBlocks, kVecThreads, 0, C->s>>>(C->V, N, ctl, 1, C->w, N, C->partial);
-    k_final_reduce_cnt<<<m, kVecThreads, 0, C->s>>>(C->partial, kRedBlocks, ctl, 1, C->hdev + pass * (m + 2));
+    k_mdot_final_cnt<<<kRedBlocks, kVecThreads, 0, C->s>>>(C->V, N, ctl, 1, C->w, N, C->partial, C->kd.ticket,
+                                                           C->hdev + pass * (m + 2));
     k_maxpy_cnt<<<nb, kVecThreads, 0, C->s>>>(C->V, N, ctl, 1, C->hdev + pass * (m + 2), C->w, N, -1.0);
   }
-  k_mdot_partial<<<kRedBlocks, kVecThreads, 0, C->s>>>(C->w, N, 1, C->w, N, C->partial);
-  k_final_reduce<<<1, kVecThreads, 0, C->s>>>(C->partial, kRedBlocks, 1, C->hdev + 2 * (m + 2));
+  k_mdot_final_cnt<<<kRedBlocks, kVecThreads, 0, C->s>>>(nullptr, N, nullptr, 0, C->w, N, C->partial, C->kd.ticket,
+                                                         C->hdev + 2 * (m + 2));
   k_scale_to_slot<<<nb, kVecThreads, 0, C->s>>>(C->w, C->hdev + 2 * (m + 2), C->V, N, ctl, N);
   k_fgmres_givens<<<1, 32, 0, C->s>>>(C->kd, cond, set_cond ? 1 : 0);
-  C->cap_count += 10;
+  C->cap_count += 8;
 }
 
 // Builds the device Krylov graph: a conditional while node whose body is krylov_body.  Returns

@@ -168,6 +168,36 @@ __global__ void k_mdot_partial_cnt(const double *__restrict__ V, long long ldv, 
   }
 }
 
+__global__ void k_mdot_final_cnt(const double *__restrict__ V, long long ldv, const int *__restrict__ ctl, int add,
+                                 const double *__restrict__ w, long long n, double *__restrict__ partial,
+                                 unsigned *__restrict__ ticket, double *__restrict__ out) {
+  pdl_enter();
+  __shared__ double sh[32];
+  __shared__ int last;
+  const int nvec = ctl ? ctl[0] + add : 1;
+  for (int j = 0; j < nvec; ++j) {
+    const double *v = ctl ? V + (long long)j * ldv : w;
+    double s = 0.0;
+    SMF_GRID_LOOP(i, n) s += v[i] * w[i];
+    s = block_reduce_sum<double>(s, sh);
+    if (threadIdx.x == 0) partial[(long long)j * gridDim.x + blockIdx.x] = s;
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();  // this block's partial sums before its ticket
+    last = atomicInc(ticket, gridDim.x - 1) == gridDim.x - 1;  // the counter wraps back to 0
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int nparts = gridDim.x;
+  for (int j = 0; j < nvec; ++j) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nparts; b += blockDim.x) s += __ldcg(partial + (long long)j * nparts + b);
+    s = block_reduce_sum<double>(s, sh);
+    if (threadIdx.x == 0) out[j] = s;
+  }
+}
+
 __global__ void k_final_reduce_cnt(const double *__restrict__ partial, int nparts, const int *__restrict__ ctl, int add,
                                    double *__restrict__ out) {
   pdl_enter();

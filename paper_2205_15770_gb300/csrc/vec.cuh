@@ -415,8 +415,16 @@ struct KrylovDev {
   double *hcol = nullptr;  // CGS2 coefficients of the two passes ([0, m+2), [m+2, 2m+4)) and ||w||^2
   double *thresh = nullptr;  // rtol * ||b||
   int *ctl = nullptr;
+  unsigned *ticket = nullptr;  // finished blocks of k_mdot_final_cnt (returns to 0 after every launch)
   int m = 0;
 };
+// k_mdot_partial_cnt and k_final_reduce_cnt in one launch: every block writes its partial sums, the
+// last block to finish (a ticket counter, after a fence) sums them per vector in the same fixed
+// order as k_final_reduce_cnt and writes out[jj] for jj < ctl[0] + add (V == w, add == 1 - ctl[0]
+// gives ||w||^2 through ctl = null: then one vector, V = w).
+__global__ void k_mdot_final_cnt(const double *__restrict__ V, long long ldv, const int *__restrict__ ctl, int add,
+                                 const double *__restrict__ w, long long n, double *__restrict__ partial,
+                                 unsigned *__restrict__ ticket, double *__restrict__ out);
 // partial[jj * gridDim.x + b] = block b's part of V_jj . w for jj < ctl[0] + add
 __global__ void k_mdot_partial_cnt(const double *__restrict__ V, long long ldv, const int *__restrict__ ctl, int add,
                                    const double *__restrict__ w, long long n, double *__restrict__ partial);
@@ -469,6 +477,29 @@ __global__ void k_convert_to_slot(const Tin *__restrict__ a, double *__restrict_
     const double v = (double)a[i];
     z[i] = v;
     zj[i] = v;
+  }
+}
+// The same, and y = the identity rows of z (z on constrained velocity DoFs, 0 elsewhere): the
+// start of y = K z (k_init_identity) in the same pass.
+template <typename Tin>
+__global__ void k_convert_to_slot_id(const LevelDesc<double> L, const Tin *__restrict__ a, double *__restrict__ z,
+                                     double *__restrict__ Z, long long ldz, const int *__restrict__ ctl,
+                                     double *__restrict__ y) {
+  pdl_enter();
+  double *zj = Z + (long long)ctl[0] * ldz;
+  SMF_GRID_LOOP(i, L.n_u + L.n_p) {
+    const double v = (double)a[i];
+    z[i] = v;
+    zj[i] = v;
+    double yi = 0.0;
+    if (i < L.n_u) {
+      const long long node = i % L.nv;
+      const int gx = (int)(node % L.N[0]);
+      const long long r = node / L.N[0];
+      const int gy = (int)(r % L.N[1]), gz = (int)(r / L.N[1]);
+      if (vel_constrained(L.N, L.faces, L.dim, gx, gy, gz)) yi = v;
+    }
+    y[i] = yi;
   }
 }
 
