@@ -78,7 +78,7 @@ def tuning_string(S):
     timings taken under a profiler choose differently)."""
     j = lambda v: ",".join(str(int(x)) for x in v)
     return (f"s32={j(S.launch_shapes(32))};s64={j(S.launch_shapes(64))};f32={j(S.fused_levels(32))};"
-            f"f64={j(S.fused_levels(64))}")
+            f"f64={j(S.fused_levels(64))};g32={j(S.geometry_stored(32))}")
 
 
 # ---------------------------------------------------------------------------------------------
@@ -586,7 +586,8 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk,
         "launch_shapes_fp32": S32[0].launch_shapes(32),
-        "fp64_geometry_stored": S32[0].geometry_stored(),
+        "fp64_geometry_stored": S32[0].geometry_stored(64),
+        "fp32_geometry_stored": S32[0].geometry_stored(32),
         "fused_smoothing_levels": {"fp32": S32[0].fused_levels(32), "fp64": S32[0].fused_levels(64)},
         "tuning": tuning_string(S32[0]),
         "batched": batched,
@@ -1128,7 +1129,8 @@ def run_level_times(args):
         e1.record()
         e1.synchronize()
         row = {"n": n, "levels": nl, "vcycle_fp32_ms": round(e0.elapsed_time(e1) / 50, 4),
-               "launch_shapes_fp32": S.launch_shapes(32), "fused_smoothing_levels": S.fused_levels(32)}
+               "launch_shapes_fp32": S.launch_shapes(32), "fused_smoothing_levels": S.fused_levels(32),
+               "fp32_geometry_stored": S.geometry_stored(32)}
         if n == 32:
             apply_us = {}
             for l in range(1, nl):

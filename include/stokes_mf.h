@@ -325,17 +325,21 @@ void stokes_destroy_batch(stokes_batch *batch);
  * the component's whole tensor in registers; 3D Cartesian levels with k = 2, 3 and FP32 trilinear
  * levels with k = 2, the Laplacian form with a constant rho; other applications on such a level run
  * in the 4-warp column kernel), 0 = not tuned (2D, or STOKES_NO_AUTOTUNE=1).  The environment variable
- * STOKES_TUNING="s32=..;s64=..;f32=..;f64=.." (comma lists, one value per level, coarsest first)
+ * STOKES_TUNING="s32=..;s64=..;f32=..;f64=..[;g32=..]" (comma lists, one value per level, coarsest first)
  * replaces the setup's timings of shapes and smoother forms, e.g. to profile the configuration a
  * plain run chose (a profiler changes the timings); malformed values make setup fail with
  * STOKES_EINVAL.  HOST output. */
 int stokes_get_launch_shape(const stokes_ctx *ctx, int level, int precision, int *shape);
 
-/* 1 if the FP64 per-point geometry of `level` (G, w adj(J), w det J per Gauss point with mu and
- * gamma rho folded in; 3D trilinear levels) was stored at setup, 0 if the FP64 kernels evaluate it
- * on the fly (Cartesian levels, STOKES_GEO=none, or a level larger than the budget: 1/16 of the
- * device memory, and at most half of the memory free at setup).  HOST output. */
-int stokes_get_geometry_stored(const stokes_ctx *ctx, int level, int *stored);
+/* 1 if the column kernels of `level` in `precision` (32 or 64) read the per-point geometry (G,
+ * w adj(J), w det J per Gauss point with mu and gamma rho folded in; 3D trilinear levels) stored at
+ * setup, 0 if they evaluate it on the fly.  FP64: stored unless the level is Cartesian,
+ * STOKES_GEO=none, or the level is larger than the budget (1/16 of the device memory, and at most
+ * half of the memory free at setup).  FP32: stored for levels of at most 32^3 cells and read where
+ * the setup's timing of the column kernel keeps it (STOKES_TUNING's g32 list otherwise; 0 without
+ * autotuning).  The cell-component kernel (shape 5) evaluates the FP32 geometry itself either way.
+ * HOST output. */
+int stokes_get_geometry_stored(const stokes_ctx *ctx, int level, int precision, int *stored);
 
 /* 1 if smoothing on `level` / `precision` runs in the fused form (k_A = 1, 3D, column kernel: the
  * Chebyshev-Jacobi and Uzawa vector updates of Sec. 3.3.1 evaluated inside the cell-kernel

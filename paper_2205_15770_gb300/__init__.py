@@ -347,12 +347,13 @@ class StokesMG:
             out.append(v.value)
         return out
 
-    def geometry_stored(self):
-        """Per level: True where the FP64 per-point geometry is stored (stokes_get_geometry_stored)."""
+    def geometry_stored(self, precision=64):
+        """Per level: True where the column kernels of that precision read the per-point geometry stored
+        at setup (stokes_get_geometry_stored)."""
         out = []
         for l in range(self.n_levels):
             v = C.c_int()
-            self._check(self._lib.stokes_get_geometry_stored(self._ctx, l, C.byref(v)))
+            self._check(self._lib.stokes_get_geometry_stored(self._ctx, l, precision, C.byref(v)))
             out.append(bool(v.value))
         return out
 

@@ -66,7 +66,7 @@ SIGNATURES = {
     "stokes_batch_last_error": (C.c_char_p, [P]),
     "stokes_destroy_batch": (None, [P]),
     "stokes_set_launch_shape": (C.c_int, [P, C.c_int, C.c_int, C.c_int]),
-    "stokes_get_geometry_stored": (C.c_int, [P, C.c_int, C.POINTER(C.c_int)]),
+    "stokes_get_geometry_stored": (C.c_int, [P, C.c_int, C.c_int, C.POINTER(C.c_int)]),
     "stokes_launch_count": (C.c_longlong, [P]),
     "stokes_krylov_mode": (C.c_int, [P]),
     "stokes_set_wait_cycles": (C.c_int, [P, C.c_uint]),

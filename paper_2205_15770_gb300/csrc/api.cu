@@ -177,7 +177,8 @@ struct LevelRT {
   int fshape = 4;  // column-kernel shape of the fused smoother's launches (1, 3 or 4)
   XferTabs<T> xf{};  // 1D transfer matrices between this level and the next coarser one
   bool fuse = true;  // fused smoothing on this level (set by the setup's timing, when eligible)
-  const T *geo = nullptr;  // FP64 3D trilinear: precomputed per-point geometry of the column kernel
+  const T *geo = nullptr;  // 3D trilinear: precomputed per-point geometry the column kernel reads
+  const T *geo_stored = nullptr;  // FP32: the stored geometry, used (geo) where the setup's timing keeps it
   const T *rho = nullptr;  // per-cell density of the gamma rho mass term (null: rho = 1)
   const T *Ce = nullptr;   // packed element matrices of the stabilisation block C (null: on the fly)
   T *DAinv = nullptr, *DSinv = nullptr;
@@ -1306,23 +1307,34 @@ static int time_graph(stokes_ctx *C, cudaGraphExec_t ex, cudaEvent_t e0, cudaEve
 // Candidates are interleaved over several rounds and each keeps its best round, so clock ramps
 // and one-off effects do not bias the choice; the default shape (4 warps) is kept unless another
 // is faster by more than 3 %.  The fastest column shape is also kept apart (fshape): the fused
-// smoother's launches run in the column kernel.
+// smoother's launches run in the column kernel.  Where an FP32 level has its per-point geometry
+// stored (geo_stored), the column shapes are timed with the stored geometry as well, and the level
+// reads it (geo) if the column shape kept for it is fastest that way.
 template <typename T>
 static int autotune_level(stokes_ctx *C, LevelRT<T> &R, const Tab1D<T> *tab) {
   if (R.d.dim != 3) return STOKES_OK;
   const bool cc = cc_level_supported(R.d.dim, R.d.k, R.d.cartesian, sizeof(T)) && !C->sym && !R.rho &&
                   (R.d.cartesian || sizeof(T) == 4 || R.geo);
-  const int NC = cc ? 5 : 4;
-  const int cands[5] = {4, 1, 3, -1, 5};
+  const bool sg = R.geo_stored && !R.geo;
+  // candidates: column shapes 4, 1, 3 (on-the-fly geometry), point kernel, cell-component kernel,
+  // then the column shapes reading the stored geometry
+  constexpr int NMAX = 8;
+  const int cands[NMAX] = {4, 1, 3, -1, 5, 4, 1, 3};
+  const bool cgeo[NMAX] = {false, false, false, false, false, true, true, true};
+  bool use[NMAX] = {true, true, true, true, cc, sg, sg, sg};
   const int reps = sizeof(T) == 8 ? 3 : 20, rounds = 3;
   cudaEvent_t e0, e1;
   SMF_CUDA_OK(cudaEventCreate(&e0));
   SMF_CUDA_OK(cudaEventCreate(&e1));
-  cudaGraphExec_t ex[5] = {};
-  float best[5] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
+  cudaGraphExec_t ex[NMAX] = {};
+  float best[NMAX];
+  for (float &b : best) b = 1e30f;
   int st = STOKES_OK;
-  for (int ci = 0; ci < NC && st == STOKES_OK; ++ci) {
+  const T *geo0 = R.geo;
+  for (int ci = 0; ci < NMAX && st == STOKES_OK; ++ci) {
+    if (!use[ci]) continue;
     R.shape = cands[ci];
+    R.geo = cgeo[ci] ? R.geo_stored : geo0;
     st = capture_graph(
         C,
         [&] {
@@ -1332,8 +1344,10 @@ static int autotune_level(stokes_ctx *C, LevelRT<T> &R, const Tab1D<T> *tab) {
         },
         &ex[ci]);
   }
+  R.geo = geo0;
   for (int round = -1; round < rounds && st == STOKES_OK; ++round)  // round -1: warm-up
-    for (int ci = 0; ci < NC && st == STOKES_OK; ++ci) {
+    for (int ci = 0; ci < NMAX && st == STOKES_OK; ++ci) {
+      if (!use[ci]) continue;
       float ms = 0.f;
       st = time_graph(C, ex[ci], e0, e1, &ms);
       if (round >= 0) best[ci] = std::min(best[ci], ms);
@@ -1345,13 +1359,15 @@ static int autotune_level(stokes_ctx *C, LevelRT<T> &R, const Tab1D<T> *tab) {
   cudaEventDestroy(e1);
   if (st != STOKES_OK) return st;
   int choice = 0;
-  for (int ci = 1; ci < NC; ++ci)
-    if (best[ci] < 0.97f * best[choice]) choice = ci;
+  for (int ci = 1; ci < NMAX; ++ci)
+    if (use[ci] && best[ci] < 0.97f * best[choice]) choice = ci;
   R.shape = cands[choice];
-  int fc = 0;  // column shapes only: 4, 1, 3
-  for (int ci = 1; ci < 3; ++ci)
-    if (best[ci] < 0.97f * best[fc]) fc = ci;
+  int fc = 0;  // column shapes only: 4, 1, 3, each with the stored geometry where timed
+  for (int ci = 1; ci < NMAX; ++ci)
+    if (use[ci] && (cands[ci] == 1 || cands[ci] == 3 || cands[ci] == 4) && best[ci] < 0.97f * best[fc]) fc = ci;
+  if (cands[choice] == 1 || cands[choice] == 3 || cands[choice] == 4) fc = choice;
   R.fshape = cands[fc];
+  R.geo = cgeo[fc] ? R.geo_stored : geo0;
   SMF_CUDA_OK(cudaMemsetAsync(R.r, 0, (R.d.n_u + R.d.n_p) * sizeof(T), C->s));
   return STOKES_OK;
 }
@@ -1398,15 +1414,20 @@ static int autotune_fusion(stokes_ctx *C, int l) {
   return zero_level_work(C, L);
 }
 
-// STOKES_TUNING="s32=a,b,..;s64=..;f32=..;f64=.." replaces the setup's timings: launch shapes
-// (1, 3, 4, -1 or 5) and smoother forms (1 fused, 0 unfused) per level, coarsest first, for FP32 and
-// FP64.  Timings taken under a profiler differ from plain runs; a profile of the configuration
-// that a plain run chose passes that run's choices here (stokes_get_launch_shape and
-// stokes_get_smoother_fusion read them).
-static int parse_tuning(const char *spec, int nl, std::vector<int> tune[4]) {
-  const char *keys[4] = {"s32=", "s64=", "f32=", "f64="};
-  for (int t = 0; t < 4; ++t) {
+// STOKES_TUNING="s32=a,b,..;s64=..;f32=..;f64=..[;g32=..]" replaces the setup's timings: launch
+// shapes (1, 3, 4, -1 or 5) and smoother forms (1 fused, 0 unfused) per level, coarsest first, for
+// FP32 and FP64, and optionally whether the FP32 column kernels read the stored per-point geometry
+// (1) or evaluate it (0, the default).  Timings taken under a profiler differ from plain runs; a
+// profile of the configuration that a plain run chose passes that run's choices here
+// (stokes_get_launch_shape, stokes_get_smoother_fusion and stokes_get_geometry_stored read them).
+static int parse_tuning(const char *spec, int nl, std::vector<int> tune[5]) {
+  const char *keys[5] = {"s32=", "s64=", "f32=", "f64=", "g32="};
+  for (int t = 0; t < 5; ++t) {
     const char *p = std::strstr(spec, keys[t]);
+    if (!p && t == 4) {
+      tune[t].assign(nl, 0);
+      continue;
+    }
     if (!p) {
       set_error(std::string("STOKES_TUNING lacks ") + keys[t]);
       return STOKES_EINVAL;
@@ -1679,6 +1700,17 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
         launch_col_geometry<double>(d, geo_l, C->s);
         SMF_CUDA_OK(cudaGetLastError());
       }
+      // FP32 levels of at most 32^3 cells (56.6 MB for k = 2): stored as a candidate that the
+      // setup's timing keeps or drops per level.  On the small levels a launch is a dependency
+      // chain (vertex loads, Jacobian, adjugate and its division, then the contractions); stored
+      // factors are loaded together with the DoF values instead.
+      if (g64 && cells <= 32768) {
+        float *gf = nullptr;
+        if ((st = dalloc(C, &gf, cells * per))) return st;
+        launch_col_geometry<float>(f, gf, C->s);
+        SMF_CUDA_OK(cudaGetLastError());
+        C->L32[l].geo_stored = gf;
+      }
     }
     C->L64[l].d = d;
     C->L32[l].d = f;
@@ -1749,7 +1781,7 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
 
   // launch-shape autotuning (STOKES_NO_AUTOTUNE=1 keeps the default shape; STOKES_TUNING fixes
   // shapes and smoother forms instead, see parse_tuning)
-  std::vector<int> tune[4];
+  std::vector<int> tune[5];
   const bool pinned = getenv("STOKES_TUNING") != nullptr && !C->det;
   if (pinned && (st = parse_tuning(getenv("STOKES_TUNING"), nl, tune))) return st;
   if (pinned) {
@@ -1757,6 +1789,12 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
       if (dim == 3) {
         C->L32[l].shape = tune[0][l];
         C->L64[l].shape = tune[1][l];
+        if (tune[4][l] && !C->L32[l].geo_stored) {
+          set_error("STOKES_TUNING: g32 asks for stored FP32 geometry on level " + std::to_string(l) +
+                    ", which has none (3D trilinear levels of at most 32^3 cells)");
+          return STOKES_EINVAL;
+        }
+        C->L32[l].geo = tune[4][l] ? C->L32[l].geo_stored : nullptr;
       }
     }
   }
@@ -3537,12 +3575,12 @@ void stokes_destroy_batch(stokes_batch *Bt) {
   delete Bt;
 }
 
-int stokes_get_geometry_stored(const stokes_ctx *C, int level, int *stored) {
-  if (!C || level < 0 || level >= C->nl || !stored) {
+int stokes_get_geometry_stored(const stokes_ctx *C, int level, int precision, int *stored) {
+  if (!C || level < 0 || level >= C->nl || !stored || (precision != 32 && precision != 64)) {
     set_error("invalid stokes_get_geometry_stored arguments");
     return STOKES_EINVAL;
   }
-  *stored = C->L64[level].geo ? 1 : 0;
+  *stored = (precision == 64 ? C->L64[level].geo != nullptr : C->L32[level].geo != nullptr) ? 1 : 0;
   return STOKES_OK;
 }
 

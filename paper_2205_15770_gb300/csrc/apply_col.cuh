@@ -283,10 +283,12 @@ __global__ void __launch_bounds__(32 * WARPS)
   // mu and gamma rho enter the per-point factors (G, Wd) where they are formed
   const T mu = L.mu_cell ? (valid ? L.mu_cell[cell] : T(0)) : L.mu;
   const T grho = L.gamma_rho;
-  // geo (FP64 trilinear levels): precomputed at setup, the geometry being a quarter of the FP64
-  // flops; otherwise evaluated on the fly.  (A separate kernel argument: a larger level
-  // descriptor changes the register allocation of the FP32 kernels.)
-  if (sizeof(T) == 8 && !CART && geo) {
+  // geo (trilinear levels): precomputed at setup where the setup stores it (FP64: the geometry is
+  // a quarter of the flops of an application; FP32 small levels: it takes the vertex loads and the
+  // Jacobian's arithmetic off each launch's dependency chain); otherwise evaluated on the fly.  (A
+  // separate kernel argument: a larger level descriptor changes the register allocation of the
+  // FP32 kernels.)
+  if (!CART && geo) {
     // precomputed by k_col_geometry (col_geometry, same arithmetic): [cell][16][qz][iy][ix]
     const T *gp = geo + (valid ? cell : 0) * (long long)(16 * NQ * NV * NV) + iy * NV + ix;
     constexpr int ST = NQ * NV * NV;  // stride between the 16 fields
