@@ -1807,6 +1807,16 @@ static int do_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
       }
     }
   }
+  // stored FP32 geometry that the timing (or the pinned tuning) did not keep is released
+  for (int l = 0; l < nl; ++l) {
+    LevelRT<float> &R = C->L32[l];
+    if (R.geo_stored && !R.geo) {
+      void *g = const_cast<float *>(R.geo_stored);
+      C->allocs.erase(std::remove(C->allocs.begin(), C->allocs.end(), g), C->allocs.end());
+      SMF_CUDA_OK(cudaFree(g));
+      R.geo_stored = nullptr;
+    }
+  }
 
   // Krylov / Lanczos work space
   const LevelDesc<double> &top = C->L64[nl - 1].d;
