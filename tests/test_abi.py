@@ -91,3 +91,24 @@ def test_sampled_oracle_rows_match_assembled_operator():
     x = W.random_vector(lev.size, 1)
     rows = np.random.default_rng(0).choice(lev.size, 60, replace=False)
     np.testing.assert_allclose(apply_rows(lev, x, rows, 0.7, 5.0), (ops["K"] @ x)[rows], rtol=1e-12, atol=1e-12)
+
+
+def _declared_arity():
+    """Parameter count of every prototype in the header (comments stripped)."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for name in _declared_functions():
+        m = re.search(r"\b" + name + r"\s*\(([^;{]*?)\)\s*;", text, flags=re.S)
+        assert m, name
+        params = m.group(1).strip()
+        assert "(" not in params, name  # no function-pointer parameters in this ABI
+        out[name] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_signatures_match_the_header():
+    """Every ctypes declaration of the binding takes as many arguments as the header's prototype
+    (a changed entry point must change both)."""
+    from paper_2205_15770_gb300 import _lib
+    for name, n in _declared_arity().items():
+        assert len(_lib.SIGNATURES[name][1]) == n, (name, n, len(_lib.SIGNATURES[name][1]))
