@@ -337,7 +337,7 @@ int stokes_get_launch_shape(const stokes_ctx *ctx, int level, int precision, int
  * STOKES_GEO=none, or the level is larger than the budget (1/16 of the device memory, and at most
  * half of the memory free at setup).  FP32: stored for levels of at most 32^3 cells and read where
  * the setup's timing of the column kernel keeps it (STOKES_TUNING's g32 list otherwise; 0 without
- * autotuning), released at setup where it is not kept.  The cell-component kernel (shape 5) evaluates the FP32 geometry itself either way.
+ * autotuning), released at setup where it is not kept; STOKES_GEO=none stores neither precision.  The cell-component kernel (shape 5) evaluates the FP32 geometry itself either way.
  * HOST output. */
 int stokes_get_geometry_stored(const stokes_ctx *ctx, int level, int precision, int *stored);
 
