@@ -33,13 +33,6 @@ __global__ void k_sub(const T *__restrict__ a, const T *__restrict__ b, T *__res
   SMF_GRID_LOOP(i, n) out[i] = a[i] - b[i];
 }
 
-// out = a + s * b
-template <typename T>
-__global__ void k_axpy_out(const T *__restrict__ a, T s, const T *__restrict__ b, T *__restrict__ out, long long n) {
-  pdl_enter();
-  SMF_GRID_LOOP(i, n) out[i] = a[i] + s * b[i];
-}
-
 // x += s * b
 template <typename T>
 __global__ void k_axpy(T *__restrict__ x, T s, const T *__restrict__ b, long long n) {
@@ -467,20 +460,9 @@ __global__ void k_slot_convert(const double *__restrict__ V, long long ldv, cons
     if (zero) zero[i] = Tout(0);
   }
 }
-// z = (double) a and Z_{ctl[0]} = z: the preconditioned vector for the operator and the update
-template <typename Tin>
-__global__ void k_convert_to_slot(const Tin *__restrict__ a, double *__restrict__ z, double *__restrict__ Z,
-                                  long long ldz, const int *__restrict__ ctl, long long n) {
-  pdl_enter();
-  double *zj = Z + (long long)ctl[0] * ldz;
-  SMF_GRID_LOOP(i, n) {
-    const double v = (double)a[i];
-    z[i] = v;
-    zj[i] = v;
-  }
-}
-// The same, and y = the identity rows of z (z on constrained velocity DoFs, 0 elsewhere): the
-// start of y = K z (k_init_identity) in the same pass.
+// z = (double) a and Z_{ctl[0]} = z (the preconditioned vector for the operator and the update),
+// and y = the identity rows of z (z on constrained velocity DoFs, 0 elsewhere): the start of
+// y = K z (k_init_identity) in the same pass.
 template <typename Tin>
 __global__ void k_convert_to_slot_id(const LevelDesc<double> L, const Tin *__restrict__ a, double *__restrict__ z,
                                      double *__restrict__ Z, long long ldz, const int *__restrict__ ctl,
