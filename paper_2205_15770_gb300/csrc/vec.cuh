@@ -41,13 +41,13 @@ __global__ void k_axpy(T *__restrict__ x, T s, const T *__restrict__ b, long lon
 }
 
 template <typename T>
-__global__ void k_scale(const T *__restrict__ a, T s, T *__restrict__ out, long long n) {
+__global__ void k_scale(const T *a, T s, T *out, long long n) {  // a and out may be the same vector
   pdl_enter();
   SMF_GRID_LOOP(i, n) out[i] = s * a[i];
 }
 
 template <typename T>
-__global__ void k_mul(const T *__restrict__ a, const T *__restrict__ b, T *__restrict__ out, long long n) {
+__global__ void k_mul(const T *a, const T *b, T *out, long long n) {  // out may be a or b (in place)
   pdl_enter();
   SMF_GRID_LOOP(i, n) out[i] = a[i] * b[i];
 }
@@ -191,8 +191,10 @@ __device__ __forceinline__ void cheb_init_packj(long long j, const T *a, const T
     }
   }
 }
+// a / b may be the vectors za / zb that the same thread zeroes after reading them (the smoother's
+// accumulators are consumed and cleared in one pass), so neither is declared __restrict__.
 template <typename T, int V>
-__global__ void k_cheb_init(const T *__restrict__ a, const T *__restrict__ b, T sr, const T *__restrict__ Dinv,
+__global__ void k_cheb_init(const T *a, const T *b, T sr, const T *__restrict__ Dinv,
                             T c0, T *__restrict__ r_out, T *__restrict__ d, T *__restrict__ x, const T *__restrict__ base,
                             T fscale, T *__restrict__ final_out, T *__restrict__ acc_out, T *za, T *zb, long long n) {
   pdl_enter();
