@@ -194,8 +194,8 @@ int stokes_solve(stokes_ctx *ctx, const double *b, double *x, double rtol, int m
  * of one restart cycle are one CUDA-graph launch with a conditional while node, and the host
  * synchronises once per restart cycle), 0 = host-driven (one synchronisation per iteration;
  * STOKES_HOST_KRYLOV=1, STOKES_NO_GRAPHS=1, or conditional graph nodes refused by the runtime),
- * -1 = not decided yet (no solve so far).  No counterpart in the paper (the outer Krylov loop is
- * a layer on top of its Algorithm 1). */
+ * -1 = not decided yet (no solve so far, or a null context).  No counterpart in the paper (the
+ * outer Krylov loop is a layer on top of its Algorithm 1). */
 int stokes_krylov_mode(const stokes_ctx *ctx);
 
 /* Deterministic mode (opts.deterministic): replace the grid-barrier wait budget of opts.wait_cycles
@@ -209,10 +209,11 @@ int stokes_set_wait_cycles(stokes_ctx *ctx, unsigned int cycles);
  * member 3D, k = 2, FP32 cycle, no stabilisation / symmetric gradient / rho term; otherwise 1):
  * each cycle is recorded once as its operation list (cell-kernel applications, Chebyshev-Jacobi
  * vector steps, restriction with the residual, prolongation, coarse solve), split into work items
- * (bricks of 40 cells, ranges of DoFs), and the kernel's CTAs take items from one queue (a list
+ * (bricks of 160 cells, ranges of DoFs), and the kernel's CTAs take items from one queue (a list
  * schedule: each operation at the time it could start were its member alone), each waiting until
  * the member's previous operation has finished; 0 =
- * host-driven lockstep; -1 = no solve yet.  No counterpart in the paper (a layer on Algorithm 1). */
+ * host-driven lockstep; -1 = no solve yet (or a null batch).  No counterpart in the paper (a layer
+ * on Algorithm 1). */
 int stokes_batch_krylov_mode(const stokes_batch *batch);
 
 /* Work-queue mode (2): the budget of every dependency wait in clock64() cycles (0 = 2^31, about a
@@ -356,6 +357,9 @@ int stokes_set_launch_shape(stokes_ctx *ctx, int level, int precision, int shape
  * library for reporting; not thread-safe). */
 long long stokes_launch_count(const stokes_ctx *ctx);
 
+/* Text of the last error of a context (of the calling thread's last call with no usable context,
+ * such as a failed setup or a null handle, when ctx is null; stokes_batch_last_error likewise for a
+ * batch).  The pointer stays valid until the next call on the same context or thread.  HOST. */
 const char *stokes_last_error(const stokes_ctx *ctx);
 const char *stokes_global_last_error(void);
 void stokes_destroy(stokes_ctx *ctx);

@@ -112,3 +112,32 @@ def test_binding_signatures_match_the_header():
     from paper_2205_15770_gb300 import _lib
     for name, n in _declared_arity().items():
         assert len(_lib.SIGNATURES[name][1]) == n, (name, n, len(_lib.SIGNATURES[name][1]))
+
+
+def test_every_entry_point_rejects_a_null_context(lib):
+    """Each entry point taking a context or batch handle returns STOKES_EINVAL for a null handle
+    (null pointers and zero sizes elsewhere), before any device work, and keeps the reason as the
+    thread's last error; the mode queries answer -1, the launch counter 0, the error-text queries of
+    a null handle the thread's last error, and the destroy calls accept null."""
+    from paper_2205_15770_gb300 import _lib
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    checked = 0
+    for name, n in _declared_arity().items():
+        m = re.search(r"\b" + name + r"\s*\(([^;{]*?)\)\s*;", text, flags=re.S)
+        first = m.group(1).split(",")[0]
+        restype, argtypes = _lib.SIGNATURES[name]
+        if restype is not C.c_int or not ("stokes_ctx" in first or "stokes_batch" in first):
+            continue
+        args = [0 if t in (C.c_int, C.c_uint, C.c_longlong, C.c_size_t) else 0.0 if t in (C.c_double, C.c_float)
+                else None for t in argtypes]
+        expect = -1 if name in ("stokes_krylov_mode", "stokes_batch_krylov_mode") else 1
+        assert getattr(lib, name)(*args) == expect, name
+        if expect == 1:
+            assert lib.stokes_global_last_error() != b"", name
+        checked += 1
+    assert checked >= 30
+    assert lib.stokes_last_error(None) == lib.stokes_global_last_error()
+    assert lib.stokes_batch_last_error(None) == lib.stokes_global_last_error()
+    assert lib.stokes_launch_count(None) == 0
+    lib.stokes_destroy(None)
+    lib.stokes_destroy_batch(None)
