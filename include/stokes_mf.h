@@ -109,7 +109,9 @@ typedef struct {
 
 /* Fill *o with kA = kS = 3, m = 2, V-cycle, local Schur diagonal, FP32 cycle,
  * restart 30, 40 Lanczos steps, safety 1.1, seed 0x5EED, no stabilisation, the Laplacian form,
- * atomic (not deterministic) scatter. */
+ * atomic (not deterministic) scatter: the smoother of Sec. 3.3.1 at one of the settings the paper
+ * sweeps (Sec. 4.3-4.5; its runs use the W-cycle of Sec. 4.1, opts.cycle = 1).  A null o is
+ * ignored. */
 void stokes_default_opts(stokes_opts *o);
 
 /* Build the level hierarchy, geometry, 1D tables, Jacobi/Schur diagonals, the
@@ -123,7 +125,10 @@ int stokes_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
                  const double *mu_cell, const stokes_opts *opts, void *stream,
                  stokes_ctx **out);
 
-/* Sizes of level `level` (0 = coarsest, n_levels-1 = finest). */
+/* Sizes of level `level` (0 = coarsest, n_levels-1 = finest): n_u = dim x the velocity nodes of
+ * the Q_k lattice, n_p = the Q_{k-1} pressure nodes (Sec. 2; Dirichlet DoFs included, as in the
+ * paper's DoF counts).  HOST outputs (nullable); STOKES_EINVAL for a null context or a level out
+ * of range. */
 int stokes_sizes(const stokes_ctx *ctx, int level, long long *n_u, long long *n_p);
 
 /* y = K x on `level` (Sec. 3.1: Kx = sum_tau P_tau K_tau P_tau^T x by sum
@@ -137,12 +142,15 @@ int stokes_vmult(stokes_ctx *ctx, int level, int precision, const void *x, void 
  * row written), Z = identity on free velocity DoFs, 0 on constrained ones.  Bit 64 adds -C p
  * to yp (the stabilisation block; with bit 4, yp = B u - C p; not with 8 / 16).  Outputs are
  * overwritten; unused pointers may be NULL.  For blocks 1-7, rows of constrained velocity DoFs
- * of yu are zero (no identity term) and constrained entries of u are ignored. */
+ * of yu are zero (no identity term) and constrained entries of u are ignored.  The blocks are the
+ * forms a(u, v), b(v, q) and c(p, q) of Sec. 2 applied as in Sec. 3.1.  Device vectors in the
+ * precision given; STOKES_EINVAL for an unknown bit set. */
 int stokes_apply_blocks(stokes_ctx *ctx, int level, int precision, int blocks, const void *u,
                         const void *p, void *yu, void *yp, void *stream);
 
 /* b = [Z M_v f ; 0]: right-hand side of a forcing given by its velocity nodal values
- * f (n_u entries).  Constrained rows are zero. */
+ * f (n_u entries).  Constrained rows are zero.  The load (f, v) of Sec. 2 for an f interpolated
+ * at the velocity nodes; f and b are device vectors in the precision given (b: n_u + n_p). */
 int stokes_mass_rhs(stokes_ctx *ctx, int level, int precision, const void *f, void *b, void *stream);
 
 /* `steps` steps of the inexact symmetric Uzawa smoother in compact form
@@ -185,7 +193,10 @@ int mg_vcycle(stokes_ctx *ctx, int precision, const void *b, void *x, void *stre
  * iteration (FP32 or FP64 per opts.vcycle_fp32), from the initial guess in x, to
  * ||b - K x||_2 <= rtol ||b||_2.  b, x: device double vectors.  Synchronises the
  * stream.  Under full Dirichlet data the returned pressure has zero mean.
- * iters, final_rel_res: HOST outputs (nullable).  STOKES_ENOTCONV after maxit. */
+ * iters, final_rel_res: HOST outputs (nullable).  STOKES_ENOTCONV after maxit, STOKES_EBREAKDOWN
+ * on a non-finite residual, STOKES_EINVAL for rtol <= 0 or maxit < 0.  The outer loop is a layer
+ * on the paper's method (it iterates the cycle as a stationary method, Sec. 4.1; Algorithm 1 is
+ * the preconditioner here). */
 int stokes_solve(stokes_ctx *ctx, const double *b, double *x, double rtol, int maxit, int *iters,
                  double *final_rel_res, void *stream);
 
@@ -229,7 +240,10 @@ int stokes_batch_set_wait_cycles(stokes_batch *batch, unsigned int cycles);
  * out.  Synchronises the stream.  No counterpart in the paper (the batch layer). */
 int stokes_batch_vcycle(stokes_batch *batch, const float *const *b, float *const *x, void *stream);
 
-/* stokes_solve with HOST vectors: copies b in, solves from x = 0, copies x out. */
+/* stokes_solve with HOST vectors: copies b in, solves from x = 0, copies x out (pinned or
+ * pageable host memory of n_u + n_p doubles each; the copies are ordered after the work already
+ * on `stream` and the call returns with x_host written).  Same arguments checks and status codes
+ * as stokes_solve.  No counterpart in the paper (an end-to-end entry point). */
 int stokes_solve_host(stokes_ctx *ctx, const double *b_host, double *x_host, double rtol, int maxit,
                       int *iters, double *final_rel_res, void *stream);
 
@@ -250,7 +264,8 @@ int stokes_cell_grad(stokes_ctx *ctx, const double *u, const double *lam, double
 /* Physical coordinates of the velocity nodes of `level` (the Gauss-Lobatto nodes of every cell
  * mapped by its bi/trilinear map), for building nodal data (forcing, Dirichlet values): xyz is a
  * device array of nv x dim doubles, interleaved, in the lattice order of one velocity component
- * (nv = n_u / dim). */
+ * (nv = n_u / dim).  The node placement of reading R8 (Sec. 2 leaves it to Fig. 1): Gauss-Lobatto
+ * nodes per cell. */
 int stokes_velocity_nodes(stokes_ctx *ctx, int level, double *xyz, void *stream);
 
 /* Lifting of inhomogeneous Dirichlet data on the finest level: b -= Z K_full u_D, where uD
@@ -274,14 +289,17 @@ int stokes_get_level_params(const stokes_ctx *ctx, int level, double *beta_A, do
                             double *sigma, double *tau);
 
 /* Copy the FP64 Jacobi diagonal D_A (n_u) and the Schur diagonal approximation
- * D_S (n_p) of a level into device buffers (either may be NULL). */
+ * D_S (n_p) of a level into device buffers (either may be NULL): the diagonals of Sec. 3.3.1 that
+ * Algorithm 2 computes (D_S by opts.schur_diag: loc, p, d or exact).  STOKES_EINVAL for level 0
+ * (no smoother there) or a level out of range. */
 int stokes_get_diagonals(stokes_ctx *ctx, int level, double *DA, double *DS, void *stream);
 
 /* Measurement helper: launch the cell kernel of `blocks` (as in stokes_apply_blocks) on
  * `level` reps times back to back on the library's internal stream, between two CUDA
  * events recorded on that stream, using internal buffers as input and output (no
  * allocation, no memset between launches).  *avg_ms (HOST) = elapsed / reps.
- * Synchronises the stream. */
+ * Synchronises the stream.  No counterpart in the paper (measurement); STOKES_EINVAL for reps < 1
+ * or an unknown bit set. */
 int stokes_time_apply(stokes_ctx *ctx, int level, int precision, int blocks, int reps, double *avg_ms,
                       void *stream);
 
@@ -300,7 +318,9 @@ int stokes_setup_batch(int n_meshes, const stokes_mesh *meshes, const int *k, co
                        const double *gamma_rho, const stokes_opts *opts, void *stream,
                        stokes_batch **out);
 
-/* The context of batch member `mesh` (owned by the batch; for sizes, right-hand sides, vmult). */
+/* The context of batch member `mesh` (owned by the batch; for sizes, right-hand sides, vmult):
+ * *ctx is valid until stokes_destroy_batch and must not be destroyed by the caller.  STOKES_EINVAL
+ * for an index out of range.  No counterpart in the paper (the batch layer). */
 int stokes_batch_context(stokes_batch *batch, int mesh, stokes_ctx **ctx);
 
 /* Solve every member: b[i], x[i] are device double vectors of member i (x[i] = initial guess
@@ -312,10 +332,12 @@ int stokes_batch_context(stokes_batch *batch, int mesh, stokes_ctx **ctx);
  * lockstep, the FP32 cycles of one iteration of all members as one graph launch.  iters,
  * final_rel_res: HOST arrays of n_meshes entries (nullable).  Synchronises the stream.  Returns
  * the first non-OK member status (STOKES_ENOTCONV / STOKES_EBREAKDOWN), or STOKES_ETIMEOUT when a
- * work-queue wait ran out. */
+ * work-queue wait ran out.  No counterpart in the paper (the batch layer). */
 int stokes_solve_batch(stokes_batch *batch, const double *const *b, double *const *x, double rtol,
                        int maxit, int *iters, double *final_rel_res, void *stream);
 
+/* Text of the batch's last error (see stokes_last_error), and the release of the batch with every
+ * member context and its device memory (a null batch is ignored).  No counterpart in the paper. */
 const char *stokes_batch_last_error(const stokes_batch *batch);
 void stokes_destroy_batch(stokes_batch *batch);
 
@@ -329,7 +351,7 @@ void stokes_destroy_batch(stokes_batch *batch);
  * STOKES_TUNING="s32=..;s64=..;f32=..;f64=..[;g32=..]" (comma lists, one value per level, coarsest first)
  * replaces the setup's timings of shapes and smoother forms, e.g. to profile the configuration a
  * plain run chose (a profiler changes the timings); malformed values make setup fail with
- * STOKES_EINVAL.  HOST output. */
+ * STOKES_EINVAL.  HOST output.  No counterpart in the paper (a launch choice of this library). */
 int stokes_get_launch_shape(const stokes_ctx *ctx, int level, int precision, int *shape);
 
 /* 1 if the column kernels of `level` in `precision` (32 or 64) read the per-point geometry (G,
@@ -338,8 +360,10 @@ int stokes_get_launch_shape(const stokes_ctx *ctx, int level, int precision, int
  * STOKES_GEO=none, or the level is larger than the budget (1/16 of the device memory, and at most
  * half of the memory free at setup).  FP32: stored for levels of at most 32^3 cells and read where
  * the setup's timing of the column kernel keeps it (STOKES_TUNING's g32 list otherwise; 0 without
- * autotuning), released at setup where it is not kept; STOKES_GEO=none stores neither precision.  The cell-component kernel (shape 5) evaluates the FP32 geometry itself either way.
- * HOST output. */
+ * autotuning), released at setup where it is not kept; STOKES_GEO=none stores neither precision.
+ * The cell-component kernel (shape 5) evaluates the FP32 geometry itself either way.  The geometry
+ * is that of the cells' bi/trilinear maps T_tau (Sec. 2) at the Gauss points.  HOST output;
+ * STOKES_EINVAL for a level out of range or a precision other than 32 / 64. */
 int stokes_get_geometry_stored(const stokes_ctx *ctx, int level, int precision, int *stored);
 
 /* 1 if smoothing on `level` / `precision` runs in the fused form (k_A = 1, 3D, column kernel: the
@@ -350,16 +374,21 @@ int stokes_get_geometry_stored(const stokes_ctx *ctx, int level, int precision, 
 int stokes_get_smoother_fusion(stokes_ctx *ctx, int level, int precision, int *fused);
 
 /* Override the launch shape of `level` / `precision` (values as above; 0 is not accepted).
- * Captured cycle graphs of the context are dropped and recaptured on next use. */
+ * Captured cycle graphs of the context are dropped and recaptured on next use.  No counterpart in
+ * the paper (a launch choice); STOKES_EINVAL for a shape outside {1, 3, 4, -1, 5} (a shape the
+ * level's kernels do not serve falls back to the 4-warp column kernel where it applies). */
 int stokes_set_launch_shape(stokes_ctx *ctx, int level, int precision, int shape);
 
 /* Number of kernel launches this context issued since setup (a counter kept by the
- * library for reporting; not thread-safe). */
+ * library for reporting; not thread-safe; graph-replayed kernels included; 0 for a null context).
+ * No counterpart in the paper. */
 long long stokes_launch_count(const stokes_ctx *ctx);
 
 /* Text of the last error of a context (of the calling thread's last call with no usable context,
  * such as a failed setup or a null handle, when ctx is null; stokes_batch_last_error likewise for a
- * batch).  The pointer stays valid until the next call on the same context or thread.  HOST. */
+ * batch).  The pointer stays valid until the next call on the same context or thread.  HOST.
+ * stokes_destroy releases a context and all its device memory (a null context is ignored).  No
+ * counterpart in the paper. */
 const char *stokes_last_error(const stokes_ctx *ctx);
 const char *stokes_global_last_error(void);
 void stokes_destroy(stokes_ctx *ctx);

@@ -3222,7 +3222,7 @@ int stokes_solve(stokes_ctx *C, const double *b, double *x, double rtol, int max
 
 int stokes_solve_host(stokes_ctx *C, const double *b_host, double *x_host, double rtol, int maxit, int *iters,
                       double *final_rel_res, void *stream) {
-  if (!C || !b_host || !x_host) {
+  if (!C || !b_host || !x_host || !(rtol > 0) || maxit < 0) {
     set_error("invalid stokes_solve_host arguments");
     if (C) C->err = g_last_error;
     return STOKES_EINVAL;
@@ -3230,6 +3230,7 @@ int stokes_solve_host(stokes_ctx *C, const double *b_host, double *x_host, doubl
   const int top = C->nl - 1;
   const long long N = C->L64[top].d.n_u + C->L64[top].d.n_p;
   StreamGuard sg(C, stream);
+  det_begin(C, C->s);
   double *db = C->lz0, *dx = C->lz1;
   cudaMemcpyAsync(db, b_host, N * sizeof(double), cudaMemcpyHostToDevice, C->s);
   cudaMemsetAsync(dx, 0, N * sizeof(double), C->s);

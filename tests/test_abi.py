@@ -141,3 +141,14 @@ def test_every_entry_point_rejects_a_null_context(lib):
     assert lib.stokes_launch_count(None) == 0
     lib.stokes_destroy(None)
     lib.stokes_destroy_batch(None)
+
+
+def test_every_declaration_cites_its_passage():
+    """The comment above each prototype names the paper passage it implements (a section, an
+    algorithm, a lemma, a reading of the paper) or says that it has no counterpart in the paper."""
+    text = open(HEADER).read()
+    for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M):
+        before = text[:m.start()]
+        end = before.rfind("*/")
+        comment = before[before.rfind("/*", 0, end):end]
+        assert re.search(r"Sec\.|Algorithm|Lemma|reading|counterpart", comment), m.group(1)
