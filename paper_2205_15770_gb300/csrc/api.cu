@@ -3130,6 +3130,7 @@ int stokes_smooth_noalloc(stokes_ctx *C, int level, int precision, int steps, co
     return st;
   }
   StreamGuard sg(C, stream);
+  det_begin(C, C->s);  // deterministic mode: a fresh grid-barrier state, as in stokes_smooth
   // the scratch keeps the previous call's contents: the smoother's accumulation targets must start
   // at zero, so the used part is cleared first
   cudaMemsetAsync(base, 0, need, C->s);
