@@ -152,3 +152,4 @@ def test_every_declaration_cites_its_passage():
         end = before.rfind("*/")
         comment = before[before.rfind("/*", 0, end):end]
         assert re.search(r"Sec\.|Algorithm|Lemma|reading|counterpart", comment), m.group(1)
+

@@ -143,3 +143,23 @@ def test_mms_convergence_rates():
     # ||u-u_h||_L2 = O(h^{k+1}) = O(h^3); ||p-p_h||_L2 = O(h^k) = O(h^2)  (Sec. 2 estimates)
     assert np.all(rates[1:, 0] > 2.9), rates
     assert np.all(rates[:, 1] > 1.9), rates
+
+
+@pytest.mark.parametrize("k", [3, 4])
+def test_sampled_oracle_rows_on_an_anisotropic_channel(k):
+    """Sampled rows of K x (the oracle's full-size parity reference) against the assembled operator
+    on a Cartesian channel box [0,4] x [0,1]^2 of anisotropic cells with the do-nothing face open
+    (x = 4), for the higher degrees: the row-by-row gathering of the touching cells' element
+    matrices must reproduce every kind of row (Dirichlet, outflow face, interior, pressure)."""
+    import workloads as W
+    from oracle.assemble import assemble
+    from oracle.mesh import Level
+    from oracle.sampled import apply_rows
+    n = (4, 2, 2)
+    lev = Level(3, k, n, W.lattice_vertices(3, n, hi=(4.0, 1.0, 1.0)), dirichlet_faces=0x3F & ~0x2)
+    ops = assemble(lev, mu=1e-3, gamma_rho=0.0)
+    x = W.random_vector(lev.size, 3)
+    rows = np.random.default_rng(1).choice(lev.size, 80, replace=False)
+    y = ops["K"] @ x
+    np.testing.assert_allclose(apply_rows(lev, x, rows, 1e-3, 0.0), y[rows], rtol=1e-12,
+                               atol=1e-12 * np.abs(y).max())
