@@ -24,6 +24,21 @@
  *  - Every call returns a status; on error, stokes_last_error(ctx) (or
  *    stokes_global_last_error() when no context exists) holds a message.  No C++
  *    exception crosses this boundary.  A context is not thread-safe.
+ *
+ * Environment variables (read at setup or at the first use; none changes a result beyond rounding
+ * order, except STOKES_TUNING's fused / unfused smoother forms, which are the same arithmetic):
+ *  - STOKES_NO_AUTOTUNE=1: no setup timing; default launch shapes, fused smoothing where eligible,
+ *    per-point geometry evaluated by the FP32 kernels.
+ *  - STOKES_TUNING="s32=..;s64=..;f32=..;f64=..[;g32=..]": the setup's choices pinned (see
+ *    stokes_get_launch_shape).
+ *  - STOKES_NO_FUSE=1: unfused smoothing everywhere.  STOKES_NO_GRAPHS=1: no CUDA-graph capture.
+ *  - STOKES_HOST_KRYLOV=1: the FGMRES iterations driven from the host (stokes_krylov_mode).
+ *  - STOKES_BATCH_QUEUE=1: the batch's FP32 cycles in the persistent work-queue kernel.
+ *  - STOKES_GEO=none: no stored per-point geometry (stokes_get_geometry_stored).
+ *    STOKES_C_MATRIX=none: the stabilisation block C on the fly instead of stored element matrices.
+ *  - STOKES_NO_PDL=1: no programmatic dependent launch; STOKES_PDL=all: PDL inside captured graphs
+ *    too (off there by default).  STOKES_GENERIC_KERNEL=1: every 3D application in the
+ *    point-per-thread kernel (for comparisons).
  */
 #ifndef STOKES_MF_H
 #define STOKES_MF_H
