@@ -25,8 +25,8 @@
  *    stokes_global_last_error() when no context exists) holds a message.  No C++
  *    exception crosses this boundary.  A context is not thread-safe.
  *
- * Environment variables (read at setup or at the first use; none changes a result beyond rounding
- * order, except STOKES_TUNING's fused / unfused smoother forms, which are the same arithmetic):
+ * Environment variables (read at setup or at the first use; they choose among forms of the same
+ * arithmetic, so none changes a result beyond rounding order):
  *  - STOKES_NO_AUTOTUNE=1: no setup timing; default launch shapes, fused smoothing where eligible,
  *    per-point geometry evaluated by the FP32 kernels.
  *  - STOKES_TUNING="s32=..;s64=..;f32=..;f64=..[;g32=..]": the setup's choices pinned (see
