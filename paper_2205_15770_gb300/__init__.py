@@ -34,15 +34,30 @@ def _torch():
     return torch
 
 
-def _ptr(t, dtype):
+def _ptr(t, dtype, n=None, device=None, what="vector"):
+    """Device pointer of a contiguous CUDA tensor of the given dtype; with n / device, also checks
+    its entry count and its device (the C ABI takes bare pointers: a short vector or one on another
+    GPU would be read out of bounds there)."""
     torch = _torch()
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
-        raise TypeError("expected a CUDA torch tensor")
+        raise TypeError(f"{what}: expected a CUDA torch tensor")
     if t.dtype != dtype:
-        raise TypeError(f"expected dtype {dtype}, got {t.dtype}")
+        raise TypeError(f"{what}: expected dtype {dtype}, got {t.dtype}")
     if not t.is_contiguous():
-        raise ValueError("tensor must be contiguous")
+        raise ValueError(f"{what}: tensor must be contiguous")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{what}: expected {n} entries, got {t.numel()}")
+    if device is not None and t.device != device:
+        raise ValueError(f"{what}: tensor on {t.device}, the solver's context on {device}")
     return C.c_void_p(t.data_ptr())
+
+
+def _host_doubles(a, n, what):
+    """Contiguous float64 copy of a host array with exactly n entries (the setup reads n values)."""
+    v = np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1))
+    if v.size != n:
+        raise ValueError(f"{what}: expected {n} values, got {v.size}")
+    return v
 
 
 def fma_peak(precision=32):
@@ -78,13 +93,17 @@ class StokesMG:
         mesh.n_levels = n_levels
         mesh.dirichlet_faces = ALL_FACES[dim] if dirichlet_faces is None else int(dirichlet_faces)
         self._keep = []
+        n_cells, n_vert = 1, 1
+        for a in range(dim):
+            n_cells *= int(nn[a])
+            n_vert *= int(nn[a]) + 1
         if vertices is not None:
-            v = np.ascontiguousarray(np.asarray(vertices, dtype=np.float64).reshape(-1))
+            v = _host_doubles(vertices, n_vert * dim, "vertices")
             self._keep.append(v)
             mesh.vertices = v.ctypes.data_as(C.POINTER(C.c_double))
         mu_ptr = None
         if mu_cell is not None:
-            mc = np.ascontiguousarray(np.asarray(mu_cell, dtype=np.float64).reshape(-1))
+            mc = _host_doubles(mu_cell, n_cells, "mu_cell")
             self._keep.append(mc)
             mu_ptr = mc.ctypes.data_as(C.POINTER(C.c_double))
         opts = L.StokesOpts()
@@ -103,7 +122,7 @@ class StokesMG:
         opts.deterministic = {False: 0, True: 1, 0: 0, 1: 1, 2: 2, "owner": 1, "colour": 2}[deterministic]
         opts.wait_cycles = int(wait_cycles)
         if rho_cell is not None:
-            rc = np.ascontiguousarray(np.asarray(rho_cell, dtype=np.float64).reshape(-1))
+            rc = _host_doubles(rho_cell, n_cells, "rho_cell")
             self._keep.append(rc)
             opts.rho_cell = rc.ctypes.data_as(C.POINTER(C.c_double))
         ctx = C.c_void_p()
@@ -140,9 +159,14 @@ class StokesMG:
         return self.n_levels - 1 if level is None else level
 
     def sizes(self, level=None):
-        nu, npr = C.c_longlong(), C.c_longlong()
-        self._check(self._lib.stokes_sizes(self._ctx, self._level(level), C.byref(nu), C.byref(npr)))
-        return nu.value, npr.value
+        """(n_u, n_p) of a level (fixed for the context's lifetime, so asked once per level)."""
+        lv = self._level(level)
+        cache = self.__dict__.setdefault("_sizes", {})
+        if lv not in cache:
+            nu, npr = C.c_longlong(), C.c_longlong()
+            self._check(self._lib.stokes_sizes(self._ctx, lv, C.byref(nu), C.byref(npr)))
+            cache[lv] = (nu.value, npr.value)
+        return cache[lv]
 
     def size(self, level=None):
         nu, npr = self.sizes(level)
@@ -162,12 +186,18 @@ class StokesMG:
         return torch.empty(self.size(level), dtype=dtype or torch.float64, device=self.device)
 
     # --- operators ------------------------------------------------------------------------------
+    def _v(self, t, dtype, n, what):
+        """_ptr with the entry count and the context's device checked."""
+        return _ptr(t, dtype, n=n, device=self.device, what=what)
+
     def vmult(self, x, y=None, level=None):
         """y = K x (Sec. 3.1 matrix-free operator)."""
         torch = _torch()
         y = torch.empty_like(x) if y is None else y
         pr = self._prec(x)
-        self._check(self._lib.stokes_vmult(self._ctx, self._level(level), pr, _ptr(x, x.dtype), _ptr(y, x.dtype),
+        lv = self._level(level)
+        n = self.size(lv)
+        self._check(self._lib.stokes_vmult(self._ctx, lv, pr, self._v(x, x.dtype, n, "x"), self._v(y, x.dtype, n, "y"),
                                            self._stream()))
         return y
 
@@ -182,8 +212,8 @@ class StokesMG:
         yu = torch.empty(nu, dtype=dt, device=self.device) if blocks & (1 | 2 | 8 | 16) else None
         yp = torch.empty(npr, dtype=dt, device=self.device) if blocks & (4 | 64) else None
         self._check(self._lib.stokes_apply_blocks(
-            self._ctx, lv, self._prec(ref), blocks, _ptr(u, dt) if u is not None else None,
-            _ptr(p, dt) if p is not None else None, _ptr(yu, dt) if yu is not None else None,
+            self._ctx, lv, self._prec(ref), blocks, self._v(u, dt, nu, "u") if u is not None else None,
+            self._v(p, dt, npr, "p") if p is not None else None, _ptr(yu, dt) if yu is not None else None,
             _ptr(yp, dt) if yp is not None else None, self._stream()))
         return yu, yp
 
@@ -192,28 +222,34 @@ class StokesMG:
         torch = _torch()
         lv = self._level(level)
         b = torch.empty(self.size(lv), dtype=f.dtype, device=self.device)
-        self._check(self._lib.stokes_mass_rhs(self._ctx, lv, self._prec(f), _ptr(f, f.dtype), _ptr(b, f.dtype),
-                                              self._stream()))
+        self._check(self._lib.stokes_mass_rhs(self._ctx, lv, self._prec(f), self._v(f, f.dtype, self.sizes(lv)[0], "f"),
+                                              _ptr(b, f.dtype), self._stream()))
         return b
 
     def smooth(self, b, x, steps=1, level=None):
         """x <- S^steps (x, b): inexact symmetric Uzawa smoother (in place)."""
-        self._check(self._lib.stokes_smooth(self._ctx, self._level(level), self._prec(x), steps, _ptr(b, x.dtype),
-                                            _ptr(x, x.dtype), self._stream()))
+        lv = self._level(level)
+        n = self.size(lv)
+        self._check(self._lib.stokes_smooth(self._ctx, lv, self._prec(x), steps, self._v(b, x.dtype, n, "b"),
+                                            self._v(x, x.dtype, n, "x"), self._stream()))
         return x
 
     def smooth_noalloc(self, b, x, steps=1, level=None):
         """Same as smooth(), but the smoother's work vectors live in the library's static 16 MiB device
         array instead of the context's memory: for callers that must not allocate at this point.
         Overlapping calls race on that array; levels that need more scratch raise StokesError."""
-        self._check(self._lib.stokes_smooth_noalloc(self._ctx, self._level(level), self._prec(x), steps,
-                                                    _ptr(b, x.dtype), _ptr(x, x.dtype), self._stream()))
+        lv = self._level(level)
+        n = self.size(lv)
+        self._check(self._lib.stokes_smooth_noalloc(self._ctx, lv, self._prec(x), steps,
+                                                    self._v(b, x.dtype, n, "b"), self._v(x, x.dtype, n, "x"),
+                                                    self._stream()))
         return x
 
     def restrict(self, r_fine, fine_level):
         torch = _torch()
         out = torch.empty(self.size(fine_level - 1), dtype=r_fine.dtype, device=self.device)
-        self._check(self._lib.stokes_transfer(self._ctx, fine_level, self._prec(r_fine), 0, _ptr(r_fine, r_fine.dtype),
+        self._check(self._lib.stokes_transfer(self._ctx, fine_level, self._prec(r_fine), 0,
+                                              self._v(r_fine, r_fine.dtype, self.size(fine_level), "r_fine"),
                                               _ptr(out, r_fine.dtype), self._stream()))
         return out
 
@@ -221,23 +257,24 @@ class StokesMG:
         torch = _torch()
         out = torch.empty(self.size(fine_level), dtype=w_coarse.dtype, device=self.device)
         self._check(self._lib.stokes_transfer(self._ctx, fine_level, self._prec(w_coarse), 1,
-                                              _ptr(w_coarse, w_coarse.dtype), _ptr(out, w_coarse.dtype),
-                                              self._stream()))
+                                              self._v(w_coarse, w_coarse.dtype, self.size(fine_level - 1), "w_coarse"),
+                                              _ptr(out, w_coarse.dtype), self._stream()))
         return out
 
     def coarse_solve(self, b):
         torch = _torch()
         x = torch.empty_like(b)
-        self._check(self._lib.stokes_coarse_solve(self._ctx, self._prec(b), _ptr(b, b.dtype), _ptr(x, b.dtype),
-                                                  self._stream()))
+        self._check(self._lib.stokes_coarse_solve(self._ctx, self._prec(b), self._v(b, b.dtype, self.size(0), "b"),
+                                                  _ptr(x, b.dtype), self._stream()))
         return x
 
     def vcycle(self, b, x=None):
         """x <- MG(x, b), one cycle of Algorithm 1 on the finest level (FP32 or FP64 by dtype)."""
         torch = _torch()
         x = torch.zeros_like(b) if x is None else x
-        self._check(self._lib.mg_vcycle(self._ctx, self._prec(b), _ptr(b, b.dtype), _ptr(x, b.dtype),
-                                        self._stream()))
+        n = self.size()
+        self._check(self._lib.mg_vcycle(self._ctx, self._prec(b), self._v(b, b.dtype, n, "b"),
+                                        self._v(x, b.dtype, n, "x"), self._stream()))
         return x
 
     def solve(self, b, x=None, rtol=1e-8, maxit=200):
@@ -245,15 +282,18 @@ class StokesMG:
         torch = _torch()
         x = torch.zeros_like(b) if x is None else x
         it, rel = C.c_int(), C.c_double()
-        st = self._lib.stokes_solve(self._ctx, _ptr(b, torch.float64), _ptr(x, torch.float64), float(rtol),
-                                    int(maxit), C.byref(it), C.byref(rel), self._stream())
+        n = self.size()
+        st = self._lib.stokes_solve(self._ctx, self._v(b, torch.float64, n, "b"), self._v(x, torch.float64, n, "x"),
+                                    float(rtol), int(maxit), C.byref(it), C.byref(rel), self._stream())
         self._check(st)
         return x, it.value, rel.value
 
     def solve_host(self, b, rtol=1e-8, maxit=200, out=None):
         """stokes_solve_host: numpy float64 b in (pinned or pageable host memory), numpy x out."""
-        b = np.ascontiguousarray(b, dtype=np.float64)
+        b = _host_doubles(b, self.size(), "b")
         x = np.empty_like(b) if out is None else out
+        if not (isinstance(x, np.ndarray) and x.dtype == np.float64 and x.size == b.size and x.flags.c_contiguous):
+            raise ValueError(f"out: expected a contiguous float64 array of {b.size} entries")
         it, rel = C.c_int(), C.c_double()
         st = self._lib.stokes_solve_host(self._ctx, b.ctypes.data_as(C.POINTER(C.c_double)),
                                          x.ctypes.data_as(C.POINTER(C.c_double)), float(rtol), int(maxit),
@@ -268,7 +308,10 @@ class StokesMG:
 
     def set_viscosity(self, mu_cell):
         """Replace the per-cell viscosity of the finest level and rebuild the hierarchy's setup."""
-        mc = np.ascontiguousarray(np.asarray(mu_cell, dtype=np.float64).reshape(-1))
+        n_cells = 1
+        for v in self._n:
+            n_cells *= v
+        mc = _host_doubles(mu_cell, n_cells, "mu_cell")
         self._check(self._lib.stokes_set_viscosity(self._ctx, mc.ctypes.data_as(C.POINTER(C.c_double)),
                                                    self._stream()))
 
@@ -279,8 +322,10 @@ class StokesMG:
         for v in self._n:
             n *= v
         g = torch.empty(n, dtype=torch.float64, device=self.device)
-        self._check(self._lib.stokes_cell_grad(self._ctx, _ptr(x, torch.float64), _ptr(lam, torch.float64),
-                                               _ptr(g, torch.float64), self._stream()))
+        N = self.size()
+        self._check(self._lib.stokes_cell_grad(self._ctx, self._v(x, torch.float64, N, "x"),
+                                               self._v(lam, torch.float64, N, "lam"), _ptr(g, torch.float64),
+                                               self._stream()))
         return g
 
     def velocity_nodes(self, level=None):
@@ -295,8 +340,9 @@ class StokesMG:
     def lift_rhs(self, uD, b):
         """b -= Z K_full u_D in place (inhomogeneous Dirichlet data by lifting); returns b."""
         torch = _torch()
-        self._check(self._lib.stokes_lift_rhs(self._ctx, _ptr(uD, torch.float64), _ptr(b, torch.float64),
-                                              self._stream()))
+        n = self.size()
+        self._check(self._lib.stokes_lift_rhs(self._ctx, self._v(uD, torch.float64, n, "uD"),
+                                              self._v(b, torch.float64, n, "b"), self._stream()))
         return b
 
     def mg_iterate(self, b, x=None, max_iter=15, reduction=1e-10, allow_divergence=False):
@@ -308,8 +354,9 @@ class StokesMG:
         x = torch.zeros_like(b) if x is None else x
         it, q = C.c_int(), C.c_double()
         hist = (C.c_double * (max_iter + 1))()
-        st = self._lib.stokes_mg_iterate(self._ctx, _ptr(b, torch.float64), _ptr(x, torch.float64), int(max_iter),
-                                         float(reduction), C.byref(it), hist, C.byref(q), self._stream())
+        n = self.size()
+        st = self._lib.stokes_mg_iterate(self._ctx, self._v(b, torch.float64, n, "b"), self._v(x, torch.float64, n, "x"),
+                                         int(max_iter), float(reduction), C.byref(it), hist, C.byref(q), self._stream())
         if st == 5 and allow_divergence:
             return x, it.value, [], float("inf")
         if st not in (0, 4):
@@ -417,7 +464,10 @@ class StokesBatch:
             ms.n_levels = mb["n_levels"]
             ms.dirichlet_faces = mb.get("dirichlet_faces", ALL_FACES[dim])
             if mb.get("vertices") is not None:
-                v = np.ascontiguousarray(np.asarray(mb["vertices"], dtype=np.float64).reshape(-1))
+                n_vert = 1
+                for a in range(dim):
+                    n_vert *= int(nn[a]) + 1
+                v = _host_doubles(mb["vertices"], n_vert * dim, f"member {i} vertices")
                 self._keep.append(v)
                 ms.vertices = v.ctypes.data_as(C.POINTER(C.c_double))
             ks[i] = mb.get("k", 2)
@@ -452,6 +502,17 @@ class StokesBatch:
         if st != 0:
             raise StokesError(st, self._lib.stokes_batch_last_error(self._bt).decode())
 
+    def _member_ptrs(self, bs, xs, dtype):
+        """Pointer arrays of one vector per member, each checked against its member's size."""
+        nm = self.n_meshes
+        if len(bs) != nm or len(xs) != nm:
+            raise ValueError(f"expected {nm} right-hand sides and {nm} solution vectors, got {len(bs)} and {len(xs)}")
+        bp = (C.c_void_p * nm)(*[_ptr(b, dtype, n=M.size(), device=self.device, what=f"b[{i}]").value
+                                 for i, (b, M) in enumerate(zip(bs, self.members))])
+        xp = (C.c_void_p * nm)(*[_ptr(x, dtype, n=M.size(), device=self.device, what=f"x[{i}]").value
+                                 for i, (x, M) in enumerate(zip(xs, self.members))])
+        return bp, xp
+
     def solve(self, bs, xs=None, rtol=1e-8, maxit=200, check=True):
         """Solve all members; bs, xs: lists of float64 CUDA tensors.  Returns (xs, iterations, rel residuals);
         with check=False a failing member raises nothing and the status (the first non-OK member's,
@@ -459,8 +520,7 @@ class StokesBatch:
         torch = _torch()
         xs = [torch.zeros_like(b) for b in bs] if xs is None else xs
         nm = self.n_meshes
-        bp = (C.c_void_p * nm)(*[_ptr(b, torch.float64).value for b in bs])
-        xp = (C.c_void_p * nm)(*[_ptr(x, torch.float64).value for x in xs])
+        bp, xp = self._member_ptrs(bs, xs, torch.float64)
         its = (C.c_int * nm)()
         rel = (C.c_double * nm)()
         st = self._lib.stokes_solve_batch(self._bt, bp, xp, float(rtol), int(maxit), its, rel, StokesMG._stream())
@@ -486,9 +546,7 @@ class StokesBatch:
         (stokes_batch_vcycle); bs, xs: lists of float32 CUDA tensors.  Returns xs."""
         torch = _torch()
         xs = [torch.empty_like(b) for b in bs] if xs is None else xs
-        nm = self.n_meshes
-        bp = (C.c_void_p * nm)(*[_ptr(b, torch.float32).value for b in bs])
-        xp = (C.c_void_p * nm)(*[_ptr(x, torch.float32).value for x in xs])
+        bp, xp = self._member_ptrs(bs, xs, torch.float32)
         st = self._lib.stokes_batch_vcycle(self._bt, bp, xp, StokesMG._stream())
         if st != 0:
             raise StokesError(st, self._lib.stokes_global_last_error().decode())

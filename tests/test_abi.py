@@ -153,3 +153,21 @@ def test_every_declaration_cites_its_passage():
         comment = before[before.rfind("/*", 0, end):end]
         assert re.search(r"Sec\.|Algorithm|Lemma|reading|counterpart", comment), m.group(1)
 
+
+
+def test_binding_checks_host_arrays_before_setup():
+    """Host arrays whose size the setup would trust (vertices, per-cell mu and rho) are checked by
+    the binding before any device work: a short array would otherwise be read past its end."""
+    from paper_2205_15770_gb300 import StokesBatch, StokesMG, _ptr
+    torch = pytest.importorskip("torch")
+    n = (2, 2, 2)
+    with pytest.raises(ValueError, match="vertices"):
+        StokesMG(dim=3, n=n, n_levels=1, vertices=np.zeros(3 * 3 * 3 * 3 - 1))
+    with pytest.raises(ValueError, match="mu_cell"):
+        StokesMG(dim=3, n=n, n_levels=1, mu_cell=np.ones(7))
+    with pytest.raises(ValueError, match="rho_cell"):
+        StokesMG(dim=3, n=n, n_levels=1, rho_cell=np.ones(9))
+    with pytest.raises(ValueError, match="member 0 vertices"):
+        StokesBatch([dict(dim=2, n=(4, 4), n_levels=2, vertices=np.zeros(10))])
+    with pytest.raises(TypeError, match="CUDA"):
+        _ptr(torch.zeros(4, dtype=torch.float64), torch.float64, n=4)
