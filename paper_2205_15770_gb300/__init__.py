@@ -190,6 +190,12 @@ class StokesMG:
         """_ptr with the entry count and the context's device checked."""
         return _ptr(t, dtype, n=n, device=self.device, what=what)
 
+    @staticmethod
+    def _distinct(a, b, names):
+        """An input the library reads while it writes the other vector must not be that vector."""
+        if a.data_ptr() == b.data_ptr():
+            raise ValueError(f"{names[0]} and {names[1]} must be different vectors")
+
     def vmult(self, x, y=None, level=None):
         """y = K x (Sec. 3.1 matrix-free operator)."""
         torch = _torch()
@@ -197,6 +203,7 @@ class StokesMG:
         pr = self._prec(x)
         lv = self._level(level)
         n = self.size(lv)
+        self._distinct(x, y, ("x", "y"))
         self._check(self._lib.stokes_vmult(self._ctx, lv, pr, self._v(x, x.dtype, n, "x"), self._v(y, x.dtype, n, "y"),
                                            self._stream()))
         return y
@@ -230,6 +237,7 @@ class StokesMG:
         """x <- S^steps (x, b): inexact symmetric Uzawa smoother (in place)."""
         lv = self._level(level)
         n = self.size(lv)
+        self._distinct(b, x, ("b", "x"))
         self._check(self._lib.stokes_smooth(self._ctx, lv, self._prec(x), steps, self._v(b, x.dtype, n, "b"),
                                             self._v(x, x.dtype, n, "x"), self._stream()))
         return x
@@ -240,6 +248,7 @@ class StokesMG:
         Overlapping calls race on that array; levels that need more scratch raise StokesError."""
         lv = self._level(level)
         n = self.size(lv)
+        self._distinct(b, x, ("b", "x"))
         self._check(self._lib.stokes_smooth_noalloc(self._ctx, lv, self._prec(x), steps,
                                                     self._v(b, x.dtype, n, "b"), self._v(x, x.dtype, n, "x"),
                                                     self._stream()))
@@ -273,6 +282,7 @@ class StokesMG:
         torch = _torch()
         x = torch.zeros_like(b) if x is None else x
         n = self.size()
+        self._distinct(b, x, ("b", "x"))
         self._check(self._lib.mg_vcycle(self._ctx, self._prec(b), self._v(b, b.dtype, n, "b"),
                                         self._v(x, b.dtype, n, "x"), self._stream()))
         return x
@@ -283,6 +293,7 @@ class StokesMG:
         x = torch.zeros_like(b) if x is None else x
         it, rel = C.c_int(), C.c_double()
         n = self.size()
+        self._distinct(b, x, ("b", "x"))
         st = self._lib.stokes_solve(self._ctx, self._v(b, torch.float64, n, "b"), self._v(x, torch.float64, n, "x"),
                                     float(rtol), int(maxit), C.byref(it), C.byref(rel), self._stream())
         self._check(st)
@@ -341,6 +352,7 @@ class StokesMG:
         """b -= Z K_full u_D in place (inhomogeneous Dirichlet data by lifting); returns b."""
         torch = _torch()
         n = self.size()
+        self._distinct(uD, b, ("uD", "b"))
         self._check(self._lib.stokes_lift_rhs(self._ctx, self._v(uD, torch.float64, n, "uD"),
                                               self._v(b, torch.float64, n, "b"), self._stream()))
         return b
@@ -355,6 +367,7 @@ class StokesMG:
         it, q = C.c_int(), C.c_double()
         hist = (C.c_double * (max_iter + 1))()
         n = self.size()
+        self._distinct(b, x, ("b", "x"))
         st = self._lib.stokes_mg_iterate(self._ctx, self._v(b, torch.float64, n, "b"), self._v(x, torch.float64, n, "x"),
                                          int(max_iter), float(reduction), C.byref(it), hist, C.byref(q), self._stream())
         if st == 5 and allow_divergence:
