@@ -135,7 +135,10 @@ void stokes_default_opts(stokes_opts *o);
  * n[a] divisible by 2^(n_levels-1); mu > 0, gamma_rho >= 0.  mu_cell (HOST,
  * nullable): per-cell viscosity of the finest level (n_cells doubles, x fastest);
  * coarse cells take the mean of their 2^d children.  Synchronises the stream.
- * On success *out owns all device memory until stokes_destroy. */
+ * On success *out owns all device memory until stokes_destroy.  STOKES_EINVAL (before any device
+ * work) for sizes or coefficients out of range, non-positive mu_cell entries, non-finite vertex
+ * coordinates, or a cell whose map is not a proper image of the reference cell (det J <= 0 at a
+ * corner, from the cell's edges there). */
 int stokes_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho,
                  const double *mu_cell, const stokes_opts *opts, void *stream,
                  stokes_ctx **out);

@@ -2936,6 +2936,46 @@ void stokes_default_opts(stokes_opts *o) {
   o->wait_cycles = 0;
 }
 
+// Every cell of a vertex-given mesh must be a proper image of the reference cell (Sec. 2: T_tau
+// bijective): finite coordinates and det J > 0 at each of its 2^d corners, J formed from the cell's
+// edges that leave the corner along the +x, +y (+z) reference directions.  Host-side, before any
+// device work.
+static int check_cell_orientation(const stokes_mesh *mesh) {
+  const int dim = mesh->dim, nx = mesh->n[0], ny = mesh->n[1], nz = dim == 3 ? mesh->n[2] : 1;
+  const double *V = mesh->vertices;
+  auto vx = [&](int i, int j, int k2, int a) { return V[(((long long)k2 * (ny + 1) + j) * (nx + 1) + i) * dim + a]; };
+  const long long nv = (long long)(nx + 1) * (ny + 1) * (dim == 3 ? nz + 1 : 1) * dim;
+  for (long long i = 0; i < nv; ++i)
+    if (!std::isfinite(V[i])) {
+      set_error("vertices: coordinate " + std::to_string(i) + " is not finite");
+      return STOKES_EINVAL;
+    }
+  for (int k2 = 0; k2 < nz; ++k2)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i)
+        for (int c = 0; c < (1 << dim); ++c) {
+          const int ci = i + (c & 1), cj = j + ((c >> 1) & 1), ck = k2 + (dim == 3 ? (c >> 2) & 1 : 0);
+          // edge along axis a from this corner to its neighbour in the cell, oriented along +a
+          double e[3][3] = {};
+          for (int a = 0; a < dim; ++a) {
+            const int s = ((c >> a) & 1) ? -1 : 1;
+            const int ni = ci + (a == 0 ? s : 0), nj = cj + (a == 1 ? s : 0), nk = ck + (a == 2 ? s : 0);
+            for (int b = 0; b < dim; ++b) e[a][b] = s * (vx(ni, nj, nk, b) - vx(ci, cj, ck, b));
+          }
+          const double det = dim == 3 ? e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) -
+                                            e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                                            e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0])
+                                      : e[0][0] * e[1][1] - e[0][1] * e[1][0];
+          if (!(det > 0)) {
+            set_error("vertices: cell (" + std::to_string(i) + ", " + std::to_string(j) +
+                      (dim == 3 ? ", " + std::to_string(k2) : std::string()) +
+                      ") is inverted or degenerate at one of its corners (det J <= 0)");
+            return STOKES_EINVAL;
+          }
+        }
+  return STOKES_OK;
+}
+
 int stokes_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho, const double *mu_cell,
                  const stokes_opts *opts, void *stream, stokes_ctx **out) {
   if (!out) {
@@ -2963,6 +3003,7 @@ int stokes_setup(const stokes_mesh *mesh, int k, double mu, double gamma_rho, co
         return STOKES_EINVAL;
       }
   }
+  if (mesh->vertices && check_cell_orientation(mesh) != STOKES_OK) return STOKES_EINVAL;
   {
     void *scratch = nullptr;  // device address of the allocation-free scratch, once per device
     const int sa = noalloc_scratch_address(&scratch);

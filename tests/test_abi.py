@@ -171,3 +171,36 @@ def test_binding_checks_host_arrays_before_setup():
         StokesBatch([dict(dim=2, n=(4, 4), n_levels=2, vertices=np.zeros(10))])
     with pytest.raises(TypeError, match="CUDA"):
         _ptr(torch.zeros(4, dtype=torch.float64), torch.float64, n=4)
+
+
+def test_setup_rejects_inverted_or_non_finite_cells(lib):
+    """A vertex-given mesh whose cell maps are not proper images of the reference cell (det J <= 0 at
+    a corner) or whose coordinates are not finite is rejected before any device work."""
+    import workloads as W
+    from paper_2205_15770_gb300 import _lib
+
+    def setup(V, n, dim):
+        mesh = _lib.StokesMesh()
+        mesh.dim = dim
+        for a in range(3):
+            mesh.n[a] = n[a] if a < dim else 1
+            mesh.hi[a] = 1.0
+        mesh.n_levels = 1
+        mesh.dirichlet_faces = 0x3F if dim == 3 else 0xF
+        v = np.ascontiguousarray(V.reshape(-1))
+        mesh.vertices = v.ctypes.data_as(C.POINTER(C.c_double))
+        opts = _lib.StokesOpts()
+        lib.stokes_default_opts(C.byref(opts))
+        ctx = C.c_void_p()
+        return lib.stokes_setup(C.byref(mesh), 2, 1.0, 0.0, None, C.byref(opts), None, C.byref(ctx))
+
+    V = W.lattice_vertices(3, (2, 2, 2))
+    V[1, 1, 1, 0] += 1.0  # the middle vertex pushed past its +x neighbour: cell (1, 0, 0) folds
+    assert setup(V, (2, 2, 2), 3) == 1
+    assert b"cell (1, 0, 0) is inverted" in lib.stokes_global_last_error()
+    V = W.lattice_vertices(3, (2, 2, 2))
+    V[0, 0, 0, 2] = np.nan
+    assert setup(V, (2, 2, 2), 3) == 1 and b"not finite" in lib.stokes_global_last_error()
+    V = W.lattice_vertices(2, (4, 4))
+    V[2, 2, 1] += 0.6  # 2D: the vertex (2, 2) moved past the next row
+    assert setup(V, (4, 4), 2) == 1 and b"cell (1, 2) is inverted" in lib.stokes_global_last_error()
