@@ -5,11 +5,10 @@ a batch.  Each case checks the status, the error text, and that the context solv
 The stopping protocol follows Sec. 4.1 (iteration limit, residual reduction)."""
 import math
 
-import numpy as np
 import pytest
 
 import workloads as W
-from parity_cases import CASES, gpu_solver, oracle_hierarchy
+from parity_cases import CASES, gpu_solver
 
 pytestmark = pytest.mark.gpu
 

@@ -8,7 +8,7 @@ import pytest
 
 import workloads as W
 from oracle.assemble import assemble
-from oracle.fe import gauss_lobatto, lagrange_values
+from oracle.fe import gauss_lobatto
 from oracle.mesh import Hierarchy, Level
 from oracle.smoother import (LevelSmoother, cheb_C, cheb_scalar_error, chebyshev, lanczos_max,
                              lemma1_scaling, local_schur_diag, splitmix64_uniform)
