@@ -204,3 +204,35 @@ def test_setup_rejects_inverted_or_non_finite_cells(lib):
     V = W.lattice_vertices(2, (4, 4))
     V[2, 2, 1] += 0.6  # 2D: the vertex (2, 2) moved past the next row
     assert setup(V, (4, 4), 2) == 1 and b"cell (1, 2) is inverted" in lib.stokes_global_last_error()
+
+
+def test_header_is_plain_c_and_a_c_program_links(lib, tmp_path):
+    """The boundary is a C ABI: the header compiles as strict C99 (no C++ or torch types), and a C
+    program links against the library and calls it (the defaults, and a rejected setup)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_abi.c"
+    src.write_text(
+        '#include "stokes_mf.h"\n'
+        "#include <stdio.h>\n"
+        "int main(void) {\n"
+        "  stokes_opts o; stokes_ctx *ctx = 0; stokes_mesh m = {0};\n"
+        "  stokes_default_opts(&o);\n"
+        "  if (o.kA != 3 || o.kS != 3 || o.m != 2) return 1;\n"
+        "  m.dim = 3; m.n[0] = m.n[1] = m.n[2] = 6; m.hi[0] = m.hi[1] = m.hi[2] = 1.0; m.n_levels = 3;\n"
+        "  if (stokes_setup(&m, 2, 1.0, 0.0, 0, &o, 0, &ctx) != STOKES_EINVAL || ctx) return 2;\n"
+        '  printf("%s\\n", stokes_global_last_error());\n'
+        "  return 0;\n"
+        "}\n")
+    libdir = os.path.join(ROOT, "paper_2205_15770_gb300")
+    exe = tmp_path / "use_abi"
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-L", libdir, "-lstokes_mf", "-Wl,-rpath," + libdir, "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    assert "multiple" in r.stdout
